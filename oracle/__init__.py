@@ -1,0 +1,217 @@
+"""FP64 CPU oracle for the per-particle Lagrangian step (test infrastructure).
+
+This package is the plain, slow reference the CUDA path is checked against.
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the library under ``paper_2603_26691_gb300``
+never does.  The arithmetic lives in ``oracle.c`` (plain C, double precision,
+no FMA contraction); this module compiles it with gcc and wraps it with
+ctypes, converting numpy arrays.  It holds no arithmetic of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so (gcc, -O2, no FP contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    hdr = os.path.join(_HERE, "oracle.h")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("chunk_edge", C.c_int32), ("L", C.c_double * 3),
+                ("rho_p", C.c_double), ("mu", C.c_double), ("g", C.c_double * 3),
+                ("alpha", C.c_double), ("mult", C.c_double)]
+
+
+def make_grid(n, L=(1.0, 1.0, 1.0), chunk_edge=8, rho_p=1000.0, mu=1.8e-5,
+              g=(0.0, 0.0, -9.81), alpha=1.0, mult=1.0) -> Grid:
+    if isinstance(n, int):
+        n = (n, n, n)
+    G = Grid()
+    G.n[:] = [int(v) for v in n]
+    G.chunk_edge = int(chunk_edge)
+    G.L[:] = [float(v) for v in L]
+    G.rho_p, G.mu = float(rho_p), float(mu)
+    G.g[:] = [float(v) for v in g]
+    G.alpha, G.mult = float(alpha), float(mult)
+    return G
+
+
+_P = C.POINTER
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            d, i64, i32 = C.c_double, C.c_int64, C.c_int32
+            pd, pi64, pu32 = _P(d), _P(i64), _P(C.c_uint32)
+            pg = _P(Grid)
+            L.orc_wrap.argtypes, L.orc_wrap.restype = [d, d], d
+            L.orc_cell.argtypes, L.orc_cell.restype = [pg, pd, _P(i32)], None
+            L.orc_gather.argtypes, L.orc_gather.restype = [pg, pd, pd, pd], None
+            L.orc_advance.argtypes, L.orc_advance.restype = [pg, d, pd, d, pd, pd], None
+            L.orc_mass.argtypes, L.orc_mass.restype = [pg, d], d
+            L.orc_particle_step.argtypes = [pg, pd, d, d, pd, pd, pi64, pd]
+            L.orc_particle_step.restype = None
+            L.orc_run.argtypes = [pg, pd, i64, pd, pd, pd, i32, d, pd, pi64, pi64]
+            L.orc_run.restype = C.c_int
+            L.orc_key.argtypes, L.orc_key.restype = [pg, i32, i32, i32], C.c_uint32
+            L.orc_sort_perm.argtypes, L.orc_sort_perm.restype = [i64, pu32, pi64], None
+            L.orc_cell_counts.argtypes, L.orc_cell_counts.restype = [pg, i64, pd, pi64], None
+            L.orc_invariants.argtypes, L.orc_invariants.restype = [pg, i64, pd, pd, pd, pd], None
+            L.orc_adjoint.argtypes = [pg, pd, i64, pd, pd, pd, i32, d, pd, pd, pd, pd]
+            L.orc_adjoint.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _pd(a):
+    return a.ctypes.data_as(_P(C.c_double))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def ncell(G: Grid) -> int:
+    return int(G.n[0]) * int(G.n[1]) * int(G.n[2])
+
+
+def wrap(x: float, L: float) -> float:
+    return lib().orc_wrap(float(x), float(L))
+
+
+def cell(G: Grid, x) -> tuple:
+    x = _f64(x, (3,))
+    out = (C.c_int32 * 3)()
+    lib().orc_cell(C.byref(G), _pd(x), out)
+    return tuple(out)
+
+
+def gather(G: Grid, U: np.ndarray, x) -> np.ndarray:
+    U = _f64(U)
+    x = _f64(x, (3,))
+    out = np.zeros(3)
+    lib().orc_gather(C.byref(G), _pd(U), _pd(x), _pd(out))
+    return out
+
+
+def advance(G: Grid, d: float, up, dt: float, x, v):
+    x = _f64(x, (3,)).copy()
+    v = _f64(v, (3,)).copy()
+    up = _f64(up, (3,))
+    lib().orc_advance(C.byref(G), float(d), _pd(up), float(dt), _pd(x), _pd(v))
+    return x, v
+
+
+def mass(G: Grid, d: float) -> float:
+    return lib().orc_mass(C.byref(G), float(d))
+
+
+def run(G: Grid, U, pos, vel, d, nsteps: int, dt: float, src=None, trace=False, frozen=None):
+    """Advance particles nsteps in the frozen field U.
+
+    pos, vel: [3, n] float64 (copied); d: [n].  Returns (pos, vel, src, trace)
+    with src [3, ncell] (accumulated onto the given src if any) and trace
+    [nsteps, n] int64 deposit cells when requested.
+    """
+    U = _f64(U)
+    pos = _f64(pos).reshape(3, -1).copy()
+    vel = _f64(vel).reshape(3, -1).copy()
+    d = _f64(d).reshape(-1)
+    n = d.shape[0]
+    nc = ncell(G)
+    src = np.zeros((3, nc)) if src is None else _f64(src).reshape(3, nc).copy()
+    tr = np.zeros((max(nsteps, 0), n), dtype=np.int64) if trace else None
+    fr = None
+    if frozen is not None:
+        fr = np.ascontiguousarray(frozen, dtype=np.int64).reshape(nsteps, n)
+    rc = lib().orc_run(C.byref(G), _pd(U), n, _pd(pos), _pd(vel), _pd(d), int(nsteps), float(dt),
+                       _pd(src), tr.ctypes.data_as(_P(C.c_int64)) if tr is not None else None,
+                       fr.ctypes.data_as(_P(C.c_int64)) if fr is not None else None)
+    if rc != 0:
+        raise ValueError(f"orc_run failed ({rc})")
+    return pos, vel, src, tr
+
+
+def key(G: Grid, i: int, j: int, k: int) -> int:
+    return int(lib().orc_key(C.byref(G), int(i), int(j), int(k)))
+
+
+def keys_of_positions(G: Grid, pos) -> np.ndarray:
+    pos = _f64(pos).reshape(3, -1)
+    out = np.empty(pos.shape[1], dtype=np.uint32)
+    for p in range(pos.shape[1]):
+        i, j, k = cell(G, pos[:, p])
+        out[p] = key(G, i, j, k)
+    return out
+
+
+def sort_perm(keys) -> np.ndarray:
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    n = keys.shape[0]
+    perm = np.zeros(n, dtype=np.int64)
+    lib().orc_sort_perm(n, keys.ctypes.data_as(_P(C.c_uint32)), perm.ctypes.data_as(_P(C.c_int64)))
+    return perm
+
+
+def cell_counts(G: Grid, pos) -> np.ndarray:
+    pos = _f64(pos).reshape(3, -1)
+    out = np.zeros(ncell(G), dtype=np.int64)
+    lib().orc_cell_counts(C.byref(G), pos.shape[1], _pd(pos), out.ctypes.data_as(_P(C.c_int64)))
+    return out
+
+
+def invariants(G: Grid, vel, d, src=None) -> np.ndarray:
+    vel = _f64(vel).reshape(3, -1)
+    d = _f64(d).reshape(-1)
+    out = np.zeros(8)
+    s = _f64(src).reshape(-1) if src is not None else None
+    lib().orc_invariants(C.byref(G), d.shape[0], _pd(vel), _pd(d), _pd(s) if s is not None else None,
+                         _pd(out))
+    return out
+
+
+def adjoint(G: Grid, U, pos0, vel0, d, nsteps: int, dt: float, lam):
+    """Gradients (dL/dd [n], dL/dalpha, dL/dU [ncell, 3]) given lam = dL/dJtot [3, ncell]."""
+    U = _f64(U)
+    pos0 = _f64(pos0).reshape(3, -1)
+    vel0 = _f64(vel0).reshape(3, -1)
+    d = _f64(d).reshape(-1)
+    lam = _f64(lam).reshape(3, -1)
+    n = d.shape[0]
+    gd = np.zeros(n)
+    ga = C.c_double(0.0)
+    gU = np.zeros((ncell(G), 3))
+    rc = lib().orc_adjoint(C.byref(G), _pd(U), n, _pd(pos0), _pd(vel0), _pd(d), int(nsteps), float(dt),
+                           _pd(lam), _pd(gd), C.byref(ga), _pd(gU))
+    if rc != 0:
+        raise ValueError(f"orc_adjoint failed ({rc})")
+    return gd, ga.value, gU

@@ -1,0 +1,375 @@
+/*
+ * FP64 CPU oracle: plain scalar implementation of the per-particle
+ * Lagrangian step.  TEST INFRASTRUCTURE ONLY (see oracle.h for the scope,
+ * the citations and the pins).  Everything is double precision, evaluated in
+ * the order written, with no fused multiply-add (built with
+ * -ffp-contract=off).
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static const double kPi = 3.14159265358979323846;
+
+static double cell_size(const orc_grid* G, int ax) { return G->L[ax] / (double)G->n[ax]; }
+
+static int64_t ncell_of(const orc_grid* G) {
+  return (int64_t)G->n[0] * (int64_t)G->n[1] * (int64_t)G->n[2];
+}
+
+static int64_t linear_cell(const orc_grid* G, int32_t i, int32_t j, int32_t k) {
+  return (int64_t)i + (int64_t)G->n[0] * ((int64_t)j + (int64_t)G->n[1] * (int64_t)k);
+}
+
+/* Periodic box: positions live in [0, L).  x - L floor(x / L) is the
+ * periodic image; the two guards catch the cases where rounding lands the
+ * result just outside [0, L). */
+double orc_wrap(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y < 0.0) y = y + L;
+  if (y >= L) y = 0.0;
+  return y;
+}
+
+/* The cell holding a particle (Sec. 2.5: sources go to the cell containing
+ * the particle): i = floor(x / h), clamped to the last cell. */
+void orc_cell(const orc_grid* G, const double x[3], int32_t idx[3]) {
+  for (int ax = 0; ax < 3; ++ax) {
+    double h = cell_size(G, ax);
+    int32_t i = (int32_t)floor(x[ax] / h);
+    if (i < 0) i = 0;
+    if (i > G->n[ax] - 1) i = G->n[ax] - 1;
+    idx[ax] = i;
+  }
+}
+
+static int32_t wrap_index(int32_t i, int32_t n) {
+  int32_t r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+/* Trilinear interpolation of cell-centred values (centres at (i + 1/2) h):
+ * s = x / h - 1/2, i0 = floor(s), f = s - i0; the value is the sum over the
+ * eight corners (i0 + di, j0 + dj, k0 + dk), indices taken periodically, of
+ * the corner value times prod over axes of (f if the offset is 1 else 1 - f). */
+void orc_gather(const orc_grid* G, const double* U, const double x[3], double up[3]) {
+  int32_t i0[3];
+  double f[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    double s = x[ax] / cell_size(G, ax) - 0.5;
+    double fl = floor(s);
+    i0[ax] = (int32_t)fl;
+    f[ax] = s - fl;
+  }
+  up[0] = up[1] = up[2] = 0.0;
+  for (int dk = 0; dk < 2; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        int64_t c = linear_cell(G, wrap_index(i0[0] + di, G->n[0]), wrap_index(i0[1] + dj, G->n[1]),
+                                wrap_index(i0[2] + dk, G->n[2]));
+        for (int q = 0; q < 3; ++q) up[q] = up[q] + w * U[3 * c + q];
+      }
+}
+
+/* Newton's second law (Sec. 2.1, Eqs. 9-10) with Stokes drag and gravity:
+ *   dx/dt = v,  dv/dt = alpha (u_p - v) / tau + g,  tau = rho_p d^2 / (18 mu).
+ * With a = alpha / tau and u_p frozen over the step the solution is exact:
+ *   w_t = u_p + g / a            (the velocity v relaxes towards)
+ *   v'  = w_t + (v - w_t) e^{-a dt}
+ *   x'  = x + w_t dt + (v - w_t) (1 - e^{-a dt}) / a
+ * and 1 - e^{-a dt} is taken as -expm1(-a dt). */
+void orc_advance(const orc_grid* G, double d, const double up[3], double dt, double x[3],
+                 double v[3]) {
+  double tau = G->rho_p * d * d / (18.0 * G->mu);
+  double a = G->alpha / tau;
+  double E = exp(-a * dt);
+  double E1 = -expm1(-a * dt);
+  for (int ax = 0; ax < 3; ++ax) {
+    double wt = up[ax] + G->g[ax] / a;
+    double vn = wt + (v[ax] - wt) * E;
+    double dx = wt * dt + (v[ax] - wt) * (E1 / a);
+    x[ax] = x[ax] + dx;
+    v[ax] = vn;
+  }
+}
+
+/* Mass of a spherical particle, times the parcel multiplicity (Sec. 3.2
+ * lumps identical droplets into parcels). */
+double orc_mass(const orc_grid* G, double d) {
+  return G->mult * G->rho_p * kPi * d * d * d / 6.0;
+}
+
+/* One step of one particle.  The impulse given to the fluid is the drag
+ * part of the particle's momentum change (Sec. 2.1, Eq. 11, with the sign
+ * that enters the fluid's momentum equation Eq. 2 as +S_u):
+ *   J = -m [(v' - v) - g dt],
+ * computed from the stored v' and v, and deposited into the start-of-step
+ * cell c0. */
+void orc_particle_step(const orc_grid* G, const double* U, double dt, double d, double x[3],
+                       double v[3], int64_t* c0, double J[3]) {
+  int32_t idx[3];
+  double up[3], vold[3];
+  orc_cell(G, x, idx);
+  *c0 = linear_cell(G, idx[0], idx[1], idx[2]);
+  orc_gather(G, U, x, up);
+  vold[0] = v[0];
+  vold[1] = v[1];
+  vold[2] = v[2];
+  orc_advance(G, d, up, dt, x, v);
+  for (int ax = 0; ax < 3; ++ax) x[ax] = orc_wrap(x[ax], G->L[ax]);
+  double m = orc_mass(G, d);
+  for (int ax = 0; ax < 3; ++ax) J[ax] = -m * ((v[ax] - vold[ax]) - G->g[ax] * dt);
+}
+
+static int grid_ok(const orc_grid* G) {
+  for (int ax = 0; ax < 3; ++ax) {
+    if (G->n[ax] <= 0 || !(G->L[ax] > 0.0)) return 0;
+  }
+  return G->rho_p > 0.0 && G->mu > 0.0 && G->alpha > 0.0;
+}
+
+int orc_run(const orc_grid* G, const double* U, int64_t n, double* pos, double* vel,
+            const double* d, int32_t nsteps, double dt, double* src, int64_t* trace,
+            const int64_t* frozen) {
+  if (!grid_ok(G) || n < 0 || nsteps < 0) return -1;
+  int64_t nc = ncell_of(G);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    for (int64_t p = 0; p < n; ++p) {
+      double x[3] = {pos[p], pos[n + p], pos[2 * n + p]};
+      double v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
+      int64_t c0;
+      double J[3];
+      orc_particle_step(G, U, dt, d[p], x, v, &c0, J);
+      if (frozen) c0 = frozen[(int64_t)s * n + p];
+      if (trace) trace[(int64_t)s * n + p] = c0;
+      if (src) {
+        for (int ax = 0; ax < 3; ++ax) src[ax * nc + c0] = src[ax * nc + c0] + J[ax];
+      }
+      pos[p] = x[0];
+      pos[n + p] = x[1];
+      pos[2 * n + p] = x[2];
+      vel[p] = v[0];
+      vel[n + p] = v[1];
+      vel[2 * n + p] = v[2];
+    }
+  }
+  return 0;
+}
+
+/* Chunk-major key: chunks are B^3 blocks of cells numbered x-fastest; inside
+ * a chunk the cell's local coordinates are bit-interleaved (bit b of the
+ * local x, y, z goes to bit 3b, 3b+1, 3b+2). */
+uint32_t orc_key(const orc_grid* G, int32_t i, int32_t j, int32_t k) {
+  int32_t B = G->chunk_edge;
+  int32_t ncx = (G->n[0] + B - 1) / B;
+  int32_t ncy = (G->n[1] + B - 1) / B;
+  uint32_t chunk = (uint32_t)(i / B) + (uint32_t)ncx * ((uint32_t)(j / B) + (uint32_t)ncy * (uint32_t)(k / B));
+  uint32_t li = (uint32_t)(i % B), lj = (uint32_t)(j % B), lk = (uint32_t)(k % B);
+  uint32_t morton = 0;
+  for (int b = 0; (1 << b) < B; ++b) {
+    morton |= ((li >> b) & 1u) << (3 * b);
+    morton |= ((lj >> b) & 1u) << (3 * b + 1);
+    morton |= ((lk >> b) & 1u) << (3 * b + 2);
+  }
+  return chunk * (uint32_t)(B * B * B) + morton;
+}
+
+typedef struct {
+  uint32_t key;
+  int64_t idx;
+} key_idx;
+
+/* Ordering on (key, original index): sorting by it with any sort is a
+ * stable sort by key. */
+static int cmp_key_idx(const void* a, const void* b) {
+  const key_idx* x = (const key_idx*)a;
+  const key_idx* y = (const key_idx*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+  return 0;
+}
+
+void orc_sort_perm(int64_t n, const uint32_t* keys, int64_t* perm) {
+  if (n <= 0) return;
+  key_idx* t = (key_idx*)malloc((size_t)n * sizeof(key_idx));
+  if (!t) return;
+  for (int64_t p = 0; p < n; ++p) {
+    t[p].key = keys[p];
+    t[p].idx = p;
+  }
+  qsort(t, (size_t)n, sizeof(key_idx), cmp_key_idx);
+  for (int64_t r = 0; r < n; ++r) perm[r] = t[r].idx;
+  free(t);
+}
+
+void orc_cell_counts(const orc_grid* G, int64_t n, const double* pos, int64_t* counts) {
+  int64_t nc = ncell_of(G);
+  for (int64_t c = 0; c < nc; ++c) counts[c] = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    double x[3] = {pos[p], pos[n + p], pos[2 * n + p]};
+    int32_t idx[3];
+    orc_cell(G, x, idx);
+    counts[linear_cell(G, idx[0], idx[1], idx[2])] += 1;
+  }
+}
+
+void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const double* d,
+                    const double* src, double out[8]) {
+  int64_t nc = ncell_of(G);
+  for (int q = 0; q < 8; ++q) out[q] = 0.0;
+  out[0] = (double)n;
+  for (int64_t p = 0; p < n; ++p) {
+    double m = orc_mass(G, d[p]);
+    out[1] = out[1] + m * vel[p];
+    out[2] = out[2] + m * vel[n + p];
+    out[3] = out[3] + m * vel[2 * n + p];
+    out[7] = out[7] + m;
+  }
+  if (src) {
+    for (int ax = 0; ax < 3; ++ax)
+      for (int64_t c = 0; c < nc; ++c) out[4 + ax] = out[4 + ax] + src[ax * nc + c];
+  }
+}
+
+/* Reverse-mode derivative of orc_run.  Per particle and step (forward):
+ *   c0 = cell(x);  u_p = sum_corners W(f) U;  a = 18 mu alpha / (rho_p d^2)
+ *   E = e^{-a dt};  E1 = 1 - E;  Q = E1 / a;  w_t = u_p + g / a
+ *   v' = w_t E1 + v E;  x' = x + w_t (dt - Q) + v Q
+ *   J = -m (v' - v - g dt),  m = mult rho_p pi d^3 / 6;  Jtot[c0] += J.
+ * The backward sweep runs the chain rule through these lines in reverse,
+ * with lam[c0] as the adjoint of J.  The periodic wrap is a translation
+ * (derivative one) and the deposit cell is held fixed. */
+int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
+                const double* vel0, const double* d, int32_t nsteps, double dt,
+                const double* lam, double* grad_d, double* grad_alpha, double* gradU) {
+  if (!grid_ok(G) || n < 0 || nsteps < 0) return -1;
+  int64_t nc = ncell_of(G);
+  for (int64_t c = 0; c < 3 * nc; ++c) gradU[c] = 0.0;
+  *grad_alpha = 0.0;
+  size_t per = (size_t)(nsteps > 0 ? nsteps : 1);
+  double* tx = (double*)malloc(per * 3 * sizeof(double));
+  double* tv = (double*)malloc(per * 3 * sizeof(double));
+  int64_t* tc = (int64_t*)malloc(per * sizeof(int64_t));
+  if (!tx || !tv || !tc) {
+    free(tx);
+    free(tv);
+    free(tc);
+    return -2;
+  }
+  for (int64_t p = 0; p < n; ++p) {
+    /* forward sweep of this particle, storing the start-of-step states */
+    double x[3] = {pos0[p], pos0[n + p], pos0[2 * n + p]};
+    double v[3] = {vel0[p], vel0[n + p], vel0[2 * n + p]};
+    for (int32_t s = 0; s < nsteps; ++s) {
+      for (int ax = 0; ax < 3; ++ax) {
+        tx[3 * s + ax] = x[ax];
+        tv[3 * s + ax] = v[ax];
+      }
+      int64_t c0;
+      double J[3];
+      orc_particle_step(G, U, dt, d[p], x, v, &c0, J);
+      tc[s] = c0;
+    }
+    /* backward sweep */
+    double dp = d[p];
+    double tau = G->rho_p * dp * dp / (18.0 * G->mu);
+    double a = G->alpha / tau;
+    double E = exp(-a * dt);
+    double E1 = -expm1(-a * dt);
+    double Q = E1 / a;
+    double m = orc_mass(G, dp);
+    double xb[3] = {0.0, 0.0, 0.0}; /* adjoint of the position after step s */
+    double vb[3] = {0.0, 0.0, 0.0}; /* adjoint of the velocity after step s */
+    double db = 0.0;
+    double alphab = 0.0;
+    for (int32_t s = nsteps - 1; s >= 0; --s) {
+      const double* xs = &tx[3 * s];
+      const double* vs = &tv[3 * s];
+      /* recompute the step's intermediates */
+      int32_t i0[3];
+      double f[3], h[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        h[ax] = cell_size(G, ax);
+        double sx = xs[ax] / h[ax] - 0.5;
+        double fl = floor(sx);
+        i0[ax] = (int32_t)fl;
+        f[ax] = sx - fl;
+      }
+      double up[3];
+      orc_gather(G, U, xs, up);
+      double wt[3], vn[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        wt[ax] = up[ax] + G->g[ax] / a;
+        vn[ax] = wt[ax] + (vs[ax] - wt[ax]) * E;
+      }
+      int64_t c0 = tc[s];
+      double Jb[3] = {lam[c0], lam[nc + c0], lam[2 * nc + c0]};
+      /* J = -m (v' - v - g dt) */
+      double mb = 0.0;
+      double vnb[3], vsb[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        vnb[ax] = vb[ax] - m * Jb[ax];
+        vsb[ax] = m * Jb[ax];
+        mb = mb - (vn[ax] - vs[ax] - G->g[ax] * dt) * Jb[ax];
+      }
+      /* v' = w_t E1 + v E ;  x' = x + w_t (dt - Q) + v Q */
+      double wtb[3], ub[3];
+      double Eb = 0.0, E1b = 0.0, Qb = 0.0, ab = 0.0;
+      double xsb[3];
+      for (int ax = 0; ax < 3; ++ax) {
+        wtb[ax] = vnb[ax] * E1 + xb[ax] * (dt - Q);
+        vsb[ax] = vsb[ax] + vnb[ax] * E + xb[ax] * Q;
+        E1b = E1b + vnb[ax] * wt[ax];
+        Eb = Eb + vnb[ax] * vs[ax];
+        Qb = Qb + xb[ax] * (vs[ax] - wt[ax]);
+        xsb[ax] = xb[ax];
+        /* w_t = u_p + g / a */
+        ub[ax] = wtb[ax];
+        ab = ab - wtb[ax] * G->g[ax] / (a * a);
+      }
+      /* Q = E1 / a */
+      E1b = E1b + Qb / a;
+      ab = ab - Qb * E1 / (a * a);
+      /* E = e^{-a dt}, E1 = 1 - e^{-a dt} */
+      ab = ab + Eb * (-dt * E) + E1b * (dt * E);
+      /* a = alpha * 18 mu / (rho_p d^2) */
+      alphab = alphab + ab * a / G->alpha;
+      db = db + ab * (-2.0 * a / dp);
+      /* m = mult rho_p pi d^3 / 6 */
+      db = db + mb * 3.0 * m / dp;
+      /* u_p = sum_corners W(f) U[corner] */
+      double fb[3] = {0.0, 0.0, 0.0};
+      for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+          for (int di = 0; di < 2; ++di) {
+            double wx = di ? f[0] : 1.0 - f[0];
+            double wy = dj ? f[1] : 1.0 - f[1];
+            double wz = dk ? f[2] : 1.0 - f[2];
+            double w = wx * wy * wz;
+            int64_t c = linear_cell(G, wrap_index(i0[0] + di, G->n[0]),
+                                    wrap_index(i0[1] + dj, G->n[1]), wrap_index(i0[2] + dk, G->n[2]));
+            double dot = 0.0;
+            for (int q = 0; q < 3; ++q) {
+              gradU[3 * c + q] = gradU[3 * c + q] + w * ub[q];
+              dot = dot + U[3 * c + q] * ub[q];
+            }
+            fb[0] = fb[0] + (di ? 1.0 : -1.0) * wy * wz * dot;
+            fb[1] = fb[1] + wx * (dj ? 1.0 : -1.0) * wz * dot;
+            fb[2] = fb[2] + wx * wy * (dk ? 1.0 : -1.0) * dot;
+          }
+      for (int ax = 0; ax < 3; ++ax) {
+        xb[ax] = xsb[ax] + fb[ax] / h[ax];
+        vb[ax] = vsb[ax];
+      }
+    }
+    grad_d[p] = db;
+    *grad_alpha = *grad_alpha + alphab;
+  }
+  free(tx);
+  free(tv);
+  free(tc);
+  return 0;
+}

@@ -1,0 +1,119 @@
+/*
+ * FP64 CPU oracle for the per-particle Lagrangian step of a two-way coupled
+ * Euler-Lagrange method (SCALE-TRACK, arXiv 2603.26691).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This code is the plain, slow, scalar reference
+ * that the CUDA path is checked against.  Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it.  It shares no
+ * code, header, table or constant with the CUDA library, and the library
+ * never calls it.
+ *
+ * What it computes (each function cites the passage it follows):
+ *   - Newton's second law for a particle (Sec. 2.1, Eqs. 9-10) with Stokes
+ *     drag (relaxation time tau = rho_p d^2 / (18 mu)) and gravity, advanced
+ *     by the exponential integrator, which is exact while the fluid velocity
+ *     seen by the particle is frozen over the step;
+ *   - the fluid velocity at the particle by trilinear interpolation of
+ *     cell-centred values on a periodic uniform grid (used here in place of
+ *     the nearest-grid-point rule of Sec. 2.5);
+ *   - the momentum given to the fluid, J = -m [(v' - v) - g dt], which is the
+ *     drag part of d(m u_p)/dt in the momentum source of Sec. 2.1, Eq. 11,
+ *     deposited whole into the cell that holds the particle (Sec. 2.5) at the
+ *     start of the step;
+ *   - the chunk-major ordering key and a stable sort of particles by it
+ *     (chunks organised as structures of arrays, Sec. 2.2);
+ *   - global invariants (particle count, momentum, summed source, mass);
+ *   - the hand-derived adjoint of the step for a loss on the time-summed
+ *     source field.
+ *
+ * Pins (tests/test_oracle_pins.py): closed-form and ODE-integrated
+ * uniform-flow solutions, terminal velocity, exact reproduction of
+ * trilinear functions, the momentum balance, brute-force deposit and sort
+ * checks on tiny inputs, and central finite differences for the adjoint.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC.
+ */
+#ifndef SCALETRACK_ORACLE_H
+#define SCALETRACK_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Grid, box and physical parameters.  Field and source arrays index cells
+ * linearly as c = i + nx * (j + ny * k). */
+typedef struct {
+  int32_t n[3];        /* cells along x, y, z */
+  int32_t chunk_edge;  /* B: cells per chunk edge (power of two) */
+  double L[3];         /* periodic box lengths */
+  double rho_p;        /* particle material density */
+  double mu;           /* fluid dynamic viscosity */
+  double g[3];         /* gravitational acceleration */
+  double alpha;        /* drag scale multiplying the Stokes drag */
+  double mult;         /* parcel multiplicity w (particles per parcel) */
+} orc_grid;
+
+/* Periodic wrap of one coordinate into [0, L). */
+double orc_wrap(double x, double L);
+
+/* Cell index (i, j, k) of a wrapped position. */
+void orc_cell(const orc_grid* G, const double x[3], int32_t idx[3]);
+
+/* Trilinear interpolation of the cell-centred field U[c][3] at x. */
+void orc_gather(const orc_grid* G, const double* U, const double x[3], double up[3]);
+
+/* One exponential-integrator step of a particle of diameter d that sees the
+ * frozen fluid velocity up: updates v and x in place (x not wrapped). */
+void orc_advance(const orc_grid* G, double d, const double up[3], double dt,
+                 double x[3], double v[3]);
+
+/* Particle mass (parcel multiplicity included). */
+double orc_mass(const orc_grid* G, double d);
+
+/* One full step of one particle: start cell c0 (linear), gather, advance,
+ * wrap, and the impulse J given to the fluid. */
+void orc_particle_step(const orc_grid* G, const double* U, double dt, double d,
+                       double x[3], double v[3], int64_t* c0, double J[3]);
+
+/* nsteps steps of n particles (SoA pos[3][n], vel[3][n]) in the frozen field U.
+ * Adds each step's impulses into src[3][ncell] in step-major, particle-index
+ * order.  If trace != NULL it records the deposit cell of every particle and
+ * step (trace[s*n + p]); if frozen != NULL the deposit cells are taken from
+ * it instead of being computed (finite differences with the cell sequence
+ * held fixed).  Returns 0, or -1 on bad arguments. */
+int orc_run(const orc_grid* G, const double* U, int64_t n, double* pos, double* vel,
+            const double* d, int32_t nsteps, double dt, double* src,
+            int64_t* trace, const int64_t* frozen);
+
+/* Chunk-major ordering key of cell (i, j, k): chunk index (x fastest) times
+ * B^3 plus the Morton (bit-interleaved, x lowest) index inside the chunk. */
+uint32_t orc_key(const orc_grid* G, int32_t i, int32_t j, int32_t k);
+
+/* Stable sort permutation: perm[r] = index of the r-th particle in key
+ * order, ties kept in index order. */
+void orc_sort_perm(int64_t n, const uint32_t* keys, int64_t* perm);
+
+/* Particles per cell (counts[ncell]) for the wrapped positions pos[3][n]. */
+void orc_cell_counts(const orc_grid* G, int64_t n, const double* pos, int64_t* counts);
+
+/* Invariants: out = {count, P_x, P_y, P_z, sumJ_x, sumJ_y, sumJ_z, sum m}
+ * with P = sum_p m_p v_p and sumJ = sum over cells of the source. */
+void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const double* d,
+                    const double* src, double out[8]);
+
+/* Adjoint of orc_run for a loss L(Jtot) with Jtot the time-summed source:
+ * given lam[3][ncell] = dL/dJtot, returns dL/dd_p, dL/dalpha and
+ * dL/dU (gradU[c][3], same layout as U).  Deposit cells are treated as
+ * locally constant (the derivative that exists almost everywhere).  The
+ * forward trajectory is stored whole (no checkpointing).  pos0/vel0 are
+ * not modified.  Returns 0, -1 on bad arguments, -2 on allocation failure. */
+int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
+                const double* vel0, const double* d, int32_t nsteps, double dt,
+                const double* lam, double* grad_d, double* grad_alpha, double* gradU);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
