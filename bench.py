@@ -1,0 +1,358 @@
+"""Throughput of the per-particle Lagrangian step on GB300.
+
+Workload (one GPU): a 256^3 periodic grid with a seeded divergence-free random
+Fourier field stored in FP32, 1e9 particles in the mixed-precision storage
+(int32 cell + FP32 offset, FP32 velocity, FP32 diameter), dt = 5e-4, counting
+sort every 10 steps.  A "step" is one pass of the whole hot path: the
+counting sort when it is due (every 10th step), then gather, integrate,
+relocate and deposit for every particle.  The particle state (32 GB) is far
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line.  With --impl reference the same metric is measured for
+the FP64 CPU oracle on a bounded sample of the workload on the host cores.
+Launch on N GPUs: python -m torch.distributed.run --nproc-per-node N bench.py
+--gpus N (each rank runs its own replica of the workload: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 1e9 particles, % HBM roofline; mixed vs FP64 at fixed error"
+UNIT = "particle-steps/s"
+# algorithmic bytes per particle-step of the step kernel (read + write of the particle state)
+STEP_BYTES = {"mixed_f32": 32 + 28, "mixed_bf16": 26 + 22, "fp64": 56 + 48}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload, U, budget_s: float = 15.0, n_sample: int = 20000):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload (host cores)."""
+    import oracle
+    from paper_2603_26691_gb300 import inputs
+
+    N = workload.grid
+    G = oracle.make_grid(N, chunk_edge=workload.chunk_edge)
+    pos, vel, d, _ = inputs.particles(workload.seed, 0, n_sample)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        pos, vel, _, _ = oracle.run(G, U, pos, vel, d, 1, workload.dt, src=None)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n_sample * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_sample} particles of the workload x {steps} steps (single thread), {el:.1f} s"}
+
+
+def run_reference(args, workload):
+    """The oracle arm: same metric, FP64 CPU oracle, bounded sample per step."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2603_26691_gb300 import inputs
+
+    U = workload.make_field()
+    G = oracle.make_grid(workload.grid, chunk_edge=workload.chunk_edge)
+    n_sample = args.ref_sample
+    pos, vel, d, _ = inputs.particles(workload.seed, 0, n_sample)
+    src = np.zeros((3, workload.grid ** 3))
+    for _ in range(args.warmup):
+        pos, vel, src, _ = oracle.run(G, U, pos, vel, d, 1, workload.dt, src=src)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pos, vel, src, _ = oracle.run(G, U, pos, vel, d, 1, workload.dt, src=src)
+    el = time.perf_counter() - t0
+    value = n_sample * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload.name, "grid": workload.grid, "particles_per_step": n_sample,
+                       "precision": "fp64 (CPU oracle)", "dt": workload.dt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sample} particles of the workload per step (single thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def setup_sim(workload, n, U32, precision, device, batch=50_000_000):
+    import torch
+
+    from paper_2603_26691_gb300 import inputs
+    from paper_2603_26691_gb300.sim import Sim
+
+    sim = Sim(workload.grid, precision=precision, chunk_edge=workload.chunk_edge, device=device)
+    sim.set_params(reorder_every=0)  # the bench calls the sort itself so that it can time it apart
+    sim.set_fluid(torch.as_tensor(U32, device=device))
+    sim.reserve(n)
+    q = inputs.lognormal_qtable()
+    first = 0
+    while first < n:
+        cnt = min(batch, n - first)
+        pos, vel, d, ids = sim.gen_particles(workload.seed, first, cnt, q, vmax=workload.vmax)
+        sim.add_particles(pos, d, vel, ids)
+        del pos, vel, d, ids
+        first += cnt
+    torch.cuda.synchronize()
+    return sim
+
+
+def timed_steps(sim, steps, dt, reorder_every, step_index0):
+    """Run `steps` steps with the sort every `reorder_every` steps; per-kernel CUDA events."""
+    import torch
+
+    ev = []
+    for s in range(steps):
+        idx = step_index0 + s
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sorted_now = reorder_every > 0 and idx % reorder_every == 0
+        if sorted_now:
+            sim.reorder()
+        e1.record()
+        sim.step(1, dt)
+        e2.record()
+        ev.append((e0, e1, e2, sorted_now))
+    return ev
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fourier256_mixed_1e9")
+    ap.add_argument("--n", type=int, default=None, help="particles per GPU (default: the workload's)")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fp64-n", type=int, default=None, help="particles for the FP64-step comparison (0 = skip)")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    from paper_2603_26691_gb300 import inputs
+
+    workload = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, workload)
+
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    precision = args.precision or workload.precision
+    n = args.n or workload.n
+    K, W = args.steps, args.warmup
+    assert W >= 3, "at least 3 warm-up steps"
+    U = workload.make_field()
+    U32 = U.astype(np.float32)
+
+    sim = setup_sim(workload, n, U32, precision, device)
+    dt = workload.dt
+    reorder_every = workload.reorder_every
+    # warm-up (sorts at step 0, 10, ... as in the timed region)
+    for ev in timed_steps(sim, W, dt, reorder_every, 0):
+        pass
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                          if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = sim.kernel_launches
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    evs = timed_steps(sim, K, dt, reorder_every, W)
+    t_end.record()
+    torch.cuda.synchronize()
+    launches = sim.kernel_launches - launches0
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    step_ms = [e1.elapsed_time(e2) for (e0, e1, e2, _) in evs]
+    sort_ms = [e0.elapsed_time(e1) for (e0, e1, e2, s) in evs if s]
+    t_max = total_ms
+    if ws > 1:
+        t = torch.tensor([total_ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = n * ws * K / (t_max * 1e-3)
+
+    peak, peak_kind = _peaks()
+    step_avg = sum(step_ms) / len(step_ms)
+    bytes_per_launch = STEP_BYTES[precision] * n
+    achieved = bytes_per_launch / (step_avg * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "step_mixed_kernel" if precision != "fp64" else "step_f64_kernel",
+                "algorithmic_bytes_per_particle_step": STEP_BYTES[precision], "peak_kind": peak_kind,
+                "step_kernel_ms": step_avg}
+
+    # end to end through the C ABI with host buffers: each step receives the fluid field from
+    # pinned host memory and returns the per-cell sources to pinned host memory
+    Uh = torch.from_numpy(U32).pin_memory()
+    src_h = torch.empty((3, sim.ncell), dtype=torch.float64).pin_memory()
+    E = args.e2e_steps
+    torch.cuda.synchronize()
+    import ctypes as C
+
+    lib = sim.lib
+    e_t0 = time.perf_counter()
+    for s in range(E):
+        sim._chk(lib.st_set_fluid(sim.h, C.c_void_p(Uh.data_ptr()), 0, 0), "st_set_fluid")
+        if reorder_every > 0 and (W + K + s) % reorder_every == 0:
+            sim.reorder()
+        sim.step(1, dt)
+        sim._chk(lib.st_get_sources(sim.h, C.c_void_p(src_h.data_ptr()), 1, 0), "st_get_sources")
+    torch.cuda.synchronize()
+    e_el = time.perf_counter() - e_t0
+    e2e = {"value": n * ws * E / e_el, "unit": UNIT, "h2d_bytes_per_step": int(U32.nbytes),
+           "d2h_bytes_per_step": int(src_h.numel() * 8), "steps": E,
+           "what": "per step: fluid field H2D from pinned host, step (sort when due), sources D2H to pinned host"}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # FP64 GPU step on the same workload, for the mixed-vs-FP64 comparison
+    fp64 = None
+    fp64_n = n if args.fp64_n is None else args.fp64_n
+    if fp64_n > 0 and precision != "fp64":
+        s64 = setup_sim(workload, fp64_n, U32, "fp64", device)
+        for _ in timed_steps(s64, 1, dt, reorder_every, 0):
+            pass
+        torch.cuda.synchronize()
+        ev64 = timed_steps(s64, args.fp64_steps, dt, 0, 1)
+        torch.cuda.synchronize()
+        ms64 = sum(e1.elapsed_time(e2) for (e0, e1, e2, _) in ev64) / len(ev64)
+        rate64 = fp64_n / (ms64 * 1e-3)
+        fp64 = {"particles": fp64_n, "step_kernel_ms": ms64, "particle_steps_per_s": rate64,
+                "mixed_step_kernel_particle_steps_per_s": n / (step_avg * 1e-3),
+                "speedup_mixed_over_fp64_step_kernel": (n / (step_avg * 1e-3)) / rate64,
+                "bound": "alu (FP64)"}
+        s64.close()
+        del s64
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(workload, U32.astype(np.float64), budget_s=args.cpu_budget)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if precision != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": workload.name, "grid": workload.grid, "particles_per_gpu": n,
+                       "precision": precision, "dt": dt, "reorder_every": reorder_every,
+                       "chunk_edge": workload.chunk_edge, "field": "divergence-free random Fourier, k<=8, rms 1",
+                       "l2": "no flush: 32 B x particles of state per step, far larger than L2",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "breakdown": {"step_kernel_ms_avg": step_avg, "sort_ms_avg": (sum(sort_ms) / len(sort_ms)) if sort_ms else None,
+                          "sorts_in_timed_region": len(sort_ms)},
+            "fp64_step": fp64}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * scaletrack.h - C ABI of the GB300 (sm_103a) per-particle Lagrangian step of a
+ * two-way coupled Euler-Lagrange method (SCALE-TRACK, arXiv 2603.26691).
+ *
+ * The library advances point particles through a frozen, cell-centred fluid
+ * velocity field on a periodic uniform grid and returns the momentum they
+ * exchanged with the fluid as per-cell sources.  This follows the paper's
+ * statement of the coupling problem (Sec. 2.5): the Lagrangian code is given
+ * the domain geometry, the mesh and the Eulerian fields, and gives back
+ * source terms.  One step of one particle:
+ *   1. gather the fluid velocity u_p by trilinear interpolation of the
+ *      cell-centred field (in place of the nearest-grid-point rule of
+ *      Sec. 2.5);
+ *   2. advance Newton's law (Sec. 2.1, Eqs. 9-10) under Stokes drag with
+ *      relaxation time tau = rho_p d^2 / (18 mu), scaled by drag_scale, and
+ *      gravity, with the exponential integrator (exact for frozen u_p):
+ *        a = drag_scale / tau, w = u_p + g / a,
+ *        v' = w + (v - w) e^{-a dt},
+ *        x' = x + w dt + (v - w) (1 - e^{-a dt}) / a;
+ *   3. wrap x' into the periodic box and relocate the particle to its new
+ *      cell and chunk;
+ *   4. deposit J = -m [(v' - v) - g dt] (the drag part of d(m u_p)/dt in the
+ *      momentum source, Sec. 2.1 Eq. 11, with the sign of a gain for the
+ *      fluid) whole into the cell that held the particle at the start of the
+ *      step (Sec. 2.5).
+ * Particles are kept as structures of arrays (Sec. 2.2) and reordered
+ * periodically by a stable counting sort on a chunk-major key.
+ *
+ * Conventions for every call:
+ *   - Every call returns st_status; nothing throws across the ABI.  After an
+ *     error, st_last_error(h) gives a message; the handle stays usable
+ *     unless the status is ST_ERR_CUDA from an asynchronous fault.
+ *   - Pointers passed in are borrowed for the duration of the call only.
+ *     Output buffers belong to the caller.  `on_device` = 1 means the
+ *     pointer is CUDA device memory on the handle's device, 0 means host
+ *     memory (pageable or pinned).
+ *   - Work is ordered on the caller's CUDA stream (st_create_grid).  Calls
+ *     that return data to the caller (st_get_*, st_invariants,
+ *     st_num_particles) synchronise that stream; st_step, st_reorder,
+ *     st_set_fluid and st_add_particles from device memory do not.
+ *   - Cells are numbered c = i + nx * (j + ny * k).  Per-cell arrays of three
+ *     components are component-major: out[q * ncell + c].  Particle arrays of
+ *     three components are component-major too: xyz[q * count + p].
+ *   - Fluid fields are cell-centred (centre of cell (i,j,k) at
+ *     ((i + 1/2) h_x, (j + 1/2) h_y, (k + 1/2) h_z)), laid out u[k][j][i][3].
+ */
+#ifndef SCALETRACK_H
+#define SCALETRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct st_ctx* st_handle;
+
+/* Device-memory provider.  alloc returns device memory of at least `bytes`
+ * bytes aligned to 256 bytes, or NULL; free releases it.  Both are called
+ * from the thread that calls into the library; memory is used on the
+ * handle's stream.  A NULL st_allocator pointer selects cudaMalloc/cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} st_allocator;
+
+typedef enum {
+  ST_OK = 0,
+  ST_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+  ST_ERR_OOM = 2,         /* the allocator returned NULL */
+  ST_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  ST_ERR_STATE = 4,       /* call not valid in the handle's current state */
+  ST_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  ST_ERR_NONFINITE = 6,   /* a field value, particle value or parameter is NaN/Inf */
+  ST_ERR_OVERFLOW = 7     /* the source accumulator's range would be exceeded */
+} st_status;
+
+/* Storage and arithmetic of the particle state. */
+typedef enum {
+  ST_FP64 = 0,       /* x, y, z, u, v, w, d as FP64 (56 bytes per particle) */
+  ST_MIXED_F32 = 1,  /* int32 cell + FP32 in-cell offset, FP32 velocity, FP32 d (32 B) */
+  ST_MIXED_BF16V = 2 /* as ST_MIXED_F32 with the velocity stored in BF16 (26 B) */
+} st_precision;
+
+enum { ST_DTYPE_F32 = 0, ST_DTYPE_F64 = 1 };
+
+/* Create a simulation on the current CUDA device: an nx x ny x nz periodic
+ * grid over the box [0,Lx) x [0,Ly) x [0,Lz) (Sec. 2.5: the mesh and
+ * geometry the Lagrangian solver needs).  chunk_edge B (power of two,
+ * 1..32) sets the chunk of B^3 cells used as the major part of the ordering
+ * key (chunks as particle-set partitions stored as structures of arrays,
+ * Sec. 2.2).  1 <= n* <= 1024.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  Parameters start as rho_p = 1000, mu = 1.8e-5,
+ * g = (0, 0, -9.81), drag_scale = 1, multiplicity = 1, reorder_every = 10.
+ * The fluid starts at rest.  Errors: INVALID_ARG, OOM, CUDA. */
+st_status st_create_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz, int chunk_edge,
+                         int precision, const st_allocator* allocator, void* stream, st_handle* out);
+
+/* Release everything the handle owns.  Safe on NULL. */
+void st_destroy(st_handle h);
+
+/* Message for the last error on this handle ("" if none).  The string
+ * belongs to the handle and lives until the next call on it. */
+const char* st_last_error(st_handle h);
+
+/* Change the CUDA stream later calls are ordered on. */
+st_status st_set_stream(st_handle h, void* stream);
+
+/* Wait for all work the handle has queued. */
+st_status st_synchronize(st_handle h);
+
+/* Physical parameters (Sec. 2.1): particle density rho_p > 0, fluid dynamic
+ * viscosity mu > 0, gravity g[3], drag_scale alpha > 0 multiplying the
+ * Stokes drag, parcel multiplicity w > 0 (particles lumped per parcel,
+ * Sec. 3.2; it multiplies the mass in the source), and reorder_every K
+ * (counting sort every K steps and before the first step; 0 = only on
+ * st_reorder).  Errors: INVALID_ARG, NONFINITE. */
+st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3], double drag_scale,
+                        double multiplicity, int reorder_every);
+
+/* Copy in the cell-centred fluid velocity u[k][j][i][3] (dtype
+ * ST_DTYPE_F32 or ST_DTYPE_F64) - the Eulerian state of Sec. 2.3 that the
+ * Lagrangian step reads.  FP64 handles keep it in FP64, mixed handles in
+ * FP32.  Errors: INVALID_ARG, NONFINITE (any NaN/Inf), CUDA. */
+st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device);
+
+/* Make room for `capacity` particles in total (optional; st_add_particles
+ * grows geometrically otherwise).  Errors: INVALID_ARG, OOM. */
+st_status st_reserve(st_handle h, int64_t capacity);
+
+/* Append n particles: positions xyz[3][n] (any real values; wrapped into
+ * the box), velocities vel[3][n] (NULL = at rest), diameters d[n] > 0,
+ * optional ids[n] (NULL = consecutive from the number already held).  The
+ * FP64 values are converted to the handle's storage.  The new particles
+ * are unsorted until the next reorder.  Errors: INVALID_ARG (d <= 0),
+ * NONFINITE, OOM, CUDA. */
+st_status st_add_particles(st_handle h, int64_t n, const double* xyz, const double* vel,
+                           const double* d, const uint32_t* ids, int on_device);
+
+/* Number of particles held. */
+st_status st_num_particles(st_handle h, int64_t* n);
+
+/* Advance all particles nsteps steps of length dt > 0 through the current
+ * fluid field (the fixed sub-steps per Eulerian step of Sec. 3.3), adding
+ * each step's impulses to the per-cell source accumulator.  Runs the
+ * counting sort first when it is due.  Asynchronous on the stream.
+ * Errors: INVALID_ARG, STATE (no fluid set), OVERFLOW, CUDA. */
+st_status st_step(st_handle h, int nsteps, double dt);
+
+/* Read the accumulated per-cell source: out[3][ncell] in FP64, the raw
+ * impulse given to the fluid in each cell (kg m/s) summed over every step
+ * since the last reset.  The momentum-source density of Sec. 2.1 Eq. 11 is
+ * out / (V_cell * T) over the accumulation time T.  The accumulator is
+ * exact fixed point (see the design notes), so the result does not depend
+ * on thread scheduling.  reset = 1 clears it afterwards.  Synchronises.
+ * Errors: INVALID_ARG, CUDA. */
+st_status st_get_sources(st_handle h, double* out, int reset, int on_device);
+
+/* Stable counting sort of the particles now, by the chunk-major key of
+ * their cell: chunk index (x fastest) times B^3 plus the Morton index of
+ * the cell inside its chunk.  Particles with equal keys keep their order.
+ * Asynchronous.  Errors: OOM, CUDA. */
+st_status st_reorder(st_handle h);
+
+/* Copy out particles [first, first + count) in the current storage order:
+ * absolute positions xyz[3][count] reconstructed in FP64 (mixed handles:
+ * x = (i + offset) h), velocities vel[3][count], diameters d[count], ids.
+ * Any output pointer may be NULL.  Synchronises.  Errors: INVALID_ARG, CUDA. */
+st_status st_get_particles(st_handle h, int64_t first, int64_t count, double* xyz, double* vel,
+                           double* d, uint32_t* ids, int on_device);
+
+/* Cell index of particles [first, first + count) as int32 linear cell
+ * numbers c = i + nx (j + ny k).  Synchronises. */
+st_status st_get_cells(st_handle h, int64_t first, int64_t count, int32_t* cells, int on_device);
+
+/* Particles per cell, counts[ncell], as of the last reorder (after a
+ * reorder the particles of cell c occupy a contiguous range of the storage
+ * order).  Errors: STATE if never sorted.  Synchronises. */
+st_status st_get_cell_counts(st_handle h, int64_t* counts, int on_device);
+
+/* Global invariants in FP64: out = {particle count, P_x, P_y, P_z, S_x, S_y,
+ * S_z, M} with P = sum_p m_p v_p, S = sum over cells of the accumulated
+ * source and M = sum_p m_p.  With no fluid forcing beyond drag,
+ * P(T) - P(0) - M g T + S = 0.  Synchronises. */
+st_status st_invariants(st_handle h, double out[8]);
+
+/* Number of CUDA kernels this handle has launched since it was created (a
+ * diagnostic for profiling: every kernel of the library counts once per
+ * launch). */
+st_status st_kernel_launches(st_handle h, int64_t* count);
+
+/* Seeded synthetic particles (an input generator, not part of the method):
+ * particles first .. first+count-1 of the counter-based SplitMix64 stream
+ * `seed`, written as FP64 device arrays xyz[3][count], vel[3][count]
+ * (uniform in [-vmax, vmax) per component, or zero when vmax == 0),
+ * d[count] (inverse-transform sampled from qtable[nq + 1], a device array
+ * of quantiles) and ids[count] = index.  The same definition is implemented
+ * on the host by the package's input module.  Any output may be NULL.
+ * Asynchronous.  Errors: INVALID_ARG, CUDA. */
+st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t count, const double L[3],
+                           double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
+                           uint32_t* ids);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,367 @@
+// Stable counting sort of the particles by their chunk-major cell key.
+//
+// LSD radix sort of (key, slot) pairs with 8-bit digits; each pass is a
+// stable counting sort in three phases: per-tile digit histograms (warp-
+// aggregated shared-memory counts), one exclusive scan over the digit-major
+// histogram matrix, and a scatter in which every element's rank among the
+// equal digits of its tile comes from warp match/prefix operations combined
+// across warps in warp order.  No phase waits on another block.  The
+// structure-of-arrays payload is then gathered once through the final
+// permutation.  Equal keys keep their storage order, so the permutation is
+// unique.
+#include <vector>
+
+#include "st_common.cuh"
+
+namespace st {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kSortThreads * kItems;  // 4096 items per tile
+constexpr int kRadix = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanBlock = kScanThreads * kScanItems;  // 2048
+
+struct KeyGeo {
+  int n[3];
+  double inv_h[3];
+  int B, logB, ncx, ncy;
+};
+
+__global__ void keys_f64_kernel(F64State s, int64_t n, KeyGeo g, uint32_t* __restrict__ keys,
+                                uint32_t* __restrict__ vals) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int c[3];
+    for (int q = 0; q < 3; ++q) {
+      int i = (int)floor(s.x[q][p] * g.inv_h[q]);
+      c[q] = min(max(i, 0), g.n[q] - 1);
+    }
+    keys[p] = chunk_key(c[0], c[1], c[2], g.B, g.logB, g.ncx, g.ncy);
+    vals[p] = (uint32_t)p;
+  }
+}
+
+__global__ void keys_mixed_kernel(const int32_t* __restrict__ cell, int64_t n, KeyGeo g, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int32_t c = cell[p];
+    keys[p] = chunk_key(cell_i(c), cell_j(c), cell_k(c), g.B, g.logB, g.ncx, g.ncy);
+    vals[p] = (uint32_t)p;
+  }
+}
+
+// phase 1: digit histogram of each tile, stored digit-major: hist[d * ntiles + t]
+__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                                int64_t ntiles, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[kRadix];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t t = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  for (int r = 0; r < kItems; ++r) {
+    int64_t i = t * kTile + (int64_t)r * kSortThreads + threadIdx.x;
+    bool valid = i < n;
+    uint32_t dig = valid ? ((keys[i] >> shift) & 0xffu) : (0x100u + lane);
+    unsigned peers = __match_any_sync(0xffffffffu, dig);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[dig], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * ntiles + t] = cnt[threadIdx.x];
+}
+
+// exclusive scan, three kernels: block sums, scan of the block sums (one block,
+// sequential over chunks with a carry), then block-local scans plus offsets
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t wsum[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    uint32_t s = lane < nw ? wsum[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) wsum[lane] = s;
+  }
+  __syncthreads();
+  uint32_t before = (w > 0 ? wsum[w - 1] : 0u) + x - v;
+  *total = wsum[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t m,
+                                                                   uint32_t* __restrict__ bsum) {
+  uint32_t s = 0;
+  int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < m) s += in[base + k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ uint32_t ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) scan_blocksums_kernel(uint32_t* __restrict__ bsum, int64_t nb) {
+  uint32_t carry = 0;
+  for (int64_t c = 0; c < nb; c += 1024) {
+    int64_t i = c + threadIdx.x;
+    uint32_t v = i < nb ? bsum[i] : 0u;
+    uint32_t total;
+    uint32_t ex = block_exclusive_scan(v, &total);
+    if (i < nb) bsum[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in,
+                                                                  uint32_t* __restrict__ out, int64_t m,
+                                                                  const uint32_t* __restrict__ bsum) {
+  uint32_t v[kScanItems];
+  int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
+  uint32_t s = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < m) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t total;
+  uint32_t ex = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < m) out[base + k] = ex;
+    ex += v[k];
+  }
+}
+
+// phase 3: stable scatter.  Warp w owns items [w*512, (w+1)*512) of the tile in
+// 16 coalesced rounds; ranks inside a round come from match_any + popc, across
+// rounds from a per-warp running count, across warps from a prefix in warp order.
+__global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint32_t* __restrict__ kin,
+                                                                  const uint32_t* __restrict__ vin,
+                                                                  uint32_t* __restrict__ kout,
+                                                                  uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                                  int64_t ntiles, const uint32_t* __restrict__ offs) {
+  constexpr int kWarps = kSortThreads / 32;
+  __shared__ uint32_t wcnt[kWarps][kRadix];
+  __shared__ uint32_t base[kRadix];
+  for (int w = 0; w < kWarps; ++w) wcnt[w][threadIdx.x] = 0;
+  const int64_t t = blockIdx.x;
+  base[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t key[kItems], val[kItems], rank[kItems];
+  const int64_t start = t * kTile + (int64_t)w * (kItems * 32);
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    int64_t i = start + r * 32 + lane;
+    bool valid = i < n;
+    key[r] = valid ? kin[i] : 0u;
+    val[r] = valid ? vin[i] : 0u;
+    uint32_t dig = valid ? ((key[r] >> shift) & 0xffu) : (0x100u + lane);
+    unsigned peers = __match_any_sync(0xffffffffu, dig);
+    uint32_t before = 0;
+    if (valid) before = wcnt[w][dig];
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[w][dig] = before + __popc(peers);
+    __syncwarp();
+    rank[r] = valid ? before + __popc(peers & lt) : 0xffffffffu;
+  }
+  __syncthreads();
+  {
+    uint32_t s = 0;
+    for (int ww = 0; ww < kWarps; ++ww) {
+      uint32_t c = wcnt[ww][threadIdx.x];
+      wcnt[ww][threadIdx.x] = s;
+      s += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kItems; ++r) {
+    if (rank[r] != 0xffffffffu) {
+      uint32_t dig = (key[r] >> shift) & 0xffu;
+      uint32_t dst = base[dig] + wcnt[w][dig] + rank[r];
+      kout[dst] = key[r];
+      vout[dst] = val[r];
+    }
+  }
+}
+
+// payload gather through the final permutation
+__global__ void gather_f64_kernel(F64State src, F64State dst, const uint32_t* __restrict__ sid,
+                                  uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t p = perm[i];
+    for (int q = 0; q < 3; ++q) {
+      dst.x[q][i] = src.x[q][p];
+      dst.v[q][i] = src.v[q][p];
+    }
+    dst.d[i] = src.d[p];
+    did[i] = sid[p];
+  }
+}
+
+template <typename VT>
+__global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32_t* __restrict__ sid,
+                                    uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t p = perm[i];
+    dst.cell[i] = src.cell[p];
+    for (int q = 0; q < 3; ++q) {
+      dst.xi[q][i] = src.xi[q][p];
+      ((VT*)dst.v[q])[i] = ((const VT*)src.v[q])[p];
+    }
+    dst.d[i] = src.d[p];
+    did[i] = sid[p];
+  }
+}
+
+// start[k] = first sorted position with key >= k, for k in [0, nkeys] (binary search)
+__global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t nkeys,
+                                  uint32_t* __restrict__ start) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= (int64_t)nkeys;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)keys[mid] < k) lo = mid + 1;
+      else hi = mid;
+    }
+    start[k] = (uint32_t)lo;
+  }
+}
+
+__global__ void cell_counts_kernel(const uint32_t* __restrict__ start, KeyGeo g, int64_t* __restrict__ counts) {
+  int64_t ncell = (int64_t)g.n[0] * g.n[1] * g.n[2];
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(c % g.n[0]);
+    int j = (int)((c / g.n[0]) % g.n[1]);
+    int k = (int)(c / ((int64_t)g.n[0] * g.n[1]));
+    uint32_t key = chunk_key(i, j, k, g.B, g.logB, g.ncx, g.ncy);
+    counts[c] = (int64_t)start[key + 1] - (int64_t)start[key];
+  }
+}
+
+KeyGeo key_geo(const st_ctx* h) {
+  KeyGeo g;
+  for (int q = 0; q < 3; ++q) {
+    g.n[q] = h->geo.n[q];
+    g.inv_h[q] = h->geo.inv_h[q];
+  }
+  g.B = h->geo.B;
+  g.logB = 0;
+  while ((1 << g.logB) < g.B) ++g.logB;
+  g.ncx = (g.n[0] + g.B - 1) / g.B;
+  g.ncy = (g.n[1] + g.B - 1) / g.B;
+  return g;
+}
+
+int grid_for(int64_t n, int max_blocks = 152 * 16) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+cudaError_t exclusive_scan(st_ctx* h, const uint32_t* in, uint32_t* out, int64_t m) {
+  int64_t nb = (m + kScanBlock - 1) / kScanBlock;
+  uint32_t* bsum = (uint32_t*)h->scan_aux.p;
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, h->stream>>>(in, m, bsum);
+  scan_blocksums_kernel<<<1, 1024, 0, h->stream>>>(bsum, nb);
+  scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, h->stream>>>(in, out, m, bsum);
+  h->launches += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+st_status sort_particles(st_ctx* h) {
+  const int64_t n = h->np;
+  if (n == 0) return ST_OK;
+  if (n >= (int64_t(1) << 32)) return set_error(h, ST_ERR_INVALID_ARG, "sorting needs fewer than 2^32 particles");
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t hm = ntiles * kRadix;
+  const int64_t nb = (hm + kScanBlock - 1) / kScanBlock;
+  if (h->sort_cap < h->cap) {
+    size_t kb = (size_t)h->cap * sizeof(uint32_t);
+    for (int b = 0; b < 2; ++b) {
+      if (ensure(h, h->keys[b], kb) != ST_OK || ensure(h, h->vals[b], kb) != ST_OK) return ST_ERR_OOM;
+    }
+    h->sort_cap = h->cap;
+  }
+  if (ensure(h, h->hist, (size_t)hm * 2 * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
+  if (ensure(h, h->scan_aux, (size_t)(nb + 1) * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
+  if (ensure(h, h->cell_start, ((size_t)h->nkeys + 1) * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
+  if (ensure(h, h->state_alt, state_bytes(h->prec, h->cap)) != ST_OK) return ST_ERR_OOM;
+  if (ensure(h, h->ids_alt, (size_t)h->cap * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
+
+  KeyGeo g = key_geo(h);
+  uint32_t* k0 = (uint32_t*)h->keys[0].p;
+  uint32_t* v0 = (uint32_t*)h->vals[0].p;
+  uint32_t* k1 = (uint32_t*)h->keys[1].p;
+  uint32_t* v1 = (uint32_t*)h->vals[1].p;
+  if (h->prec == ST_FP64)
+    keys_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(carve_f64(h->state.p, h->cap), n, g, k0, v0);
+  else
+    keys_mixed_kernel<<<grid_for(n), 256, 0, h->stream>>>((const int32_t*)h->state.p, n, g, k0, v0);
+  h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(h, e, "sort keys");
+  uint32_t* hist = (uint32_t*)h->hist.p;
+  uint32_t* offs = hist + hm;
+  for (int shift = 0; shift < h->key_bits; shift += 8) {
+    upsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, h->stream>>>(k0, n, shift, ntiles, hist);
+    e = exclusive_scan(h, hist, offs, hm);
+    if (e != cudaSuccess) return cuda_check(h, e, "sort scan");
+    downsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, h->stream>>>(k0, v0, k1, v1, n, shift, ntiles, offs);
+    h->launches += 2;  // upsweep + downsweep
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(h, e, "sort pass");
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  // k0/v0 now hold the sorted keys and the permutation
+  if (h->prec == ST_FP64) {
+    gather_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(carve_f64(h->state.p, h->cap),
+                                                          carve_f64(h->state_alt.p, h->cap), (const uint32_t*)h->ids.p,
+                                                          (uint32_t*)h->ids_alt.p, v0, n);
+  } else if (h->prec == ST_MIXED_F32) {
+    gather_mixed_kernel<float><<<grid_for(n), 256, 0, h->stream>>>(
+        carve_mixed(h->state.p, h->cap, false), carve_mixed(h->state_alt.p, h->cap, false), (const uint32_t*)h->ids.p,
+        (uint32_t*)h->ids_alt.p, v0, n);
+  } else {
+    gather_mixed_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, h->stream>>>(
+        carve_mixed(h->state.p, h->cap, true), carve_mixed(h->state_alt.p, h->cap, true), (const uint32_t*)h->ids.p,
+        (uint32_t*)h->ids_alt.p, v0, n);
+  }
+  cell_start_kernel<<<grid_for((int64_t)h->nkeys + 1), 256, 0, h->stream>>>(k0, n, h->nkeys, (uint32_t*)h->cell_start.p);
+  h->launches += 2;  // gather + cell starts
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(h, e, "sort gather");
+  std::swap(h->state, h->state_alt);
+  std::swap(h->ids, h->ids_alt);
+  return ST_OK;
+}
+
+cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts) {
+  KeyGeo g = key_geo(h);
+  cell_counts_kernel<<<grid_for(h->geo.ncell), 256, 0, h->stream>>>((const uint32_t*)h->cell_start.p, g, counts);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace st

@@ -1,0 +1,560 @@
+// C ABI of the Lagrangian step: handle management, argument checks, memory,
+// and the per-call orchestration of the kernels on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "st_common.cuh"
+
+namespace st {
+
+st_status set_error(st_ctx* h, st_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+st_status cuda_check(st_ctx* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return ST_OK;
+  return set_error(h, ST_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+st_status dev_alloc(st_ctx* h, Buf& b, size_t bytes) {
+  b.p = nullptr;
+  b.bytes = 0;
+  if (bytes == 0) return ST_OK;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (h->have_alloc) {
+    p = h->alloc.alloc(bytes, h->alloc.user);
+    if (!p) return set_error(h, ST_ERR_OOM, "allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(h, ST_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+  }
+  b.p = p;
+  b.bytes = bytes;
+  return ST_OK;
+}
+
+void dev_free(st_ctx* h, Buf& b) {
+  if (!b.p) return;
+  if (h->have_alloc) {
+    h->alloc.free(b.p, h->alloc.user);
+  } else {
+    cudaFree(b.p);
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+st_status ensure(st_ctx* h, Buf& b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return ST_OK;
+  dev_free(h, b);
+  return dev_alloc(h, b, bytes);
+}
+
+}  // namespace st
+
+using namespace st;
+
+#define ST_TRY(expr)                     \
+  do {                                   \
+    st_status _s = (expr);               \
+    if (_s != ST_OK) return _s;          \
+  } while (0)
+
+#define ST_CUDA(h, expr) ST_TRY(cuda_check((h), (expr), #expr))
+
+static bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+static st_status check_handle(st_handle h) {
+  if (!h) return ST_ERR_INVALID_ARG;
+  h->err.clear();
+  cudaError_t e = cudaSetDevice(h->dev);
+  return cuda_check(h, e, "cudaSetDevice");
+}
+
+extern "C" {
+
+st_status st_create_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz, int chunk_edge,
+                         int precision, const st_allocator* allocator, void* stream, st_handle* out) {
+  if (!out) return ST_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n[3] = {nx, ny, nz};
+  double L[3] = {Lx, Ly, Lz};
+  for (int q = 0; q < 3; ++q) {
+    if (n[q] < 1 || n[q] > kMaxDim) return ST_ERR_INVALID_ARG;
+    if (!std::isfinite(L[q])) return ST_ERR_NONFINITE;
+    if (!(L[q] > 0.0)) return ST_ERR_INVALID_ARG;
+  }
+  if (chunk_edge < 1 || chunk_edge > 32 || (chunk_edge & (chunk_edge - 1))) return ST_ERR_INVALID_ARG;
+  if (precision != ST_FP64 && precision != ST_MIXED_F32 && precision != ST_MIXED_BF16V) return ST_ERR_INVALID_ARG;
+  if (allocator && (!allocator->alloc || !allocator->free)) return ST_ERR_INVALID_ARG;
+  st_ctx* h = new (std::nothrow) st_ctx();
+  if (!h) return ST_ERR_OOM;
+  if (cudaGetDevice(&h->dev) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return ST_ERR_CUDA;
+  }
+  Geometry& G = h->geo;
+  for (int q = 0; q < 3; ++q) {
+    G.n[q] = n[q];
+    G.L[q] = L[q];
+    G.h[q] = L[q] / (double)n[q];
+    G.inv_h[q] = (double)n[q] / L[q];
+  }
+  G.B = chunk_edge;
+  G.ncell = (int64_t)nx * ny * nz;
+  h->prec = precision;
+  if (allocator) {
+    h->alloc = *allocator;
+    h->have_alloc = true;
+  }
+  h->stream = (cudaStream_t)stream;
+  int logB = 0;
+  while ((1 << logB) < chunk_edge) ++logB;
+  int nc[3];
+  for (int q = 0; q < 3; ++q) nc[q] = (n[q] + chunk_edge - 1) / chunk_edge;
+  uint64_t nkeys = (uint64_t)nc[0] * nc[1] * nc[2] << (3 * logB);
+  h->nkeys = (uint32_t)nkeys;
+  int bits = 0;
+  while ((1ull << bits) < nkeys) ++bits;
+  h->key_bits = bits;
+  st_status s = dev_alloc(h, h->acc, (size_t)G.ncell * 3 * 2 * sizeof(unsigned long long));
+  if (s == ST_OK) s = dev_alloc(h, h->red, 64 * 1024);
+  if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->acc.p, 0, h->acc.bytes, h->stream), "memset acc");
+  size_t fbytes = (size_t)G.ncell * (precision == ST_FP64 ? 4 * sizeof(double) : 4 * sizeof(float));
+  if (s == ST_OK) s = dev_alloc(h, h->fluid, fbytes);
+  if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->fluid.p, 0, h->fluid.bytes, h->stream), "memset fluid");
+  if (s != ST_OK) {
+    st_destroy(h);
+    return s;
+  }
+  h->fluid_set = true;  // at rest until st_set_fluid
+  h->umax = 0.0;
+  *out = h;
+  return ST_OK;
+}
+
+void st_destroy(st_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  cudaStreamSynchronize(h->stream);
+  Buf* bufs[] = {&h->fluid, &h->state, &h->state_alt, &h->ids, &h->ids_alt, &h->keys[0], &h->keys[1],
+                 &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start, &h->acc, &h->red};
+  for (Buf* b : bufs) dev_free(h, *b);
+  delete h;
+}
+
+const char* st_last_error(st_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+st_status st_set_stream(st_handle h, void* stream) {
+  ST_TRY(check_handle(h));
+  h->stream = (cudaStream_t)stream;
+  return ST_OK;
+}
+
+st_status st_synchronize(st_handle h) {
+  ST_TRY(check_handle(h));
+  ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3], double drag_scale,
+                        double multiplicity, int reorder_every) {
+  ST_TRY(check_handle(h));
+  if (!g) return set_error(h, ST_ERR_INVALID_ARG, "g is NULL");
+  if (!std::isfinite(rho_p) || !std::isfinite(mu) || !finite3(g) || !std::isfinite(drag_scale) ||
+      !std::isfinite(multiplicity))
+    return set_error(h, ST_ERR_NONFINITE, "non-finite parameter");
+  if (!(rho_p > 0) || !(mu > 0) || !(drag_scale > 0) || !(multiplicity > 0) || reorder_every < 0)
+    return set_error(h, ST_ERR_INVALID_ARG, "rho_p, mu, drag_scale, multiplicity must be > 0, reorder_every >= 0");
+  h->rho_p = rho_p;
+  h->mu = mu;
+  for (int q = 0; q < 3; ++q) h->g[q] = g[q];
+  h->alpha = drag_scale;
+  h->mult = multiplicity;
+  h->reorder_every = reorder_every;
+  return ST_OK;
+}
+
+st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!u) return set_error(h, ST_ERR_INVALID_ARG, "u is NULL");
+  if (dtype != ST_DTYPE_F32 && dtype != ST_DTYPE_F64) return set_error(h, ST_ERR_INVALID_ARG, "bad dtype");
+  size_t esz = dtype == ST_DTYPE_F64 ? 8 : 4;
+  size_t bytes = (size_t)h->geo.ncell * 3 * esz;
+  const void* src = u;
+  Buf tmp;
+  if (!on_device) {
+    ST_TRY(dev_alloc(h, tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp.p, u, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      dev_free(h, tmp);
+      return cuda_check(h, e, "copy fluid");
+    }
+    src = tmp.p;
+  }
+  double umax = 0.0;
+  int nonfinite = 0;
+  cudaError_t e = launch_maxabs(h, src, h->geo.ncell * 3, dtype, &umax, &nonfinite);
+  if (e == cudaSuccess && !nonfinite) e = launch_fluid_pack(h, src, dtype);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  ST_TRY(cuda_check(h, e, "set fluid"));
+  if (nonfinite) return set_error(h, ST_ERR_NONFINITE, "fluid field holds NaN or Inf");
+  h->umax = umax;
+  h->fluid_set = true;
+  return ST_OK;
+}
+
+static st_status grow(st_handle h, int64_t need) {
+  if (need <= h->cap) return ST_OK;
+  int64_t cap = h->cap ? h->cap : 1024;
+  while (cap < need) cap = cap + cap / 2 + 64;
+  cap = (cap + 63) & ~int64_t(63);
+  Buf ns, ni;
+  ST_TRY(dev_alloc(h, ns, state_bytes(h->prec, cap)));
+  st_status s = dev_alloc(h, ni, (size_t)cap * sizeof(uint32_t));
+  if (s != ST_OK) {
+    dev_free(h, ns);
+    return s;
+  }
+  if (h->np > 0) {
+    // copy each array of the old block to its place in the new one
+    cudaError_t e = cudaSuccess;
+    if (h->prec == ST_FP64) {
+      for (int a = 0; a < 7 && e == cudaSuccess; ++a)
+        e = cudaMemcpyAsync((double*)ns.p + a * cap, (double*)h->state.p + a * h->cap, h->np * sizeof(double),
+                            cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+      bool bf = h->prec == ST_MIXED_BF16V;
+      MixedState o = carve_mixed(h->state.p, h->cap, bf), n = carve_mixed(ns.p, cap, bf);
+      size_t vb = bf ? 2 : 4;
+      e = cudaMemcpyAsync(n.cell, o.cell, h->np * 4, cudaMemcpyDeviceToDevice, h->stream);
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync(n.xi[q], o.xi[q], h->np * 4, cudaMemcpyDeviceToDevice, h->stream);
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = cudaMemcpyAsync(n.v[q], o.v[q], h->np * vb, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(n.d, o.d, h->np * 4, cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ni.p, h->ids.p, h->np * sizeof(uint32_t), cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      dev_free(h, ns);
+      dev_free(h, ni);
+      return cuda_check(h, e, "grow particle arrays");
+    }
+  }
+  dev_free(h, h->state);
+  dev_free(h, h->ids);
+  dev_free(h, h->state_alt);
+  dev_free(h, h->ids_alt);
+  h->state = ns;
+  h->ids = ni;
+  h->cap = cap;
+  return ST_OK;
+}
+
+st_status st_reserve(st_handle h, int64_t capacity) {
+  ST_TRY(check_handle(h));
+  if (capacity < 0 || capacity > (int64_t(1) << 34)) return set_error(h, ST_ERR_INVALID_ARG, "capacity out of range");
+  return grow(h, capacity);
+}
+
+st_status st_add_particles(st_handle h, int64_t n, const double* xyz, const double* vel, const double* d,
+                           const uint32_t* ids, int on_device) {
+  ST_TRY(check_handle(h));
+  if (n < 0) return set_error(h, ST_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return ST_OK;
+  if (!xyz || !d) return set_error(h, ST_ERR_INVALID_ARG, "xyz and d are required");
+  if (h->np + n > (int64_t(1) << 34)) return set_error(h, ST_ERR_INVALID_ARG, "too many particles");
+  // stage host data on the device
+  Buf tx, tv, td, ti;
+  const double *dx = xyz, *dv = vel, *dd = d;
+  const uint32_t* di = ids;
+  auto cleanup = [&]() {
+    dev_free(h, tx);
+    dev_free(h, tv);
+    dev_free(h, td);
+    dev_free(h, ti);
+  };
+  if (!on_device) {
+    st_status s = dev_alloc(h, tx, (size_t)n * 3 * 8);
+    if (s == ST_OK && vel) s = dev_alloc(h, tv, (size_t)n * 3 * 8);
+    if (s == ST_OK) s = dev_alloc(h, td, (size_t)n * 8);
+    if (s == ST_OK && ids) s = dev_alloc(h, ti, (size_t)n * 4);
+    cudaError_t e = cudaSuccess;
+    if (s == ST_OK) e = cudaMemcpyAsync(tx.p, xyz, (size_t)n * 24, cudaMemcpyHostToDevice, h->stream);
+    if (s == ST_OK && e == cudaSuccess && vel)
+      e = cudaMemcpyAsync(tv.p, vel, (size_t)n * 24, cudaMemcpyHostToDevice, h->stream);
+    if (s == ST_OK && e == cudaSuccess) e = cudaMemcpyAsync(td.p, d, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
+    if (s == ST_OK && e == cudaSuccess && ids)
+      e = cudaMemcpyAsync(ti.p, ids, (size_t)n * 4, cudaMemcpyHostToDevice, h->stream);
+    if (s == ST_OK) s = cuda_check(h, e, "copy particles");
+    if (s != ST_OK) {
+      cleanup();
+      return s;
+    }
+    dx = (const double*)tx.p;
+    dv = vel ? (const double*)tv.p : nullptr;
+    dd = (const double*)td.p;
+    di = ids ? (const uint32_t*)ti.p : nullptr;
+  }
+  double vmax = 0, dmax = 0, dmin = 0;
+  int nonfinite = 0;
+  cudaError_t e = launch_particle_scan(h, dx, dd, n, &vmax, &dmax, &dmin, &nonfinite);
+  if (e == cudaSuccess && dv) {
+    double vm = 0;
+    int nf2 = 0;
+    e = launch_maxabs(h, dv, n * 3, ST_DTYPE_F64, &vm, &nf2);
+    vmax = vm;
+    nonfinite |= nf2;
+  }
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_check(h, e, "scan particles");
+  }
+  if (nonfinite) {
+    cleanup();
+    return set_error(h, ST_ERR_NONFINITE, "particle positions, velocities or diameters hold NaN or Inf");
+  }
+  if (!(dmin > 0.0)) {
+    cleanup();
+    return set_error(h, ST_ERR_INVALID_ARG, "diameters must be > 0");
+  }
+  st_status s = grow(h, h->np + n);
+  if (s != ST_OK) {
+    cleanup();
+    return s;
+  }
+  e = launch_import(h, h->np, n, dx, dv, dd, di);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cleanup();
+  ST_TRY(cuda_check(h, e, "import particles"));
+  h->np += n;
+  h->dmax = std::max(h->dmax, dmax);
+  h->vbound = std::max(h->vbound, vmax);
+  h->sorted = false;
+  return ST_OK;
+}
+
+st_status st_num_particles(st_handle h, int64_t* n) {
+  ST_TRY(check_handle(h));
+  if (!n) return set_error(h, ST_ERR_INVALID_ARG, "n is NULL");
+  *n = h->np;
+  return ST_OK;
+}
+
+st_status st_reorder(st_handle h) {
+  ST_TRY(check_handle(h));
+  ST_TRY(sort_particles(h));
+  h->sorted = true;
+  h->steps_since_sort = 0;
+  return ST_OK;
+}
+
+// Choose the fixed-point exponent so that a committed run at its bound maps to
+// at most 2^96 and the accumulated integer stays below 2^125.
+static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
+  const double pi = 3.14159265358979323846;
+  double gn = std::sqrt(h->g[0] * h->g[0] + h->g[1] * h->g[1] + h->g[2] * h->g[2]);
+  double tau_max = h->rho_p * h->dmax * h->dmax / (18.0 * h->mu);
+  h->vbound = std::max(h->vbound, h->umax + gn * tau_max / h->alpha);
+  double mmax = h->mult * h->rho_p * pi * h->dmax * h->dmax * h->dmax / 6.0;
+  double jb = mmax * (2.0 * h->vbound + gn * dt) * 1.01 + 1e-300;
+  double cb = jb * kMaxRun;
+  int E = kAccBits - (int)std::ceil(std::log2(cb));
+  if (!h->acc_empty && E < h->acc_E) {
+    cudaError_t e = launch_rescale_acc(h, h->acc_E - E);
+    ST_TRY(cuda_check(h, e, "rescale accumulator"));
+    h->acc_load = std::ldexp(h->acc_load, E - h->acc_E);
+  }
+  if (h->acc_empty || E < h->acc_E) h->acc_E = E;
+  E = h->acc_E;
+  // one step adds at most np * jb to any cell
+  double add = (double)h->np * jb * std::ldexp(1.0, E) + 1.0;
+  while (h->acc_load + add > 0x1p125) {
+    cudaError_t e = launch_rescale_acc(h, 1);
+    ST_TRY(cuda_check(h, e, "rescale accumulator"));
+    h->acc_E -= 1;
+    E = h->acc_E;
+    h->acc_load *= 0.5;
+    add = (double)h->np * jb * std::ldexp(1.0, E) + 1.0;
+  }
+  h->acc_load += add;
+  h->acc_empty = false;
+  *E_out = E;
+  return ST_OK;
+}
+
+st_status st_step(st_handle h, int nsteps, double dt) {
+  ST_TRY(check_handle(h));
+  if (nsteps < 0) return set_error(h, ST_ERR_INVALID_ARG, "nsteps < 0");
+  if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
+  if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");
+  if (!h->fluid_set) return set_error(h, ST_ERR_STATE, "no fluid field");
+  const double pi = 3.14159265358979323846;
+  for (int s = 0; s < nsteps; ++s) {
+    if (h->np == 0) break;
+    if (h->reorder_every > 0 && (!h->sorted || h->steps_since_sort >= h->reorder_every)) {
+      ST_TRY(st_reorder(h));
+    }
+    int E = 0;
+    ST_TRY(prepare_accumulator(h, dt, &E));
+    StepParams p;
+    p.dt = dt;
+    p.ca = 18.0 * h->mu * h->alpha / h->rho_p;
+    p.mcoef = h->mult * h->rho_p * pi / 6.0;
+    for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
+    p.E = E;
+    p.scale = std::ldexp(1.0, E);
+    cudaError_t e = h->prec == ST_FP64 ? launch_step_f64(h, p) : launch_step_mixed(h, p);
+    ST_TRY(cuda_check(h, e, "step kernel"));
+    h->steps_since_sort += 1;
+  }
+  return ST_OK;
+}
+
+st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!out) return set_error(h, ST_ERR_INVALID_ARG, "out is NULL");
+  size_t bytes = (size_t)h->geo.ncell * 3 * sizeof(double);
+  Buf tmp;
+  double* dst = out;
+  if (!on_device) {
+    ST_TRY(dev_alloc(h, tmp, bytes));
+    dst = (double*)tmp.p;
+  }
+  cudaError_t e = launch_acc_to_f64(h, dst, h->acc_E);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->acc.p, 0, h->acc.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  ST_TRY(cuda_check(h, e, "get sources"));
+  if (reset) {
+    h->acc_empty = true;
+    h->acc_load = 0.0;
+  }
+  return ST_OK;
+}
+
+st_status st_get_particles(st_handle h, int64_t first, int64_t count, double* xyz, double* vel, double* d,
+                           uint32_t* ids, int on_device) {
+  ST_TRY(check_handle(h));
+  if (first < 0 || count < 0 || first + count > h->np) return set_error(h, ST_ERR_INVALID_ARG, "range out of bounds");
+  if (count == 0) return ST_OK;
+  Buf tx, tv, td, ti;
+  double *ox = xyz, *ov = vel, *od = d;
+  uint32_t* oi = ids;
+  st_status s = ST_OK;
+  if (!on_device) {
+    if (xyz) s = dev_alloc(h, tx, (size_t)count * 24);
+    if (s == ST_OK && vel) s = dev_alloc(h, tv, (size_t)count * 24);
+    if (s == ST_OK && d) s = dev_alloc(h, td, (size_t)count * 8);
+    if (s == ST_OK && ids) s = dev_alloc(h, ti, (size_t)count * 4);
+    ox = (double*)tx.p;
+    ov = (double*)tv.p;
+    od = (double*)td.p;
+    oi = (uint32_t*)ti.p;
+  }
+  cudaError_t e = cudaSuccess;
+  if (s == ST_OK) e = launch_export(h, first, count, ox, ov, od, oi, nullptr);
+  if (s == ST_OK && !on_device) {
+    if (e == cudaSuccess && xyz) e = cudaMemcpyAsync(xyz, ox, (size_t)count * 24, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && vel) e = cudaMemcpyAsync(vel, ov, (size_t)count * 24, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && d) e = cudaMemcpyAsync(d, od, (size_t)count * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && ids) e = cudaMemcpyAsync(ids, oi, (size_t)count * 4, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (s == ST_OK && e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, tx);
+  dev_free(h, tv);
+  dev_free(h, td);
+  dev_free(h, ti);
+  ST_TRY(s);
+  return cuda_check(h, e, "get particles");
+}
+
+st_status st_get_cells(st_handle h, int64_t first, int64_t count, int32_t* cells, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!cells) return set_error(h, ST_ERR_INVALID_ARG, "cells is NULL");
+  if (first < 0 || count < 0 || first + count > h->np) return set_error(h, ST_ERR_INVALID_ARG, "range out of bounds");
+  if (count == 0) return ST_OK;
+  Buf tc;
+  int32_t* oc = cells;
+  if (!on_device) {
+    ST_TRY(dev_alloc(h, tc, (size_t)count * 4));
+    oc = (int32_t*)tc.p;
+  }
+  cudaError_t e = launch_export(h, first, count, nullptr, nullptr, nullptr, nullptr, oc);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(cells, oc, (size_t)count * 4, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, tc);
+  return cuda_check(h, e, "get cells");
+}
+
+st_status st_get_cell_counts(st_handle h, int64_t* counts, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!counts) return set_error(h, ST_ERR_INVALID_ARG, "counts is NULL");
+  if (!h->sorted && h->np > 0) return set_error(h, ST_ERR_STATE, "particles not sorted since the last change");
+  size_t bytes = (size_t)h->geo.ncell * 8;
+  Buf tmp;
+  int64_t* dst = counts;
+  if (!on_device) {
+    ST_TRY(dev_alloc(h, tmp, bytes));
+    dst = (int64_t*)tmp.p;
+  }
+  cudaError_t e = cudaSuccess;
+  if (h->np == 0) {
+    e = cudaMemsetAsync(dst, 0, bytes, h->stream);
+  } else {
+    e = launch_cell_counts(h, dst);
+  }
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(counts, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  return cuda_check(h, e, "cell counts");
+}
+
+st_status st_invariants(st_handle h, double out[8]) {
+  ST_TRY(check_handle(h));
+  if (!out) return set_error(h, ST_ERR_INVALID_ARG, "out is NULL");
+  double pm[4] = {0, 0, 0, 0}, s3[3] = {0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  if (h->np > 0) e = launch_particle_sums(h, pm);
+  if (e == cudaSuccess) e = launch_acc_sum(h, s3);
+  ST_TRY(cuda_check(h, e, "invariants"));
+  out[0] = (double)h->np;
+  for (int q = 0; q < 3; ++q) out[1 + q] = pm[q];
+  for (int q = 0; q < 3; ++q) out[4 + q] = s3[q];
+  out[7] = pm[3];
+  return ST_OK;
+}
+
+st_status st_kernel_launches(st_handle h, int64_t* count) {
+  ST_TRY(check_handle(h));
+  if (!count) return set_error(h, ST_ERR_INVALID_ARG, "count is NULL");
+  *count = h->launches;
+  return ST_OK;
+}
+
+st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t count, const double L[3], double vmax,
+                           const double* qtable, int nq, double* xyz, double* vel, double* d, uint32_t* ids) {
+  ST_TRY(check_handle(h));
+  if (first < 0 || count < 0 || !L || nq < 1 || (d && !qtable)) return set_error(h, ST_ERR_INVALID_ARG, "bad arguments");
+  if (!finite3(L) || !std::isfinite(vmax)) return set_error(h, ST_ERR_NONFINITE, "non-finite box or vmax");
+  if (nq < 2 || (nq & (nq - 1)) != 0 || nq > (1 << 20)) return set_error(h, ST_ERR_INVALID_ARG, "nq must be a power of two in [2, 2^20]");
+  if (count == 0) return ST_OK;
+  cudaError_t e = launch_gen(h, seed, first, count, L, vmax, qtable, nq, xyz, vel, d, ids);
+  return cuda_check(h, e, "generate particles");
+}
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// Internal definitions shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/scaletrack.h"
+
+namespace st {
+
+constexpr int kMaxDim = 1024;       // cells per axis (10-bit fields of the packed cell)
+constexpr int kAccBits = 96;        // a contribution at its bound maps to 2^96 in the accumulator
+constexpr int kMaxRun = 128;        // particles folded into one committed run (warp x 4)
+
+// Owned device allocation.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// FP64 cell value padded to 32 bytes (x, y, z, 0).
+struct alignas(16) D4 {
+  double x, y, z, w;
+};
+
+// Grid geometry shared by the kernels.
+struct Geometry {
+  int n[3];
+  double L[3];
+  double h[3];
+  double inv_h[3];
+  int B;
+  int64_t ncell;
+};
+
+}  // namespace st
+
+struct st_ctx {
+  int dev = 0;
+  st::Geometry geo{};
+  int prec = ST_FP64;
+  st_allocator alloc{};
+  bool have_alloc = false;
+  cudaStream_t stream = nullptr;
+
+  // physical parameters
+  double rho_p = 1000.0, mu = 1.8e-5, g[3] = {0.0, 0.0, -9.81}, alpha = 1.0, mult = 1.0;
+  int reorder_every = 10;
+
+  // fluid: FP64 handles D4[ncell] (x, y, z, 0); mixed handles float4[ncell]
+  st::Buf fluid;
+  bool fluid_set = false;
+  double umax = 0.0;
+
+  // particle state (structure of arrays), capacity a multiple of 64
+  int64_t np = 0, cap = 0;
+  // FP64: x, y, z, vx, vy, vz, d (double[cap] each)
+  // mixed: cell int32[cap], xi float[3][cap], v float[3][cap] (bf16[3][cap]), d float[cap]
+  st::Buf state, state_alt;  // one block each; arrays carved at fixed offsets
+  st::Buf ids, ids_alt;      // uint32[cap]
+  double dmax = 0.0, vbound = 0.0;
+  bool sorted = false;
+  int steps_since_sort = 0;
+
+  // sort
+  uint32_t nkeys = 0;
+  int key_bits = 0;
+  st::Buf keys[2], vals[2], hist, scan_aux, cell_start;  // cell_start uint32[nkeys + 1]
+  int64_t sort_cap = 0;
+
+  // source accumulator: int64 {lo, hi} pairs, [3][ncell], exact 128-bit fixed point
+  st::Buf acc;
+  int acc_E = 0;             // value = integer * 2^-acc_E
+  bool acc_empty = true;
+  double acc_load = 0.0;     // bound on |accumulated integer| (in units of 1), for overflow control
+
+  st::Buf red;               // small reduction scratch
+  int64_t launches = 0;      // kernels launched by this handle
+  std::string err;
+};
+
+namespace st {
+
+// ---- host helpers (st_api.cu) -------------------------------------------------------------
+st_status set_error(st_ctx* h, st_status s, const std::string& msg);
+st_status cuda_check(st_ctx* h, cudaError_t e, const char* what);
+st_status dev_alloc(st_ctx* h, Buf& b, size_t bytes);
+void dev_free(st_ctx* h, Buf& b);
+st_status ensure(st_ctx* h, Buf& b, size_t bytes);  // grow-only
+
+// carve the state block
+inline size_t state_bytes(int prec, int64_t cap) {
+  if (prec == ST_FP64) return (size_t)cap * 7 * sizeof(double);
+  size_t vb = (prec == ST_MIXED_BF16V) ? sizeof(__nv_bfloat16) : sizeof(float);
+  return (size_t)cap * (sizeof(int32_t) + 3 * sizeof(float) + 3 * vb + sizeof(float));
+}
+
+struct F64State {
+  double* x[3];
+  double* v[3];
+  double* d;
+};
+
+struct MixedState {
+  int32_t* cell;
+  float* xi[3];
+  void* v[3];  // float* or __nv_bfloat16*
+  float* d;
+};
+
+inline F64State carve_f64(void* base, int64_t cap) {
+  F64State s;
+  double* p = (double*)base;
+  for (int q = 0; q < 3; ++q) s.x[q] = p + q * cap;
+  for (int q = 0; q < 3; ++q) s.v[q] = p + (3 + q) * cap;
+  s.d = p + 6 * cap;
+  return s;
+}
+
+inline MixedState carve_mixed(void* base, int64_t cap, bool bf16) {
+  MixedState s;
+  char* p = (char*)base;
+  s.cell = (int32_t*)p;
+  p += cap * sizeof(int32_t);
+  for (int q = 0; q < 3; ++q) {
+    s.xi[q] = (float*)p;
+    p += cap * sizeof(float);
+  }
+  size_t vb = bf16 ? sizeof(__nv_bfloat16) : sizeof(float);
+  for (int q = 0; q < 3; ++q) {
+    s.v[q] = (void*)p;
+    p += cap * vb;
+  }
+  s.d = (float*)p;
+  return s;
+}
+
+// ---- packed cell: i | j << 10 | k << 20 ---------------------------------------------------
+__host__ __device__ inline int32_t pack_cell(int i, int j, int k) { return i | (j << 10) | (k << 20); }
+__host__ __device__ inline int cell_i(int32_t c) { return c & 1023; }
+__host__ __device__ inline int cell_j(int32_t c) { return (c >> 10) & 1023; }
+__host__ __device__ inline int cell_k(int32_t c) { return (c >> 20) & 1023; }
+
+// chunk-major key: chunk (x fastest) * B^3 + Morton(local), local x bit lowest
+__host__ __device__ inline uint32_t spread3(uint32_t v) {
+  // bit b of v -> bit 3b (v < 32)
+  v &= 0x1f;
+  v = (v | (v << 8)) & 0x0000f00fu;
+  v = (v | (v << 4)) & 0x000c30c3u;
+  v = (v | (v << 2)) & 0x00249249u;
+  return v;
+}
+
+__host__ __device__ inline uint32_t chunk_key(int i, int j, int k, int B, int logB, int ncx, int ncy) {
+  uint32_t ci = (uint32_t)i >> logB, cj = (uint32_t)j >> logB, ck = (uint32_t)k >> logB;
+  uint32_t li = (uint32_t)i & (B - 1), lj = (uint32_t)j & (B - 1), lk = (uint32_t)k & (B - 1);
+  uint32_t chunk = ci + (uint32_t)ncx * (cj + (uint32_t)ncy * ck);
+  uint32_t morton = spread3(li) | (spread3(lj) << 1) | (spread3(lk) << 2);
+  return (chunk << (3 * logB)) | morton;
+}
+
+// ---- exact fixed-point deposit -------------------------------------------------------------
+// The per-cell source is a 128-bit two's-complement integer per component
+// (int64 lo/hi pair) in units of 2^-E.  Integer addition is associative, so
+// the sum is the same whatever order the runs are added in.
+
+__device__ __forceinline__ void atomic_add_i128(unsigned long long* p, unsigned long long lo,
+                                                unsigned long long hi) {
+  unsigned long long carry = 0;
+  if (lo) {
+    unsigned long long old = atomicAdd(p, lo);
+    carry = (old + lo < old) ? 1ull : 0ull;
+  }
+  unsigned long long hh = hi + carry;
+  if (hh) atomicAdd(p + 1, hh);
+}
+
+// y = J * 2^E (exact), rounded to an integer, split into 64-bit words.
+// Requires |J * 2^E| < 2^117.
+__device__ __forceinline__ void f64_to_i128(double J, double scale, unsigned long long& lo,
+                                            unsigned long long& hi) {
+  double y = rint(J * scale);
+  double yh = floor(y * 0x1p-64);
+  double yl = y - yh * 0x1p64;
+  lo = (unsigned long long)__double2ull_rz(yl);
+  hi = (unsigned long long)(long long)yh;
+}
+
+// The same from an FP32 value by integer operations only (GB300's FP64 rate is
+// low): f = man * 2^(ex - 150); the scaled integer is man shifted by ex - 150 + E,
+// rounded half away from zero when shifted right.  Requires ex - 150 + E <= 103.
+__device__ __forceinline__ void f32_to_i128(float f, int E, unsigned long long& lo,
+                                            unsigned long long& hi) {
+  uint32_t b = __float_as_uint(f);
+  uint32_t ex = (b >> 23) & 0xffu;
+  unsigned long long man = b & 0x7fffffu;
+  if (ex == 0) {
+    ex = 1;
+  } else {
+    man |= 0x800000ull;
+  }
+  int s = (int)ex - 150 + E;
+  unsigned long long l, h;
+  if (s >= 64) {
+    l = 0;
+    h = man << (s - 64);
+  } else if (s > 0) {
+    l = man << s;
+    h = man >> (64 - s);
+  } else if (s == 0) {
+    l = man;
+    h = 0;
+  } else {
+    int r = -s;
+    l = r < 32 ? ((man + ((1ull << r) >> 1)) >> r) : 0ull;
+    h = 0;
+  }
+  if (b >> 31) {
+    unsigned long long nl = ~l + 1ull;
+    h = ~h + (l == 0 ? 1ull : 0ull);
+    l = nl;
+  }
+  lo = l;
+  hi = h;
+}
+
+// ---- launchers implemented in the other translation units --------------------------------
+struct StepParams {
+  double dt;
+  double ca;       // a * d^2 = 18 mu alpha / rho_p
+  double mcoef;    // m / d^3 = mult rho_p pi / 6
+  double g[3];
+  double scale;    // 2^E for the FP64 path
+  int E;           // for the FP32 path
+};
+
+cudaError_t launch_step_f64(st_ctx* h, const StepParams& p);
+cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p);
+cudaError_t launch_rescale_acc(st_ctx* h, int shift);
+cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
+cudaError_t launch_acc_sum(st_ctx* h, double out[3]);
+cudaError_t launch_particle_sums(st_ctx* h, double out[4]);  // P_x, P_y, P_z, M
+cudaError_t launch_maxabs(st_ctx* h, const void* p, int64_t n, int dtype, double* out_max, int* nonfinite);
+cudaError_t launch_particle_scan(st_ctx* h, const double* vel, const double* d, int64_t n, double* vmax,
+                                 double* dmax, double* dmin, int* nonfinite);
+cudaError_t launch_fluid_pack(st_ctx* h, const void* u, int dtype);
+cudaError_t launch_import(st_ctx* h, int64_t first, int64_t n, const double* xyz, const double* vel,
+                          const double* d, const uint32_t* ids);
+cudaError_t launch_export(st_ctx* h, int64_t first, int64_t n, double* xyz, double* vel, double* d,
+                          uint32_t* ids, int32_t* cells);
+cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, const double L[3],
+                       double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
+                       uint32_t* ids);
+st_status sort_particles(st_ctx* h);                                       // sort.cu
+cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);              // sort.cu
+
+}  // namespace st

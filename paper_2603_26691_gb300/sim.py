@@ -1,0 +1,244 @@
+"""Python binding of the Lagrangian step: a thin wrapper over the C ABI.
+
+PyTorch supplies device memory (the library allocates through torch's
+caching allocator) and the CUDA stream; every step of the path runs in the
+CUDA library.  Arrays go in and out as torch CUDA tensors or numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import StError, check
+
+
+def _is_cuda(x) -> bool:
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _as_f64(x, shape=None, device=None):
+    """Contiguous float64 tensor or numpy array, and whether it lives on the device."""
+    if isinstance(x, torch.Tensor):
+        t = x.to(torch.float64).contiguous()
+        if shape is not None:
+            t = t.reshape(shape)
+        return t, t.is_cuda
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a, False
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+class Sim:
+    """One simulation: a periodic grid, a frozen fluid field and particles.
+
+    Parameters follow st_create_grid: grid (nx, ny, nz), box lengths, chunk edge
+    B, precision "fp64" | "mixed_f32" | "mixed_bf16".
+    """
+
+    def __init__(self, grid, box=(1.0, 1.0, 1.0), chunk_edge: int = 8, precision: str = "fp64",
+                 device="cuda", stream: torch.cuda.Stream | None = None, torch_allocator: bool = True):
+        self.lib = _lib.load()
+        if isinstance(grid, int):
+            grid = (grid, grid, grid)
+        self.grid = tuple(int(g) for g in grid)
+        self.box = tuple(float(b) for b in box)
+        self.ncell = self.grid[0] * self.grid[1] * self.grid[2]
+        self.precision = precision
+        self.device = torch.device(device)
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc = None
+        if torch_allocator:
+            dev, strm = self.device.index, self.stream
+
+            def _a(size, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), dev, strm)
+                except Exception:
+                    return None
+
+            def _f(ptr, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_fns = (_lib.ALLOC_FN(_a), _lib.FREE_FN(_f))
+            self._alloc = _lib.Allocator(self._alloc_fns[0], self._alloc_fns[1], None)
+        h = C.c_void_p()
+        st = self.lib.st_create_grid(*self.grid, *self.box, int(chunk_edge), _lib.PRECISIONS[precision],
+                                     C.byref(self._alloc) if self._alloc is not None else None,
+                                     C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != _lib.ST_OK:
+            raise StError(st, "st_create_grid", "")
+        self.h = h
+
+    # -- lifetime ------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.st_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, st, where):
+        check(st, self.h, where)
+
+    # -- parameters and fields ---------------------------------------------------------------
+    def set_params(self, rho_p=1000.0, mu=1.8e-5, g=(0.0, 0.0, -9.81), drag_scale=1.0, multiplicity=1.0,
+                   reorder_every=10):
+        garr = (C.c_double * 3)(*[float(x) for x in g])
+        self._chk(self.lib.st_set_params(self.h, float(rho_p), float(mu), garr, float(drag_scale),
+                                         float(multiplicity), int(reorder_every)), "st_set_params")
+
+    def set_fluid(self, U):
+        """Cell-centred velocity [nz, ny, nx, 3] (float32 or float64; numpy or torch)."""
+        if isinstance(U, torch.Tensor):
+            t = U.contiguous()
+            if t.dtype not in (torch.float32, torch.float64):
+                t = t.to(torch.float64)
+            dt = _lib.ST_DTYPE_F32 if t.dtype == torch.float32 else _lib.ST_DTYPE_F64
+            if t.numel() != 3 * self.ncell:
+                raise ValueError("fluid field has the wrong size")
+            self._chk(self.lib.st_set_fluid(self.h, C.c_void_p(t.data_ptr()), dt, int(t.is_cuda)), "st_set_fluid")
+        else:
+            a = np.ascontiguousarray(U)
+            if a.dtype not in (np.float32, np.float64):
+                a = a.astype(np.float64)
+            if a.size != 3 * self.ncell:
+                raise ValueError("fluid field has the wrong size")
+            dt = _lib.ST_DTYPE_F32 if a.dtype == np.float32 else _lib.ST_DTYPE_F64
+            self._chk(self.lib.st_set_fluid(self.h, C.c_void_p(a.ctypes.data), dt, 0), "st_set_fluid")
+
+    # -- particles -----------------------------------------------------------------------
+    def reserve(self, n: int):
+        self._chk(self.lib.st_reserve(self.h, int(n)), "st_reserve")
+
+    def add_particles(self, pos, d, vel=None, ids=None):
+        """Append particles: pos [3, n], d [n], vel [3, n] or None, ids [n] uint32 or None."""
+        dd, dev = _as_f64(d, (-1,))
+        n = int(dd.shape[0])
+        pp, pdev = _as_f64(pos, (3, n))
+        vv = None
+        if vel is not None:
+            vv, vdev = _as_f64(vel, (3, n))
+            if vdev != dev:
+                raise ValueError("all particle arrays must be on the same side (host or device)")
+        if pdev != dev:
+            raise ValueError("all particle arrays must be on the same side (host or device)")
+        ii = None
+        if ids is not None:
+            if isinstance(ids, torch.Tensor):
+                ii = ids.to(torch.int32).contiguous() if ids.dtype != torch.int32 else ids.contiguous()
+                if ii.is_cuda != dev:
+                    raise ValueError("ids must be on the same side as the other arrays")
+            else:
+                ii = np.ascontiguousarray(ids, dtype=np.uint32)
+        if dev and pp.device != self.device:
+            raise ValueError("device arrays must be on the simulation's device")
+        self._chk(self.lib.st_add_particles(self.h, n, _ptr(pp), _ptr(vv), _ptr(dd), _ptr(ii), int(dev)),
+                  "st_add_particles")
+
+    @property
+    def n(self) -> int:
+        v = C.c_int64()
+        self._chk(self.lib.st_num_particles(self.h, C.byref(v)), "st_num_particles")
+        return int(v.value)
+
+    @property
+    def kernel_launches(self) -> int:
+        v = C.c_int64()
+        self._chk(self.lib.st_kernel_launches(self.h, C.byref(v)), "st_kernel_launches")
+        return int(v.value)
+
+    def step(self, nsteps: int, dt: float):
+        self._chk(self.lib.st_step(self.h, int(nsteps), float(dt)), "st_step")
+
+    def reorder(self):
+        self._chk(self.lib.st_reorder(self.h), "st_reorder")
+
+    def synchronize(self):
+        self._chk(self.lib.st_synchronize(self.h), "st_synchronize")
+
+    # -- outputs ---------------------------------------------------------------------------
+    def sources(self, reset: bool = False, out: torch.Tensor | None = None, host: bool = False):
+        """Accumulated per-cell impulse [3, ncell] float64 (device tensor, or numpy if host)."""
+        if host:
+            a = np.empty((3, self.ncell))
+            self._chk(self.lib.st_get_sources(self.h, C.c_void_p(a.ctypes.data), int(reset), 0), "st_get_sources")
+            return a
+        if out is None:
+            out = torch.empty((3, self.ncell), dtype=torch.float64, device=self.device)
+        self._chk(self.lib.st_get_sources(self.h, C.c_void_p(out.data_ptr()), int(reset), 1), "st_get_sources")
+        return out
+
+    def particles(self, first: int = 0, count: int | None = None, host: bool = True):
+        """(pos [3, count], vel [3, count], d [count], ids [count]) in storage order."""
+        if count is None:
+            count = self.n - first
+        if host:
+            pos, vel = np.empty((3, count)), np.empty((3, count))
+            d, ids = np.empty(count), np.empty(count, dtype=np.uint32)
+        else:
+            kw = dict(device=self.device)
+            pos = torch.empty((3, count), dtype=torch.float64, **kw)
+            vel = torch.empty((3, count), dtype=torch.float64, **kw)
+            d = torch.empty(count, dtype=torch.float64, **kw)
+            ids = torch.empty(count, dtype=torch.int32, **kw)
+        self._chk(self.lib.st_get_particles(self.h, int(first), int(count), _ptr(pos), _ptr(vel), _ptr(d), _ptr(ids),
+                                            int(not host)), "st_get_particles")
+        return pos, vel, d, ids
+
+    def cells(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        if count is None:
+            count = self.n - first
+        out = np.empty(count, dtype=np.int32)
+        self._chk(self.lib.st_get_cells(self.h, int(first), int(count), C.c_void_p(out.ctypes.data), 0), "st_get_cells")
+        return out
+
+    def cell_counts(self) -> np.ndarray:
+        out = np.empty(self.ncell, dtype=np.int64)
+        self._chk(self.lib.st_get_cell_counts(self.h, C.c_void_p(out.ctypes.data), 0), "st_get_cell_counts")
+        return out
+
+    def invariants(self) -> np.ndarray:
+        out = (C.c_double * 8)()
+        self._chk(self.lib.st_invariants(self.h, out), "st_invariants")
+        return np.array(out[:])
+
+    # -- seeded input generator (device twin of inputs.particles) --------------------------
+    def gen_particles(self, seed: int, first: int, count: int, qtable, vmax: float = 0.0, L=None):
+        """Device FP64 arrays (pos [3,count], vel [3,count], d [count], ids [count] int32)."""
+        L = self.box if L is None else L
+        q = torch.as_tensor(np.asarray(qtable, dtype=np.float64), device=self.device)
+        kw = dict(device=self.device)
+        pos = torch.empty((3, count), dtype=torch.float64, **kw)
+        vel = torch.empty((3, count), dtype=torch.float64, **kw)
+        d = torch.empty(count, dtype=torch.float64, **kw)
+        ids = torch.empty(count, dtype=torch.int32, **kw)
+        Larr = (C.c_double * 3)(*[float(x) for x in L])
+        self._chk(self.lib.st_gen_particles(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF, int(first), int(count), Larr,
+                                            float(vmax), C.c_void_p(q.data_ptr()), int(q.numel() - 1), _ptr(pos),
+                                            _ptr(vel), _ptr(d), _ptr(ids)), "st_gen_particles")
+        return pos, vel, d, ids

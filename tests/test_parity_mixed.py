@@ -1,0 +1,132 @@
+"""Mixed-precision CUDA path (int32 cell + FP32 offset, FP32 or BF16 velocity) against the FP64
+oracle, within stated error bounds.  The oracle reads the same FP32-rounded fluid field, so the
+bounds measure the step's own arithmetic and storage, not the field's storage."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_26691_gb300 import inputs
+from tests.helpers import face_distance, linear_cells, min_image
+
+pytestmark = pytest.mark.gpu
+
+# Stated bounds.  FP32 storage: position in cell widths h, velocity relative to |v| + 1 m/s,
+# sources relative to the oracle's L2 / max norm.  BF16 velocity storage rounds the velocity to
+# 8 significant bits (relative error <= 2^-9) every step, so its position error grows with the
+# distance travelled: bounded by 2^-7 x (steps x dt x max speed); velocity by 8e-3 (|v| + 1).
+BOUNDS = {
+    "mixed_f32": dict(pos_h=1e-5, vel=1e-5, src_l2=1e-5, src_max=1e-4),
+    "mixed_bf16": dict(pos_path=2.0 ** -7, vel=8e-3, src_l2=None, src_max=None),
+}
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2603_26691_gb300.sim import Sim
+
+    return Sim
+
+
+def _f32(U):
+    return U.astype(np.float32).astype(np.float64)
+
+
+def _errors(g, opos, ovel, osrc, N):
+    order = g["ids"].astype(np.int64)
+    h = 1.0 / N
+    pos_err = np.abs(min_image(g["pos"], opos[:, order])).max() / h
+    vel_err = (np.abs(g["vel"] - ovel[:, order]) / (np.abs(ovel[:, order]) + 1.0)).max()
+    src_l2 = np.linalg.norm(g["src"] - osrc) / np.linalg.norm(osrc)
+    src_max = np.abs(g["src"] - osrc).max() / np.abs(osrc).max()
+    return dict(pos_h=pos_err, vel=vel_err, src_l2=src_l2, src_max=src_max)
+
+
+def _path(ovel_max, steps, dt):
+    return steps * dt * max(ovel_max, 1.0)
+
+
+def _run(Sim, prec, N, U, pos, vel, d, steps, dt, reorder_every=10, chunk_edge=8):
+    sim = Sim(N, precision=prec, chunk_edge=chunk_edge)
+    sim.set_params(reorder_every=reorder_every)
+    sim.set_fluid(U.astype(np.float32))
+    sim.add_particles(pos, d, vel)
+    sim.step(steps, dt)
+    g = dict(src=sim.sources(host=True), inv=sim.invariants())
+    g["pos"], g["vel"], g["d"], g["ids"] = sim.particles()
+    g["cells"] = sim.cells()
+    sim.close()
+    return g
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+@pytest.mark.parametrize("N,n,steps", [(64, 200_003, 20), (32, 5_001, 40)])
+def test_mixed_within_bounds_fourier(Sim, prec, N, n, steps):
+    dt = 5e-4
+    U = _f32(inputs.random_fourier(N, seed=11))
+    pos, vel, d, _ = inputs.particles(2024, 0, n)
+    g = _run(Sim, prec, N, U, pos, vel, d, steps, dt)
+    opos, ovel, osrc, _ = oracle.run(oracle.make_grid(N), U, pos, vel, d, steps, dt)
+    err = _errors(g, opos, ovel, osrc, N)
+    err["pos_path"] = err["pos_h"] / N / _path(np.abs(ovel).max(), steps, dt)
+    print(prec, N, n, {k: float(v) for k, v in err.items()})
+    b = BOUNDS[prec]
+    for k, lim in b.items():
+        if lim is not None:
+            assert err[k] <= lim, (prec, k, err[k], lim)
+    # cells agree bit-exactly away from faces (band = the position bound, in cell widths)
+    order = g["ids"].astype(np.int64)
+    band = b["pos_h"] if "pos_h" in b else b["pos_path"] * _path(np.abs(ovel).max(), steps, dt) * N
+    far = face_distance(opos[:, order], (N, N, N)) > band
+    assert np.array_equal(g["cells"][far], linear_cells(opos[:, order], (N, N, N))[far])
+    assert g["inv"][0] == n
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+def test_mixed_momentum_balance(Sim, prec):
+    N, n, steps, dt = 32, 100_000, 30, 5e-4
+    U = _f32(inputs.taylor_green(N))
+    pos, vel, d, _ = inputs.particles(4, 0, n, vmax=0.3)
+    sim = Sim(N, precision=prec)
+    sim.set_fluid(U.astype(np.float32))
+    sim.add_particles(pos, d, vel)
+    inv0 = sim.invariants()
+    sim.step(steps, dt)
+    inv1 = sim.invariants()
+    sim.close()
+    gv = np.array([0.0, 0.0, -9.81])
+    bal = inv1[1:4] - inv0[1:4] - inv1[7] * gv * steps * dt + inv1[4:7]
+    scale = np.abs(inv1[4:7]).max() + np.abs(inv1[7] * gv * steps * dt).max()
+    assert np.abs(bal).max() <= 1e-5 * scale
+
+
+def test_mixed_uniform_flow_closed_form(Sim):
+    N, n, steps, dt = 32, 20_000, 50, 5e-4
+    u = np.array([0.3, -0.2, 0.1])
+    U = inputs.uniform_field(N, u)
+    pos, vel, d, _ = inputs.particles(99, 0, n, vmax=1.0)
+    g = _run(Sim, "mixed_f32", N, U, pos, vel, d, steps, dt)
+    order = g["ids"].astype(np.int64)
+    gv = np.array([0.0, 0.0, -9.81])
+    # the particle's stored diameter is FP32: the closed form uses the same value
+    dd = d[order].astype(np.float32).astype(np.float64)
+    a = 18 * 1.8e-5 / (1000.0 * dd ** 2)
+    T = steps * dt
+    vinf = u[:, None] + gv[:, None] / a
+    v0 = vel[:, order].astype(np.float32).astype(np.float64)
+    vT = vinf + (v0 - vinf) * np.exp(-a * T)
+    xT = pos[:, order] + vinf * T + (v0 - vinf) * (-np.expm1(-a * T)) / a
+    assert np.abs(min_image(g["pos"], xT)).max() * N <= 1e-5
+    assert (np.abs(g["vel"] - vT) / (np.abs(vT) + 1.0)).max() <= 1e-5
+
+
+def test_mixed_deterministic(Sim):
+    N, n, steps, dt = 32, 60_000, 25, 5e-4
+    U = _f32(inputs.random_fourier(N, seed=3))
+    pos, vel, d, _ = inputs.particles(8, 0, n)
+    a = _run(Sim, "mixed_f32", N, U, pos, vel, d, steps, dt)
+    b = _run(Sim, "mixed_f32", N, U, pos, vel, d, steps, dt)
+    assert np.array_equal(a["src"], b["src"])
+    assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["ids"], b["ids"])
