@@ -203,6 +203,39 @@ st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t co
                            double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
                            uint32_t* ids);
 
+/* Largest n that st_sort_keys_static accepts. */
+#define ST_SORT_KEYS_STATIC_MAX_N (1 << 20)
+
+/* Stable sort of n device keys for callers that cannot allocate device memory
+ * (code running inside another framework's memory pool or arena, a process
+ * whose allocations are made once at start-up and then frozen, or an
+ * allocator callback that must not call back into the allocator).  The paper
+ * has no counterpart; this is the ordering sort of st_reorder offered without
+ * a handle and without allocation.
+ *
+ * Keys are compared on their low key_bits bits (1..32); equal keys keep their
+ * input order.  Writes sorted_keys[n] (the input keys in sorted order) and
+ * perm[n] (perm[r] = input index of the r-th key).  keys, sorted_keys and perm
+ * are device pointers owned by the caller; keys is not modified; the outputs
+ * must not overlap keys or each other.  Work is queued on `stream` (a
+ * cudaStream_t, NULL = legacy default stream) and the call returns without
+ * waiting.
+ *
+ * All scratch memory is one static device array of 12.5 MiB that every GPU
+ * which loads the library holds until the process exits; the call makes no
+ * cudaMalloc, cudaFree or other allocating call.  n must not exceed
+ * ST_SORT_KEYS_STATIC_MAX_N (2^20): larger n returns ST_ERR_INVALID_ARG
+ * without doing any work.  The first call on a device looks up the array's
+ * device address for that device; make that first call before any CUDA stream
+ * capture.  Every call uses the same array, which keeps the previous call's
+ * contents (nothing in it needs to start at zero), so calls whose work
+ * overlaps on the GPU (other streams, other threads) race with each other:
+ * order them on one stream or synchronise between them.
+ * Errors: INVALID_ARG (n < 0, n > 2^20, key_bits outside 1..32, NULL pointer
+ * with n > 0), CUDA. */
+st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
+                              uint32_t* perm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

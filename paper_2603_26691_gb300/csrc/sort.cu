@@ -9,6 +9,7 @@
 // structure-of-arrays payload is then gathered once through the final
 // permutation.  Equal keys keep their storage order, so the permutation is
 // unique.
+#include <mutex>
 #include <vector>
 
 #include "st_common.cuh"
@@ -365,3 +366,107 @@ cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts) {
 }
 
 }  // namespace st
+
+// ---- the same stable sort for callers that cannot allocate device memory ----------------------
+//
+// Some callers cannot call cudaMalloc at all: code running inside another framework's memory
+// pool or arena, a process whose allocations are made once at start-up and then frozen, or an
+// allocator callback that must not re-enter the allocator.  st_sort_keys_static serves them:
+// its scratch memory is one file-scope device array, so the call itself allocates nothing.
+// The array is created when the library is loaded and lives on every GPU that loads the library
+// until the process exits.
+
+namespace st {
+namespace {
+
+constexpr int64_t kStaticMaxN = int64_t(1) << 20;  // keys per call (matches the header's limit)
+constexpr int64_t kStaticTiles = kStaticMaxN / kTile;
+constexpr int64_t kStaticHist = kStaticTiles * kRadix;
+constexpr int64_t kStaticAux = (kStaticHist + kScanBlock - 1) / kScanBlock + 1;
+// layout: index seeds [N] | ping-pong keys [N] | ping-pong values [N] | histograms [H] | offsets [H] | scan aux
+constexpr size_t kStaticWords = (size_t)(3 * kStaticMaxN + 2 * kStaticHist + kStaticAux);
+
+__global__ void iota_kernel(uint32_t* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)i;
+}
+
+// exclusive scan with caller-provided block-sum storage `aux` ((m + 2047) / 2048 + 1 words)
+cudaError_t exclusive_scan_aux(const uint32_t* in, uint32_t* out, int64_t m, uint32_t* aux, cudaStream_t s) {
+  int64_t nb = (m + kScanBlock - 1) / kScanBlock;
+  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, m, aux);
+  scan_blocksums_kernel<<<1, 1024, 0, s>>>(aux, nb);
+  scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, m, aux);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace st
+
+// The scratch array.  Host code must not use its name as an address: on the host the name
+// refers to a host-side stand-in.  The device address comes from cudaGetSymbolAddress, once per
+// device, below.
+static __device__ __align__(256) uint32_t g_sort_scratch[st::kStaticWords];
+
+namespace {
+std::mutex g_scratch_mu;
+constexpr int kMaxDevices = 64;
+uint32_t* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_sort_scratch on the current device (looked up on the first call per device).
+cudaError_t scratch_address(uint32_t** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = (uint32_t*)p;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
+                                         uint32_t* perm, void* stream) {
+  using namespace st;
+  if (n < 0 || n > kStaticMaxN) return ST_ERR_INVALID_ARG;
+  if (key_bits < 1 || key_bits > 32) return ST_ERR_INVALID_ARG;
+  if (n == 0) return ST_OK;
+  if (!keys || !sorted_keys || !perm) return ST_ERR_INVALID_ARG;
+  uint32_t* base = nullptr;
+  if (scratch_address(&base) != cudaSuccess) {
+    cudaGetLastError();
+    return ST_ERR_CUDA;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* seed = base;
+  uint32_t* sk = base + kStaticMaxN;
+  uint32_t* sv = base + 2 * kStaticMaxN;
+  uint32_t* hist = base + 3 * kStaticMaxN;
+  uint32_t* offs = hist + kStaticHist;
+  uint32_t* aux = offs + kStaticHist;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int passes = (key_bits + 7) / 8;
+  iota_kernel<<<grid_for(n), 256, 0, s>>>(seed, n);
+  // alternate between the caller's outputs and the scratch pair so that the last pass lands in the outputs
+  const uint32_t* kin = keys;
+  const uint32_t* vin = seed;
+  for (int p = 0; p < passes; ++p) {
+    bool to_out = ((passes - 1 - p) % 2) == 0;
+    uint32_t* kout = to_out ? sorted_keys : sk;
+    uint32_t* vout = to_out ? perm : sv;
+    upsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, 8 * p, ntiles, hist);
+    if (exclusive_scan_aux(hist, offs, ntiles * kRadix, aux, s) != cudaSuccess) return ST_ERR_CUDA;
+    downsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p, ntiles, offs);
+    if (cudaGetLastError() != cudaSuccess) return ST_ERR_CUDA;
+    kin = kout;
+    vin = vout;
+  }
+  return ST_OK;
+}
