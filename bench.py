@@ -210,7 +210,8 @@ def main():
     ap.add_argument("--workload", default="fourier256_mixed_1e9")
     ap.add_argument("--n", type=int, default=None, help="particles per GPU (default: the workload's)")
     ap.add_argument("--precision", default=None)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--grid", type=int, default=None, help="cells per axis (default: the workload's)")
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-n", type=int, default=None, help="particles for the FP64-step comparison (0 = skip)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
@@ -221,6 +222,10 @@ def main():
     from paper_2603_26691_gb300 import inputs
 
     workload = inputs.WORKLOADS[args.workload]
+    if args.grid:
+        import dataclasses
+
+        workload = dataclasses.replace(workload, grid=args.grid)
     if args.impl == "reference":
         return run_reference(args, workload)
 
@@ -303,8 +308,8 @@ def main():
         sim.step(1, dt)
         sim._chk(lib.st_get_sources(sim.h, C.c_void_p(src_h.data_ptr()), 1, 0), "st_get_sources")
     torch.cuda.synchronize()
-    e_el = time.perf_counter() - e_t0
-    e2e = {"value": n * ws * E / e_el, "unit": UNIT, "h2d_bytes_per_step": int(U32.nbytes),
+    e_el = max(time.perf_counter() - e_t0, 1e-9)
+    e2e = {"value": n * ws * E / e_el if E > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(U32.nbytes),
            "d2h_bytes_per_step": int(src_h.numel() * 8), "steps": E,
            "what": "per step: fluid field H2D from pinned host, step (sort when due), sources D2H to pinned host"}
     sim.close()

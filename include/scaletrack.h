@@ -186,6 +186,34 @@ st_status st_get_cell_counts(st_handle h, int64_t* counts, int on_device);
  * P(T) - P(0) - M g T + S = 0.  Synchronises. */
 st_status st_invariants(st_handle h, double out[8]);
 
+/* Remove all particles (the fluid, parameters and accumulated sources stay). */
+st_status st_clear_particles(st_handle h);
+
+/* Forward run for differentiation: advance all particles nsteps steps of
+ * length dt (no reordering during the run), adding the impulses to the source
+ * accumulator as st_step does, and keep checkpoints of positions and
+ * velocities every checkpoint_every steps (6 x n x 8 bytes each).  With
+ * Jtot the time-summed per-cell source, st_adjoint_backward then returns the
+ * gradient of any loss L(Jtot).  The method has no adjoint in the paper; this
+ * differentiates the step of Sec. 2.1 (Eqs. 9-11) as implemented here, with the
+ * deposit cell held fixed (its derivative is zero almost everywhere).  FP64
+ * handles only.  Changing particles, parameters or the fluid, or reordering,
+ * invalidates the recorded run.
+ * Errors: STATE (not FP64, no particles), INVALID_ARG, NONFINITE, OOM, CUDA. */
+st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every);
+
+/* Reverse sweep of the last st_adjoint_forward run, segment by segment from
+ * the last checkpoint, recomputing each segment's states forward first.
+ * lam[3][ncell] = dL/dJtot (host or device, lam_on_device).  Outputs (any may
+ * be NULL; host or device per on_device): grad_d[n] = dL/dd per particle in
+ * the current storage order, *grad_alpha = dL/d(drag_scale) (host pointer
+ * always), grad_U[ncell][3] = dL/dU in the layout of st_set_fluid.  All sums
+ * are formed in a fixed order or in exact fixed point, so results are
+ * bit-reproducible.  Synchronises.
+ * Errors: STATE (no recorded run), INVALID_ARG, OOM, CUDA. */
+st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device, double* grad_d,
+                              double* grad_alpha, double* grad_U, int on_device);
+
 /* Number of CUDA kernels this handle has launched since it was created (a
  * diagnostic for profiling: every kernel of the library counts once per
  * launch). */

@@ -60,6 +60,9 @@ SIGNATURES = {
     "st_get_cell_counts": (_i, [_vp, _vp, _i]),
     "st_invariants": (_i, [_vp, _P(_d)]),
     "st_kernel_launches": (_i, [_vp, _P(_i64)]),
+    "st_clear_particles": (_i, [_vp]),
+    "st_adjoint_forward": (_i, [_vp, _i, _d, _i]),
+    "st_adjoint_backward": (_i, [_vp, _vp, _i, _vp, _P(_d), _vp, _i]),
     "st_sort_keys_static": (_i, [_vp, _i64, _i, _vp, _vp, _vp]),
     "st_gen_particles": (_i, [_vp, _u64, _i64, _i64, _P(_d), _d, _vp, _i, _vp, _vp, _vp, _vp]),
 }

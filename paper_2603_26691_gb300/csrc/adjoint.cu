@@ -1,0 +1,242 @@
+// Hand-written adjoint of the FP64 Lagrangian step, run backward through
+// checkpointed segments with recomputation.
+//
+// For a loss L(Jtot) of the time-summed per-cell source, with
+// lam = dL/dJtot given per cell, one reverse step of one particle runs the
+// chain rule backward through the forward step
+//   c0 = cell(x);  u_p = sum_corners W(f) U;  a = 18 mu alpha / (rho_p d^2)
+//   E = e^{-a dt};  E1 = 1 - E;  Q = E1 / a;  w = u_p + g / a
+//   v' = w E1 + v E;  x' = x + w (dt - Q) + v Q
+//   J = -m (v' - v - g dt),  m = mult rho_p pi d^3 / 6,  Jtot[c0] += J
+// with the deposit cell held fixed (its derivative is zero almost everywhere)
+// and the periodic wrap a translation.  Per particle it carries the adjoints
+// of x and v between steps and accumulates dL/dd; dL/dalpha is reduced
+// per block in a fixed order; dL/dU is scattered through the transposed
+// trilinear weights into an exact carry-save fixed-point accumulator, so
+// every output is independent of thread scheduling.
+#include "st_common.cuh"
+
+namespace st {
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+// Carry-save accumulator: value = sum_i w[i] * 2^(32 i + kWideBase); each
+// contribution adds 32-bit digits, so each int64 word absorbs 2^31 of them.
+__device__ __forceinline__ void wide_add(long long* w, double x) {
+  if (x == 0.0) return;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  unsigned long long man = b & 0xfffffffffffffull;
+  if (ex != 0) man |= 1ull << 52;  // subnormals: man * 2^(1 - 1075)
+  int s = (ex == 0 ? 1 : ex) - 1075 - kWideBase;  // bit position of man's lowest bit
+  if (s < 0) {
+    if (s <= -64) return;
+    man = (man + ((1ull << (-s)) >> 1)) >> (-s);
+    s = 0;
+  }
+  const int q = s >> 5, r = s & 31;
+  const unsigned long long lo = man << r;                       // bits r .. 63
+  const unsigned long long hi = r ? (man >> (64 - r)) : 0ull;   // bits 64 .. 84
+  long long d0 = (long long)(lo & 0xffffffffull);
+  long long d1 = (long long)(lo >> 32);
+  long long d2 = (long long)hi;
+  if (b >> 63) {
+    d0 = -d0;
+    d1 = -d1;
+    d2 = -d2;
+  }
+  if (q < kWideWords) atomicAdd((unsigned long long*)&w[q], (unsigned long long)d0);
+  if (q + 1 < kWideWords) atomicAdd((unsigned long long*)&w[q + 1], (unsigned long long)d1);
+  if (q + 2 < kWideWords) atomicAdd((unsigned long long*)&w[q + 2], (unsigned long long)d2);
+}
+
+struct AdjArgs {
+  const double* __restrict__ x[3];   // state at the start of the step (tape)
+  const double* __restrict__ v[3];
+  const double* __restrict__ d;
+  double* __restrict__ xb[3];        // adjoint of the state after the step (in), before it (out)
+  double* __restrict__ vb[3];
+  double* __restrict__ db;           // accumulated dL/dd
+  double* __restrict__ ab_part;      // [gridDim.x] dL/dalpha partial sums, accumulated over steps
+  const D4* __restrict__ U;
+  const double* __restrict__ lam;    // [3][ncell]
+  long long* __restrict__ Uw;        // [ncell][3][kWideWords] carry-save dL/dU
+  int64_t n, ncell;
+  int nx, ny, nz;
+  double inv_h[3];
+  double dt, ca, mcoef, alpha, g[3];
+};
+
+__device__ __forceinline__ D4 ld_cell(const D4* __restrict__ U, int64_t c) {
+  const double2* p = reinterpret_cast<const double2*>(U + c);
+  double2 a = __ldg(p), b = __ldg(p + 1);
+  return D4{a.x, a.y, b.x, b.y};
+}
+
+__global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs a) {
+  const int n3[3] = {a.nx, a.ny, a.nz};
+  double alphab_sum = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    double x[3], v[3], xb[3], vb[3];
+    for (int q = 0; q < 3; ++q) {
+      x[q] = a.x[q][p];
+      v[q] = a.v[q][p];
+      xb[q] = a.xb[q][p];
+      vb[q] = a.vb[q][p];
+    }
+    const double d = a.d[p];
+    // recompute the forward intermediates
+    int c0[3], i0[3], i1[3];
+    double f[3];
+    for (int q = 0; q < 3; ++q) {
+      const double sx = x[q] * a.inv_h[q];
+      c0[q] = min(max((int)floor(sx), 0), n3[q] - 1);
+      const double s2 = sx - 0.5;
+      const double fl = floor(s2);
+      const int ii = (int)fl;
+      f[q] = s2 - fl;
+      i0[q] = ii < 0 ? ii + n3[q] : ii;
+      i1[q] = ii + 1 >= n3[q] ? ii + 1 - n3[q] : ii + 1;
+    }
+    const int64_t key = c0[0] + (int64_t)a.nx * (c0[1] + (int64_t)a.ny * c0[2]);
+    int64_t corner[8];
+    D4 Uc[8];
+    for (int k = 0; k < 8; ++k) {
+      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
+      corner[k] = (di ? i1[0] : i0[0]) + (int64_t)a.nx * ((dj ? i1[1] : i0[1]) + (int64_t)a.ny * (dk ? i1[2] : i0[2]));
+      Uc[k] = ld_cell(a.U, corner[k]);
+    }
+    double up[3] = {0.0, 0.0, 0.0};
+    double W[8];
+    for (int k = 0; k < 8; ++k) {
+      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
+      W[k] = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+      up[0] += W[k] * Uc[k].x;
+      up[1] += W[k] * Uc[k].y;
+      up[2] += W[k] * Uc[k].z;
+    }
+    const double dd = d * d;
+    const double ra = a.ca / dd;
+    const double E = exp(-ra * a.dt);
+    const double E1 = -expm1(-ra * a.dt);
+    const double Q = E1 / ra;
+    const double m = a.mcoef * dd * d;
+    double wt[3], vn[3];
+    for (int q = 0; q < 3; ++q) {
+      wt[q] = up[q] + a.g[q] / ra;
+      vn[q] = wt[q] + (v[q] - wt[q]) * E;
+    }
+    // reverse sweep
+    const double Jb[3] = {a.lam[key], a.lam[a.ncell + key], a.lam[2 * a.ncell + key]};
+    double mb = 0.0, Eb = 0.0, E1b = 0.0, Qb = 0.0, ab = 0.0;
+    double ub[3], vsb[3];
+    for (int q = 0; q < 3; ++q) {
+      const double vnb = vb[q] - m * Jb[q];
+      vsb[q] = m * Jb[q] + vnb * E + xb[q] * Q;
+      mb -= (vn[q] - v[q] - a.g[q] * a.dt) * Jb[q];
+      const double wtb = vnb * E1 + xb[q] * (a.dt - Q);
+      E1b += vnb * wt[q];
+      Eb += vnb * v[q];
+      Qb += xb[q] * (v[q] - wt[q]);
+      ub[q] = wtb;
+      ab -= wtb * a.g[q] / (ra * ra);
+    }
+    E1b += Qb / ra;
+    ab -= Qb * E1 / (ra * ra);
+    ab += a.dt * E * (E1b - Eb);
+    alphab_sum += ab * ra / a.alpha;
+    double dbv = a.db[p] + ab * (-2.0 * ra / d) + mb * 3.0 * m / d;
+    a.db[p] = dbv;
+    // transposed trilinear weights: dL/dU and dL/df
+    double fb[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < 8; ++k) {
+      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
+      const double wx = di ? f[0] : 1.0 - f[0];
+      const double wy = dj ? f[1] : 1.0 - f[1];
+      const double wz = dk ? f[2] : 1.0 - f[2];
+      const double dot = Uc[k].x * ub[0] + Uc[k].y * ub[1] + Uc[k].z * ub[2];
+      fb[0] += (di ? 1.0 : -1.0) * wy * wz * dot;
+      fb[1] += wx * (dj ? 1.0 : -1.0) * wz * dot;
+      fb[2] += wx * wy * (dk ? 1.0 : -1.0) * dot;
+      long long* w = a.Uw + corner[k] * 3 * kWideWords;
+      wide_add(w, W[k] * ub[0]);
+      wide_add(w + kWideWords, W[k] * ub[1]);
+      wide_add(w + 2 * kWideWords, W[k] * ub[2]);
+    }
+    for (int q = 0; q < 3; ++q) {
+      a.xb[q][p] = xb[q] + fb[q] * a.inv_h[q];
+      a.vb[q][p] = vsb[q];
+    }
+  }
+  // fixed-order block reduction of dL/dalpha
+  __shared__ double sh[kAdjThreads / 32];
+  double s = alphab_sum;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) t += sh[w];
+    a.ab_part[blockIdx.x] += t;
+  }
+}
+
+// value of each carry-save accumulator in FP64: out[c][q]
+__global__ void wide_to_f64_kernel(const long long* __restrict__ Uw, double* __restrict__ out, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    // compensated sum from the smallest word up
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < kWideWords; ++k) {
+      const double t = ldexp((double)Uw[i * kWideWords + k], 32 * k + kWideBase);
+      const double y = t - c;
+      const double z = s + y;
+      c = (z - s) - y;
+      s = z;
+    }
+    out[i] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s) {
+  AdjArgs a;
+  for (int q = 0; q < 3; ++q) {
+    a.x[q] = s.x[q];
+    a.v[q] = s.v[q];
+    a.xb[q] = s.xb[q];
+    a.vb[q] = s.vb[q];
+    a.inv_h[q] = h->geo.inv_h[q];
+    a.g[q] = h->g[q];
+  }
+  a.d = s.d;
+  a.db = s.db;
+  a.ab_part = s.ab_part;
+  a.U = (const D4*)h->fluid.p;
+  a.lam = s.lam;
+  a.Uw = s.Uw;
+  a.n = h->np;
+  a.ncell = h->geo.ncell;
+  a.nx = h->geo.n[0];
+  a.ny = h->geo.n[1];
+  a.nz = h->geo.n[2];
+  a.dt = s.dt;
+  a.ca = 18.0 * h->mu * h->alpha / h->rho_p;
+  a.mcoef = h->mult * h->rho_p * 3.14159265358979323846 / 6.0;
+  a.alpha = h->alpha;
+  adjoint_step_kernel<<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wide_to_f64(st_ctx* h, const long long* Uw, double* out, int64_t m) {
+  int64_t b = (m + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  wide_to_f64_kernel<<<(int)b, 256, 0, h->stream>>>(Uw, out, m);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace st

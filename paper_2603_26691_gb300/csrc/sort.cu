@@ -231,19 +231,23 @@ __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32
   }
 }
 
-// start[k] = first sorted position with key >= k, for k in [0, nkeys] (binary search)
-__global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t nkeys,
-                                  uint32_t* __restrict__ start) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= (int64_t)nkeys;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if ((int64_t)keys[mid] < k) lo = mid + 1;
-      else hi = mid;
-    }
-    start[k] = (uint32_t)lo;
+// start[k] = first sorted position with key >= k, for k in [0, nkeys]: position i writes the keys
+// in (key[i-1], key[i]] (one pass over the sorted keys; the keys after the last one are filled by
+// cell_start_tail_kernel)
+__global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ start) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k1 = keys[i];
+    const int64_t k0 = i > 0 ? (int64_t)keys[i - 1] : -1;
+    for (int64_t k = k0 + 1; k <= k1; ++k) start[k] = (uint32_t)i;
   }
+}
+
+__global__ void cell_start_tail_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t nkeys,
+                                       uint32_t* __restrict__ start) {
+  const int64_t first = (int64_t)keys[n - 1] + 1;
+  for (int64_t k = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= (int64_t)nkeys;
+       k += (int64_t)gridDim.x * blockDim.x)
+    start[k] = (uint32_t)n;
 }
 
 __global__ void cell_counts_kernel(const uint32_t* __restrict__ start, KeyGeo g, int64_t* __restrict__ counts) {
@@ -349,8 +353,10 @@ st_status sort_particles(st_ctx* h) {
         carve_mixed(h->state.p, h->cap, true), carve_mixed(h->state_alt.p, h->cap, true), (const uint32_t*)h->ids.p,
         (uint32_t*)h->ids_alt.p, v0, n);
   }
-  cell_start_kernel<<<grid_for((int64_t)h->nkeys + 1), 256, 0, h->stream>>>(k0, n, h->nkeys, (uint32_t*)h->cell_start.p);
-  h->launches += 2;  // gather + cell starts
+  cell_start_kernel<<<grid_for(n), 256, 0, h->stream>>>(k0, n, (uint32_t*)h->cell_start.p);
+  cell_start_tail_kernel<<<grid_for((int64_t)h->nkeys + 1), 256, 0, h->stream>>>(k0, n, h->nkeys,
+                                                                                   (uint32_t*)h->cell_start.p);
+  h->launches += 3;  // gather + cell starts (two kernels)
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(h, e, "sort gather");
   std::swap(h->state, h->state_alt);

@@ -73,6 +73,19 @@ using namespace st;
 
 static bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
+// Report (and clear) device-side error flags raised by bounded waits that gave up.
+static st_status check_flags(st_handle h) {
+  int f = 0;
+  cudaError_t e = cudaMemcpyAsync(&f, h->flags.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_check(h, e, "read error flags");
+  if (f != 0) {
+    cudaMemsetAsync(h->flags.p, 0, sizeof(int), h->stream);
+    return set_error(h, ST_ERR_TIMEOUT, "a bounded device-side wait gave up (flags " + std::to_string(f) + ")");
+  }
+  return ST_OK;
+}
+
 static st_status check_handle(st_handle h) {
   if (!h) return ST_ERR_INVALID_ARG;
   h->err.clear();
@@ -130,9 +143,17 @@ st_status st_create_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz
   st_status s = dev_alloc(h, h->acc, (size_t)G.ncell * 3 * 2 * sizeof(unsigned long long));
   if (s == ST_OK) s = dev_alloc(h, h->red, 64 * 1024);
   if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->acc.p, 0, h->acc.bytes, h->stream), "memset acc");
-  size_t fbytes = (size_t)G.ncell * (precision == ST_FP64 ? 4 * sizeof(double) : 4 * sizeof(float));
-  if (s == ST_OK) s = dev_alloc(h, h->fluid, fbytes);
-  if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->fluid.p, 0, h->fluid.bytes, h->stream), "memset fluid");
+  if (precision == ST_FP64) {
+    if (s == ST_OK) s = dev_alloc(h, h->fluid, (size_t)G.ncell * 4 * sizeof(double));
+    if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->fluid.p, 0, h->fluid.bytes, h->stream), "memset fluid");
+  } else {
+    size_t padded = (size_t)(nx + 2 * kFluidPad) * (ny + 2 * kFluidPad) * (nz + 2 * kFluidPad);
+    if (s == ST_OK) s = dev_alloc(h, h->fluid_pad, padded * 4 * sizeof(float));
+    if (s == ST_OK)
+      s = cuda_check(h, cudaMemsetAsync(h->fluid_pad.p, 0, h->fluid_pad.bytes, h->stream), "memset fluid");
+  }
+  if (s == ST_OK) s = dev_alloc(h, h->flags, 256);
+  if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->flags.p, 0, 256, h->stream), "memset flags");
   if (s != ST_OK) {
     st_destroy(h);
     return s;
@@ -147,7 +168,7 @@ void st_destroy(st_handle h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  Buf* bufs[] = {&h->fluid, &h->state, &h->state_alt, &h->ids, &h->ids_alt, &h->keys[0], &h->keys[1],
+  Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt, &h->keys[0], &h->keys[1],
                  &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start, &h->acc, &h->red};
   for (Buf* b : bufs) dev_free(h, *b);
   delete h;
@@ -164,7 +185,7 @@ st_status st_set_stream(st_handle h, void* stream) {
 st_status st_synchronize(st_handle h) {
   ST_TRY(check_handle(h));
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
-  return ST_OK;
+  return check_flags(h);
 }
 
 st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3], double drag_scale,
@@ -182,6 +203,7 @@ st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3],
   h->alpha = drag_scale;
   h->mult = multiplicity;
   h->reorder_every = reorder_every;
+  h->adj_ready = false;
   return ST_OK;
 }
 
@@ -212,6 +234,7 @@ st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device) {
   if (nonfinite) return set_error(h, ST_ERR_NONFINITE, "fluid field holds NaN or Inf");
   h->umax = umax;
   h->fluid_set = true;
+  h->adj_ready = false;
   return ST_OK;
 }
 
@@ -344,6 +367,7 @@ st_status st_add_particles(st_handle h, int64_t n, const double* xyz, const doub
   h->dmax = std::max(h->dmax, dmax);
   h->vbound = std::max(h->vbound, vmax);
   h->sorted = false;
+  h->adj_ready = false;
   return ST_OK;
 }
 
@@ -357,6 +381,7 @@ st_status st_num_particles(st_handle h, int64_t* n) {
 st_status st_reorder(st_handle h) {
   ST_TRY(check_handle(h));
   ST_TRY(sort_particles(h));
+  h->adj_ready = false;
   h->sorted = true;
   h->steps_since_sort = 0;
   return ST_OK;
@@ -417,7 +442,13 @@ st_status st_step(st_handle h, int nsteps, double dt) {
     for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
     p.E = E;
     p.scale = std::ldexp(1.0, E);
-    cudaError_t e = h->prec == ST_FP64 ? launch_step_f64(h, p) : launch_step_mixed(h, p);
+    cudaError_t e;
+    if (h->prec == ST_FP64)
+      e = launch_step_f64(h, p);
+    else if (h->sorted && tma_step_supported(h))
+      e = launch_step_mixed_tma(h, p);
+    else
+      e = launch_step_mixed(h, p);
     ST_TRY(cuda_check(h, e, "step kernel"));
     h->steps_since_sort += 1;
   }
@@ -440,6 +471,7 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   dev_free(h, tmp);
   ST_TRY(cuda_check(h, e, "get sources"));
+  ST_TRY(check_flags(h));
   if (reset) {
     h->acc_empty = true;
     h->acc_load = 0.0;
@@ -536,6 +568,167 @@ st_status st_invariants(st_handle h, double out[8]) {
   for (int q = 0; q < 3; ++q) out[1 + q] = pm[q];
   for (int q = 0; q < 3; ++q) out[4 + q] = s3[q];
   out[7] = pm[3];
+  return ST_OK;
+}
+
+
+st_status st_clear_particles(st_handle h) {
+  ST_TRY(check_handle(h));
+  h->np = 0;
+  h->sorted = false;
+  h->steps_since_sort = 0;
+  h->dmax = 0.0;
+  h->vbound = 0.0;
+  h->adj_ready = false;
+  return ST_OK;
+}
+
+st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every) {
+  ST_TRY(check_handle(h));
+  if (h->prec != ST_FP64) return set_error(h, ST_ERR_STATE, "the adjoint needs an FP64 handle");
+  if (nsteps < 1 || checkpoint_every < 1) return set_error(h, ST_ERR_INVALID_ARG, "nsteps and checkpoint_every must be >= 1");
+  if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
+  if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");
+  if (h->np == 0) return set_error(h, ST_ERR_STATE, "no particles");
+  const int64_t n = h->np;
+  const int K = (nsteps + checkpoint_every - 1) / checkpoint_every;
+  ST_TRY(ensure(h, h->ckpt, (size_t)K * 6 * n * sizeof(double)));
+  const double pi = 3.14159265358979323846;
+  F64State s = carve_f64(h->state.p, h->cap);
+  double* ck = (double*)h->ckpt.p;
+  for (int step = 0; step < nsteps; ++step) {
+    if (step % checkpoint_every == 0) {
+      double* slot = ck + (size_t)(step / checkpoint_every) * 6 * n;
+      cudaError_t e = cudaSuccess;
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+        e = cudaMemcpyAsync(slot + q * n, s.x[q], n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(slot + (3 + q) * n, s.v[q], n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+      }
+      ST_TRY(cuda_check(h, e, "checkpoint"));
+    }
+    int E = 0;
+    ST_TRY(prepare_accumulator(h, dt, &E));
+    StepParams p;
+    p.dt = dt;
+    p.ca = 18.0 * h->mu * h->alpha / h->rho_p;
+    p.mcoef = h->mult * h->rho_p * pi / 6.0;
+    for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
+    p.E = E;
+    p.scale = std::ldexp(1.0, E);
+    ST_TRY(cuda_check(h, launch_step_f64(h, p), "adjoint forward step"));
+  }
+  h->adj_nsteps = nsteps;
+  h->adj_every = checkpoint_every;
+  h->adj_dt = dt;
+  h->adj_ready = true;
+  return ST_OK;
+}
+
+st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device, double* grad_d, double* grad_alpha,
+                              double* grad_U, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!h->adj_ready) return set_error(h, ST_ERR_STATE, "no st_adjoint_forward run to differentiate");
+  if (!lam) return set_error(h, ST_ERR_INVALID_ARG, "lam is NULL");
+  const int64_t n = h->np, nc = h->geo.ncell;
+  const int C = h->adj_every, nsteps = h->adj_nsteps;
+  const int K = (nsteps + C - 1) / C;
+  const double pi = 3.14159265358979323846;
+  // scratch: lam, working state (x, v), tape of C states, adjoints, carry-save dL/dU
+  Buf blam, work, tape, adj, abp, Uw, tmp;
+  auto cleanup = [&]() {
+    for (Buf* b : {&blam, &work, &tape, &adj, &abp, &Uw, &tmp}) dev_free(h, *b);
+  };
+  st_status s = dev_alloc(h, work, (size_t)6 * n * sizeof(double));
+  if (s == ST_OK) s = dev_alloc(h, tape, (size_t)C * 6 * n * sizeof(double));
+  if (s == ST_OK) s = dev_alloc(h, adj, (size_t)7 * n * sizeof(double));
+  if (s == ST_OK) s = dev_alloc(h, abp, (size_t)kAdjBlocks * sizeof(double));
+  if (s == ST_OK) s = dev_alloc(h, Uw, (size_t)nc * 3 * kWideWords * sizeof(long long));
+  if (s == ST_OK && !lam_on_device) s = dev_alloc(h, blam, (size_t)3 * nc * sizeof(double));
+  if (s == ST_OK && (!on_device)) s = dev_alloc(h, tmp, (size_t)(std::max<int64_t>(n, 3 * nc)) * sizeof(double));
+  if (s != ST_OK) {
+    cleanup();
+    return s;
+  }
+  cudaError_t e = cudaSuccess;
+  const double* dlam = lam;
+  if (!lam_on_device) {
+    e = cudaMemcpyAsync(blam.p, lam, (size_t)3 * nc * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    dlam = (const double*)blam.p;
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(adj.p, 0, adj.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(abp.p, 0, abp.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Uw.p, 0, Uw.bytes, h->stream);
+  F64State st = carve_f64(h->state.p, h->cap);
+  double* W = (double*)work.p;
+  double* A = (double*)adj.p;
+  F64State ws;
+  for (int q = 0; q < 3; ++q) {
+    ws.x[q] = W + q * n;
+    ws.v[q] = W + (3 + q) * n;
+  }
+  ws.d = st.d;
+  StepParams p;
+  p.dt = h->adj_dt;
+  p.ca = 18.0 * h->mu * h->alpha / h->rho_p;
+  p.mcoef = h->mult * h->rho_p * pi / 6.0;
+  for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
+  p.E = 0;
+  p.scale = 1.0;
+  for (int seg = K - 1; seg >= 0 && e == cudaSuccess; --seg) {
+    const int s0 = seg * C, s1 = std::min(nsteps, s0 + C);
+    e = cudaMemcpyAsync(W, (double*)h->ckpt.p + (size_t)seg * 6 * n, (size_t)6 * n * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream);
+    // recompute the segment, keeping the state at the start of every step
+    for (int k = s0; k < s1 && e == cudaSuccess; ++k) {
+      double* slot = (double*)tape.p + (size_t)(k - s0) * 6 * n;
+      e = cudaMemcpyAsync(slot, W, (size_t)6 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess && k + 1 < s1) e = launch_step_f64_state(h, ws, nullptr, p);
+    }
+    // reverse sweep
+    for (int k = s1 - 1; k >= s0 && e == cudaSuccess; --k) {
+      const double* slot = (const double*)tape.p + (size_t)(k - s0) * 6 * n;
+      AdjointStepArgs a;
+      for (int q = 0; q < 3; ++q) {
+        a.x[q] = slot + q * n;
+        a.v[q] = slot + (3 + q) * n;
+        a.xb[q] = A + q * n;
+        a.vb[q] = A + (3 + q) * n;
+      }
+      a.d = st.d;
+      a.db = A + 6 * n;
+      a.ab_part = (double*)abp.p;
+      a.lam = dlam;
+      a.Uw = (long long*)Uw.p;
+      a.dt = h->adj_dt;
+      e = launch_adjoint_step(h, a);
+    }
+  }
+  // outputs
+  std::vector<double> hab(kAdjBlocks);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hab.data(), abp.p, kAdjBlocks * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && grad_d) {
+    if (on_device) {
+      e = cudaMemcpyAsync(grad_d, A + 6 * n, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+      e = cudaMemcpyAsync(grad_d, A + 6 * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    }
+  }
+  if (e == cudaSuccess && grad_U) {
+    double* dst = on_device ? grad_U : (double*)tmp.p;
+    e = launch_wide_to_f64(h, (const long long*)Uw.p, dst, 3 * nc);
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(grad_U, dst, (size_t)3 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cleanup();
+  ST_TRY(cuda_check(h, e, "adjoint backward"));
+  if (grad_alpha) {
+    double t = 0.0;
+    for (int b = 0; b < kAdjBlocks; ++b) t += hab[b];
+    *grad_alpha = t;
+  }
   return ST_OK;
 }
 

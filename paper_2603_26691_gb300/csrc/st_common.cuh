@@ -14,6 +14,7 @@ namespace st {
 constexpr int kMaxDim = 1024;       // cells per axis (10-bit fields of the packed cell)
 constexpr int kAccBits = 96;        // a contribution at its bound maps to 2^96 in the accumulator
 constexpr int kMaxRun = 128;        // particles folded into one committed run (warp x 4)
+constexpr int kFluidPad = 3;        // ghost layers around the mixed-precision field
 
 // Owned device allocation.
 struct Buf {
@@ -52,6 +53,7 @@ struct st_ctx {
 
   // fluid: FP64 handles D4[ncell] (x, y, z, 0); mixed handles float4[ncell]
   st::Buf fluid;
+  st::Buf fluid_pad;         // mixed handles: float4 field with kFluidPad ghost layers, periodic
   bool fluid_set = false;
   double umax = 0.0;
 
@@ -78,6 +80,13 @@ struct st_ctx {
   double acc_load = 0.0;     // bound on |accumulated integer| (in units of 1), for overflow control
 
   st::Buf red;               // small reduction scratch
+  st::Buf flags;             // device error flags (bounded waits that gave up)
+
+  // adjoint: checkpoints of (x, v) every adj_every steps of the last st_adjoint_forward
+  st::Buf ckpt;
+  int adj_nsteps = 0, adj_every = 0;
+  double adj_dt = 0.0;
+  bool adj_ready = false;
   int64_t launches = 0;      // kernels launched by this handle
   std::string err;
 };
@@ -238,7 +247,31 @@ struct StepParams {
 };
 
 cudaError_t launch_step_f64(st_ctx* h, const StepParams& p);
+// the FP64 step on an explicit state; acc == nullptr skips the deposit (adjoint recomputation)
+cudaError_t launch_step_f64_state(st_ctx* h, const F64State& s, unsigned long long* acc, const StepParams& p);
+
+// ---- adjoint (adjoint.cu) ----------------------------------------------------------------------
+constexpr int kWideWords = 8;     // carry-save accumulator: 8 words of 32-bit digits
+constexpr int kWideBase = -160;   // weight of the lowest digit: 2^-160
+constexpr int kAdjBlocks = 152 * 8;
+
+struct AdjointStepArgs {
+  const double* x[3];
+  const double* v[3];
+  const double* d;
+  double* xb[3];
+  double* vb[3];
+  double* db;
+  double* ab_part;
+  const double* lam;
+  long long* Uw;
+  double dt;
+};
+cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s);
+cudaError_t launch_wide_to_f64(st_ctx* h, const long long* Uw, double* out, int64_t m);
 cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p);
+bool tma_step_supported(const st_ctx* h);                               // step_mixed_tma.cu
+cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p);      // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
 cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]);

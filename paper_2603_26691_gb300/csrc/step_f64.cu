@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
         J[2] += t2;
       }
     }
-    if (head && key >= 0) {
+    if (a.acc && head && key >= 0) {
       for (int q = 0; q < 3; ++q) {
         unsigned long long lo, hi;
         f64_to_i128(J[q], a.p.scale, lo, hi);
@@ -135,10 +135,14 @@ __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
 }  // namespace
 
 cudaError_t launch_step_f64(st_ctx* h, const StepParams& p) {
+  return launch_step_f64_state(h, carve_f64(h->state.p, h->cap), (unsigned long long*)h->acc.p, p);
+}
+
+cudaError_t launch_step_f64_state(st_ctx* h, const F64State& s, unsigned long long* acc, const StepParams& p) {
   F64Args a;
-  a.s = carve_f64(h->state.p, h->cap);
+  a.s = s;
   a.U = (const D4*)h->fluid.p;
-  a.acc = (unsigned long long*)h->acc.p;
+  a.acc = acc;
   a.n = h->np;
   a.ncell = h->geo.ncell;
   a.nx = h->geo.n[0];

@@ -114,32 +114,27 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
         if (j < nvalid) {
           const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
           key[j] = ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
-          // trilinear stencil from (cell, offset): centres at offset 1/2
-          int i0[3], i1[3];
+          // trilinear stencil from (cell, offset): centres at offset 1/2; the field carries
+          // kFluidPad ghost layers, so corner indices ii and ii + 1 (ii in [-1, n-1]) need no wrap
+          int i0[3];
           float f[3];
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const float o = xi[q][j];
-            int ii;
-            if (o >= 0.5f) {
-              ii = ci[q];
-              f[q] = o - 0.5f;
-            } else {
-              ii = ci[q] - 1;
-              f[q] = o + 0.5f;
-            }
-            i0[q] = ii < 0 ? ii + n3[q] : ii;
-            i1[q] = ii + 1 >= n3[q] ? ii + 1 - n3[q] : ii + 1;
+            const bool hi = o >= 0.5f;
+            i0[q] = ci[q] - (hi ? 0 : 1) + kFluidPad;
+            f[q] = o + (hi ? -0.5f : 0.5f);
           }
-          const int row = a.nx, slab = a.nx * a.ny;
-          const float4 U000 = __ldg(&a.U[i0[0] + row * i0[1] + slab * i0[2]]);
-          const float4 U100 = __ldg(&a.U[i1[0] + row * i0[1] + slab * i0[2]]);
-          const float4 U010 = __ldg(&a.U[i0[0] + row * i1[1] + slab * i0[2]]);
-          const float4 U110 = __ldg(&a.U[i1[0] + row * i1[1] + slab * i0[2]]);
-          const float4 U001 = __ldg(&a.U[i0[0] + row * i0[1] + slab * i1[2]]);
-          const float4 U101 = __ldg(&a.U[i1[0] + row * i0[1] + slab * i1[2]]);
-          const float4 U011 = __ldg(&a.U[i0[0] + row * i1[1] + slab * i1[2]]);
-          const float4 U111 = __ldg(&a.U[i1[0] + row * i1[1] + slab * i1[2]]);
+          const int64_t row = a.nx + 2 * kFluidPad, slab = row * (a.ny + 2 * kFluidPad);
+          const float4* b = a.U + i0[0] + row * i0[1] + slab * i0[2];
+          const float4 U000 = __ldg(b);
+          const float4 U100 = __ldg(b + 1);
+          const float4 U010 = __ldg(b + row);
+          const float4 U110 = __ldg(b + row + 1);
+          const float4 U001 = __ldg(b + slab);
+          const float4 U101 = __ldg(b + slab + 1);
+          const float4 U011 = __ldg(b + slab + row);
+          const float4 U111 = __ldg(b + slab + row + 1);
           float r00[3], r10[3], r01[3], r11[3], up[3];
           lerp3(U000, U100, f[0], r00);
           lerp3(U010, U110, f[0], r10);
@@ -259,7 +254,7 @@ cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p) {
   MixedArgs a;
   bool bf = h->prec == ST_MIXED_BF16V;
   a.s = carve_mixed(h->state.p, h->cap, bf);
-  a.U = (const float4*)h->fluid.p;
+  a.U = (const float4*)h->fluid_pad.p;
   a.acc = (unsigned long long*)h->acc.p;
   a.n = h->np;
   a.ncell = h->geo.ncell;

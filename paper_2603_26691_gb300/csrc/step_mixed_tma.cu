@@ -1,0 +1,668 @@
+// Mixed-precision Lagrangian step for sorted particles: a persistent,
+// warp-specialised kernel fed by the Tensor Memory Accelerator.
+//
+// After the counting sort the particles of every aligned U^3 block of cells
+// (U = min(B, 8); the Morton order inside a chunk makes each such block a
+// contiguous key range) are contiguous in storage.  Each CTA owns a sequence of
+// these units.  Per unit:
+//   * a producer warp loads the unit's fluid tile - the U^3 cells plus a halo
+//     of G cells - from the ghost-padded field with one 4-D TMA tensor copy
+//     (double-buffered across units), and streams the unit's particle arrays
+//     through a ring of shared-memory stages with 1-D bulk copies
+//     (cp.async.bulk), signalling completion on mbarriers;
+//   * consumer warps take 4 consecutive particles per lane from the stage,
+//     gather the fluid velocity from the shared tile (8 LDS.128 with immediate
+//     offsets; particles that drifted out of the tile read the padded field
+//     from L2), advance and relocate them, store the new state with 128-bit
+//     streaming stores, and reduce their impulses over runs of equal
+//     start-of-step cell across the warp;
+//   * each run is added, as 64-bit fixed point, to a shared deposit tile of
+//     the unit's cells plus a halo of R cells (integer shared-memory atomics:
+//     exact and order independent); runs outside it go straight to the global
+//     128-bit accumulator; at the end of the unit the tile is flushed, exactly,
+//     into the global accumulator.
+// Every wait is bounded: a wait that gives up sets an error flag and the CTA
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+
+#include "st_common.cuh"
+
+namespace st {
+namespace {
+
+constexpr int kU = 8;                       // unit edge (cells)
+constexpr int kG = 3;                       // fluid halo = padding of the field
+constexpr int kTE = kU + 2 * kG;            // fluid tile edge (14)
+constexpr int kR = 2;                       // deposit halo
+constexpr int kDE = kU + 2 * kR;            // deposit tile edge (12)
+constexpr int kConsumerWarps = 11;
+constexpr int kT = kConsumerWarps * 128;    // particles per stage (1408)
+constexpr int kStages = 2;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+constexpr int kFluidBytes = kTE * kTE * kTE * 16;          // 43904
+constexpr int kDepositCells = kDE * kDE * kDE;              // 1728
+constexpr int kDepositBytes = kDepositCells * 3 * 8;        // 41472
+constexpr int kStageBytes = kT * 32;                        // 45056 (FP32 layout; BF16 uses less)
+constexpr int kSmemBytes = 2 * kFluidBytes + kDepositBytes + kStages * kStageBytes + 16 * 8;
+
+// ---- PTX wrappers ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sptr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sptr(b)), "r"(tx) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sptr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(sptr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_test(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   sptr(dst)),
+               "l"(src), "r"(bytes), "r"(sptr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map, int c1, int c2, int c3,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(sptr(dst)),
+      "l"(map), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(sptr(bar))
+      : "memory");
+}
+
+// 1 - e^{-x} for x >= 0: Taylor series (x < 1/8, truncation below 4e-9 relative) or 1 - 2^(-x log2 e)
+__device__ __forceinline__ float one_minus_exp(float x, float* e) {
+  float ex;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(-1.4426950408889634f * x));
+  float s = fmaf(x, -0.2f, 1.0f);
+  s = fmaf(x * 0.25f, -s, 1.0f);
+  s = fmaf(x * (1.0f / 3.0f), -s, 1.0f);
+  s = fmaf(x * 0.5f, -s, 1.0f);
+  const float small = x * s;
+  const float big = 1.0f - ex;
+  const float r = x < 0.125f ? small : big;
+  *e = x < 0.125f ? 1.0f - r : ex;
+  return r;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+struct TmaArgs {
+  MixedState s;
+  const float4* __restrict__ Up;      // ghost-padded field [nz+2G][ny+2G][nx+2G]
+  unsigned long long* __restrict__ acc;
+  const uint32_t* __restrict__ cell_start;
+  int* __restrict__ err;
+  int64_t ncell;
+  int nx, ny, nz;
+  int nunits;                         // units of kU^3 cells in key order
+  int logB, ncx, ncy;                 // chunk geometry for decoding a unit's origin
+  float inv_h[3];
+  float dt, cadt, inv_ca, mcoef;
+  float g[3], gdt[3];
+  int E;                              // global accumulator exponent
+};
+
+// de-interleave 3 bits per level (local x bit lowest)
+__device__ __forceinline__ uint32_t compact3(uint32_t v) {
+  v &= 0x09249249u;
+  v = (v | (v >> 2)) & 0x030c30c3u;
+  v = (v | (v >> 4)) & 0x0300f00fu;
+  v = (v | (v >> 8)) & 0xff0000ffu;
+  v = (v | (v >> 16)) & 0x000003ffu;
+  return v;
+}
+
+__device__ __forceinline__ void unit_origin(const TmaArgs& a, int u, int& ox, int& oy, int& oz) {
+  const uint32_t key = (uint32_t)u * (kU * kU * kU);
+  const uint32_t chunk = key >> (3 * a.logB);
+  const uint32_t m = key & ((1u << (3 * a.logB)) - 1u);
+  const int B = 1 << a.logB;
+  const int cx = (int)(chunk % (uint32_t)a.ncx);
+  const int cy = (int)((chunk / (uint32_t)a.ncx) % (uint32_t)a.ncy);
+  const int cz = (int)(chunk / ((uint32_t)a.ncx * (uint32_t)a.ncy));
+  ox = cx * B + (int)compact3(m);
+  oy = cy * B + (int)compact3(m >> 1);
+  oz = cz * B + (int)compact3(m >> 2);
+}
+
+__device__ __forceinline__ int periodic_delta(int d, int n) {
+  if (d > (n >> 1)) d -= n;
+  if (d < -(n >> 1)) d += n;
+  return d;
+}
+
+template <bool BF16>
+__device__ __forceinline__ int stage_bytes(int cnt) {
+  return cnt * (BF16 ? 26 : 32);
+}
+
+// round(f * 2^E) as a 64-bit integer from the float's bits (integer operations only; the
+// caller guarantees |f| * 2^E < 2^62)
+__device__ __forceinline__ long long scaled_i64(float f, int E) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ex = (b >> 23) & 0xffu;
+  unsigned long long man = b & 0x7fffffu;
+  if (ex != 0) man |= 0x800000ull;
+  const int s = (int)(ex == 0 ? 1 : ex) - 150 + E;
+  unsigned long long v;
+  if (s >= 0) {
+    v = man << s;
+  } else {
+    const int r = -s;
+    v = r < 32 ? ((man + ((1ull << r) >> 1)) >> r) : 0ull;
+  }
+  return (b >> 31) ? -(long long)v : (long long)v;
+}
+
+// commit one run sum to the global 128-bit accumulator
+__device__ __forceinline__ void commit_global(const TmaArgs& a, int key, float j0, float j1, float j2) {
+  unsigned long long lo, hi;
+  f32_to_i128(j0, a.E, lo, hi);
+  atomic_add_i128(a.acc + 2 * key, lo, hi);
+  f32_to_i128(j1, a.E, lo, hi);
+  atomic_add_i128(a.acc + 2 * (a.ncell + key), lo, hi);
+  f32_to_i128(j2, a.E, lo, hi);
+  atomic_add_i128(a.acc + 2 * (2 * a.ncell + key), lo, hi);
+}
+
+template <bool BF16>
+__global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
+                                                                      const TmaArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float4* fluid = reinterpret_cast<float4*>(smem);                                   // [2][kTE^3]
+  long long* dep = reinterpret_cast<long long*>(smem + 2 * kFluidBytes);             // [3][kDE^3]
+  unsigned char* ring = smem + 2 * kFluidBytes + kDepositBytes;                       // [kStages][kStageBytes]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
+  uint64_t* full = bars;                    // [kStages]   producer -> consumers (bytes landed)
+  uint64_t* empty = bars + kStages;         // [kStages]   consumers -> producer (stage free)
+  uint64_t* tile_full = bars + 2 * kStages;  // [2]        fluid tile landed
+  uint64_t* tile_empty = tile_full + 2;      // [2]        consumers done with a fluid tile
+  uint64_t* dep_done = tile_empty + 2;       // [1]        all consumer warps finished a unit's deposits
+  uint64_t* flush_done = dep_done + 1;       // [1]        deposit tile flushed and cleared
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tile_full[b], 1);
+      mbar_init(&tile_empty[b], kConsumerWarps);
+    }
+    mbar_init(dep_done, kConsumerWarps);
+    mbar_init(flush_done, kConsumerWarps);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < 3 * kDepositCells; i += blockDim.x) dep[i] = 0;
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {
+    // ================= producer =================
+    if (lane == 0) {
+      int loaded = 0;    // non-empty units whose fluid tile was issued
+      int64_t gt = 0;    // particle stages issued
+      for (int u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+        const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
+        const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
+        if (E <= S) continue;
+        const int buf = loaded & 1;
+        if (loaded >= 2 && !mbar_wait(&tile_empty[buf], ((loaded >> 1) - 1) & 1)) {
+          atomicOr(a.err, 1);
+          return;
+        }
+        int ox, oy, oz;
+        unit_origin(a, u, ox, oy, oz);
+        mbar_expect_tx(&tile_full[buf], kFluidBytes);
+        tma_load_tile(fluid + buf * (kTE * kTE * kTE), &fluid_map, ox, oy, oz, &tile_full[buf]);
+        ++loaded;
+        const int64_t A = S & ~int64_t(7);
+        const int64_t Z = (E + 7) & ~int64_t(7);
+        for (int64_t t0 = A; t0 < Z; t0 += kT) {
+          const int cnt = (int)min((int64_t)kT, Z - t0);
+          const int st = (int)(gt % kStages);
+          if (gt >= kStages && !mbar_wait(&empty[st], ((gt / kStages) - 1) & 1)) {
+            atomicOr(a.err, 2);
+            return;
+          }
+          unsigned char* dst = ring + st * kStageBytes;
+          mbar_expect_tx(&full[st], stage_bytes<BF16>(cnt));
+          bulk_load(dst, a.s.cell + t0, cnt * 4, &full[st]);
+          for (int q = 0; q < 3; ++q) bulk_load(dst + (1 + q) * kT * 4, a.s.xi[q] + t0, cnt * 4, &full[st]);
+          const int vb = BF16 ? 2 : 4;
+          for (int q = 0; q < 3; ++q)
+            bulk_load(dst + 4 * kT * 4 + q * kT * vb, (const char*)a.s.v[q] + t0 * vb, cnt * vb, &full[st]);
+          bulk_load(dst + 4 * kT * 4 + 3 * kT * vb, a.s.d + t0, cnt * 4, &full[st]);
+          ++gt;
+        }
+      }
+      // let the last copies land before the CTA can exit
+      const int64_t first = gt > kStages ? gt - kStages : 0;
+      for (int64_t k = first; k < gt; ++k) mbar_wait(&empty[k % kStages], (k / kStages) & 1);
+    }
+    return;
+  }
+
+  // ================= consumers =================
+  const int ctid = threadIdx.x;  // 0 .. 255
+  const int n3[3] = {a.nx, a.ny, a.nz};
+  const int px = a.nx + 2 * kG, pxy = (a.nx + 2 * kG) * (a.ny + 2 * kG);
+  int loaded = 0;
+  int64_t gt = 0;
+  int units_done = 0;
+  for (int u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+    const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
+    const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
+    if (E <= S) continue;
+    const int buf = loaded & 1;
+    if (!mbar_wait(&tile_full[buf], (loaded >> 1) & 1)) {
+      atomicOr(a.err, 4);
+      return;
+    }
+    const float4* tile = fluid + buf * (kTE * kTE * kTE);
+    int uo[3];
+    unit_origin(a, u, uo[0], uo[1], uo[2]);
+    // deposit tile scale: a unit of cnt particles keeps every tile cell below 2^62
+    const int64_t count = E - S;
+    int lg = 0;
+    while ((int64_t(1) << lg) <= count) ++lg;
+    const int shift = 28 + lg;          // tile value = global integer >> shift
+    const int Es = a.E - shift;
+
+    const int64_t A = S & ~int64_t(7);
+    const int64_t Z = (E + 7) & ~int64_t(7);
+    for (int64_t t0 = A; t0 < Z; t0 += kT) {
+      const int st = (int)(gt % kStages);
+      if (!mbar_wait(&full[st], (gt / kStages) & 1)) {
+        atomicOr(a.err, 8);
+        return;
+      }
+      const unsigned char* src = ring + st * kStageBytes;
+      const int L = 4 * ctid;
+      const int64_t p0 = t0 + L;
+      int cell[4];
+      float xi[3][4], v[3][4], dv[4];
+      {
+        int4 c4 = *reinterpret_cast<const int4*>(src + L * 4);
+        cell[0] = c4.x;
+        cell[1] = c4.y;
+        cell[2] = c4.z;
+        cell[3] = c4.w;
+        for (int q = 0; q < 3; ++q) {
+          float4 x4 = *reinterpret_cast<const float4*>(src + (1 + q) * kT * 4 + L * 4);
+          xi[q][0] = x4.x;
+          xi[q][1] = x4.y;
+          xi[q][2] = x4.z;
+          xi[q][3] = x4.w;
+        }
+        if (BF16) {
+          for (int q = 0; q < 3; ++q) {
+            uint2 r = *reinterpret_cast<const uint2*>(src + 4 * kT * 4 + q * kT * 2 + L * 2);
+            float2 l = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.x));
+            float2 h = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&r.y));
+            v[q][0] = l.x;
+            v[q][1] = l.y;
+            v[q][2] = h.x;
+            v[q][3] = h.y;
+          }
+          float4 d4 = *reinterpret_cast<const float4*>(src + 4 * kT * 4 + 3 * kT * 2 + L * 4);
+          dv[0] = d4.x;
+          dv[1] = d4.y;
+          dv[2] = d4.z;
+          dv[3] = d4.w;
+        } else {
+          for (int q = 0; q < 3; ++q) {
+            float4 r = *reinterpret_cast<const float4*>(src + 4 * kT * 4 + q * kT * 4 + L * 4);
+            v[q][0] = r.x;
+            v[q][1] = r.y;
+            v[q][2] = r.z;
+            v[q][3] = r.w;
+          }
+          float4 d4 = *reinterpret_cast<const float4*>(src + 7 * kT * 4 + L * 4);
+          dv[0] = d4.x;
+          dv[1] = d4.y;
+          dv[2] = d4.z;
+          dv[3] = d4.w;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);  // the stage is in registers: hand it back early
+      ++gt;
+
+      // owned particles of this lane: [lo, hi) of 0..3 (the rest belong to neighbouring units
+      // or lie past the unit); the others are replaced by a harmless particle so that all four
+      // are computed without branches and interleave
+      const int lo = (int)max((int64_t)0, min((int64_t)4, S - p0));
+      const int hi = (int)max((int64_t)0, min((int64_t)4, E - p0));
+      bool own[4];
+      int key[4];
+      float J[4][3];
+      const int ucell = pack_cell(uo[0], uo[1], uo[2]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        own[j] = (j >= lo) && (j < hi);
+        if (!own[j]) {
+          cell[j] = ucell;
+          xi[0][j] = xi[1][j] = xi[2][j] = 0.5f;
+          dv[j] = 1e-5f;
+        }
+        key[j] = own[j] ? cell[j] : -1;  // runs are keyed by the packed start cell
+      }
+      int cn[4][3];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
+        int i0[3], lt[3];
+        float f[3];
+        bool in_tile = true;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float o = xi[q][j];
+          const bool hi2 = o >= 0.5f;
+          i0[q] = ci[q] - (hi2 ? 0 : 1);
+          f[q] = o + (hi2 ? -0.5f : 0.5f);
+          int dl = i0[q] - uo[q] + kG;   // tile-local index, periodic
+          if (dl < -kG) dl += n3[q];
+          else if (dl >= n3[q] - kG) dl -= n3[q];
+          const int dc = min(max(dl, 0), kTE - 2);
+          in_tile = in_tile && (dc == dl);
+          lt[q] = dc;
+        }
+        const float4* b = tile + lt[0] + kTE * (lt[1] + kTE * lt[2]);
+        float4 c000 = b[0], c100 = b[1], c010 = b[kTE], c110 = b[kTE + 1];
+        float4 c001 = b[kTE * kTE], c101 = b[kTE * kTE + 1], c011 = b[kTE * kTE + kTE], c111 = b[kTE * kTE + kTE + 1];
+        if (!in_tile) {  // drifted out of the unit's halo: read the padded field (L2)
+          const float4* g = a.Up + (i0[0] + kG) + (int64_t)px * (i0[1] + kG) + (int64_t)pxy * (i0[2] + kG);
+          c000 = __ldg(g);
+          c100 = __ldg(g + 1);
+          c010 = __ldg(g + px);
+          c110 = __ldg(g + px + 1);
+          c001 = __ldg(g + pxy);
+          c101 = __ldg(g + pxy + 1);
+          c011 = __ldg(g + pxy + px);
+          c111 = __ldg(g + pxy + px + 1);
+        }
+        float up[3];
+        {
+          const float fx = f[0], fy = f[1], fz = f[2];
+          const float ax = fmaf(fx, c100.x - c000.x, c000.x), bx = fmaf(fx, c110.x - c010.x, c010.x);
+          const float cx = fmaf(fx, c101.x - c001.x, c001.x), dx = fmaf(fx, c111.x - c011.x, c011.x);
+          const float ay = fmaf(fx, c100.y - c000.y, c000.y), by = fmaf(fx, c110.y - c010.y, c010.y);
+          const float cy = fmaf(fx, c101.y - c001.y, c001.y), dy = fmaf(fx, c111.y - c011.y, c011.y);
+          const float az = fmaf(fx, c100.z - c000.z, c000.z), bz = fmaf(fx, c110.z - c010.z, c010.z);
+          const float cz = fmaf(fx, c101.z - c001.z, c001.z), dz = fmaf(fx, c111.z - c011.z, c011.z);
+          const float ex = fmaf(fy, bx - ax, ax), gx = fmaf(fy, dx - cx, cx);
+          const float ey = fmaf(fy, by - ay, ay), gy = fmaf(fy, dy - cy, cy);
+          const float ez = fmaf(fy, bz - az, az), gz = fmaf(fy, dz - cz, cz);
+          up[0] = fmaf(fz, gx - ex, ex);
+          up[1] = fmaf(fz, gy - ey, ey);
+          up[2] = fmaf(fz, gz - ez, ez);
+        }
+        const float d = dv[j];
+        const float dd = d * d;
+        const float adt = a.cadt * rcp_approx(dd);
+        float Ee;
+        const float E1 = one_minus_exp(adt, &Ee);
+        const float inv_a = dd * a.inv_ca;
+        const float Q = E1 * inv_a;
+        const float m = a.mcoef * dd * d;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float wt = fmaf(a.g[q], inv_a, up[q]);
+          const float dvw = v[q][j] - wt;
+          float vn = fmaf(dvw, Ee, wt);
+          if (BF16) vn = __bfloat162float(__float2bfloat16_rn(vn));
+          const float dxv = fmaf(wt, a.dt, dvw * Q);
+          float o = fmaf(dxv, a.inv_h[q], xi[q][j]);
+          int ii;
+          if (fabsf(o) < 4194304.0f) {
+            // whole cells carried: k = round(o - 1/2) by the 1.5 * 2^23 shift (an FP32 add and an
+            // integer subtract, exact for |o| < 2^22), so no rounding or conversion instructions
+            const float t = (o - 0.5f) + 12582912.0f;
+            const int k = __float_as_int(t) - 0x4B400000;
+            o = o - (t - 12582912.0f);
+            ii = ci[q] + k;
+          } else {  // moved more than 2^22 cells in one step
+            const float fl = floorf(o);
+            o = o - fl;
+            ii = (int)(((long long)ci[q] + (long long)fl) % n3[q]);
+          }
+          if (o >= 1.0f) {  // on the upper face: offset 0 of the next cell
+            o -= 1.0f;
+            ii += 1;
+          }
+          if (o < 0.0f) {   // round-half-even put a value just below a face in the cell above
+            o += 1.0f;
+            ii -= 1;
+            if (o >= 1.0f) {
+              o = 0.0f;
+              ii += 1;
+            }
+          }
+          if (ii >= n3[q]) ii -= n3[q];
+          else if (ii < 0) ii += n3[q];
+          if ((unsigned)ii >= (unsigned)n3[q]) {  // moved more than a box length
+            ii %= n3[q];
+            if (ii < 0) ii += n3[q];
+          }
+          cn[j][q] = ii;
+          xi[q][j] = o;
+          J[j][q] = own[j] ? -m * ((vn - v[q][j]) - a.gdt[q]) : 0.0f;
+          v[q][j] = vn;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cell[j] = pack_cell(cn[j][0], cn[j][1], cn[j][2]);
+      // ---- store the owned particles (128-bit when the lane owns all four) ----
+      const bool all_own = own[0] && own[1] && own[2] && own[3];
+      if (all_own) {
+        __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
+        for (int q = 0; q < 3; ++q)
+          __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
+        if (BF16) {
+          for (int q = 0; q < 3; ++q) {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[q][0], v[q][1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(v[q][2], v[q][3]);
+            uint2 r;
+            r.x = *reinterpret_cast<unsigned*>(&lo);
+            r.y = *reinterpret_cast<unsigned*>(&hi);
+            __stcs((uint2*)((__nv_bfloat16*)a.s.v[q] + p0), r);
+          }
+        } else {
+          for (int q = 0; q < 3; ++q)
+            __stcs((float4*)((float*)a.s.v[q] + p0), make_float4(v[q][0], v[q][1], v[q][2], v[q][3]));
+        }
+      } else {
+        for (int j = 0; j < 4; ++j) {
+          if (!own[j]) continue;
+          a.s.cell[p0 + j] = cell[j];
+          for (int q = 0; q < 3; ++q) {
+            a.s.xi[q][p0 + j] = xi[q][j];
+            if (BF16)
+              ((__nv_bfloat16*)a.s.v[q])[p0 + j] = __float2bfloat16_rn(v[q][j]);
+            else
+              ((float*)a.s.v[q])[p0 + j] = v[q][j];
+          }
+        }
+      }
+      // ---- deposit: the lane's runs of equal start cell, added to the shared tile as 64-bit fixed
+      // point with integer atomics (exact and independent of the order of the adds) ----
+      float Sx[4][3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Sx[3][q] = J[3][q];
+#pragma unroll
+      for (int j = 2; j >= 0; --j) {
+        const bool same = key[j] == key[j + 1];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) Sx[j][q] = J[j][q] + (same ? Sx[j + 1][q] : 0.0f);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool start = (j == 0) || (key[j] != key[j - 1]);
+        if (start && key[j] >= 0) {
+          const int ci = cell_i(key[j]), cj = cell_j(key[j]), ck = cell_k(key[j]);
+          const int li = periodic_delta(ci - uo[0], a.nx) + kR;
+          const int lj = periodic_delta(cj - uo[1], a.ny) + kR;
+          const int lk = periodic_delta(ck - uo[2], a.nz) + kR;
+          if ((unsigned)li < (unsigned)kDE && (unsigned)lj < (unsigned)kDE && (unsigned)lk < (unsigned)kDE) {
+            const int t = li + kDE * (lj + kDE * lk);
+            atomicAdd((unsigned long long*)&dep[t], (unsigned long long)scaled_i64(Sx[j][0], Es));
+            atomicAdd((unsigned long long*)&dep[kDepositCells + t], (unsigned long long)scaled_i64(Sx[j][1], Es));
+            atomicAdd((unsigned long long*)&dep[2 * kDepositCells + t],
+                      (unsigned long long)scaled_i64(Sx[j][2], Es));
+          } else {
+            commit_global(a, ci + a.nx * (cj + a.ny * ck), Sx[j][0], Sx[j][1], Sx[j][2]);
+          }
+        }
+      }
+    }
+    // all gathers of this unit are done: the producer may reuse its fluid buffer
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&tile_empty[buf]);
+      mbar_arrive(dep_done);
+    }
+    ++loaded;
+    // flush the deposit tile once every consumer warp has finished this unit
+    if (!mbar_wait(dep_done, units_done & 1)) {
+      atomicOr(a.err, 16);
+      return;
+    }
+    for (int t = ctid; t < kDepositCells; t += kConsumerWarps * 32) {
+      const int li = t % kDE, lj = (t / kDE) % kDE, lk = t / (kDE * kDE);
+      int gi = uo[0] - kR + li, gj = uo[1] - kR + lj, gk = uo[2] - kR + lk;
+      gi = gi < 0 ? gi + a.nx : (gi >= a.nx ? gi - a.nx : gi);
+      gj = gj < 0 ? gj + a.ny : (gj >= a.ny ? gj - a.ny : gj);
+      gk = gk < 0 ? gk + a.nz : (gk >= a.nz ? gk - a.nz : gk);
+      const int64_t gc = gi + (int64_t)a.nx * (gj + (int64_t)a.ny * gk);
+      for (int q = 0; q < 3; ++q) {
+        const long long val = dep[q * kDepositCells + t];
+        if (val != 0) {
+          dep[q * kDepositCells + t] = 0;
+          const unsigned long long lo = (unsigned long long)val << shift;
+          const unsigned long long hi = (unsigned long long)(val >> (64 - shift));
+          atomic_add_i128(a.acc + 2 * (q * a.ncell + gc), lo, hi);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(flush_done);
+    if (!mbar_wait(flush_done, units_done & 1)) {
+      atomicOr(a.err, 32);
+      return;
+    }
+    ++units_done;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+bool tma_step_supported(const st_ctx* h) {
+  if (h->prec == ST_FP64) return false;
+  if (h->geo.B < kU) return false;
+  for (int q = 0; q < 3; ++q)
+    if (h->geo.n[q] % h->geo.B != 0 || h->geo.n[q] < kTE) return false;
+  return h->fluid_pad.p != nullptr;
+}
+
+cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
+  static bool attr_set[2] = {false, false};
+  const bool bf = h->prec == ST_MIXED_BF16V;
+  if (!attr_set[bf]) {
+    cudaError_t e = bf ? cudaFuncSetAttribute(step_mixed_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              kSmemBytes)
+                       : cudaFuncSetAttribute(step_mixed_tma_kernel<false>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr_set[bf] = true;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const int nx = h->geo.n[0], ny = h->geo.n[1], nz = h->geo.n[2];
+  cuuint64_t dims[4] = {4, (cuuint64_t)(nx + 2 * kG), (cuuint64_t)(ny + 2 * kG), (cuuint64_t)(nz + 2 * kG)};
+  cuuint64_t strides[3] = {16, (cuuint64_t)16 * (nx + 2 * kG), (cuuint64_t)16 * (nx + 2 * kG) * (ny + 2 * kG)};
+  cuuint32_t box[4] = {4, kTE, kTE, kTE};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h->fluid_pad.p, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  TmaArgs a;
+  a.s = carve_mixed(h->state.p, h->cap, bf);
+  a.Up = (const float4*)h->fluid_pad.p;
+  a.acc = (unsigned long long*)h->acc.p;
+  a.cell_start = (const uint32_t*)h->cell_start.p;
+  a.err = (int*)h->flags.p;
+  a.ncell = h->geo.ncell;
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  a.nunits = (int)(h->nkeys / (kU * kU * kU));
+  int logB = 0;
+  while ((1 << logB) < h->geo.B) ++logB;
+  a.logB = logB;
+  a.ncx = nx / h->geo.B;
+  a.ncy = ny / h->geo.B;
+  for (int q = 0; q < 3; ++q) {
+    a.inv_h[q] = (float)h->geo.inv_h[q];
+    a.g[q] = (float)p.g[q];
+    a.gdt[q] = (float)(p.g[q] * p.dt);
+  }
+  a.dt = (float)p.dt;
+  a.cadt = (float)(p.ca * p.dt);
+  a.inv_ca = (float)(1.0 / p.ca);
+  a.mcoef = (float)p.mcoef;
+  a.E = p.E;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
+  int grid = sms > 0 ? sms : 152;
+  if (grid > a.nunits) grid = a.nunits;
+  if (bf)
+    step_mixed_tma_kernel<true><<<grid, kThreads, kSmemBytes, h->stream>>>(map, a);
+  else
+    step_mixed_tma_kernel<false><<<grid, kThreads, kSmemBytes, h->stream>>>(map, a);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace st

@@ -71,10 +71,22 @@ __global__ void pack_f64_kernel(const T* __restrict__ u, D4* __restrict__ out, i
     out[c] = D4{(double)u[3 * c], (double)u[3 * c + 1], (double)u[3 * c + 2], 0.0};
 }
 
+// FP32 field with P ghost layers on every side, filled periodically: padded cell (a, b, c)
+// holds cell ((a - P) mod nx, (b - P) mod ny, (c - P) mod nz)
 template <typename T>
-__global__ void pack_f32_kernel(const T* __restrict__ u, float4* __restrict__ out, int64_t ncell) {
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
-    out[c] = make_float4((float)u[3 * c], (float)u[3 * c + 1], (float)u[3 * c + 2], 0.0f);
+__global__ void pack_f32_padded_kernel(const T* __restrict__ u, float4* __restrict__ out, int nx, int ny, int nz,
+                                       int P) {
+  const int64_t px = nx + 2 * P, py = ny + 2 * P, pz = nz + 2 * P;
+  const int64_t total = px * py * pz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int a = (int)(t % px), b = (int)((t / px) % py), c = (int)(t / (px * py));
+    int i = (a - P) % nx, j = (b - P) % ny, k = (c - P) % nz;
+    i += i < 0 ? nx : 0;
+    j += j < 0 ? ny : 0;
+    k += k < 0 ? nz : 0;
+    const int64_t s = i + (int64_t)nx * (j + (int64_t)ny * k);
+    out[t] = make_float4((float)u[3 * s], (float)u[3 * s + 1], (float)u[3 * s + 2], 0.0f);
+  }
 }
 
 // ---- particle import / export --------------------------------------------------------------
@@ -385,10 +397,14 @@ cudaError_t launch_fluid_pack(st_ctx* h, const void* u, int dtype) {
     else
       pack_f64_kernel<float><<<grid_for(nc), kThreads, 0, h->stream>>>((const float*)u, (D4*)h->fluid.p, nc);
   } else {
+    const Geometry& G = h->geo;
+    const int64_t tot = (int64_t)(G.n[0] + 2 * kFluidPad) * (G.n[1] + 2 * kFluidPad) * (G.n[2] + 2 * kFluidPad);
     if (dtype == ST_DTYPE_F64)
-      pack_f32_kernel<double><<<grid_for(nc), kThreads, 0, h->stream>>>((const double*)u, (float4*)h->fluid.p, nc);
+      pack_f32_padded_kernel<double><<<grid_for(tot), kThreads, 0, h->stream>>>(
+          (const double*)u, (float4*)h->fluid_pad.p, G.n[0], G.n[1], G.n[2], kFluidPad);
     else
-      pack_f32_kernel<float><<<grid_for(nc), kThreads, 0, h->stream>>>((const float*)u, (float4*)h->fluid.p, nc);
+      pack_f32_padded_kernel<float><<<grid_for(tot), kThreads, 0, h->stream>>>(
+          (const float*)u, (float4*)h->fluid_pad.p, G.n[0], G.n[1], G.n[2], kFluidPad);
   }
   h->launches += 1;
   return cudaGetLastError();

@@ -83,6 +83,8 @@ class Sim:
         if st != _lib.ST_OK:
             raise StError(st, "st_create_grid", "")
         self.h = h
+        self.params = dict(rho_p=1000.0, mu=1.8e-5, g=(0.0, 0.0, -9.81), drag_scale=1.0, multiplicity=1.0,
+                           reorder_every=10)
 
     # -- lifetime ------------------------------------------------------------------------
     def close(self):
@@ -108,6 +110,8 @@ class Sim:
     # -- parameters and fields ---------------------------------------------------------------
     def set_params(self, rho_p=1000.0, mu=1.8e-5, g=(0.0, 0.0, -9.81), drag_scale=1.0, multiplicity=1.0,
                    reorder_every=10):
+        self.params = dict(rho_p=rho_p, mu=mu, g=tuple(g), drag_scale=drag_scale, multiplicity=multiplicity,
+                           reorder_every=reorder_every)
         garr = (C.c_double * 3)(*[float(x) for x in g])
         self._chk(self.lib.st_set_params(self.h, float(rho_p), float(mu), garr, float(drag_scale),
                                          float(multiplicity), int(reorder_every)), "st_set_params")
@@ -171,6 +175,32 @@ class Sim:
         v = C.c_int64()
         self._chk(self.lib.st_kernel_launches(self.h, C.byref(v)), "st_kernel_launches")
         return int(v.value)
+
+    def clear_particles(self):
+        self._chk(self.lib.st_clear_particles(self.h), "st_clear_particles")
+
+    def adjoint_forward(self, nsteps: int, dt: float, checkpoint_every: int):
+        self._chk(self.lib.st_adjoint_forward(self.h, int(nsteps), float(dt), int(checkpoint_every)),
+                  "st_adjoint_forward")
+
+    def adjoint_backward(self, lam):
+        """Gradients of L(Jtot) given lam = dL/dJtot [3, ncell]: (dL/dd [n], dL/dalpha, dL/dU [ncell, 3])."""
+        n = self.n
+        if isinstance(lam, torch.Tensor) and lam.is_cuda:
+            lt = lam.to(torch.float64).contiguous()
+            gd = torch.empty(n, dtype=torch.float64, device=self.device)
+            gU = torch.empty((self.ncell, 3), dtype=torch.float64, device=self.device)
+            ga = C.c_double()
+            self._chk(self.lib.st_adjoint_backward(self.h, _ptr(lt), 1, _ptr(gd), C.byref(ga), _ptr(gU), 1),
+                      "st_adjoint_backward")
+            return gd, ga.value, gU
+        la = np.ascontiguousarray(lam, dtype=np.float64)
+        gd = np.empty(n)
+        gU = np.empty((self.ncell, 3))
+        ga = C.c_double()
+        self._chk(self.lib.st_adjoint_backward(self.h, _ptr(la), 0, _ptr(gd), C.byref(ga), _ptr(gU), 0),
+                  "st_adjoint_backward")
+        return gd, ga.value, gU
 
     def step(self, nsteps: int, dt: float):
         self._chk(self.lib.st_step(self.h, int(nsteps), float(dt)), "st_step")
