@@ -249,7 +249,7 @@ st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t co
  * cudaStream_t, NULL = legacy default stream) and the call returns without
  * waiting.
  *
- * All scratch memory is one static device array of 12.5 MiB that every GPU
+ * All scratch memory is one static device array of 12.0 MiB that every GPU
  * which loads the library holds until the process exits; the call makes no
  * cudaMalloc, cudaFree or other allocating call.  n must not exceed
  * ST_SORT_KEYS_STATIC_MAX_N (2^20): larger n returns ST_ERR_INVALID_ARG

@@ -4,7 +4,7 @@
 // stable counting sort in three phases: per-tile digit histograms (warp-
 // aggregated shared-memory counts), one exclusive scan over the digit-major
 // histogram matrix, and a scatter in which every element's rank among the
-// equal digits of its tile comes from warp match/prefix operations combined
+// equal digits of its tile comes from warp digit ballots and prefix counts combined
 // across warps in warp order.  No phase waits on another block.  The
 // structure-of-arrays payload is then gathered once through the final
 // permutation.  Equal keys keep their storage order, so the permutation is
@@ -19,7 +19,9 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kItems = 16;
-constexpr int kTile = kSortThreads * kItems;  // 4096 items per tile
+constexpr int kTile = kSortThreads * kItems;  // 4096 items per chunk
+constexpr int kChunks = 16;
+constexpr int64_t kBigTile = (int64_t)kTile * kChunks;  // 65536 items per tile (one CTA, chunks in order)
 constexpr int kRadix = 256;
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -53,6 +55,20 @@ __global__ void keys_mixed_kernel(const int32_t* __restrict__ cell, int64_t n, K
   }
 }
 
+// lanes of the warp holding the same 8-bit digit (and the same validity): the intersection of one
+// ballot per digit bit, a fixed cost whatever the number of distinct digits in the warp
+__device__ __forceinline__ unsigned match_digit(uint32_t dig, bool valid) {
+  unsigned m = __ballot_sync(0xffffffffu, valid);
+  m = valid ? m : ~m;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (dig >> b) & 1u;
+    const unsigned bb = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? bb : ~bb;
+  }
+  return m;
+}
+
 // phase 1: digit histogram of each tile, stored digit-major: hist[d * ntiles + t]
 __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                                                 int64_t ntiles, uint32_t* __restrict__ hist) {
@@ -61,12 +77,22 @@ __global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint32_t* _
   __syncthreads();
   const int64_t t = blockIdx.x;
   const int lane = threadIdx.x & 31;
-  for (int r = 0; r < kItems; ++r) {
-    int64_t i = t * kTile + (int64_t)r * kSortThreads + threadIdx.x;
-    bool valid = i < n;
-    uint32_t dig = valid ? ((keys[i] >> shift) & 0xffu) : (0x100u + lane);
-    unsigned peers = __match_any_sync(0xffffffffu, dig);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[dig], (uint32_t)__popc(peers));
+  for (int c = 0; c < kChunks; ++c) {
+    const int64_t base = t * kBigTile + (int64_t)c * kTile;
+    uint32_t k[kItems];
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+      k[r] = i < n ? keys[i] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+      const bool valid = i < n;
+      const uint32_t dig = (k[r] >> shift) & 0xffu;
+      const unsigned peers = match_digit(dig, valid);
+      if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[dig], (uint32_t)__popc(peers));
+    }
   }
   __syncthreads();
   hist[(int64_t)threadIdx.x * ntiles + t] = cnt[threadIdx.x];
@@ -147,9 +173,10 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t
   }
 }
 
-// phase 3: stable scatter.  Warp w owns items [w*512, (w+1)*512) of the tile in
-// 16 coalesced rounds; ranks inside a round come from match_any + popc, across
-// rounds from a per-warp running count, across warps from a prefix in warp order.
+// phase 3: stable scatter.  A tile is processed as kChunks chunks in order; in a chunk warp w
+// owns items [w*512, (w+1)*512) in 16 coalesced rounds.  Ranks inside a round come from
+// digit ballots + popc, across rounds from a per-warp running count, across warps from a prefix in
+// warp order, and across chunks from per-digit running offsets.
 __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
                                                                   uint32_t* __restrict__ kout,
@@ -158,47 +185,60 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint32_t*
   constexpr int kWarps = kSortThreads / 32;
   __shared__ uint32_t wcnt[kWarps][kRadix];
   __shared__ uint32_t base[kRadix];
-  for (int w = 0; w < kWarps; ++w) wcnt[w][threadIdx.x] = 0;
+  __shared__ uint32_t chunk_total[kRadix];
   const int64_t t = blockIdx.x;
   base[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + t];
-  __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  uint32_t key[kItems], val[kItems], rank[kItems];
-  const int64_t start = t * kTile + (int64_t)w * (kItems * 32);
+  for (int c = 0; c < kChunks; ++c) {
+    const int64_t cstart = t * kBigTile + (int64_t)c * kTile;
+    if (cstart >= n) break;
+    for (int ww = 0; ww < kWarps; ++ww) wcnt[ww][threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t key[kItems], val[kItems], rank[kItems];
+    const int64_t start = cstart + (int64_t)w * (kItems * 32);
 #pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    int64_t i = start + r * 32 + lane;
-    bool valid = i < n;
-    key[r] = valid ? kin[i] : 0u;
-    val[r] = valid ? vin[i] : 0u;
-    uint32_t dig = valid ? ((key[r] >> shift) & 0xffu) : (0x100u + lane);
-    unsigned peers = __match_any_sync(0xffffffffu, dig);
-    uint32_t before = 0;
-    if (valid) before = wcnt[w][dig];
-    __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) wcnt[w][dig] = before + __popc(peers);
-    __syncwarp();
-    rank[r] = valid ? before + __popc(peers & lt) : 0xffffffffu;
-  }
-  __syncthreads();
-  {
-    uint32_t s = 0;
-    for (int ww = 0; ww < kWarps; ++ww) {
-      uint32_t c = wcnt[ww][threadIdx.x];
-      wcnt[ww][threadIdx.x] = s;
-      s += c;
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t i = start + r * 32 + lane;
+      key[r] = i < n ? kin[i] : 0u;
+      val[r] = i < n ? vin[i] : 0u;
     }
-  }
-  __syncthreads();
 #pragma unroll
-  for (int r = 0; r < kItems; ++r) {
-    if (rank[r] != 0xffffffffu) {
-      uint32_t dig = (key[r] >> shift) & 0xffu;
-      uint32_t dst = base[dig] + wcnt[w][dig] + rank[r];
-      kout[dst] = key[r];
-      vout[dst] = val[r];
+    for (int r = 0; r < kItems; ++r) {
+      const int64_t i = start + r * 32 + lane;
+      const bool valid = i < n;
+      const uint32_t dig = (key[r] >> shift) & 0xffu;
+      const unsigned peers = match_digit(dig, valid);
+      uint32_t before = 0;
+      if (valid) before = wcnt[w][dig];
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) wcnt[w][dig] = before + __popc(peers);
+      __syncwarp();
+      rank[r] = valid ? before + __popc(peers & lt) : 0xffffffffu;
     }
+    __syncthreads();
+    {
+      uint32_t acc = 0;
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t cc = wcnt[ww][threadIdx.x];
+        wcnt[ww][threadIdx.x] = acc;
+        acc += cc;
+      }
+      chunk_total[threadIdx.x] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      if (rank[r] != 0xffffffffu) {
+        const uint32_t dig = (key[r] >> shift) & 0xffu;
+        const uint32_t dst = base[dig] + wcnt[w][dig] + rank[r];
+        kout[dst] = key[r];
+        vout[dst] = val[r];
+      }
+    }
+    __syncthreads();
+    base[threadIdx.x] += chunk_total[threadIdx.x];
+    __syncthreads();
   }
 }
 
@@ -216,18 +256,64 @@ __global__ void gather_f64_kernel(F64State src, F64State dst, const uint32_t* __
   }
 }
 
-template <typename VT>
+// mixed-precision payload gather, 4 consecutive outputs per thread: one 16-byte load of the
+// permutation, then every gathered load of the 4 particles in flight at once, then 128-bit
+// (64-bit for BF16 velocities) coalesced stores
+template <bool BF16>
 __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32_t* __restrict__ sid,
                                     uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t p = perm[i];
-    dst.cell[i] = src.cell[p];
-    for (int q = 0; q < 3; ++q) {
-      dst.xi[q][i] = src.xi[q][p];
-      ((VT*)dst.v[q])[i] = ((const VT*)src.v[q])[p];
+  const int64_t n4 = n >> 2;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 pp = __ldg(reinterpret_cast<const uint4*>(perm) + g);
+    const uint32_t p[4] = {pp.x, pp.y, pp.z, pp.w};
+    int c[4];
+    float x[3][4], v[3][4], d[4];
+    uint32_t id[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      c[k] = __ldg(src.cell + p[k]);
+      d[k] = __ldg(src.d + p[k]);
+      id[k] = __ldg(sid + p[k]);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        x[q][k] = __ldg(src.xi[q] + p[k]);
+        v[q][k] = BF16 ? __bfloat162float(__ldg((const __nv_bfloat16*)src.v[q] + p[k]))
+                       : __ldg((const float*)src.v[q] + p[k]);
+      }
     }
-    dst.d[i] = src.d[p];
-    did[i] = sid[p];
+    const int64_t o = g << 2;
+    __stcs(reinterpret_cast<int4*>(dst.cell + o), make_int4(c[0], c[1], c[2], c[3]));
+    __stcs(reinterpret_cast<float4*>(dst.d + o), make_float4(d[0], d[1], d[2], d[3]));
+    __stcs(reinterpret_cast<uint4*>(did + o), make_uint4(id[0], id[1], id[2], id[3]));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      __stcs(reinterpret_cast<float4*>(dst.xi[q] + o), make_float4(x[q][0], x[q][1], x[q][2], x[q][3]));
+      if (BF16) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[q][0], v[q][1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[q][2], v[q][3]);
+        uint2 r;
+        r.x = *reinterpret_cast<unsigned*>(&lo);
+        r.y = *reinterpret_cast<unsigned*>(&hi);
+        __stcs(reinterpret_cast<uint2*>((__nv_bfloat16*)dst.v[q] + o), r);
+      } else {
+        __stcs(reinterpret_cast<float4*>((float*)dst.v[q] + o), make_float4(v[q][0], v[q][1], v[q][2], v[q][3]));
+      }
+    }
+  }
+  // ragged tail
+  for (int64_t i = (n4 << 2) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t pi = perm[i];
+    dst.cell[i] = src.cell[pi];
+    dst.d[i] = src.d[pi];
+    did[i] = sid[pi];
+    for (int q = 0; q < 3; ++q) {
+      dst.xi[q][i] = src.xi[q][pi];
+      if (BF16)
+        ((__nv_bfloat16*)dst.v[q])[i] = ((const __nv_bfloat16*)src.v[q])[pi];
+      else
+        ((float*)dst.v[q])[i] = ((const float*)src.v[q])[pi];
+    }
   }
 }
 
@@ -298,7 +384,7 @@ st_status sort_particles(st_ctx* h) {
   const int64_t n = h->np;
   if (n == 0) return ST_OK;
   if (n >= (int64_t(1) << 32)) return set_error(h, ST_ERR_INVALID_ARG, "sorting needs fewer than 2^32 particles");
-  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t ntiles = (n + kBigTile - 1) / kBigTile;
   const int64_t hm = ntiles * kRadix;
   const int64_t nb = (hm + kScanBlock - 1) / kScanBlock;
   if (h->sort_cap < h->cap) {
@@ -345,11 +431,11 @@ st_status sort_particles(st_ctx* h) {
                                                           carve_f64(h->state_alt.p, h->cap), (const uint32_t*)h->ids.p,
                                                           (uint32_t*)h->ids_alt.p, v0, n);
   } else if (h->prec == ST_MIXED_F32) {
-    gather_mixed_kernel<float><<<grid_for(n), 256, 0, h->stream>>>(
+    gather_mixed_kernel<false><<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
         carve_mixed(h->state.p, h->cap, false), carve_mixed(h->state_alt.p, h->cap, false), (const uint32_t*)h->ids.p,
         (uint32_t*)h->ids_alt.p, v0, n);
   } else {
-    gather_mixed_kernel<__nv_bfloat16><<<grid_for(n), 256, 0, h->stream>>>(
+    gather_mixed_kernel<true><<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
         carve_mixed(h->state.p, h->cap, true), carve_mixed(h->state_alt.p, h->cap, true), (const uint32_t*)h->ids.p,
         (uint32_t*)h->ids_alt.p, v0, n);
   }
@@ -386,7 +472,7 @@ namespace st {
 namespace {
 
 constexpr int64_t kStaticMaxN = int64_t(1) << 20;  // keys per call (matches the header's limit)
-constexpr int64_t kStaticTiles = kStaticMaxN / kTile;
+constexpr int64_t kStaticTiles = kStaticMaxN / kBigTile;
 constexpr int64_t kStaticHist = kStaticTiles * kRadix;
 constexpr int64_t kStaticAux = (kStaticHist + kScanBlock - 1) / kScanBlock + 1;
 // layout: index seeds [N] | ping-pong keys [N] | ping-pong values [N] | histograms [H] | offsets [H] | scan aux
@@ -457,7 +543,7 @@ extern "C" st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int ke
   uint32_t* hist = base + 3 * kStaticMaxN;
   uint32_t* offs = hist + kStaticHist;
   uint32_t* aux = offs + kStaticHist;
-  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t ntiles = (n + kBigTile - 1) / kBigTile;
   const int passes = (key_bits + 7) / 8;
   iota_kernel<<<grid_for(n), 256, 0, s>>>(seed, n);
   // alternate between the caller's outputs and the scratch pair so that the last pass lands in the outputs

@@ -140,7 +140,7 @@ st_status st_create_grid(int nx, int ny, int nz, double Lx, double Ly, double Lz
   int bits = 0;
   while ((1ull << bits) < nkeys) ++bits;
   h->key_bits = bits;
-  st_status s = dev_alloc(h, h->acc, (size_t)G.ncell * 3 * 2 * sizeof(unsigned long long));
+  st_status s = dev_alloc(h, h->acc, (size_t)G.ncell * 3 * kAccWords * sizeof(long long));
   if (s == ST_OK) s = dev_alloc(h, h->red, 64 * 1024);
   if (s == ST_OK) s = cuda_check(h, cudaMemsetAsync(h->acc.p, 0, h->acc.bytes, h->stream), "memset acc");
   if (precision == ST_FP64) {
@@ -402,6 +402,7 @@ static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
     cudaError_t e = launch_rescale_acc(h, h->acc_E - E);
     ST_TRY(cuda_check(h, e, "rescale accumulator"));
     h->acc_load = std::ldexp(h->acc_load, E - h->acc_E);
+    h->acc_count = 1.0;
   }
   if (h->acc_empty || E < h->acc_E) h->acc_E = E;
   E = h->acc_E;
@@ -410,6 +411,7 @@ static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
   while (h->acc_load + add > 0x1p125) {
     cudaError_t e = launch_rescale_acc(h, 1);
     ST_TRY(cuda_check(h, e, "rescale accumulator"));
+    h->acc_count = 1.0;
     h->acc_E -= 1;
     E = h->acc_E;
     h->acc_load *= 0.5;
@@ -417,6 +419,14 @@ static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
   }
   h->acc_load += add;
   h->acc_empty = false;
+  // each word takes at most one digit per contribution; a step adds at most one contribution per
+  // particle to any cell, plus one per neighbouring unit's tile flush (at most 27)
+  const double per_step = (double)h->np + 27.0;
+  if (h->acc_count + per_step > 0x1p30) {
+    ST_TRY(cuda_check(h, launch_normalize_acc(h), "normalise accumulator"));
+    h->acc_count = 1.0;
+  }
+  h->acc_count += per_step;
   *E_out = E;
   return ST_OK;
 }
@@ -475,6 +485,7 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
   if (reset) {
     h->acc_empty = true;
     h->acc_load = 0.0;
+    h->acc_count = 0.0;
   }
   return ST_OK;
 }

@@ -73,8 +73,9 @@ struct st_ctx {
   st::Buf keys[2], vals[2], hist, scan_aux, cell_start;  // cell_start uint32[nkeys + 1]
   int64_t sort_cap = 0;
 
-  // source accumulator: int64 {lo, hi} pairs, [3][ncell], exact 128-bit fixed point
+  // source accumulator: carry-save words [3][ncell][kAccWords] (int64), units of 2^-acc_E
   st::Buf acc;
+  double acc_count = 0.0;    // bound on contributions added to any word since the last normalisation
   int acc_E = 0;             // value = integer * 2^-acc_E
   bool acc_empty = true;
   double acc_load = 0.0;     // bound on |accumulated integer| (in units of 1), for overflow control
@@ -172,10 +173,77 @@ __host__ __device__ inline uint32_t chunk_key(int i, int j, int k, int B, int lo
 }
 
 // ---- exact fixed-point deposit -------------------------------------------------------------
-// The per-cell source is a 128-bit two's-complement integer per component
-// (int64 lo/hi pair) in units of 2^-E.  Integer addition is associative, so
-// the sum is the same whatever order the runs are added in.
+// The per-cell source is an integer multiple of 2^-E per component, kept in carry-save form:
+// kAccWords int64 words w[k] of signed 32-bit digits, value = sum_k w[k] 2^(32 k).  A
+// contribution adds at most three digits with fire-and-forget atomic adds (no return value, so
+// no round trip to L2 stalls the warp); integer addition is associative, so the sum is the same
+// whatever order the contributions arrive in.  Each word absorbs 2^31 contributions before a
+// normalisation pass (carry propagation) is needed; the host tracks that bound.
 
+constexpr int kAccWords = 4;
+
+// add sign * m * 2^s (m < 2^64, 0 <= s, s + 64 <= 32 * kAccWords + 32) to the words p[0..3]
+__device__ __forceinline__ void acc_add_mag(long long* p, unsigned long long m, int s, bool neg) {
+  if (m == 0) return;
+  const int q = s >> 5, r = s & 31;
+  const unsigned long long lo = m << r;
+  const unsigned long long hi = r ? (m >> (64 - r)) : 0ull;
+  long long d0 = (long long)(lo & 0xffffffffull), d1 = (long long)(lo >> 32), d2 = (long long)hi;
+  if (neg) {
+    d0 = -d0;
+    d1 = -d1;
+    d2 = -d2;
+  }
+  if (d0 && q < kAccWords) atomicAdd((unsigned long long*)&p[q], (unsigned long long)d0);
+  if (d1 && q + 1 < kAccWords) atomicAdd((unsigned long long*)&p[q + 1], (unsigned long long)d1);
+  if (d2 && q + 2 < kAccWords) atomicAdd((unsigned long long*)&p[q + 2], (unsigned long long)d2);
+}
+
+// add round(f * 2^E) (FP32 input; integer operations only) -- requires |f| 2^E < 2^100
+__device__ __forceinline__ void acc_add_f32(long long* p, float f, int E) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t ex = (b >> 23) & 0xffu;
+  unsigned long long man = b & 0x7fffffu;
+  if (ex != 0) man |= 0x800000ull;
+  int s = (int)(ex == 0 ? 1 : ex) - 150 + E;
+  if (s < 0) {
+    const int r = -s;
+    man = r < 32 ? ((man + ((1ull << r) >> 1)) >> r) : 0ull;
+    s = 0;
+  }
+  acc_add_mag(p, man, s, (b >> 31) != 0);
+}
+
+// add round(x * 2^E) (FP64 input; integer operations only) -- requires |x| 2^E < 2^100
+__device__ __forceinline__ void acc_add_f64(long long* p, double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  unsigned long long man = b & 0xfffffffffffffull;
+  if (ex != 0) man |= 1ull << 52;
+  int s = (ex == 0 ? 1 : ex) - 1075 + E;
+  if (s < 0) {
+    const int r = -s;
+    man = r < 64 ? ((man + ((1ull << r) >> 1)) >> r) : 0ull;
+    s = 0;
+  }
+  acc_add_mag(p, man, s, (b >> 63) != 0);
+}
+
+// exact value of carry-save words as a 128-bit two's-complement integer (lo, hi)
+__device__ __forceinline__ void acc_value(const long long* w, unsigned long long& lo, long long& hi) {
+  long long c = 0;
+  unsigned long long d[3];
+  for (int k = 0; k < 3; ++k) {
+    const long long t = w[k] + c;
+    d[k] = (unsigned long long)t & 0xffffffffull;
+    c = t >> 32;
+  }
+  const long long top = w[3] + c;
+  lo = d[0] | (d[1] << 32);
+  hi = (long long)d[2] + (long long)((unsigned long long)top << 32);
+}
+
+// 128-bit add with carry-out, used by the exact reductions (returns the old value from memory)
 __device__ __forceinline__ void atomic_add_i128(unsigned long long* p, unsigned long long lo,
                                                 unsigned long long hi) {
   unsigned long long carry = 0;
@@ -198,44 +266,6 @@ __device__ __forceinline__ void f64_to_i128(double J, double scale, unsigned lon
   hi = (unsigned long long)(long long)yh;
 }
 
-// The same from an FP32 value by integer operations only (GB300's FP64 rate is
-// low): f = man * 2^(ex - 150); the scaled integer is man shifted by ex - 150 + E,
-// rounded half away from zero when shifted right.  Requires ex - 150 + E <= 103.
-__device__ __forceinline__ void f32_to_i128(float f, int E, unsigned long long& lo,
-                                            unsigned long long& hi) {
-  uint32_t b = __float_as_uint(f);
-  uint32_t ex = (b >> 23) & 0xffu;
-  unsigned long long man = b & 0x7fffffu;
-  if (ex == 0) {
-    ex = 1;
-  } else {
-    man |= 0x800000ull;
-  }
-  int s = (int)ex - 150 + E;
-  unsigned long long l, h;
-  if (s >= 64) {
-    l = 0;
-    h = man << (s - 64);
-  } else if (s > 0) {
-    l = man << s;
-    h = man >> (64 - s);
-  } else if (s == 0) {
-    l = man;
-    h = 0;
-  } else {
-    int r = -s;
-    l = r < 32 ? ((man + ((1ull << r) >> 1)) >> r) : 0ull;
-    h = 0;
-  }
-  if (b >> 31) {
-    unsigned long long nl = ~l + 1ull;
-    h = ~h + (l == 0 ? 1ull : 0ull);
-    l = nl;
-  }
-  lo = l;
-  hi = h;
-}
-
 // ---- launchers implemented in the other translation units --------------------------------
 struct StepParams {
   double dt;
@@ -248,7 +278,7 @@ struct StepParams {
 
 cudaError_t launch_step_f64(st_ctx* h, const StepParams& p);
 // the FP64 step on an explicit state; acc == nullptr skips the deposit (adjoint recomputation)
-cudaError_t launch_step_f64_state(st_ctx* h, const F64State& s, unsigned long long* acc, const StepParams& p);
+cudaError_t launch_step_f64_state(st_ctx* h, const F64State& s, long long* acc, const StepParams& p);
 
 // ---- adjoint (adjoint.cu) ----------------------------------------------------------------------
 constexpr int kWideWords = 8;     // carry-save accumulator: 8 words of 32-bit digits
@@ -273,6 +303,7 @@ cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p);
 bool tma_step_supported(const st_ctx* h);                               // step_mixed_tma.cu
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p);      // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
+cudaError_t launch_normalize_acc(st_ctx* h);
 cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]);
 cudaError_t launch_particle_sums(st_ctx* h, double out[4]);  // P_x, P_y, P_z, M

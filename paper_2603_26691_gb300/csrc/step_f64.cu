@@ -12,7 +12,7 @@ namespace {
 struct F64Args {
   F64State s;
   const D4* __restrict__ U;
-  unsigned long long* __restrict__ acc;
+  long long* __restrict__ acc;
   int64_t n;
   int64_t ncell;
   int nx, ny, nz;
@@ -123,11 +123,7 @@ __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
       }
     }
     if (a.acc && head && key >= 0) {
-      for (int q = 0; q < 3; ++q) {
-        unsigned long long lo, hi;
-        f64_to_i128(J[q], a.p.scale, lo, hi);
-        atomic_add_i128(a.acc + 2 * (q * a.ncell + key), lo, hi);
-      }
+      for (int q = 0; q < 3; ++q) acc_add_f64(a.acc + kAccWords * (q * a.ncell + key), J[q], a.p.E);
     }
   }
 }
@@ -135,10 +131,10 @@ __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
 }  // namespace
 
 cudaError_t launch_step_f64(st_ctx* h, const StepParams& p) {
-  return launch_step_f64_state(h, carve_f64(h->state.p, h->cap), (unsigned long long*)h->acc.p, p);
+  return launch_step_f64_state(h, carve_f64(h->state.p, h->cap), (long long*)h->acc.p, p);
 }
 
-cudaError_t launch_step_f64_state(st_ctx* h, const F64State& s, unsigned long long* acc, const StepParams& p) {
+cudaError_t launch_step_f64_state(st_ctx* h, const F64State& s, long long* acc, const StepParams& p) {
   F64Args a;
   a.s = s;
   a.U = (const D4*)h->fluid.p;

@@ -13,7 +13,7 @@ namespace {
 struct MixedArgs {
   MixedState s;
   const float4* __restrict__ U;
-  unsigned long long* __restrict__ acc;
+  long long* __restrict__ acc;
   int64_t n;
   int64_t ncell;
   int nx, ny, nz;
@@ -30,13 +30,9 @@ __device__ __forceinline__ void lerp3(float4 a, float4 b, float f, float r[3]) {
 }
 
 __device__ __forceinline__ void commit(const MixedArgs& a, int key, float j0, float j1, float j2) {
-  unsigned long long lo, hi;
-  f32_to_i128(j0, a.E, lo, hi);
-  atomic_add_i128(a.acc + 2 * key, lo, hi);
-  f32_to_i128(j1, a.E, lo, hi);
-  atomic_add_i128(a.acc + 2 * (a.ncell + key), lo, hi);
-  f32_to_i128(j2, a.E, lo, hi);
-  atomic_add_i128(a.acc + 2 * (2 * a.ncell + key), lo, hi);
+  acc_add_f32(a.acc + kAccWords * key, j0, a.E);
+  acc_add_f32(a.acc + kAccWords * (a.ncell + key), j1, a.E);
+  acc_add_f32(a.acc + kAccWords * (2 * a.ncell + key), j2, a.E);
 }
 
 template <bool BF16>
@@ -80,6 +76,20 @@ __device__ __forceinline__ float stored(float v) {
   return v;
 }
 
+// periodic index for a particle that moved more than a box length in one step (rare)
+__device__ __noinline__ int wrap_index_slow(int ii, int n) {
+  ii %= n;
+  return ii < 0 ? ii + n : ii;
+}
+
+// cell index after a move of 2^22 cells or more in one step (rare); the offset is set here too
+__device__ __noinline__ int relocate_far(float& o, int ci, int n) {
+  const float fl = floorf(o);
+  o = fmaxf(fminf(o - fl, 0.99999994f), 0.0f);
+  long long k = ((long long)ci + (long long)fl) % n;
+  return (int)(k < 0 ? k + n : k);
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
   const int lane = threadIdx.x & 31;
@@ -91,6 +101,17 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
     int key[4] = {-1, -1, -1, -1};
     float J[4][3];
     for (int j = 0; j < 4; ++j) J[j][0] = J[j][1] = J[j][2] = 0.0f;
+    {
+      // pull the next iteration's particle lines towards L2 while this one computes
+      const int64_t pn = p0 + nwarp * 128;
+      if (pn < a.n) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.s.cell + pn));
+        for (int q = 0; q < 3; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.s.xi[q] + pn));
+        for (int q = 0; q < 3; ++q)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"((const char*)a.s.v[q] + pn * (BF16 ? 2 : 4)));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a.s.d + pn));
+      }
+    }
     if (p0 < a.n) {
       // ---- load (128-bit, streaming) ----
       int4 c4 = __ldcs((const int4*)(a.s.cell + p0));
@@ -162,21 +183,24 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
             const float dvw = v[q][j] - wt;
             const float vn = stored<BF16>(fmaf(dvw, E, wt));
             const float dx = fmaf(wt, a.dt, dvw * Q);
-            // relocate: offset in cell units, carry whole cells into the index
+            // relocate: offset in cell units, carry whole cells into the index (k = round(o - 1/2)
+            // by the 1.5 * 2^23 shift: no rounding or conversion instructions)
             float o = fmaf(dx, a.inv_h[q], xi[q][j]);
-            const float fl = floorf(o);
-            o = o - fl;
-            int ii = ci[q] + (int)fl;
-            if (o >= 1.0f) {  // o was a tiny negative number: it sits on the lower face of the next cell
-              o -= 1.0f;
-              ii += 1;
-            }
-            if (o < 0.0f) o = 0.0f;
-            if (ii >= n3[q]) ii -= n3[q];
-            else if (ii < 0) ii += n3[q];
-            if (ii < 0 || ii >= n3[q]) {  // moved more than a box length
-              ii %= n3[q];
-              if (ii < 0) ii += n3[q];
+            int ii;
+            if (__builtin_expect(fabsf(o) < 4194304.0f, 1)) {
+              const float t = (o - 0.5f) + 12582912.0f;
+              ii = ci[q] + (__float_as_int(t) - 0x4B400000);
+              o = o - (t - 12582912.0f);
+              if (o >= 1.0f) {  // on the upper face: offset 0 of the next cell
+                o = 0.0f;
+                ii += 1;
+              }
+              o = fmaxf(o, 0.0f);
+              if (ii >= n3[q]) ii -= n3[q];
+              else if (ii < 0) ii += n3[q];
+              if (__builtin_expect((unsigned)ii >= (unsigned)n3[q], 0)) ii = wrap_index_slow(ii, n3[q]);
+            } else {
+              ii = relocate_far(o, ci[q], n3[q]);
             }
             cn[q] = ii;
             xi[q][j] = o;
@@ -255,7 +279,7 @@ cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p) {
   bool bf = h->prec == ST_MIXED_BF16V;
   a.s = carve_mixed(h->state.p, h->cap, bf);
   a.U = (const float4*)h->fluid_pad.p;
-  a.acc = (unsigned long long*)h->acc.p;
+  a.acc = (long long*)h->acc.p;
   a.n = h->np;
   a.ncell = h->geo.ncell;
   a.nx = h->geo.n[0];

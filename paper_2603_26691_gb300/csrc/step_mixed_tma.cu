@@ -16,11 +16,10 @@
 //     from L2), advance and relocate them, store the new state with 128-bit
 //     streaming stores, and reduce their impulses over runs of equal
 //     start-of-step cell across the warp;
-//   * each run is added, as 64-bit fixed point, to a shared deposit tile of
-//     the unit's cells plus a halo of R cells (integer shared-memory atomics:
-//     exact and order independent); runs outside it go straight to the global
-//     128-bit accumulator; at the end of the unit the tile is flushed, exactly,
-//     into the global accumulator.
+//   * each run is added once to the global carry-save fixed-point accumulator
+//     with fire-and-forget integer atomic adds (exact and independent of the
+//     order of the adds); sorted storage keeps runs long and the touched
+//     accumulator lines hot in L2.
 // Every wait is bounded: a wait that gives up sets an error flag and the CTA
 // returns.
 #include <cuda.h>
@@ -36,19 +35,24 @@ namespace {
 constexpr int kU = 8;                       // unit edge (cells)
 constexpr int kG = 3;                       // fluid halo = padding of the field
 constexpr int kTE = kU + 2 * kG;            // fluid tile edge (14)
-constexpr int kR = 2;                       // deposit halo
-constexpr int kDE = kU + 2 * kR;            // deposit tile edge (12)
 constexpr int kConsumerWarps = 11;
 constexpr int kT = kConsumerWarps * 128;    // particles per stage (1408)
 constexpr int kStages = 2;
+constexpr int kFluidBufs = 1;              // fluid tiles in flight (one reload bubble per unit)
+constexpr int kR = 2;                      // deposit halo
+constexpr int kDE = kU + 2 * kR;           // deposit tile edge (12)
+constexpr int kDepositCells = kDE * kDE * kDE;  // 1728
+constexpr int kDigits = 3;                 // 15-bit digits per value in the shared deposit tile
+constexpr int kDigitBits = 15;
+constexpr int kDepShift = 51;              // shared tile units = global units * 2^kDepShift
+constexpr int64_t kDepMaxCount = 65535;    // per-unit particles for which no digit word can overflow
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 constexpr int kFluidBytes = kTE * kTE * kTE * 16;          // 43904
-constexpr int kDepositCells = kDE * kDE * kDE;              // 1728
-constexpr int kDepositBytes = kDepositCells * 3 * 8;        // 41472
 constexpr int kStageBytes = kT * 32;                        // 45056 (FP32 layout; BF16 uses less)
-constexpr int kSmemBytes = 2 * kFluidBytes + kDepositBytes + kStages * kStageBytes + 16 * 8;
+constexpr int kDepositBytes = kDepositCells * 3 * kDigits * 4;  // 62208
+constexpr int kSmemBytes = kFluidBufs * kFluidBytes + kDepositBytes + kStages * kStageBytes + 16 * 8;
 
 // ---- PTX wrappers ----------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -116,7 +120,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 struct TmaArgs {
   MixedState s;
   const float4* __restrict__ Up;      // ghost-padded field [nz+2G][ny+2G][nx+2G]
-  unsigned long long* __restrict__ acc;
+  long long* __restrict__ acc;
   const uint32_t* __restrict__ cell_start;
   int* __restrict__ err;
   int64_t ncell;
@@ -163,48 +167,63 @@ __device__ __forceinline__ int stage_bytes(int cnt) {
   return cnt * (BF16 ? 26 : 32);
 }
 
-// round(f * 2^E) as a 64-bit integer from the float's bits (integer operations only; the
-// caller guarantees |f| * 2^E < 2^62)
-__device__ __forceinline__ long long scaled_i64(float f, int E) {
-  const uint32_t b = __float_as_uint(f);
+// periodic index for a particle that moved more than a box length in one step (rare)
+__device__ __noinline__ int wrap_index_slow(int ii, int n) {
+  ii %= n;
+  return ii < 0 ? ii + n : ii;
+}
+
+// cell index after a move of 2^22 cells or more in one step (rare); the offset is set by the caller
+__device__ __noinline__ int relocate_far(float& o, int ci, int n) {
+  const float fl = floorf(o);
+  o = fmaxf(fminf(o - fl, 0.99999994f), 0.0f);
+  long long k = ((long long)ci + (long long)fl) % n;
+  return (int)(k < 0 ? k + n : k);
+}
+
+// add round(r * 2^Es) (|.| < 2^45) to a shared deposit-tile value kept as three signed 15-bit
+// digits in int32 words (w[0], w[kDepositCells], w[2 kDepositCells]); integer operations only and
+// native 32-bit shared atomics, so the sum is exact and independent of the order of the adds
+__device__ __forceinline__ void dep_add(int* w, float r, int Es) {
+  const uint32_t b = __float_as_uint(r);
   const uint32_t ex = (b >> 23) & 0xffu;
   unsigned long long man = b & 0x7fffffu;
   if (ex != 0) man |= 0x800000ull;
-  const int s = (int)(ex == 0 ? 1 : ex) - 150 + E;
+  const int s = (int)(ex == 0 ? 1 : ex) - 150 + Es;
   unsigned long long v;
   if (s >= 0) {
     v = man << s;
   } else {
-    const int r = -s;
-    v = r < 32 ? ((man + ((1ull << r) >> 1)) >> r) : 0ull;
+    const int rr = -s;
+    v = rr < 32 ? ((man + ((1ull << rr) >> 1)) >> rr) : 0ull;
   }
-  return (b >> 31) ? -(long long)v : (long long)v;
+  const int sg = (b >> 31) ? -1 : 1;
+  const int d0 = (int)(v & 0x7fffu), d1 = (int)((v >> 15) & 0x7fffu), d2 = (int)(v >> 30);
+  if (d0) atomicAdd(w, sg * d0);
+  if (d1) atomicAdd(w + kDepositCells, sg * d1);
+  if (d2) atomicAdd(w + 2 * kDepositCells, sg * d2);
 }
 
-// commit one run sum to the global 128-bit accumulator
+// commit one run sum to the global carry-save accumulator (fire-and-forget atomic adds)
 __device__ __forceinline__ void commit_global(const TmaArgs& a, int key, float j0, float j1, float j2) {
-  unsigned long long lo, hi;
-  f32_to_i128(j0, a.E, lo, hi);
-  atomic_add_i128(a.acc + 2 * key, lo, hi);
-  f32_to_i128(j1, a.E, lo, hi);
-  atomic_add_i128(a.acc + 2 * (a.ncell + key), lo, hi);
-  f32_to_i128(j2, a.E, lo, hi);
-  atomic_add_i128(a.acc + 2 * (2 * a.ncell + key), lo, hi);
+  acc_add_f32(a.acc + kAccWords * key, j0, a.E);
+  acc_add_f32(a.acc + kAccWords * (a.ncell + key), j1, a.E);
+  acc_add_f32(a.acc + kAccWords * (2 * a.ncell + key), j2, a.E);
 }
 
 template <bool BF16>
 __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float4* fluid = reinterpret_cast<float4*>(smem);                                   // [2][kTE^3]
-  long long* dep = reinterpret_cast<long long*>(smem + 2 * kFluidBytes);             // [3][kDE^3]
-  unsigned char* ring = smem + 2 * kFluidBytes + kDepositBytes;                       // [kStages][kStageBytes]
+  float4* fluid = reinterpret_cast<float4*>(smem);                               // [kFluidBufs][kTE^3]
+  int* dep = reinterpret_cast<int*>(smem + kFluidBufs * kFluidBytes);            // [3][kDigits][kDE^3]
+  unsigned char* ring = smem + kFluidBufs * kFluidBytes + kDepositBytes;          // [kStages][kStageBytes]
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
   uint64_t* full = bars;                    // [kStages]   producer -> consumers (bytes landed)
   uint64_t* empty = bars + kStages;         // [kStages]   consumers -> producer (stage free)
   uint64_t* tile_full = bars + 2 * kStages;  // [2]        fluid tile landed
   uint64_t* tile_empty = tile_full + 2;      // [2]        consumers done with a fluid tile
-  uint64_t* dep_done = tile_empty + 2;       // [1]        all consumer warps finished a unit's deposits
+  uint64_t* dep_done = tile_empty + 2;       // [1]        every consumer warp finished a unit's deposits
   uint64_t* flush_done = dep_done + 1;       // [1]        deposit tile flushed and cleared
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -221,7 +240,7 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
     mbar_init(flush_done, kConsumerWarps);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < 3 * kDepositCells; i += blockDim.x) dep[i] = 0;
+  for (int i = threadIdx.x; i < 3 * kDigits * kDepositCells; i += blockDim.x) dep[i] = 0;
   __syncthreads();
 
   if (warp == kConsumerWarps) {
@@ -233,8 +252,8 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
         const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
         const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
         if (E <= S) continue;
-        const int buf = loaded & 1;
-        if (loaded >= 2 && !mbar_wait(&tile_empty[buf], ((loaded >> 1) - 1) & 1)) {
+        const int buf = loaded % kFluidBufs;
+        if (loaded >= kFluidBufs && !mbar_wait(&tile_empty[buf], ((loaded / kFluidBufs) - 1) & 1)) {
           atomicOr(a.err, 1);
           return;
         }
@@ -276,26 +295,20 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
   const int px = a.nx + 2 * kG, pxy = (a.nx + 2 * kG) * (a.ny + 2 * kG);
   int loaded = 0;
   int64_t gt = 0;
-  int units_done = 0;
   for (int u = blockIdx.x; u < a.nunits; u += gridDim.x) {
     const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
     const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
     if (E <= S) continue;
-    const int buf = loaded & 1;
-    if (!mbar_wait(&tile_full[buf], (loaded >> 1) & 1)) {
+    const int buf = loaded % kFluidBufs;
+    if (!mbar_wait(&tile_full[buf], (loaded / kFluidBufs) & 1)) {
       atomicOr(a.err, 4);
       return;
     }
     const float4* tile = fluid + buf * (kTE * kTE * kTE);
     int uo[3];
     unit_origin(a, u, uo[0], uo[1], uo[2]);
-    // deposit tile scale: a unit of cnt particles keeps every tile cell below 2^62
-    const int64_t count = E - S;
-    int lg = 0;
-    while ((int64_t(1) << lg) <= count) ++lg;
-    const int shift = 28 + lg;          // tile value = global integer >> shift
-    const int Es = a.E - shift;
-
+    const bool use_tile = (E - S) <= kDepMaxCount;  // every digit word stays below 2^31
+    const int Es = a.E - kDepShift;
     const int64_t A = S & ~int64_t(7);
     const int64_t Z = (E + 7) & ~int64_t(7);
     for (int64_t t0 = A; t0 < Z; t0 += kT) {
@@ -373,28 +386,33 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
           xi[0][j] = xi[1][j] = xi[2][j] = 0.5f;
           dv[j] = 1e-5f;
         }
-        key[j] = own[j] ? cell[j] : -1;  // runs are keyed by the packed start cell
       }
       int cn[4][3];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
-        int i0[3], lt[3];
+        int i0[3], lt[3], ld[3];
         float f[3];
-        bool in_tile = true;
+        bool in_tile = true, in_dep = use_tile;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const float o = xi[q][j];
           const bool hi2 = o >= 0.5f;
           i0[q] = ci[q] - (hi2 ? 0 : 1);
           f[q] = o + (hi2 ? -0.5f : 0.5f);
-          int dl = i0[q] - uo[q] + kG;   // tile-local index, periodic
+          int dl = i0[q] - uo[q] + kG;   // fluid-tile index of the stencil base, periodic
           if (dl < -kG) dl += n3[q];
           else if (dl >= n3[q] - kG) dl -= n3[q];
           const int dc = min(max(dl, 0), kTE - 2);
           in_tile = in_tile && (dc == dl);
           lt[q] = dc;
+          ld[q] = dl - kG + kR + (hi2 ? 0 : 1);  // deposit-tile index of the start cell
+          in_dep = in_dep && ((unsigned)ld[q] < (unsigned)kDE);
         }
+        // runs are keyed by the deposit-tile index, or by kDepositCells + the linear start cell
+        key[j] = !own[j] ? -1
+                 : in_dep ? ld[0] + kDE * (ld[1] + kDE * ld[2])
+                          : kDepositCells + ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
         const float4* b = tile + lt[0] + kTE * (lt[1] + kTE * lt[2]);
         float4 c000 = b[0], c100 = b[1], c010 = b[kTE], c110 = b[kTE + 1];
         float4 c001 = b[kTE * kTE], c101 = b[kTE * kTE + 1], c011 = b[kTE * kTE + kTE], c111 = b[kTE * kTE + kTE + 1];
@@ -442,35 +460,22 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
           const float dxv = fmaf(wt, a.dt, dvw * Q);
           float o = fmaf(dxv, a.inv_h[q], xi[q][j]);
           int ii;
-          if (fabsf(o) < 4194304.0f) {
+          if (__builtin_expect(fabsf(o) < 4194304.0f, 1)) {
             // whole cells carried: k = round(o - 1/2) by the 1.5 * 2^23 shift (an FP32 add and an
             // integer subtract, exact for |o| < 2^22), so no rounding or conversion instructions
             const float t = (o - 0.5f) + 12582912.0f;
-            const int k = __float_as_int(t) - 0x4B400000;
-            o = o - (t - 12582912.0f);
-            ii = ci[q] + k;
-          } else {  // moved more than 2^22 cells in one step
-            const float fl = floorf(o);
-            o = o - fl;
-            ii = (int)(((long long)ci[q] + (long long)fl) % n3[q]);
-          }
-          if (o >= 1.0f) {  // on the upper face: offset 0 of the next cell
-            o -= 1.0f;
-            ii += 1;
-          }
-          if (o < 0.0f) {   // round-half-even put a value just below a face in the cell above
-            o += 1.0f;
-            ii -= 1;
-            if (o >= 1.0f) {
+            ii = ci[q] + (__float_as_int(t) - 0x4B400000);
+            o = o - (t - 12582912.0f);  // in [0, 1]; below 0 only for |o| < 2^-24 before the shift
+            if (o >= 1.0f) {            // on the upper face: offset 0 of the next cell
               o = 0.0f;
               ii += 1;
             }
-          }
-          if (ii >= n3[q]) ii -= n3[q];
-          else if (ii < 0) ii += n3[q];
-          if ((unsigned)ii >= (unsigned)n3[q]) {  // moved more than a box length
-            ii %= n3[q];
-            if (ii < 0) ii += n3[q];
+            o = fmaxf(o, 0.0f);
+            if (ii >= n3[q]) ii -= n3[q];
+            else if (ii < 0) ii += n3[q];
+            if (__builtin_expect((unsigned)ii >= (unsigned)n3[q], 0)) ii = wrap_index_slow(ii, n3[q]);
+          } else {
+            ii = relocate_far(o, ci[q], n3[q]);
           }
           cn[j][q] = ii;
           xi[q][j] = o;
@@ -512,8 +517,10 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
           }
         }
       }
-      // ---- deposit: the lane's runs of equal start cell, added to the shared tile as 64-bit fixed
-      // point with integer atomics (exact and independent of the order of the adds) ----
+      // ---- deposit: runs of equal start cell over the warp's 128 particles (lane-local suffix sums,
+      // then a segmented suffix scan across lanes chains runs that span lanes); the lane holding
+      // a run's first particle adds it to the shared tile as 64-bit fixed point (integer atomics:
+      // exact and independent of the order of the adds) ----
       float Sx[4][3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) Sx[3][q] = J[3][q];
@@ -523,22 +530,50 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
 #pragma unroll
         for (int q = 0; q < 3; ++q) Sx[j][q] = J[j][q] + (same ? Sx[j + 1][q] : 0.0f);
       }
+      const int tail = (key[2] != key[3]) ? 3 : (key[1] != key[2]) ? 2 : (key[0] != key[1]) ? 1 : 0;
+      const int nk0 = __shfl_down_sync(0xffffffffu, key[0], 1);
+      const int nall = __shfl_down_sync(0xffffffffu, (int)(tail == 0), 1);
+      float R[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) R[q] = __shfl_down_sync(0xffffffffu, Sx[0][q], 1);
+      const bool link = (lane < 31) && (nk0 == key[3]) && (key[3] >= 0);
+      int Bl = (link && nall) ? 1 : 0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) R[q] = link ? R[q] : 0.0f;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        float t0v = __shfl_down_sync(0xffffffffu, R[0], off);
+        float t1v = __shfl_down_sync(0xffffffffu, R[1], off);
+        float t2v = __shfl_down_sync(0xffffffffu, R[2], off);
+        int tb = __shfl_down_sync(0xffffffffu, Bl, off);
+        if (lane + off > 31) {
+          tb = 0;
+          t0v = t1v = t2v = 0.0f;
+        }
+        if (Bl) {
+          R[0] += t0v;
+          R[1] += t1v;
+          R[2] += t2v;
+        }
+        Bl &= tb;
+      }
+      const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
+      const bool head_lane = (lane == 0) || (pk3 != key[0]);
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const bool start = (j == 0) || (key[j] != key[j - 1]);
+        const bool start = (j == 0) ? head_lane : (key[j] != key[j - 1]);
         if (start && key[j] >= 0) {
-          const int ci = cell_i(key[j]), cj = cell_j(key[j]), ck = cell_k(key[j]);
-          const int li = periodic_delta(ci - uo[0], a.nx) + kR;
-          const int lj = periodic_delta(cj - uo[1], a.ny) + kR;
-          const int lk = periodic_delta(ck - uo[2], a.nz) + kR;
-          if ((unsigned)li < (unsigned)kDE && (unsigned)lj < (unsigned)kDE && (unsigned)lk < (unsigned)kDE) {
-            const int t = li + kDE * (lj + kDE * lk);
-            atomicAdd((unsigned long long*)&dep[t], (unsigned long long)scaled_i64(Sx[j][0], Es));
-            atomicAdd((unsigned long long*)&dep[kDepositCells + t], (unsigned long long)scaled_i64(Sx[j][1], Es));
-            atomicAdd((unsigned long long*)&dep[2 * kDepositCells + t],
-                      (unsigned long long)scaled_i64(Sx[j][2], Es));
+          const bool to_end = j == tail;
+          const float r0 = Sx[j][0] + (to_end ? R[0] : 0.0f);
+          const float r1 = Sx[j][1] + (to_end ? R[1] : 0.0f);
+          const float r2 = Sx[j][2] + (to_end ? R[2] : 0.0f);
+          const int kk = key[j];
+          if (kk < kDepositCells) {
+            dep_add(dep + kk, r0, Es);
+            dep_add(dep + kDigits * kDepositCells + kk, r1, Es);
+            dep_add(dep + 2 * kDigits * kDepositCells + kk, r2, Es);
           } else {
-            commit_global(a, ci + a.nx * (cj + a.ny * ck), Sx[j][0], Sx[j][1], Sx[j][2]);
+            commit_global(a, kk - kDepositCells, r0, r1, r2);
           }
         }
       }
@@ -549,9 +584,8 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       mbar_arrive(&tile_empty[buf]);
       mbar_arrive(dep_done);
     }
-    ++loaded;
     // flush the deposit tile once every consumer warp has finished this unit
-    if (!mbar_wait(dep_done, units_done & 1)) {
+    if (!mbar_wait(dep_done, loaded & 1)) {
       atomicOr(a.err, 16);
       return;
     }
@@ -563,22 +597,25 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       gk = gk < 0 ? gk + a.nz : (gk >= a.nz ? gk - a.nz : gk);
       const int64_t gc = gi + (int64_t)a.nx * (gj + (int64_t)a.ny * gk);
       for (int q = 0; q < 3; ++q) {
-        const long long val = dep[q * kDepositCells + t];
+        int* w = dep + q * kDigits * kDepositCells + t;
+        const long long val = (long long)w[0] + ((long long)w[kDepositCells] << kDigitBits) +
+                              ((long long)w[2 * kDepositCells] << (2 * kDigitBits));
         if (val != 0) {
-          dep[q * kDepositCells + t] = 0;
-          const unsigned long long lo = (unsigned long long)val << shift;
-          const unsigned long long hi = (unsigned long long)(val >> (64 - shift));
-          atomic_add_i128(a.acc + 2 * (q * a.ncell + gc), lo, hi);
+          w[0] = 0;
+          w[kDepositCells] = 0;
+          w[2 * kDepositCells] = 0;
+          acc_add_mag(a.acc + kAccWords * (q * a.ncell + gc), (unsigned long long)(val < 0 ? -val : val), kDepShift,
+                      val < 0);
         }
       }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(flush_done);
-    if (!mbar_wait(flush_done, units_done & 1)) {
+    if (!mbar_wait(flush_done, loaded & 1)) {
       atomicOr(a.err, 32);
       return;
     }
-    ++units_done;
+    ++loaded;
   }
 }
 
@@ -630,7 +667,7 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
   TmaArgs a;
   a.s = carve_mixed(h->state.p, h->cap, bf);
   a.Up = (const float4*)h->fluid_pad.p;
-  a.acc = (unsigned long long*)h->acc.p;
+  a.acc = (long long*)h->acc.p;
   a.cell_start = (const uint32_t*)h->cell_start.p;
   a.err = (int*)h->flags.p;
   a.ncell = h->geo.ncell;

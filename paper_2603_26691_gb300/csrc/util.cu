@@ -199,20 +199,38 @@ __global__ void export_mixed_kernel(MixedState s, bool bf16, const uint32_t* __r
 
 // ---- accumulator ----------------------------------------------------------------------
 
-__global__ void acc_to_f64_kernel(const unsigned long long* __restrict__ acc, double* __restrict__ out, int64_t m,
+__global__ void acc_to_f64_kernel(const long long* __restrict__ acc, double* __restrict__ out, int64_t m,
                                   double inv_scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long lo = acc[2 * i], hi = acc[2 * i + 1];
-    double v = (double)(long long)hi * 0x1p64 + (double)lo;
-    out[i] = v * inv_scale;
+    unsigned long long lo;
+    long long hi;
+    acc_value(acc + kAccWords * i, lo, hi);
+    out[i] = ((double)hi * 0x1p64 + (double)lo) * inv_scale;
   }
 }
 
-// arithmetic right shift of the 128-bit values by `sh` bits (1..126), rounding half up
-__global__ void rescale_kernel(unsigned long long* __restrict__ acc, int64_t m, int sh) {
+// carry propagation: rewrite every value with digits in [0, 2^32) below a signed top word
+__global__ void normalize_kernel(long long* __restrict__ acc, int64_t m) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long lo = acc[2 * i], hi = acc[2 * i + 1];
-    // add 2^(sh-1) for rounding
+    long long* w = acc + kAccWords * i;
+    unsigned long long lo;
+    long long hi;
+    acc_value(w, lo, hi);
+    w[0] = (long long)(lo & 0xffffffffull);
+    w[1] = (long long)(lo >> 32);
+    w[2] = (long long)((unsigned long long)hi & 0xffffffffull);
+    w[3] = hi >> 32;
+  }
+}
+
+// arithmetic right shift of every value by `sh` bits (1..120), rounding half up; also normalises
+__global__ void rescale_kernel(long long* __restrict__ acc, int64_t m, int sh) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    long long* w = acc + kAccWords * i;
+    unsigned long long lo;
+    long long shi;
+    acc_value(w, lo, shi);
+    unsigned long long hi = (unsigned long long)shi;
     unsigned long long alo, ahi;
     if (sh - 1 < 64) {
       alo = 1ull << (sh - 1);
@@ -224,7 +242,7 @@ __global__ void rescale_kernel(unsigned long long* __restrict__ acc, int64_t m, 
     unsigned long long nlo = lo + alo;
     hi = hi + ahi + (nlo < lo ? 1ull : 0ull);
     lo = nlo;
-    long long shi = (long long)hi;
+    shi = (long long)hi;
     if (sh < 64) {
       lo = (lo >> sh) | (hi << (64 - sh));
       shi = shi >> sh;
@@ -232,20 +250,24 @@ __global__ void rescale_kernel(unsigned long long* __restrict__ acc, int64_t m, 
       lo = (unsigned long long)(shi >> (sh - 64));
       shi = shi >> 63;
     }
-    acc[2 * i] = lo;
-    acc[2 * i + 1] = (unsigned long long)shi;
+    w[0] = (long long)(lo & 0xffffffffull);
+    w[1] = (long long)(lo >> 32);
+    w[2] = (long long)((unsigned long long)shi & 0xffffffffull);
+    w[3] = shi >> 32;
   }
 }
 
 // exact 128-bit sums of each component over all cells
-__global__ void acc_sum_kernel(const unsigned long long* __restrict__ acc, int64_t ncell,
+__global__ void acc_sum_kernel(const long long* __restrict__ acc, int64_t ncell,
                                unsigned long long* __restrict__ out /* [3][2] */) {
   int q = blockIdx.y;
   unsigned long long lo = 0, hi = 0;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-    unsigned long long a = acc[2 * (q * ncell + c)], b = acc[2 * (q * ncell + c) + 1];
+    unsigned long long a;
+    long long b;
+    acc_value(acc + kAccWords * (q * ncell + c), a, b);
     unsigned long long n = lo + a;
-    hi += b + (n < lo ? 1ull : 0ull);
+    hi += (unsigned long long)b + (n < lo ? 1ull : 0ull);
     lo = n;
   }
   atomic_add_i128(out + 2 * q, lo, hi);
@@ -443,7 +465,7 @@ cudaError_t launch_export(st_ctx* h, int64_t first, int64_t n, double* xyz, doub
 
 cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E) {
   int64_t m = h->geo.ncell * 3;
-  acc_to_f64_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((const unsigned long long*)h->acc.p, out, m,
+  acc_to_f64_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((const long long*)h->acc.p, out, m,
                                                              std::ldexp(1.0, -E));
   h->launches += 1;
   return cudaGetLastError();
@@ -454,7 +476,7 @@ cudaError_t launch_rescale_acc(st_ctx* h, int shift) {
   while (shift > 0) {
     int s = shift > 120 ? 120 : shift;
     int64_t m = h->geo.ncell * 3;
-    rescale_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((unsigned long long*)h->acc.p, m, s);
+    rescale_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((long long*)h->acc.p, m, s);
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -463,12 +485,19 @@ cudaError_t launch_rescale_acc(st_ctx* h, int shift) {
   return cudaSuccess;
 }
 
+cudaError_t launch_normalize_acc(st_ctx* h) {
+  int64_t m = h->geo.ncell * 3;
+  normalize_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((long long*)h->acc.p, m);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]) {
   unsigned long long* r = (unsigned long long*)h->red.p;
   cudaError_t e = cudaMemsetAsync(r, 0, 6 * 8, h->stream);
   if (e != cudaSuccess) return e;
   dim3 grid(grid_for(h->geo.ncell, kThreads, 1024), 3);
-  acc_sum_kernel<<<grid, kThreads, 0, h->stream>>>((const unsigned long long*)h->acc.p, h->geo.ncell, r);
+  acc_sum_kernel<<<grid, kThreads, 0, h->stream>>>((const long long*)h->acc.p, h->geo.ncell, r);
   h->launches += 1;
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

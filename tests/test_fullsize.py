@@ -1,0 +1,140 @@
+"""Parity at full workload sizes, in the configuration bench.py times: sampled particles against the
+oracle (particles are independent given the frozen field), the per-cell sources of a seeded
+subsample run alone, and the momentum balance of the full run."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_26691_gb300 import inputs
+from tests.helpers import face_distance, linear_cells, min_image
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _populate(sim, w, n, batch=50_000_000, vmax=0.0):
+    q = inputs.lognormal_qtable()
+    sim.reserve(n)
+    for first in range(0, n, batch):
+        cnt = min(batch, n - first)
+        p, v, d, ids = sim.gen_particles(w.seed, first, cnt, q, vmax=vmax)
+        sim.add_particles(p, d, v, ids)
+
+
+def _sample_state(torch, sim, sample):
+    """State (storage order ignored) of the particles with the given ids, via an inverse map on device."""
+    pos, vel, d, ids = sim.particles(host=False)
+    inv = torch.empty_like(ids, dtype=torch.int64)
+    inv[ids.long()] = torch.arange(ids.numel(), device=ids.device)
+    rows = inv[torch.as_tensor(sample, device=ids.device)]
+    cells = torch.as_tensor(sim.cells(), device=ids.device)[rows]
+    return (pos[:, rows].cpu().numpy(), vel[:, rows].cpu().numpy(), d[rows].cpu().numpy(), cells.cpu().numpy())
+
+
+def _balance(inv0, inv1, steps, dt):
+    g = np.array([0.0, 0.0, -9.81])
+    bal = inv1[1:4] - inv0[1:4] - inv1[7] * g * steps * dt + inv1[4:7]
+    return np.abs(bal).max() / (np.abs(inv1[4:7]).max() + np.abs(inv1[7] * g * steps * dt).max())
+
+
+def test_fourier128_fp64_1e8_sampled(torch_cuda):
+    """128^3 random Fourier field (FP64), 1e8 particles, 50 steps of 5e-4, sort every 10."""
+    from paper_2603_26691_gb300.sim import Sim
+
+    torch = torch_cuda
+    w = inputs.WORKLOADS["fourier128_fp64_1e8"]
+    U = w.make_field()
+    N = w.grid
+    sim = Sim(N, precision="fp64", chunk_edge=w.chunk_edge)
+    sim.set_params(reorder_every=w.reorder_every)
+    sim.set_fluid(U)
+    _populate(sim, w, w.n)
+    inv0 = sim.invariants()
+    sim.step(w.steps, w.dt)
+    inv1 = sim.invariants()
+    sample = np.sort(np.random.default_rng(1).choice(w.n, 3000, replace=False))
+    gpos, gvel, gd, gcell = _sample_state(torch, sim, sample)
+    sim.close()
+    pos, vel, d, _ = inputs.particles_at(w.seed, sample)
+    opos, ovel, _, _ = oracle.run(oracle.make_grid(N), U, pos, vel, d, w.steps, w.dt)
+    assert np.array_equal(gd, d)
+    assert np.abs(min_image(gpos, opos)).max() <= 1e-10
+    assert (np.abs(gvel - ovel) / np.maximum(np.abs(ovel), 1.0)).max() <= 1e-10
+    far = face_distance(opos, (N, N, N)) > 1e-9
+    assert np.array_equal(gcell[far], linear_cells(opos, (N, N, N))[far])
+    assert inv1[0] == w.n
+    assert _balance(inv0, inv1, w.steps, w.dt) <= 1e-12
+
+
+def test_uniform_flow_128_1e6_closed_form(torch_cuda):
+    """The uniform-flow sub-case: u = (0.3, -0.2, 0.1), 1e6 particles with random initial velocity."""
+    from paper_2603_26691_gb300.sim import Sim
+
+    w = inputs.WORKLOADS["uniform128_fp64_1e6"]
+    N = w.grid
+    sim = Sim(N, precision="fp64", chunk_edge=w.chunk_edge)
+    sim.set_params(reorder_every=w.reorder_every)
+    sim.set_fluid(w.make_field())
+    _populate(sim, w, w.n, vmax=w.vmax)
+    sim.step(w.steps, w.dt)
+    gpos, gvel, gd, ids = sim.particles()
+    sim.close()
+    pos, vel, d, _ = inputs.particles_at(w.seed, ids.astype(np.int64), vmax=w.vmax)
+    u = np.asarray(w.uniform_u)[:, None]
+    g = np.array([0.0, 0.0, -9.81])[:, None]
+    a = 18 * 1.8e-5 / (1000.0 * d ** 2)
+    T = w.steps * w.dt
+    vinf = u + g / a
+    vT = vinf + (vel - vinf) * np.exp(-a * T)
+    xT = pos + vinf * T + (vel - vinf) * (-np.expm1(-a * T)) / a
+    assert np.abs(min_image(gpos, xT)).max() <= 1e-10
+    assert (np.abs(gvel - vT) / np.maximum(np.abs(vT), 1.0)).max() <= 1e-10
+
+
+def test_fourier256_mixed_1e9_sampled(torch_cuda):
+    """The bench workload: 256^3 FP32 Fourier field, 1e9 mixed-precision particles, 20 steps of 5e-4,
+    sort every 10 - a seeded 1e5-particle subsample against the oracle (about 20 s of single-thread
+    oracle work), the subsample's own per-cell sources, and the momentum balance of the full run."""
+    from paper_2603_26691_gb300.sim import Sim
+
+    torch = torch_cuda
+    w = inputs.WORKLOADS["fourier256_mixed_1e9"]
+    U = w.make_field()  # FP32-rounded
+    N = w.grid
+    sim = Sim(N, precision="mixed_f32", chunk_edge=w.chunk_edge)
+    sim.set_params(reorder_every=w.reorder_every)
+    sim.set_fluid(U.astype(np.float32))
+    _populate(sim, w, w.n)
+    inv0 = sim.invariants()
+    sim.step(w.steps, w.dt)
+    inv1 = sim.invariants()
+    sample = np.sort(np.random.default_rng(2).choice(w.n, 100_000, replace=False))
+    gpos, gvel, gd, gcell = _sample_state(torch, sim, sample)
+    sim.close()
+    torch.cuda.empty_cache()
+    assert inv1[0] == w.n
+    assert _balance(inv0, inv1, w.steps, w.dt) <= 1e-5
+    pos, vel, d, _ = inputs.particles_at(w.seed, sample)
+    opos, ovel, osrc, _ = oracle.run(oracle.make_grid(N), U, pos, vel, d, w.steps, w.dt)
+    h = 1.0 / N
+    assert np.abs(min_image(gpos, opos)).max() <= 1e-5 * h
+    assert (np.abs(gvel - ovel) / (np.abs(ovel) + 1.0)).max() <= 1e-5
+    far = face_distance(opos, (N, N, N)) > 1e-5
+    assert np.array_equal(gcell[far], linear_cells(opos, (N, N, N))[far])
+    # the subsample alone through the same path: per-cell sources against the oracle's
+    sub = Sim(N, precision="mixed_f32", chunk_edge=w.chunk_edge)
+    sub.set_params(reorder_every=w.reorder_every)
+    sub.set_fluid(U.astype(np.float32))
+    sub.add_particles(pos, d, vel)
+    sub.step(w.steps, w.dt)
+    gsrc = sub.sources(host=True)
+    sub.close()
+    assert np.linalg.norm(gsrc - osrc) <= 1e-5 * np.linalg.norm(osrc)
+    assert np.abs(gsrc - osrc).max() <= 1e-4 * np.abs(osrc).max()
