@@ -25,6 +25,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "st_common.cuh"
@@ -52,7 +54,8 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kFluidBytes = kTE * kTE * kTE * 16;          // 43904
 constexpr int kStageBytes = kT * 32;                        // 45056 (FP32 layout; BF16 uses less)
 constexpr int kDepositBytes = kDepositCells * 3 * kDigits * 4;  // 62208
-constexpr int kSmemBytes = kFluidBufs * kFluidBytes + kDepositBytes + kStages * kStageBytes + 16 * 8;
+constexpr int kHeadBytes = kConsumerWarps * 128 * 16;           // 22528: per-warp run records
+constexpr int kSmemBytes = kFluidBufs * kFluidBytes + kDepositBytes + kHeadBytes + kStages * kStageBytes + 16 * 8;
 
 // ---- PTX wrappers ----------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -131,6 +134,7 @@ struct TmaArgs {
   float dt, cadt, inv_ca, mcoef;
   float g[3], gdt[3];
   int E;                              // global accumulator exponent
+  float s1, s2;                       // s1 * s2 = 2^(E - kDepShift): global units -> deposit-tile units
 };
 
 // de-interleave 3 bits per level (local x bit lowest)
@@ -156,59 +160,83 @@ __device__ __forceinline__ void unit_origin(const TmaArgs& a, int u, int& ox, in
   oz = cz * B + (int)compact3(m >> 2);
 }
 
-__device__ __forceinline__ int periodic_delta(int d, int n) {
-  if (d > (n >> 1)) d -= n;
-  if (d < -(n >> 1)) d += n;
-  return d;
-}
-
 template <bool BF16>
 __device__ __forceinline__ int stage_bytes(int cnt) {
   return cnt * (BF16 ? 26 : 32);
 }
 
-// periodic index for a particle that moved more than a box length in one step (rare)
-__device__ __noinline__ int wrap_index_slow(int ii, int n) {
-  ii %= n;
-  return ii < 0 ? ii + n : ii;
-}
-
-// cell index after a move of 2^22 cells or more in one step (rare); the offset is set by the caller
-__device__ __noinline__ int relocate_far(float& o, int ci, int n) {
+// cell and offset of a coordinate that the fast relocation cannot take (rare): a move of 2^22 cells
+// or more, or of more than one box length, in one step; the cell carried is floor(o) reduced
+// periodically (fmodf is exact), the offset o - floor(o)
+struct Relocated {
+  int cell;
+  float offset;
+};
+__device__ __noinline__ Relocated relocate_general(float o, int ci, int n) {
+  if (!(fabsf(o) <= 3.0e38f)) return Relocated{ci, 0.5f};  // non-finite: keep the cell
   const float fl = floorf(o);
-  o = fmaxf(fminf(o - fl, 0.99999994f), 0.0f);
-  long long k = ((long long)ci + (long long)fl) % n;
-  return (int)(k < 0 ? k + n : k);
+  int k = (ci + (int)fmodf(fl, (float)n)) % n;
+  return Relocated{k < 0 ? k + n : k, fmaxf(fminf(o - fl, 0.99999994f), 0.0f)};
 }
 
-// add round(r * 2^Es) (|.| < 2^45) to a shared deposit-tile value kept as three signed 15-bit
-// digits in int32 words (w[0], w[kDepositCells], w[2 kDepositCells]); integer operations only and
-// native 32-bit shared atomics, so the sum is exact and independent of the order of the adds
-__device__ __forceinline__ void dep_add(int* w, float r, int Es) {
-  const uint32_t b = __float_as_uint(r);
-  const uint32_t ex = (b >> 23) & 0xffu;
-  unsigned long long man = b & 0x7fffffu;
-  if (ex != 0) man |= 0x800000ull;
-  const int s = (int)(ex == 0 ? 1 : ex) - 150 + Es;
-  unsigned long long v;
-  if (s >= 0) {
-    v = man << s;
-  } else {
-    const int rr = -s;
-    v = rr < 32 ? ((man + ((1ull << rr) >> 1)) >> rr) : 0ull;
+// trilinear interpolation of the 8 corner velocities (corner c_xyz, x fastest) at weights f
+__device__ __forceinline__ void trilerp(const float4& c000, const float4& c100, const float4& c010,
+                                        const float4& c110, const float4& c001, const float4& c101,
+                                        const float4& c011, const float4& c111, float fx, float fy, float fz,
+                                        float* up) {
+  const float ax = fmaf(fx, c100.x - c000.x, c000.x), bx = fmaf(fx, c110.x - c010.x, c010.x);
+  const float cx = fmaf(fx, c101.x - c001.x, c001.x), dx = fmaf(fx, c111.x - c011.x, c011.x);
+  const float ay = fmaf(fx, c100.y - c000.y, c000.y), by = fmaf(fx, c110.y - c010.y, c010.y);
+  const float cy = fmaf(fx, c101.y - c001.y, c001.y), dy = fmaf(fx, c111.y - c011.y, c011.y);
+  const float az = fmaf(fx, c100.z - c000.z, c000.z), bz = fmaf(fx, c110.z - c010.z, c010.z);
+  const float cz = fmaf(fx, c101.z - c001.z, c001.z), dz = fmaf(fx, c111.z - c011.z, c011.z);
+  const float ex = fmaf(fy, bx - ax, ax), gx = fmaf(fy, dx - cx, cx);
+  const float ey = fmaf(fy, by - ay, ay), gy = fmaf(fy, dy - cy, cy);
+  const float ez = fmaf(fy, bz - az, az), gz = fmaf(fy, dz - cz, cz);
+  up[0] = fmaf(fz, gx - ex, ex);
+  up[1] = fmaf(fz, gy - ey, ey);
+  up[2] = fmaf(fz, gz - ez, ez);
+}
+
+// fluid velocity of a particle outside its unit's tile, from the ghost-padded field (L2); the same
+// stencil and arithmetic as the tile path
+__device__ __noinline__ float3 gather_padded(const float4* __restrict__ Up, int px, int pxy, int cell, float o0,
+                                             float o1, float o2) {
+  const int ci[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+  const float o[3] = {o0, o1, o2};
+  int i0[3];
+  float f[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const bool hi2 = o[q] >= 0.5f;
+    i0[q] = ci[q] - (hi2 ? 0 : 1);
+    f[q] = o[q] + (hi2 ? -0.5f : 0.5f);
   }
-  const int sg = (b >> 31) ? -1 : 1;
-  const int d0 = (int)(v & 0x7fffu), d1 = (int)((v >> 15) & 0x7fffu), d2 = (int)(v >> 30);
-  if (d0) atomicAdd(w, sg * d0);
-  if (d1) atomicAdd(w + kDepositCells, sg * d1);
-  if (d2) atomicAdd(w + 2 * kDepositCells, sg * d2);
+  const float4* g = Up + (i0[0] + kG) + (int64_t)px * (i0[1] + kG) + (int64_t)pxy * (i0[2] + kG);
+  float up[3];
+  trilerp(__ldg(g), __ldg(g + 1), __ldg(g + px), __ldg(g + px + 1), __ldg(g + pxy), __ldg(g + pxy + 1),
+          __ldg(g + pxy + px), __ldg(g + pxy + px + 1), f[0], f[1], f[2], up);
+  return make_float3(up[0], up[1], up[2]);
 }
 
-// commit one run sum to the global carry-save accumulator (fire-and-forget atomic adds)
-__device__ __forceinline__ void commit_global(const TmaArgs& a, int key, float j0, float j1, float j2) {
-  acc_add_f32(a.acc + kAccWords * key, j0, a.E);
-  acc_add_f32(a.acc + kAccWords * (a.ncell + key), j1, a.E);
-  acc_add_f32(a.acc + kAccWords * (2 * a.ncell + key), j2, a.E);
+// add round(r * 2^Es) to a shared deposit-tile value kept as three signed digits in int32 words
+// (w[0] + 2^15 w[kDepositCells] + 2^30 w[2 kDepositCells]); s1 * s2 = 2^Es.  The scaled value t
+// (|t| < 2^45) is split exactly into balanced digits by round-to-nearest additions of 1.5 * 2^(23+b),
+// which leave the nearest multiple of 2^b: t = 2^30 d2 + 2^15 d1 + d0 + (t - round(t)) with
+// |d0|, |d1| <= 2^14 and |d2| <= 2^15.  Integer atomics make the sum exact and independent of the
+// order of the adds.
+__device__ __forceinline__ void dep_add(int* w, float r, float s1, float s2) {
+  const float t = __fmul_rn(__fmul_rn(r, s1), s2);
+  const float h = __fsub_rn(__fadd_rn(t, 0x1.8p53f), 0x1.8p53f);   // multiple of 2^30
+  const float l = __fsub_rn(t, h);                                   // |l| <= 2^29, exact
+  const float m = __fsub_rn(__fadd_rn(l, 0x1.8p38f), 0x1.8p38f);   // multiple of 2^15
+  const float l2 = __fsub_rn(l, m);                                  // |l2| <= 2^14, exact
+  const int d2 = __float_as_int(__fmaf_rn(h, 0x1p-30f, 12582912.0f)) - 0x4B400000;
+  const int d1 = __float_as_int(__fmaf_rn(m, 0x1p-15f, 12582912.0f)) - 0x4B400000;
+  const int d0 = __float_as_int(__fadd_rn(l2, 12582912.0f)) - 0x4B400000;
+  if (d0) atomicAdd(w, d0);
+  if (d1) atomicAdd(w + kDepositCells, d1);
+  if (d2) atomicAdd(w + 2 * kDepositCells, d2);
 }
 
 template <bool BF16>
@@ -217,7 +245,8 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
   extern __shared__ __align__(128) unsigned char smem[];
   float4* fluid = reinterpret_cast<float4*>(smem);                               // [kFluidBufs][kTE^3]
   int* dep = reinterpret_cast<int*>(smem + kFluidBufs * kFluidBytes);            // [3][kDigits][kDE^3]
-  unsigned char* ring = smem + kFluidBufs * kFluidBytes + kDepositBytes;          // [kStages][kStageBytes]
+  int4* heads = reinterpret_cast<int4*>(smem + kFluidBufs * kFluidBytes + kDepositBytes);  // [warps][128]
+  unsigned char* ring = smem + kFluidBufs * kFluidBytes + kDepositBytes + kHeadBytes;  // [kStages][kStageBytes]
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
   uint64_t* full = bars;                    // [kStages]   producer -> consumers (bytes landed)
   uint64_t* empty = bars + kStages;         // [kStages]   consumers -> producer (stage free)
@@ -308,7 +337,6 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
     int uo[3];
     unit_origin(a, u, uo[0], uo[1], uo[2]);
     const bool use_tile = (E - S) <= kDepMaxCount;  // every digit word stays below 2^31
-    const int Es = a.E - kDepShift;
     const int64_t A = S & ~int64_t(7);
     const int64_t Z = (E + 7) & ~int64_t(7);
     for (int64_t t0 = A; t0 < Z; t0 += kT) {
@@ -374,10 +402,8 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       // are computed without branches and interleave
       const int lo = (int)max((int64_t)0, min((int64_t)4, S - p0));
       const int hi = (int)max((int64_t)0, min((int64_t)4, E - p0));
-      bool own[4];
-      int key[4];
-      float J[4][3];
       const int ucell = pack_cell(uo[0], uo[1], uo[2]);
+      bool own[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         own[j] = (j >= lo) && (j < hi);
@@ -387,62 +413,55 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
           dv[j] = 1e-5f;
         }
       }
-      int cn[4][3];
+      // ---- start cell relative to the unit, deposit key, fluid gather from the tile ----
+      // A start cell within kR cells of the unit (the deposit tile) has its whole stencil inside
+      // the fluid tile; the rest ("far" particles) read the padded field and commit globally.
+      int key[4];
+      float up[4][3];
+      unsigned far = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
-        int i0[3], lt[3], ld[3];
+        int rc[3], rb[3];
         float f[3];
-        bool in_tile = true, in_dep = use_tile;
+        bool in_dep = true;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const float o = xi[q][j];
           const bool hi2 = o >= 0.5f;
-          i0[q] = ci[q] - (hi2 ? 0 : 1);
           f[q] = o + (hi2 ? -0.5f : 0.5f);
-          int dl = i0[q] - uo[q] + kG;   // fluid-tile index of the stencil base, periodic
-          if (dl < -kG) dl += n3[q];
-          else if (dl >= n3[q] - kG) dl -= n3[q];
-          const int dc = min(max(dl, 0), kTE - 2);
-          in_tile = in_tile && (dc == dl);
-          lt[q] = dc;
-          ld[q] = dl - kG + kR + (hi2 ? 0 : 1);  // deposit-tile index of the start cell
-          in_dep = in_dep && ((unsigned)ld[q] < (unsigned)kDE);
+          int r = ci[q] - uo[q];  // periodic offset from the unit origin, valid within the tile
+          if (r >= n3[q] - kR) r -= n3[q];
+          else if (r < kDE - kR - n3[q]) r += n3[q];
+          in_dep = in_dep && ((unsigned)(r + kR) < (unsigned)kDE);
+          rc[q] = r;
+          rb[q] = r - (hi2 ? 0 : 1);  // stencil base relative to the unit origin
         }
-        // runs are keyed by the deposit-tile index, or by kDepositCells + the linear start cell
-        key[j] = !own[j] ? -1
-                 : in_dep ? ld[0] + kDE * (ld[1] + kDE * ld[2])
-                          : kDepositCells + ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
-        const float4* b = tile + lt[0] + kTE * (lt[1] + kTE * lt[2]);
-        float4 c000 = b[0], c100 = b[1], c010 = b[kTE], c110 = b[kTE + 1];
-        float4 c001 = b[kTE * kTE], c101 = b[kTE * kTE + 1], c011 = b[kTE * kTE + kTE], c111 = b[kTE * kTE + kTE + 1];
-        if (!in_tile) {  // drifted out of the unit's halo: read the padded field (L2)
-          const float4* g = a.Up + (i0[0] + kG) + (int64_t)px * (i0[1] + kG) + (int64_t)pxy * (i0[2] + kG);
-          c000 = __ldg(g);
-          c100 = __ldg(g + 1);
-          c010 = __ldg(g + px);
-          c110 = __ldg(g + px + 1);
-          c001 = __ldg(g + pxy);
-          c101 = __ldg(g + pxy + 1);
-          c011 = __ldg(g + pxy + px);
-          c111 = __ldg(g + pxy + px + 1);
+        const int tofs = in_dep ? (rb[0] + kG) + kTE * ((rb[1] + kG) + kTE * (rb[2] + kG)) : 0;
+        key[j] = !own[j]                ? -1
+                 : (in_dep && use_tile) ? (rc[0] + kR) + kDE * ((rc[1] + kR) + kDE * (rc[2] + kR))
+                                        : kDepositCells + ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
+        far |= in_dep ? 0u : (1u << j);
+        const float4* b = tile + tofs;
+        trilerp(b[0], b[1], b[kTE], b[kTE + 1], b[kTE * kTE], b[kTE * kTE + 1], b[kTE * kTE + kTE],
+                b[kTE * kTE + kTE + 1], f[0], f[1], f[2], up[j]);
+      }
+      if (__builtin_expect(far != 0, 0)) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (far & (1u << j)) {
+            const float3 g = gather_padded(a.Up, px, pxy, cell[j], xi[0][j], xi[1][j], xi[2][j]);
+            up[j][0] = g.x;
+            up[j][1] = g.y;
+            up[j][2] = g.z;
+          }
         }
-        float up[3];
-        {
-          const float fx = f[0], fy = f[1], fz = f[2];
-          const float ax = fmaf(fx, c100.x - c000.x, c000.x), bx = fmaf(fx, c110.x - c010.x, c010.x);
-          const float cx = fmaf(fx, c101.x - c001.x, c001.x), dx = fmaf(fx, c111.x - c011.x, c011.x);
-          const float ay = fmaf(fx, c100.y - c000.y, c000.y), by = fmaf(fx, c110.y - c010.y, c010.y);
-          const float cy = fmaf(fx, c101.y - c001.y, c001.y), dy = fmaf(fx, c111.y - c011.y, c011.y);
-          const float az = fmaf(fx, c100.z - c000.z, c000.z), bz = fmaf(fx, c110.z - c010.z, c010.z);
-          const float cz = fmaf(fx, c101.z - c001.z, c001.z), dz = fmaf(fx, c111.z - c011.z, c011.z);
-          const float ex = fmaf(fy, bx - ax, ax), gx = fmaf(fy, dx - cx, cx);
-          const float ey = fmaf(fy, by - ay, ay), gy = fmaf(fy, dy - cy, cy);
-          const float ez = fmaf(fy, bz - az, az), gz = fmaf(fy, dz - cz, cz);
-          up[0] = fmaf(fz, gx - ex, ex);
-          up[1] = fmaf(fz, gy - ey, ey);
-          up[2] = fmaf(fz, gz - ez, ez);
-        }
+      }
+      // ---- drag and gravity (exponential integrator), relocation, exchanged momentum ----
+      float J[4][3];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
         const float d = dv[j];
         const float dd = d * d;
         const float adt = a.cadt * rcp_approx(dd);
@@ -451,40 +470,40 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
         const float inv_a = dd * a.inv_ca;
         const float Q = E1 * inv_a;
         const float m = a.mcoef * dd * d;
+        float oraw[3];
+        int ii[3];
+        bool bad = false;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const float wt = fmaf(a.g[q], inv_a, up[q]);
+          const float wt = fmaf(a.g[q], inv_a, up[j][q]);
           const float dvw = v[q][j] - wt;
           float vn = fmaf(dvw, Ee, wt);
           if (BF16) vn = __bfloat162float(__float2bfloat16_rn(vn));
           const float dxv = fmaf(wt, a.dt, dvw * Q);
-          float o = fmaf(dxv, a.inv_h[q], xi[q][j]);
-          int ii;
-          if (__builtin_expect(fabsf(o) < 4194304.0f, 1)) {
-            // whole cells carried: k = round(o - 1/2) by the 1.5 * 2^23 shift (an FP32 add and an
-            // integer subtract, exact for |o| < 2^22), so no rounding or conversion instructions
-            const float t = (o - 0.5f) + 12582912.0f;
-            ii = ci[q] + (__float_as_int(t) - 0x4B400000);
-            o = o - (t - 12582912.0f);  // in [0, 1]; below 0 only for |o| < 2^-24 before the shift
-            if (o >= 1.0f) {            // on the upper face: offset 0 of the next cell
-              o = 0.0f;
-              ii += 1;
-            }
-            o = fmaxf(o, 0.0f);
-            if (ii >= n3[q]) ii -= n3[q];
-            else if (ii < 0) ii += n3[q];
-            if (__builtin_expect((unsigned)ii >= (unsigned)n3[q], 0)) ii = wrap_index_slow(ii, n3[q]);
-          } else {
-            ii = relocate_far(o, ci[q], n3[q]);
-          }
-          cn[j][q] = ii;
-          xi[q][j] = o;
+          const float o = fmaf(dxv, a.inv_h[q], xi[q][j]);
+          oraw[q] = o;
+          // whole cells carried: floor(o) from an add of 1.5 * 2^23 rounded toward -inf (exact for
+          // |o| < 2^22), so no conversion instructions; the offset o - floor(o) lies in [0, 1]
+          const float t = __fadd_rd(o, 12582912.0f);
+          int k = (int)((unsigned)ci[q] + (unsigned)(__float_as_int(t) - 0x4B400000));
+          if (k >= n3[q]) k -= n3[q];
+          else if (k < 0) k += n3[q];
+          bad = bad || !(fabsf(o) < 4194304.0f) || ((unsigned)k >= (unsigned)n3[q]);
+          ii[q] = k;
+          xi[q][j] = fminf(o - (t - 12582912.0f), 0.99999994f);
           J[j][q] = own[j] ? -m * ((vn - v[q][j]) - a.gdt[q]) : 0.0f;
           v[q][j] = vn;
         }
-      }
+        if (__builtin_expect(bad, 0)) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) cell[j] = pack_cell(cn[j][0], cn[j][1], cn[j][2]);
+          for (int q = 0; q < 3; ++q) {
+            const Relocated rl = relocate_general(oraw[q], ci[q], n3[q]);
+            ii[q] = rl.cell;
+            xi[q][j] = rl.offset;
+          }
+        }
+        cell[j] = pack_cell(ii[0], ii[1], ii[2]);
+      }
       // ---- store the owned particles (128-bit when the lane owns all four) ----
       const bool all_own = own[0] && own[1] && own[2] && own[3];
       if (all_own) {
@@ -518,9 +537,7 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
         }
       }
       // ---- deposit: runs of equal start cell over the warp's 128 particles (lane-local suffix sums,
-      // then a segmented suffix scan across lanes chains runs that span lanes); the lane holding
-      // a run's first particle adds it to the shared tile as 64-bit fixed point (integer atomics:
-      // exact and independent of the order of the adds) ----
+      // then a segmented suffix scan across lanes chains runs that span lanes) ----
       float Sx[4][3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) Sx[3][q] = J[3][q];
@@ -559,23 +576,35 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       }
       const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
       const bool head_lane = (lane == 0) || (pk3 != key[0]);
+      // the run sums, one {key, J} record per run, packed into the warp's scratch in (j, lane)
+      // order; then each lane takes one component of one record at a time, so a step with few
+      // runs costs one pass and a drifted one ceil(3 runs / 32)
+      int4* hs = heads + warp * 128;
+      const unsigned lt_mask = (1u << lane) - 1u;
+      int nh = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const bool start = (j == 0) ? head_lane : (key[j] != key[j - 1]);
-        if (start && key[j] >= 0) {
+        const bool start = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
+        const unsigned hm = __ballot_sync(0xffffffffu, start);
+        if (start) {
           const bool to_end = j == tail;
-          const float r0 = Sx[j][0] + (to_end ? R[0] : 0.0f);
-          const float r1 = Sx[j][1] + (to_end ? R[1] : 0.0f);
-          const float r2 = Sx[j][2] + (to_end ? R[2] : 0.0f);
-          const int kk = key[j];
-          if (kk < kDepositCells) {
-            dep_add(dep + kk, r0, Es);
-            dep_add(dep + kDigits * kDepositCells + kk, r1, Es);
-            dep_add(dep + 2 * kDigits * kDepositCells + kk, r2, Es);
-          } else {
-            commit_global(a, kk - kDepositCells, r0, r1, r2);
-          }
+          hs[nh + __popc(hm & lt_mask)] =
+              make_int4(key[j], __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f)),
+                        __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f)),
+                        __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f)));
         }
+        nh += __popc(hm);
+      }
+      __syncwarp();
+      for (unsigned vv = lane; vv < 3u * nh; vv += 32) {
+        const unsigned e = vv / 3u, comp = vv - 3u * e;
+        const int* rec = reinterpret_cast<const int*>(hs + e);
+        const int kk = rec[0];
+        const float r = __int_as_float(rec[1 + comp]);
+        if (kk < kDepositCells)
+          dep_add(dep + comp * (kDigits * kDepositCells) + kk, r, a.s1, a.s2);
+        else
+          acc_add_f32(a.acc + kAccWords * (comp * a.ncell + (kk - kDepositCells)), r, a.E);
       }
     }
     // all gathers of this unit are done: the producer may reuse its fluid buffer
@@ -690,6 +719,13 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
   a.inv_ca = (float)(1.0 / p.ca);
   a.mcoef = (float)p.mcoef;
   a.E = p.E;
+  {
+    // 2^(E - kDepShift) as two representable factors; beyond +-250 every scaled impulse is 0 or
+    // overflows the bound the exponent was chosen for, so clamping changes nothing
+    const int Es = std::min(std::max(p.E - kDepShift, -250), 250);
+    a.s1 = std::ldexp(1.0f, Es / 2);
+    a.s2 = std::ldexp(1.0f, Es - Es / 2);
+  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
   int grid = sms > 0 ? sms : 152;
