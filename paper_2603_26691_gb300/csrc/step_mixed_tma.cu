@@ -44,6 +44,7 @@ constexpr int kFluidBufs = 1;              // fluid tiles in flight (one reload 
 constexpr int kR = 2;                      // deposit halo
 constexpr int kDE = kU + 2 * kR;           // deposit tile edge (12)
 constexpr int kDepositCells = kDE * kDE * kDE;  // 1728
+constexpr int kScanLanes = 8;              // runs are chained across at most this many lanes
 constexpr int kDigits = 3;                 // 15-bit digits per value in the shared deposit tile
 constexpr int kDigitBits = 15;
 constexpr int kDepShift = 51;              // shared tile units = global units * 2^kDepShift
@@ -179,22 +180,58 @@ __device__ __noinline__ Relocated relocate_general(float o, int ci, int n) {
   return Relocated{k < 0 ? k + n : k, fmaxf(fminf(o - fl, 0.99999994f), 0.0f)};
 }
 
-// trilinear interpolation of the 8 corner velocities (corner c_xyz, x fastest) at weights f
+// two-lane FP32 arithmetic (one instruction for a register pair; round-to-nearest, no flush to
+// zero, so each lane rounds exactly as the scalar operation would)
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// lerp c0 + w (c1 - c0) on the (x, y) pair
+__device__ __forceinline__ unsigned long long lerp2(unsigned long long w, unsigned long long c0, unsigned long long c1) {
+  return fma2(w, sub2(c1, c0), c0);
+}
+
+// trilinear interpolation of the 8 corner velocities (corner c_xyz, x fastest) at weights f: the
+// x and y components as register pairs, z alone; the same operations and rounding per component
+// as c0 + f (c1 - c0) applied along x, then y, then z
 __device__ __forceinline__ void trilerp(const float4& c000, const float4& c100, const float4& c010,
                                         const float4& c110, const float4& c001, const float4& c101,
                                         const float4& c011, const float4& c111, float fx, float fy, float fz,
                                         float* up) {
-  const float ax = fmaf(fx, c100.x - c000.x, c000.x), bx = fmaf(fx, c110.x - c010.x, c010.x);
-  const float cx = fmaf(fx, c101.x - c001.x, c001.x), dx = fmaf(fx, c111.x - c011.x, c011.x);
-  const float ay = fmaf(fx, c100.y - c000.y, c000.y), by = fmaf(fx, c110.y - c010.y, c010.y);
-  const float cy = fmaf(fx, c101.y - c001.y, c001.y), dy = fmaf(fx, c111.y - c011.y, c011.y);
+  const unsigned long long FX = pack2(fx, fx), FY = pack2(fy, fy), FZ = pack2(fz, fz);
+  const unsigned long long a = lerp2(FX, pack2(c000.x, c000.y), pack2(c100.x, c100.y));
+  const unsigned long long b = lerp2(FX, pack2(c010.x, c010.y), pack2(c110.x, c110.y));
+  const unsigned long long c = lerp2(FX, pack2(c001.x, c001.y), pack2(c101.x, c101.y));
+  const unsigned long long d = lerp2(FX, pack2(c011.x, c011.y), pack2(c111.x, c111.y));
+  const unsigned long long e = lerp2(FY, a, b), g = lerp2(FY, c, d);
+  unpack2(lerp2(FZ, e, g), up[0], up[1]);
   const float az = fmaf(fx, c100.z - c000.z, c000.z), bz = fmaf(fx, c110.z - c010.z, c010.z);
   const float cz = fmaf(fx, c101.z - c001.z, c001.z), dz = fmaf(fx, c111.z - c011.z, c011.z);
-  const float ex = fmaf(fy, bx - ax, ax), gx = fmaf(fy, dx - cx, cx);
-  const float ey = fmaf(fy, by - ay, ay), gy = fmaf(fy, dy - cy, cy);
   const float ez = fmaf(fy, bz - az, az), gz = fmaf(fy, dz - cz, cz);
-  up[0] = fmaf(fz, gx - ex, ex);
-  up[1] = fmaf(fz, gy - ey, ey);
   up[2] = fmaf(fz, gz - ez, ez);
 }
 
@@ -219,27 +256,54 @@ __device__ __noinline__ float3 gather_padded(const float4* __restrict__ Up, int 
   return make_float3(up[0], up[1], up[2]);
 }
 
-// add round(r * 2^Es) to a shared deposit-tile value kept as three signed digits in int32 words
-// (w[0] + 2^15 w[kDepositCells] + 2^30 w[2 kDepositCells]); s1 * s2 = 2^Es.  The scaled value t
-// (|t| < 2^45) is split exactly into balanced digits by round-to-nearest additions of 1.5 * 2^(23+b),
-// which leave the nearest multiple of 2^b: t = 2^30 d2 + 2^15 d1 + d0 + (t - round(t)) with
-// |d0|, |d1| <= 2^14 and |d2| <= 2^15.  Integer atomics make the sum exact and independent of the
-// order of the adds.
-__device__ __forceinline__ void dep_add(int* w, float r, float s1, float s2) {
-  const float t = __fmul_rn(__fmul_rn(r, s1), s2);
-  const float h = __fsub_rn(__fadd_rn(t, 0x1.8p53f), 0x1.8p53f);   // multiple of 2^30
-  const float l = __fsub_rn(t, h);                                   // |l| <= 2^29, exact
-  const float m = __fsub_rn(__fadd_rn(l, 0x1.8p38f), 0x1.8p38f);   // multiple of 2^15
-  const float l2 = __fsub_rn(l, m);                                  // |l2| <= 2^14, exact
-  const int d2 = __float_as_int(__fmaf_rn(h, 0x1p-30f, 12582912.0f)) - 0x4B400000;
-  const int d1 = __float_as_int(__fmaf_rn(m, 0x1p-15f, 12582912.0f)) - 0x4B400000;
-  const int d0 = __float_as_int(__fadd_rn(l2, 12582912.0f)) - 0x4B400000;
-  if (d0) atomicAdd(w, d0);
-  if (d1) atomicAdd(w + kDepositCells, d1);
-  if (d2) atomicAdd(w + 2 * kDepositCells, d2);
+// add round(r_q * 2^Es), q = 0, 1, 2, to the shared deposit-tile values of one cell, each kept as
+// three signed digits in int32 words (w[0] + 2^15 w[kDepositCells] + 2^30 w[2 kDepositCells], the
+// components kDigits kDepositCells words apart); s1 * s2 = 2^Es.  Each scaled value t
+// (|t| < 2^45) is split exactly into balanced digits by round-to-nearest additions of
+// 1.5 * 2^(23+b), which leave the nearest multiple of 2^b: t = 2^30 d2 + 2^15 d1 + d0 +
+// (t - round(t)) with |d0|, |d1| <= 2^14 and |d2| <= 2^15.  Components 0 and 1 are split as a
+// register pair.  Integer atomics make the sums exact and independent of the order of the adds.
+__device__ __forceinline__ void digits1(float t, int& d0, int& d1, int& d2) {
+  const float h = __fsub_rn(__fadd_rn(t, 0x1.8p53f), 0x1.8p53f);  // multiple of 2^30
+  const float l = __fsub_rn(t, h);                                  // |l| <= 2^29, exact
+  const float m = __fsub_rn(__fadd_rn(l, 0x1.8p38f), 0x1.8p38f);  // multiple of 2^15
+  const float l2 = __fsub_rn(l, m);                                 // |l2| <= 2^14, exact
+  d2 = __float_as_int(__fmaf_rn(h, 0x1p-30f, 12582912.0f)) - 0x4B400000;
+  d1 = __float_as_int(__fmaf_rn(m, 0x1p-15f, 12582912.0f)) - 0x4B400000;
+  d0 = __float_as_int(__fadd_rn(l2, 12582912.0f)) - 0x4B400000;
+}
+__device__ __forceinline__ void digits2(unsigned long long t, int* d0, int* d1, int* d2) {
+  const unsigned long long C53 = pack2(0x1.8p53f, 0x1.8p53f), C38 = pack2(0x1.8p38f, 0x1.8p38f);
+  const unsigned long long C23 = pack2(12582912.0f, 12582912.0f);
+  const unsigned long long h = sub2(add2(t, C53), C53);
+  const unsigned long long l = sub2(t, h);
+  const unsigned long long m = sub2(add2(l, C38), C38);
+  const unsigned long long l2 = sub2(l, m);
+  float a, b;
+  unpack2(fma2(h, pack2(0x1p-30f, 0x1p-30f), C23), a, b);
+  d2[0] = __float_as_int(a) - 0x4B400000;
+  d2[1] = __float_as_int(b) - 0x4B400000;
+  unpack2(fma2(m, pack2(0x1p-15f, 0x1p-15f), C23), a, b);
+  d1[0] = __float_as_int(a) - 0x4B400000;
+  d1[1] = __float_as_int(b) - 0x4B400000;
+  unpack2(add2(l2, C23), a, b);
+  d0[0] = __float_as_int(a) - 0x4B400000;
+  d0[1] = __float_as_int(b) - 0x4B400000;
+}
+__device__ __forceinline__ void dep_add3(int* w, float r0, float r1, float r2, float s1, float s2) {
+  int d0[3], d1[3], d2[3];
+  digits2(mul2(mul2(pack2(r0, r1), pack2(s1, s1)), pack2(s2, s2)), d0, d1, d2);
+  digits1(__fmul_rn(__fmul_rn(r2, s1), s2), d0[2], d1[2], d2[2]);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    int* wq = w + q * (kDigits * kDepositCells);
+    if (d0[q]) atomicAdd(wq, d0[q]);
+    if (d1[q]) atomicAdd(wq + kDepositCells, d1[q]);
+    if (d2[q]) atomicAdd(wq + 2 * kDepositCells, d2[q]);
+  }
 }
 
-template <bool BF16>
+template <bool BF16, bool PW2>
 __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -398,8 +462,8 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       ++gt;
 
       // owned particles of this lane: [lo, hi) of 0..3 (the rest belong to neighbouring units
-      // or lie past the unit); the others are replaced by a harmless particle so that all four
-      // are computed without branches and interleave
+      // or lie past the unit); the others are computed too, without branches, from the unit's
+      // origin cell so that every tile read stays in bounds, and neither stored nor deposited
       const int lo = (int)max((int64_t)0, min((int64_t)4, S - p0));
       const int hi = (int)max((int64_t)0, min((int64_t)4, E - p0));
       const int ucell = pack_cell(uo[0], uo[1], uo[2]);
@@ -407,61 +471,52 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         own[j] = (j >= lo) && (j < hi);
-        if (!own[j]) {
-          cell[j] = ucell;
-          xi[0][j] = xi[1][j] = xi[2][j] = 0.5f;
-          dv[j] = 1e-5f;
-        }
+        if (!own[j]) cell[j] = ucell;
       }
-      // ---- start cell relative to the unit, deposit key, fluid gather from the tile ----
-      // A start cell within kR cells of the unit (the deposit tile) has its whole stencil inside
-      // the fluid tile; the rest ("far" particles) read the padded field and commit globally.
+      // ---- per particle: start cell relative to the unit, deposit key, fluid gather, drag and
+      // gravity (exponential integrator), relocation, exchanged momentum.  A start cell within kR
+      // cells of the unit (the deposit tile) has its whole stencil inside the fluid tile; the rest
+      // ("far" particles, rare) read the padded field and commit to the global accumulator.
       int key[4];
-      float up[4][3];
-      unsigned far = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
-        int rc[3], rb[3];
-        float f[3];
-        bool in_dep = true;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float o = xi[q][j];
-          const bool hi2 = o >= 0.5f;
-          f[q] = o + (hi2 ? -0.5f : 0.5f);
-          int r = ci[q] - uo[q];  // periodic offset from the unit origin, valid within the tile
-          if (r >= n3[q] - kR) r -= n3[q];
-          else if (r < kDE - kR - n3[q]) r += n3[q];
-          in_dep = in_dep && ((unsigned)(r + kR) < (unsigned)kDE);
-          rc[q] = r;
-          rb[q] = r - (hi2 ? 0 : 1);  // stencil base relative to the unit origin
-        }
-        const int tofs = in_dep ? (rb[0] + kG) + kTE * ((rb[1] + kG) + kTE * (rb[2] + kG)) : 0;
-        key[j] = !own[j]                ? -1
-                 : (in_dep && use_tile) ? (rc[0] + kR) + kDE * ((rc[1] + kR) + kDE * (rc[2] + kR))
-                                        : kDepositCells + ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
-        far |= in_dep ? 0u : (1u << j);
-        const float4* b = tile + tofs;
-        trilerp(b[0], b[1], b[kTE], b[kTE + 1], b[kTE * kTE], b[kTE * kTE + 1], b[kTE * kTE + kTE],
-                b[kTE * kTE + kTE + 1], f[0], f[1], f[2], up[j]);
-      }
-      if (__builtin_expect(far != 0, 0)) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (far & (1u << j)) {
-            const float3 g = gather_padded(a.Up, px, pxy, cell[j], xi[0][j], xi[1][j], xi[2][j]);
-            up[j][0] = g.x;
-            up[j][1] = g.y;
-            up[j][2] = g.z;
-          }
-        }
-      }
-      // ---- drag and gravity (exponential integrator), relocation, exchanged momentum ----
       float J[4][3];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
+        float up[3];
+        {
+          int rc[3], rb[3];
+          float f[3];
+          bool in_dep = true;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float o = xi[q][j];
+            const bool hi2 = o >= 0.5f;
+            f[q] = o + (hi2 ? -0.5f : 0.5f);
+            int r = ci[q] - uo[q];  // periodic offset from the unit origin, valid within the tile
+            if (PW2) {
+              r = ((r + kR) & (n3[q] - 1)) - kR;
+            } else {
+              if (r >= n3[q] - kR) r -= n3[q];
+              else if (r < kDE - kR - n3[q]) r += n3[q];
+            }
+            in_dep = in_dep && ((unsigned)(r + kR) < (unsigned)kDE);
+            rc[q] = r;
+            rb[q] = r - (hi2 ? 0 : 1);  // stencil base relative to the unit origin
+          }
+          const int tofs = in_dep ? (rb[0] + kG) + kTE * ((rb[1] + kG) + kTE * (rb[2] + kG)) : 0;
+          key[j] = !own[j]                ? -1
+                   : (in_dep && use_tile) ? (rc[0] + kR) + kDE * ((rc[1] + kR) + kDE * (rc[2] + kR))
+                                          : kDepositCells + ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
+          const float4* b = tile + tofs;
+          trilerp(b[0], b[1], b[kTE], b[kTE + 1], b[kTE * kTE], b[kTE * kTE + 1], b[kTE * kTE + kTE],
+                  b[kTE * kTE + kTE + 1], f[0], f[1], f[2], up);
+          if (__builtin_expect(!in_dep, 0)) {
+            const float3 g = gather_padded(a.Up, px, pxy, cell[j], xi[0][j], xi[1][j], xi[2][j]);
+            up[0] = g.x;
+            up[1] = g.y;
+            up[2] = g.z;
+          }
+        }
         const float d = dv[j];
         const float dd = d * d;
         const float adt = a.cadt * rcp_approx(dd);
@@ -475,7 +530,7 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
         bool bad = false;
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const float wt = fmaf(a.g[q], inv_a, up[j][q]);
+          const float wt = fmaf(a.g[q], inv_a, up[q]);
           const float dvw = v[q][j] - wt;
           float vn = fmaf(dvw, Ee, wt);
           if (BF16) vn = __bfloat162float(__float2bfloat16_rn(vn));
@@ -486,12 +541,17 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
           // |o| < 2^22), so no conversion instructions; the offset o - floor(o) lies in [0, 1]
           const float t = __fadd_rd(o, 12582912.0f);
           int k = (int)((unsigned)ci[q] + (unsigned)(__float_as_int(t) - 0x4B400000));
-          if (k >= n3[q]) k -= n3[q];
-          else if (k < 0) k += n3[q];
-          bad = bad || !(fabsf(o) < 4194304.0f) || ((unsigned)k >= (unsigned)n3[q]);
+          if (PW2) {
+            k &= n3[q] - 1;  // any whole-cell move of fewer than 2^22 cells
+            bad = bad || !(fabsf(o) < 4194304.0f);
+          } else {
+            if (k >= n3[q]) k -= n3[q];
+            else if (k < 0) k += n3[q];
+            bad = bad || !(fabsf(o) < 4194304.0f) || ((unsigned)k >= (unsigned)n3[q]);
+          }
           ii[q] = k;
           xi[q][j] = fminf(o - (t - 12582912.0f), 0.99999994f);
-          J[j][q] = own[j] ? -m * ((vn - v[q][j]) - a.gdt[q]) : 0.0f;
+          J[j][q] = -m * ((vn - v[q][j]) - a.gdt[q]);
           v[q][j] = vn;
         }
         if (__builtin_expect(bad, 0)) {
@@ -553,17 +613,18 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       float R[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) R[q] = __shfl_down_sync(0xffffffffu, Sx[0][q], 1);
-      const bool link = (lane < 31) && (nk0 == key[3]) && (key[3] >= 0);
+      const int glane = lane & (kScanLanes - 1);
+      const bool link = (glane < kScanLanes - 1) && (nk0 == key[3]) && (key[3] >= 0);
       int Bl = (link && nall) ? 1 : 0;
 #pragma unroll
       for (int q = 0; q < 3; ++q) R[q] = link ? R[q] : 0.0f;
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
+      for (int off = 1; off < kScanLanes; off <<= 1) {
         float t0v = __shfl_down_sync(0xffffffffu, R[0], off);
         float t1v = __shfl_down_sync(0xffffffffu, R[1], off);
         float t2v = __shfl_down_sync(0xffffffffu, R[2], off);
         int tb = __shfl_down_sync(0xffffffffu, Bl, off);
-        if (lane + off > 31) {
+        if (glane + off > kScanLanes - 1) {
           tb = 0;
           t0v = t1v = t2v = 0.0f;
         }
@@ -575,36 +636,42 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
         Bl &= tb;
       }
       const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
-      const bool head_lane = (lane == 0) || (pk3 != key[0]);
-      // the run sums, one {key, J} record per run, packed into the warp's scratch in (j, lane)
-      // order; then each lane takes one component of one record at a time, so a step with few
-      // runs costs one pass and a drifted one ceil(3 runs / 32)
+      const bool head_lane = (glane == 0) || (pk3 != key[0]);
+      // the run sums, one {J, key} record per run, packed into the warp's scratch in (j, lane)
+      // order - deposit-tile records from the front, the rare global ones from the back; then each
+      // lane takes one record at a time, so a step with few runs costs one pass
       int4* hs = heads + warp * 128;
       const unsigned lt_mask = (1u << lane) - 1u;
-      int nh = 0;
+      int nt = 0, nf = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const bool start = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
-        const unsigned hm = __ballot_sync(0xffffffffu, start);
+        const bool glob = key[j] >= kDepositCells;
+        const unsigned tm = __ballot_sync(0xffffffffu, start && !glob);
+        const unsigned fm = __ballot_sync(0xffffffffu, start && glob);
         if (start) {
           const bool to_end = j == tail;
-          hs[nh + __popc(hm & lt_mask)] =
-              make_int4(key[j], __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f)),
-                        __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f)),
-                        __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f)));
+          const int slot = glob ? 127 - (nf + __popc(fm & lt_mask)) : nt + __popc(tm & lt_mask);
+          hs[slot] = make_int4(__float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f)),
+                               __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f)),
+                               __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f)), key[j]);
         }
-        nh += __popc(hm);
+        nt += __popc(tm);
+        nf += __popc(fm);
       }
       __syncwarp();
-      for (unsigned vv = lane; vv < 3u * nh; vv += 32) {
-        const unsigned e = vv / 3u, comp = vv - 3u * e;
-        const int* rec = reinterpret_cast<const int*>(hs + e);
-        const int kk = rec[0];
-        const float r = __int_as_float(rec[1 + comp]);
-        if (kk < kDepositCells)
-          dep_add(dep + comp * (kDigits * kDepositCells) + kk, r, a.s1, a.s2);
-        else
-          acc_add_f32(a.acc + kAccWords * (comp * a.ncell + (kk - kDepositCells)), r, a.E);
+      for (int e = lane; e < nt; e += 32) {
+        const int4 rec = hs[e];
+        dep_add3(dep + rec.w, __int_as_float(rec.x), __int_as_float(rec.y), __int_as_float(rec.z), a.s1, a.s2);
+      }
+      if (__builtin_expect(nf != 0, 0)) {
+        for (int e = lane; e < nf; e += 32) {
+          const int4 rec = hs[127 - e];
+          const int64_t c = rec.w - kDepositCells;
+          acc_add_f32(a.acc + kAccWords * c, __int_as_float(rec.x), a.E);
+          acc_add_f32(a.acc + kAccWords * (a.ncell + c), __int_as_float(rec.y), a.E);
+          acc_add_f32(a.acc + kAccWords * (2 * a.ncell + c), __int_as_float(rec.z), a.E);
+        }
       }
     }
     // all gathers of this unit are done: the producer may reuse its fluid buffer
@@ -671,15 +738,18 @@ bool tma_step_supported(const st_ctx* h) {
 }
 
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
-  static bool attr_set[2] = {false, false};
   const bool bf = h->prec == ST_MIXED_BF16V;
-  if (!attr_set[bf]) {
-    cudaError_t e = bf ? cudaFuncSetAttribute(step_mixed_tma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              kSmemBytes)
-                       : cudaFuncSetAttribute(step_mixed_tma_kernel<false>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  bool pw2 = true;
+  for (int q = 0; q < 3; ++q) pw2 = pw2 && (h->geo.n[q] & (h->geo.n[q] - 1)) == 0;
+  void (*kern)(const CUtensorMap, const TmaArgs) =
+      bf ? (pw2 ? step_mixed_tma_kernel<true, true> : step_mixed_tma_kernel<true, false>)
+         : (pw2 ? step_mixed_tma_kernel<false, true> : step_mixed_tma_kernel<false, false>);
+  static bool attr_set[4] = {false, false, false, false};
+  const int variant = 2 * (int)bf + (int)pw2;
+  if (!attr_set[variant]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr_set[bf] = true;
+    attr_set[variant] = true;
   }
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
@@ -730,10 +800,7 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
   int grid = sms > 0 ? sms : 152;
   if (grid > a.nunits) grid = a.nunits;
-  if (bf)
-    step_mixed_tma_kernel<true><<<grid, kThreads, kSmemBytes, h->stream>>>(map, a);
-  else
-    step_mixed_tma_kernel<false><<<grid, kThreads, kSmemBytes, h->stream>>>(map, a);
+  kern<<<grid, kThreads, kSmemBytes, h->stream>>>(map, a);
   h->launches += 1;
   return cudaGetLastError();
 }

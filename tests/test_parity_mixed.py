@@ -134,3 +134,61 @@ def test_mixed_deterministic(Sim):
     b = _run(Sim, "mixed_f32", N, U, pos, vel, d, steps, dt)
     assert np.array_equal(a["src"], b["src"])
     assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["ids"], b["ids"])
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+def test_mixed_non_power_of_two_box_grid(Sim, prec):
+    """A 40 x 48 x 56 grid (multiples of the chunk edge, not powers of two) on a 1.25 x 1.5 x 1.75
+    box: the sorted path's periodic offsets and relocation take the general (compare-and-wrap)
+    branch, and the cells are not cubes."""
+    grid, box = (40, 48, 56), (1.25, 1.5, 1.75)
+    n, steps, dt = 150_001, 20, 5e-4
+    U = _f32(inputs.taylor_green(grid, L=box) + 0.2)
+    pos, vel, d, _ = inputs.particles(77, 0, n, L=box, vmax=0.5)
+    sim = Sim(grid, box=box, precision=prec)
+    sim.set_params(reorder_every=10)
+    sim.set_fluid(U.astype(np.float32))
+    sim.add_particles(pos, d, vel)
+    sim.step(steps, dt)
+    src = sim.sources(host=True)
+    gpos, gvel, _, ids = sim.particles()
+    cells = sim.cells()
+    sim.close()
+    order = ids.astype(np.int64)
+    G = oracle.make_grid(grid, L=box)
+    opos, ovel, osrc, _ = oracle.run(G, U, pos, vel, d, steps, dt)
+    h = np.array(box) / np.array(grid)
+    dpos = np.abs(min_image(gpos, opos[:, order], L=box)) / h[:, None]
+    vmax = np.abs(ovel).max()
+    if prec == "mixed_f32":
+        assert dpos.max() <= 1e-5
+        assert (np.abs(gvel - ovel[:, order]) / (np.abs(ovel[:, order]) + 1.0)).max() <= 1e-5
+        assert np.linalg.norm(src - osrc) <= 1e-5 * np.linalg.norm(osrc)
+        band = 1e-5
+    else:
+        path = steps * dt * max(vmax, 1.0)
+        bound = steps * 2.0 ** -9
+        assert (dpos * h[:, None]).max() <= bound * path
+        assert np.abs(gvel - ovel[:, order]).max() <= bound * (vmax + 1.0)
+        assert np.linalg.norm(src - osrc) <= 1e-2 * np.linalg.norm(osrc)
+        band = (bound * path / h).max()
+    far = face_distance(opos[:, order], grid, L=box) > band
+    assert np.array_equal(cells[far], linear_cells(opos[:, order], grid, L=box)[far])
+
+
+@pytest.mark.parametrize("N", [32, 40])
+def test_mixed_moves_longer_than_the_box(Sim, N):
+    """Particles launched at up to 2.5 box lengths per step: every coordinate carries whole box
+    lengths (the masked wrap on a power-of-two grid, the general relocation otherwise); the error
+    bound scales with the path in cells (FP32 relative rounding of the displacement)."""
+    n, steps, dt = 4_099, 3, 1e-3
+    U = _f32(inputs.taylor_green(N))
+    pos, vel, d, _ = inputs.particles(5, 0, n, vmax=2500.0)
+    g = _run(Sim, "mixed_f32", N, U, pos, vel, d, steps, dt)
+    opos, ovel, osrc, _ = oracle.run(oracle.make_grid(N), U, pos, vel, d, steps, dt)
+    order = g["ids"].astype(np.int64)
+    path_cells = steps * dt * np.abs(vel).max() * N
+    assert np.abs(min_image(g["pos"], opos[:, order])).max() * N <= 1e-6 * (1.0 + path_cells)
+    assert (np.abs(g["vel"] - ovel[:, order]) / (np.abs(ovel[:, order]) + 1.0)).max() <= 1e-5
+    assert np.linalg.norm(g["src"] - osrc) <= 1e-5 * np.linalg.norm(osrc)
+    assert g["inv"][0] == n
