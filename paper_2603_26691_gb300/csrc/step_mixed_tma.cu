@@ -37,8 +37,8 @@ namespace {
 constexpr int kU = 8;                       // unit edge (cells)
 constexpr int kG = 3;                       // fluid halo = padding of the field
 constexpr int kTE = kU + 2 * kG;            // fluid tile edge (14)
-constexpr int kConsumerWarps = 11;
-constexpr int kT = kConsumerWarps * 128;    // particles per stage (1408)
+constexpr int kConsumerWarps = 15;
+constexpr int kT = kConsumerWarps * 128;    // particles per stage (1920)
 constexpr int kStages = 2;
 constexpr int kFluidBufs = 1;              // fluid tiles in flight (one reload bubble per unit)
 constexpr int kR = 2;                      // deposit halo
@@ -51,12 +51,12 @@ constexpr int kDepShift = 51;              // shared tile units = global units *
 constexpr int64_t kDepMaxCount = 65535;    // per-unit particles for which no digit word can overflow
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 
 constexpr int kFluidBytes = kTE * kTE * kTE * 16;          // 43904
-constexpr int kStageBytes = kT * 32;                        // 45056 (FP32 layout; BF16 uses less)
+constexpr int kStageBytes = kT * 32;                        // 61440 (FP32 layout; BF16 uses less)
 constexpr int kDepositBytes = kDepositCells * 3 * kDigits * 4;  // 62208
-constexpr int kHeadBytes = kConsumerWarps * 128 * 16;           // 22528: per-warp run records
-constexpr int kSmemBytes = kFluidBufs * kFluidBytes + kDepositBytes + kHeadBytes + kStages * kStageBytes + 16 * 8;
+constexpr int kSmemBytes = kFluidBufs * kFluidBytes + kDepositBytes + kStages * kStageBytes + 16 * 8;  // 229128
 
 // ---- PTX wrappers ----------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,11 +79,24 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
-    if (mbar_test(b, parity)) return true;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the phase with the given parity to complete: gives up after kWaitLimitNs of
+// wall time or kSpinLimit polls, whichever comes first
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* b, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0; i < kSpinLimit; i += 32) {
+    for (int k = 0; k < 32; ++k)
+      if (mbar_test(b, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
   return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  return mbar_test(b, parity) || mbar_wait_slow(b, parity);
 }
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -304,13 +317,12 @@ __device__ __forceinline__ void dep_add3(int* w, float r0, float r1, float r2, f
 }
 
 template <bool BF16, bool PW2>
-__global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
+__global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float4* fluid = reinterpret_cast<float4*>(smem);                               // [kFluidBufs][kTE^3]
   int* dep = reinterpret_cast<int*>(smem + kFluidBufs * kFluidBytes);            // [3][kDigits][kDE^3]
-  int4* heads = reinterpret_cast<int4*>(smem + kFluidBufs * kFluidBytes + kDepositBytes);  // [warps][128]
-  unsigned char* ring = smem + kFluidBufs * kFluidBytes + kDepositBytes + kHeadBytes;  // [kStages][kStageBytes]
+  unsigned char* ring = smem + kFluidBufs * kFluidBytes + kDepositBytes;          // [kStages][kStageBytes]
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
   uint64_t* full = bars;                    // [kStages]   producer -> consumers (bytes landed)
   uint64_t* empty = bars + kStages;         // [kStages]   consumers -> producer (stage free)
@@ -457,8 +469,6 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
           dv[3] = d4.w;
         }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);  // the stage is in registers: hand it back early
       ++gt;
 
       // owned particles of this lane: [lo, hi) of 0..3 (the rest belong to neighbouring units
@@ -637,42 +647,49 @@ __global__ void __maxnreg__(168) step_mixed_tma_kernel(const __grid_constant__ C
       }
       const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
       const bool head_lane = (glane == 0) || (pk3 != key[0]);
-      // the run sums, one {J, key} record per run, packed into the warp's scratch in (j, lane)
-      // order - deposit-tile records from the front, the rare global ones from the back; then each
-      // lane takes one record at a time, so a step with few runs costs one pass
-      int4* hs = heads + warp * 128;
+      // the run sums, one {J, key} record per run, packed in (j, lane) order into the warp's own
+      // (already consumed) part of the stage: J in the cell and first two offset arrays, the key
+      // in the third; then each lane takes one record at a time, so a step with few runs costs
+      // one pass.  The stage goes back to the producer after this.
+      int* rj0 = reinterpret_cast<int*>(const_cast<unsigned char*>(src)) + warp * 128;
+      int* rj1 = rj0 + kT;
+      int* rj2 = rj0 + 2 * kT;
+      int* rk = rj0 + 3 * kT;
       const unsigned lt_mask = (1u << lane) - 1u;
-      int nt = 0, nf = 0;
+      int nh = 0;
+      __syncwarp();
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const bool start = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
-        const bool glob = key[j] >= kDepositCells;
-        const unsigned tm = __ballot_sync(0xffffffffu, start && !glob);
-        const unsigned fm = __ballot_sync(0xffffffffu, start && glob);
+        const unsigned hm = __ballot_sync(0xffffffffu, start);
         if (start) {
           const bool to_end = j == tail;
-          const int slot = glob ? 127 - (nf + __popc(fm & lt_mask)) : nt + __popc(tm & lt_mask);
-          hs[slot] = make_int4(__float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f)),
-                               __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f)),
-                               __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f)), key[j]);
+          const int slot = nh + __popc(hm & lt_mask);
+          rj0[slot] = __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f));
+          rj1[slot] = __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f));
+          rj2[slot] = __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f));
+          rk[slot] = key[j];
         }
-        nt += __popc(tm);
-        nf += __popc(fm);
+        nh += __popc(hm);
       }
       __syncwarp();
-      for (int e = lane; e < nt; e += 32) {
-        const int4 rec = hs[e];
-        dep_add3(dep + rec.w, __int_as_float(rec.x), __int_as_float(rec.y), __int_as_float(rec.z), a.s1, a.s2);
-      }
-      if (__builtin_expect(nf != 0, 0)) {
-        for (int e = lane; e < nf; e += 32) {
-          const int4 rec = hs[127 - e];
-          const int64_t c = rec.w - kDepositCells;
-          acc_add_f32(a.acc + kAccWords * c, __int_as_float(rec.x), a.E);
-          acc_add_f32(a.acc + kAccWords * (a.ncell + c), __int_as_float(rec.y), a.E);
-          acc_add_f32(a.acc + kAccWords * (2 * a.ncell + c), __int_as_float(rec.z), a.E);
+      for (int e = lane; e < nh; e += 32) {
+        const int kk = rk[e];
+        const float r0 = __int_as_float(rj0[e]), r1 = __int_as_float(rj1[e]), r2 = __int_as_float(rj2[e]);
+        if (__builtin_expect(kk < kDepositCells, 1)) {
+          dep_add3(dep + kk, r0, r1, r2, a.s1, a.s2);
+        } else {  // start cell outside the deposit tile (rare): straight to the global accumulator
+          const int64_t c = kk - kDepositCells;
+          acc_add_f32(a.acc + kAccWords * c, r0, a.E);
+          acc_add_f32(a.acc + kAccWords * (a.ncell + c), r1, a.E);
+          acc_add_f32(a.acc + kAccWords * (2 * a.ncell + c), r2, a.E);
         }
       }
+      // the records were written through the generic proxy; order them before the producer's next
+      // bulk copy into this stage
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
     }
     // all gathers of this unit are done: the producer may reuse its fluid buffer
     __syncwarp();
