@@ -113,14 +113,15 @@ __device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map,
       : "memory");
 }
 
-// 1 - e^{-x} for x >= 0: Taylor series (x < 1/8, truncation below 4e-9 relative) or 1 - 2^(-x log2 e)
+// 1 - e^{-x} for x >= 0: its degree-5 Taylor polynomial in Horner form for x < 1/8 (truncation
+// below 5e-8 relative), else 1 - 2^(-x log2 e); *e = e^{-x}
 __device__ __forceinline__ float one_minus_exp(float x, float* e) {
   float ex;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(-1.4426950408889634f * x));
-  float s = fmaf(x, -0.2f, 1.0f);
-  s = fmaf(x * 0.25f, -s, 1.0f);
-  s = fmaf(x * (1.0f / 3.0f), -s, 1.0f);
-  s = fmaf(x * 0.5f, -s, 1.0f);
+  float s = fmaf(x, 1.0f / 120.0f, -1.0f / 24.0f);
+  s = fmaf(x, s, 1.0f / 6.0f);
+  s = fmaf(x, s, -0.5f);
+  s = fmaf(x, s, 1.0f);
   const float small = x * s;
   const float big = 1.0f - ex;
   const float r = x < 0.125f ? small : big;
@@ -318,7 +319,7 @@ __device__ __forceinline__ void dep_add3(int* w, float r0, float r1, float r2, f
 
 template <bool BF16, bool PW2>
 __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
-                                                                      const TmaArgs a) {
+                                                                      const __grid_constant__ TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   float4* fluid = reinterpret_cast<float4*>(smem);                               // [kFluidBufs][kTE^3]
   int* dep = reinterpret_cast<int*>(smem + kFluidBufs * kFluidBytes);            // [3][kDigits][kDE^3]
@@ -395,7 +396,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
   }
 
   // ================= consumers =================
-  const int ctid = threadIdx.x;  // 0 .. 255
+  const int ctid = threadIdx.x;  // 0 .. 32 kConsumerWarps - 1
   const int n3[3] = {a.nx, a.ny, a.nz};
   const int px = a.nx + 2 * kG, pxy = (a.nx + 2 * kG) * (a.ny + 2 * kG);
   int loaded = 0;
@@ -543,7 +544,14 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           const float wt = fmaf(a.g[q], inv_a, up[q]);
           const float dvw = v[q][j] - wt;
           float vn = fmaf(dvw, Ee, wt);
-          if (BF16) vn = __bfloat162float(__float2bfloat16_rn(vn));
+          if (BF16) {
+            // the stored (rounded) velocity change, so that the deposit balances the particles' momentum
+            vn = __bfloat162float(__float2bfloat16_rn(vn));
+            J[j][q] = -m * ((vn - v[q][j]) - a.gdt[q]);
+          } else {
+            // v' - v = -(v - w) (1 - E), without the cancellation of subtracting the rounded v'
+            J[j][q] = m * fmaf(dvw, E1, a.gdt[q]);
+          }
           const float dxv = fmaf(wt, a.dt, dvw * Q);
           const float o = fmaf(dxv, a.inv_h[q], xi[q][j]);
           oraw[q] = o;
@@ -561,7 +569,6 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           }
           ii[q] = k;
           xi[q][j] = fminf(o - (t - 12582912.0f), 0.99999994f);
-          J[j][q] = -m * ((vn - v[q][j]) - a.gdt[q]);
           v[q][j] = vn;
         }
         if (__builtin_expect(bad, 0)) {
