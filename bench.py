@@ -35,6 +35,15 @@ METRIC = "particle-steps/s at 1e9 particles, % HBM roofline; mixed vs FP64 at fi
 UNIT = "particle-steps/s"
 # algorithmic bytes per particle-step of the step kernel (read + write of the particle state)
 STEP_BYTES = {"mixed_f32": 32 + 28, "mixed_bf16": 26 + 22, "fp64": 56 + 48}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the sorted-step kernel,
+# per particle, from one ncu capture of the full workload, keyed by the SHA-256 of the kernel's
+# source file; a kernel whose source has changed since has no measured traffic (null)
+STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
+                           "step_mixed_tma.cu")
+MEASURED_TRAFFIC = {
+    # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches (fresh to 3 steps of drift), 64.17-64.27 B
+    ("ca8491dd11374c3356b14772fd4d585588c5381b10129fab5ff51a5965303886", "fourier256_mixed_1e9"): 64.21,
+}
 
 
 def _dist():
@@ -286,8 +295,16 @@ def main():
     step_avg = sum(step_ms) / len(step_ms)
     bytes_per_launch = STEP_BYTES[precision] * n
     achieved = bytes_per_launch / (step_avg * 1e-3) / 1e9
+    traffic = None
+    if precision != "fp64":
+        import hashlib
+
+        with open(STEP_SOURCE, "rb") as f:
+            m = MEASURED_TRAFFIC.get((hashlib.sha256(f.read()).hexdigest(), workload.name))
+        if m is not None:
+            traffic = m * n
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "step_mixed_kernel" if precision != "fp64" else "step_f64_kernel",
+                "traffic": traffic, "kernel": "step_mixed_tma_kernel" if precision != "fp64" else "step_f64_kernel",
                 "algorithmic_bytes_per_particle_step": STEP_BYTES[precision], "peak_kind": peak_kind,
                 "step_kernel_ms": step_avg}
 

@@ -389,7 +389,7 @@ st_status st_reorder(st_handle h) {
 
 // Choose the fixed-point exponent so that a committed run at its bound maps to
 // at most 2^96 and the accumulated integer stays below 2^125.
-static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
+static st_status prepare_accumulator(st_handle h, double dt, double adds_now, int* E_out) {
   const double pi = 3.14159265358979323846;
   double gn = std::sqrt(h->g[0] * h->g[0] + h->g[1] * h->g[1] + h->g[2] * h->g[2]);
   double tau_max = h->rho_p * h->dmax * h->dmax / (18.0 * h->mu);
@@ -401,8 +401,8 @@ static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
   if (!h->acc_empty && E < h->acc_E) {
     cudaError_t e = launch_rescale_acc(h, h->acc_E - E);
     ST_TRY(cuda_check(h, e, "rescale accumulator"));
+    ST_TRY(cuda_check(h, reset_acc_counter(h), "reset accumulator counter"));
     h->acc_load = std::ldexp(h->acc_load, E - h->acc_E);
-    h->acc_count = 1.0;
   }
   if (h->acc_empty || E < h->acc_E) h->acc_E = E;
   E = h->acc_E;
@@ -411,7 +411,7 @@ static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
   while (h->acc_load + add > 0x1p125) {
     cudaError_t e = launch_rescale_acc(h, 1);
     ST_TRY(cuda_check(h, e, "rescale accumulator"));
-    h->acc_count = 1.0;
+    ST_TRY(cuda_check(h, reset_acc_counter(h), "reset accumulator counter"));
     h->acc_E -= 1;
     E = h->acc_E;
     h->acc_load *= 0.5;
@@ -420,13 +420,8 @@ static st_status prepare_accumulator(st_handle h, double dt, int* E_out) {
   h->acc_load += add;
   h->acc_empty = false;
   // each word takes at most one digit per contribution; a step adds at most one contribution per
-  // particle to any cell, plus one per neighbouring unit's tile flush (at most 27)
-  const double per_step = (double)h->np + 27.0;
-  if (h->acc_count + per_step > 0x1p30) {
-    ST_TRY(cuda_check(h, launch_normalize_acc(h), "normalise accumulator"));
-    h->acc_count = 1.0;
-  }
-  h->acc_count += per_step;
+  // particle to any cell, plus one per neighbouring unit's tile flush (at most 8)
+  ST_TRY(cuda_check(h, launch_acc_maybe_normalize(h, (double)h->np + 8.0, adds_now), "normalise accumulator"));
   *E_out = E;
   return ST_OK;
 }
@@ -443,8 +438,11 @@ st_status st_step(st_handle h, int nsteps, double dt) {
     if (h->reorder_every > 0 && (!h->sorted || h->steps_since_sort >= h->reorder_every)) {
       ST_TRY(st_reorder(h));
     }
+    // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
+    // its global commits itself; the other kernels may add one contribution per particle
+    const bool tma = h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
     int E = 0;
-    ST_TRY(prepare_accumulator(h, dt, &E));
+    ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : (double)h->np + 8.0, &E));
     StepParams p;
     p.dt = dt;
     p.ca = 18.0 * h->mu * h->alpha / h->rho_p;
@@ -455,7 +453,7 @@ st_status st_step(st_handle h, int nsteps, double dt) {
     cudaError_t e;
     if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
-    else if (h->sorted && tma_step_supported(h))
+    else if (tma)
       e = launch_step_mixed_tma(h, p);
     else
       e = launch_step_mixed(h, p);
@@ -478,6 +476,7 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
   cudaError_t e = launch_acc_to_f64(h, dst, h->acc_E);
   if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && reset) e = cudaMemsetAsync(h->acc.p, 0, h->acc.bytes, h->stream);
+  if (e == cudaSuccess && reset) e = reset_acc_counter(h);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   dev_free(h, tmp);
   ST_TRY(cuda_check(h, e, "get sources"));
@@ -485,7 +484,6 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
   if (reset) {
     h->acc_empty = true;
     h->acc_load = 0.0;
-    h->acc_count = 0.0;
   }
   return ST_OK;
 }
@@ -619,7 +617,7 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
       ST_TRY(cuda_check(h, e, "checkpoint"));
     }
     int E = 0;
-    ST_TRY(prepare_accumulator(h, dt, &E));
+    ST_TRY(prepare_accumulator(h, dt, (double)h->np + 8.0, &E));
     StepParams p;
     p.dt = dt;
     p.ca = 18.0 * h->mu * h->alpha / h->rho_p;

@@ -75,7 +75,6 @@ struct st_ctx {
 
   // source accumulator: carry-save words [3][ncell][kAccWords] (int64), units of 2^-acc_E
   st::Buf acc;
-  double acc_count = 0.0;    // bound on contributions added to any word since the last normalisation
   int acc_E = 0;             // value = integer * 2^-acc_E
   bool acc_empty = true;
   double acc_load = 0.0;     // bound on |accumulated integer| (in units of 1), for overflow control
@@ -304,6 +303,15 @@ bool tma_step_supported(const st_ctx* h);                               // step_
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p);      // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
 cudaError_t launch_normalize_acc(st_ctx* h);
+// word-capacity bookkeeping of the carry-save accumulator, on the device: a counter (in the flags
+// buffer) bounds the digits added to any word since the last carry propagation; before each step
+// the propagation runs if the counter plus the step's worst case could overflow a word.  `add` is
+// what the step adds for sure (its flushes, or its worst case when it does not count itself);
+// kernels that add more (global commits of the sorted-step kernel) count them on the device.
+cudaError_t launch_acc_maybe_normalize(st_ctx* h, double worst, double add);
+cudaError_t reset_acc_counter(st_ctx* h);
+constexpr size_t kAccCounterOffset = 64;   // bytes into the flags buffer: uint64 counter
+constexpr size_t kAccFlagOffset = 72;      // int: 1 if the last check propagated carries
 cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]);
 cudaError_t launch_particle_sums(st_ctx* h, double out[4]);  // P_x, P_y, P_z, M

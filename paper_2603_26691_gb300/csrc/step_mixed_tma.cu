@@ -141,6 +141,7 @@ struct TmaArgs {
   long long* __restrict__ acc;
   const uint32_t* __restrict__ cell_start;
   int* __restrict__ err;
+  unsigned long long* __restrict__ acc_ctr;  // digits added to any accumulator word (global commits)
   int64_t ncell;
   int nx, ny, nz;
   int nunits;                         // units of kU^3 cells in key order
@@ -690,6 +691,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           acc_add_f32(a.acc + kAccWords * c, r0, a.E);
           acc_add_f32(a.acc + kAccWords * (a.ncell + c), r1, a.E);
           acc_add_f32(a.acc + kAccWords * (2 * a.ncell + c), r2, a.E);
+          atomicAdd(a.acc_ctr, 1ull);
         }
       }
       // the records were written through the generic proxy; order them before the producer's next
@@ -793,6 +795,7 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
   a.acc = (long long*)h->acc.p;
   a.cell_start = (const uint32_t*)h->cell_start.p;
   a.err = (int*)h->flags.p;
+  a.acc_ctr = (unsigned long long*)((char*)h->flags.p + kAccCounterOffset);
   a.ncell = h->geo.ncell;
   a.nx = nx;
   a.ny = ny;

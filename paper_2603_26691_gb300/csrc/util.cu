@@ -209,8 +209,10 @@ __global__ void acc_to_f64_kernel(const long long* __restrict__ acc, double* __r
   }
 }
 
-// carry propagation: rewrite every value with digits in [0, 2^32) below a signed top word
-__global__ void normalize_kernel(long long* __restrict__ acc, int64_t m) {
+// carry propagation: rewrite every value with digits in [0, 2^32) below a signed top word (only
+// when *flag is set, if a flag is given)
+__global__ void normalize_kernel(long long* __restrict__ acc, int64_t m, const int* __restrict__ flag) {
+  if (flag && *flag == 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     long long* w = acc + kAccWords * i;
     unsigned long long lo;
@@ -487,9 +489,35 @@ cudaError_t launch_rescale_acc(st_ctx* h, int shift) {
 
 cudaError_t launch_normalize_acc(st_ctx* h) {
   int64_t m = h->geo.ncell * 3;
-  normalize_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((long long*)h->acc.p, m);
+  normalize_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((long long*)h->acc.p, m, nullptr);
   h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? reset_acc_counter(h) : e;
+}
+
+// each int64 word takes digits of magnitude < 2^32: 2^31 of them cannot overflow it
+__global__ void acc_decide_kernel(unsigned long long* __restrict__ ctr, int* __restrict__ flag, double worst,
+                                  double add) {
+  const double limit = 2147483648.0 - 1048576.0;
+  unsigned long long c = *ctr;
+  const int f = (double)c + worst > limit;
+  if (f) c = 1;  // after propagation every word holds one digit
+  *ctr = c + (unsigned long long)add;
+  *flag = f;
+}
+
+cudaError_t launch_acc_maybe_normalize(st_ctx* h, double worst, double add) {
+  unsigned long long* ctr = (unsigned long long*)((char*)h->flags.p + kAccCounterOffset);
+  int* flag = (int*)((char*)h->flags.p + kAccFlagOffset);
+  acc_decide_kernel<<<1, 1, 0, h->stream>>>(ctr, flag, worst, add);
+  int64_t m = h->geo.ncell * 3;
+  normalize_kernel<<<grid_for(m), kThreads, 0, h->stream>>>((long long*)h->acc.p, m, flag);
+  h->launches += 2;
   return cudaGetLastError();
+}
+
+cudaError_t reset_acc_counter(st_ctx* h) {
+  return cudaMemsetAsync((char*)h->flags.p + kAccCounterOffset, 0, sizeof(unsigned long long), h->stream);
 }
 
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]) {
