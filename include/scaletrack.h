@@ -249,16 +249,19 @@ st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t co
  * cudaStream_t, NULL = legacy default stream) and the call returns without
  * waiting.
  *
- * All scratch memory is one static device array of 12.0 MiB that every GPU
+ * All scratch memory is one static device array of 8.5 MiB that every GPU
  * which loads the library holds until the process exits; the call makes no
  * cudaMalloc, cudaFree or other allocating call.  n must not exceed
  * ST_SORT_KEYS_STATIC_MAX_N (2^20): larger n returns ST_ERR_INVALID_ARG
  * without doing any work.  The first call on a device looks up the array's
  * device address for that device; make that first call before any CUDA stream
  * capture.  Every call uses the same array, which keeps the previous call's
- * contents (nothing in it needs to start at zero), so calls whose work
- * overlaps on the GPU (other streams, other threads) race with each other:
- * order them on one stream or synchronise between them.
+ * contents (its look-back words start zeroed with the module and afterwards
+ * carry only earlier calls' tags), so calls whose work overlaps on the GPU
+ * (other streams, other threads) race with each other: order them on one
+ * stream or synchronise between them.  Its waits on other thread blocks give
+ * up after one second; this call cannot report that (the work runs after it
+ * returns) and the output is then wrong.
  * Errors: INVALID_ARG (n < 0, n > 2^20, key_bits outside 1..32, NULL pointer
  * with n > 0), CUDA. */
 st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,

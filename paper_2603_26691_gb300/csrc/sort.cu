@@ -1,31 +1,40 @@
 // Stable counting sort of the particles by their chunk-major cell key.
 //
-// LSD radix sort of (key, slot) pairs with 8-bit digits; each pass is a
-// stable counting sort in three phases: per-tile digit histograms (warp-
-// aggregated shared-memory counts), one exclusive scan over the digit-major
-// histogram matrix, and a scatter in which every element's rank among the
-// equal digits of its tile comes from warp digit ballots and prefix counts combined
-// across warps in warp order.  No phase waits on another block.  The
-// structure-of-arrays payload is then gathered once through the final
-// permutation.  Equal keys keep their storage order, so the permutation is
-// unique.
+// LSD radix sort of (key, slot) pairs with 8-bit digits.  One read of the keys counts every
+// pass's digit totals; then each pass is a single sweep: a block takes the next tile of 4096
+// keys in order, ranks them stably inside the tile (warp digit ballots, prefix counts combined
+// across warps in warp order), publishes its per-digit counts, adds the counts of all earlier
+// tiles by looking back over their published words (decoupled look-back; each word holds a
+// count and says whether it is the tile's own count or its inclusive prefix), and writes the
+// tile out digit-run by digit-run through shared memory so that the global writes coalesce.
+// The first pass computes the keys from the particle state on the fly and uses the storage
+// slot as the value.  The structure-of-arrays payload is then gathered once through the final
+// permutation.  Equal keys keep their storage order, so the permutation is unique.
+//
+// Waits on other blocks are bounded: a look-back that gives up sets a device flag (reported as
+// ST_ERR_TIMEOUT) and carries on, so no block can hang the grid.
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "st_common.cuh"
+#include "st_ptx.cuh"
 
 namespace st {
 namespace {
 
 constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 16;
-constexpr int kTile = kSortThreads * kItems;  // 4096 items per chunk
-constexpr int kChunks = 16;
-constexpr int64_t kBigTile = (int64_t)kTile * kChunks;  // 65536 items per tile (one CTA, chunks in order)
+constexpr int kTile = kSortThreads * kItems;  // 4096 keys per tile
 constexpr int kRadix = 256;
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanBlock = kScanThreads * kScanItems;  // 2048
+constexpr int kMaxPasses = 4;
+constexpr uint32_t kLookSpinLimit = 1u << 22;
+constexpr uint64_t kLookWaitNs = 1000000000ull;  // 1 s
+
+// look-back word: epoch (30 bits) | kind (2 bits: 1 = the tile's own count, 2 = inclusive
+// prefix) | count (32 bits).  A word whose epoch is not the pass's is empty.
+constexpr unsigned long long kLookAgg = 1ull, kLookPrefix = 2ull;
 
 struct KeyGeo {
   int n[3];
@@ -33,27 +42,29 @@ struct KeyGeo {
   int B, logB, ncx, ncy;
 };
 
-__global__ void keys_f64_kernel(F64State s, int64_t n, KeyGeo g, uint32_t* __restrict__ keys,
-                                uint32_t* __restrict__ vals) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+// key sources for the first pass
+struct CellKeys {  // mixed precision: the packed cell of each slot
+  const int32_t* __restrict__ cell;
+  KeyGeo g;
+  __device__ __forceinline__ uint32_t of_cell(int32_t c) const {
+    return chunk_key(cell_i(c), cell_j(c), cell_k(c), g.B, g.logB, g.ncx, g.ncy);
+  }
+  __device__ __forceinline__ uint32_t operator()(int64_t i) const { return of_cell(cell[i]); }
+};
+struct PositionKeys {  // FP64: the cell of each position
+  F64State s;
+  KeyGeo g;
+  __device__ __forceinline__ uint32_t operator()(int64_t i) const {
     int c[3];
-    for (int q = 0; q < 3; ++q) {
-      int i = (int)floor(s.x[q][p] * g.inv_h[q]);
-      c[q] = min(max(i, 0), g.n[q] - 1);
-    }
-    keys[p] = chunk_key(c[0], c[1], c[2], g.B, g.logB, g.ncx, g.ncy);
-    vals[p] = (uint32_t)p;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) c[q] = min(max((int)floor(s.x[q][i] * g.inv_h[q]), 0), g.n[q] - 1);
+    return chunk_key(c[0], c[1], c[2], g.B, g.logB, g.ncx, g.ncy);
   }
-}
-
-__global__ void keys_mixed_kernel(const int32_t* __restrict__ cell, int64_t n, KeyGeo g, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ vals) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    int32_t c = cell[p];
-    keys[p] = chunk_key(cell_i(c), cell_j(c), cell_k(c), g.B, g.logB, g.ncx, g.ncy);
-    vals[p] = (uint32_t)p;
-  }
-}
+};
+struct ArrayKeys {  // keys given by the caller
+  const uint32_t* __restrict__ k;
+  __device__ __forceinline__ uint32_t operator()(int64_t i) const { return k[i]; }
+};
 
 // lanes of the warp holding the same 8-bit digit (and the same validity): the intersection of one
 // ballot per digit bit, a fixed cost whatever the number of distinct digits in the warp
@@ -69,146 +80,187 @@ __device__ __forceinline__ unsigned match_digit(uint32_t dig, bool valid) {
   return m;
 }
 
-// phase 1: digit histogram of each tile, stored digit-major: hist[d * ntiles + t]
-__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
-                                                                int64_t ntiles, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t cnt[kRadix];
-  cnt[threadIdx.x] = 0;
+__device__ __forceinline__ uint64_t sort_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void store_look(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long load_look(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// every pass's digit totals in one read of the keys: each lane counts runs of equal digits over
+// 16 consecutive keys and adds each run once to the block's counts
+template <class Src>
+__global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int64_t n, int passes,
+                                                                     uint32_t* __restrict__ totals) {
+  __shared__ uint32_t cnt[kMaxPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&cnt[0][0])[i] = 0;
   __syncthreads();
-  const int64_t t = blockIdx.x;
-  const int lane = threadIdx.x & 31;
-  for (int c = 0; c < kChunks; ++c) {
-    const int64_t base = t * kBigTile + (int64_t)c * kTile;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * kItems; base < n;
+       base += nthreads * kItems) {
     uint32_t k[kItems];
+    const int m = (int)min((int64_t)kItems, n - base);
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-      const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-      k[r] = i < n ? keys[i] : 0u;
-    }
+    for (int r = 0; r < kItems; ++r) k[r] = r < m ? src(base + r) : 0u;
+    for (int p = 0; p < passes; ++p) {
+      const int sh = 8 * p;
+      uint32_t cur = (k[0] >> sh) & 0xffu, run = 1;
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-      const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
-      const bool valid = i < n;
-      const uint32_t dig = (k[r] >> shift) & 0xffu;
-      const unsigned peers = match_digit(dig, valid);
-      if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[dig], (uint32_t)__popc(peers));
+      for (int r = 1; r < kItems; ++r) {
+        if (r >= m) break;
+        const uint32_t d = (k[r] >> sh) & 0xffu;
+        if (d == cur) {
+          ++run;
+        } else {
+          atomicAdd(&cnt[p][cur], run);
+          cur = d;
+          run = 1;
+        }
+      }
+      atomicAdd(&cnt[p][cur], run);
     }
   }
   __syncthreads();
-  hist[(int64_t)threadIdx.x * ntiles + t] = cnt[threadIdx.x];
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t c = (&cnt[0][0])[i];
+    if (c) atomicAdd(&totals[i], c);
+  }
 }
 
-// exclusive scan, three kernels: block sums, scan of the block sums (one block,
-// sequential over chunks with a carry), then block-local scans plus offsets
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t wsum[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t x = v;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    int nw = blockDim.x >> 5;
-    uint32_t s = lane < nw ? wsum[lane] : 0u;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
+// exclusive scan of each pass's 256 digit totals (one block of 256 threads)
+__global__ void digit_offsets_kernel(const uint32_t* __restrict__ totals, int passes, uint32_t* __restrict__ offs) {
+  __shared__ uint32_t s[kRadix];
+  for (int p = 0; p < passes; ++p) {
+    s[threadIdx.x] = totals[p * kRadix + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      for (int d = 0; d < kRadix; ++d) {
+        const uint32_t c = s[d];
+        s[d] = acc;
+        acc += c;
+      }
     }
-    if (lane < nw) wsum[lane] = s;
-  }
-  __syncthreads();
-  uint32_t before = (w > 0 ? wsum[w - 1] : 0u) + x - v;
-  *total = wsum[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return before;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t m,
-                                                                   uint32_t* __restrict__ bsum) {
-  uint32_t s = 0;
-  int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
-  for (int k = 0; k < kScanItems; ++k)
-    if (base + k < m) s += in[base + k];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ uint32_t ws[kScanThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
-    bsum[blockIdx.x] = t;
+    __syncthreads();
+    offs[p * kRadix + threadIdx.x] = s[threadIdx.x];
+    __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(1024) scan_blocksums_kernel(uint32_t* __restrict__ bsum, int64_t nb) {
-  uint32_t carry = 0;
-  for (int64_t c = 0; c < nb; c += 1024) {
-    int64_t i = c + threadIdx.x;
-    uint32_t v = i < nb ? bsum[i] : 0u;
-    uint32_t total;
-    uint32_t ex = block_exclusive_scan(v, &total);
-    if (i < nb) bsum[i] = carry + ex;
-    carry += total;
-  }
-}
+// shared memory of a pass: two staging buffers (each a key-or-cell array and a value array of a
+// tile: the next tile lands in one while the current tile is ranked and written out through the
+// other), per-warp digit counts, digit starts, two mbarriers and the tile numbers
+constexpr int kBufWords = 2 * kTile;
+constexpr int kPassBlocksPerSM = 3;  // 3 x 75.8 KB of shared memory, 80 registers
+constexpr size_t kPassSmem = 2 * kBufWords * 4 + kSortWarps * kRadix * 4 + 2 * kRadix * 4 + 2 * 8 + 2 * 8;
 
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in,
-                                                                  uint32_t* __restrict__ out, int64_t m,
-                                                                  const uint32_t* __restrict__ bsum) {
-  uint32_t v[kScanItems];
-  int64_t base = (int64_t)blockIdx.x * kScanBlock + threadIdx.x * kScanItems;
-  uint32_t s = 0;
-  for (int k = 0; k < kScanItems; ++k) {
-    v[k] = (base + k < m) ? in[base + k] : 0u;
-    s += v[k];
-  }
-  uint32_t total;
-  uint32_t ex = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
-  for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < m) out[base + k] = ex;
-    ex += v[k];
-  }
-}
-
-// phase 3: stable scatter.  A tile is processed as kChunks chunks in order; in a chunk warp w
-// owns items [w*512, (w+1)*512) in 16 coalesced rounds.  Ranks inside a round come from
-// digit ballots + popc, across rounds from a per-warp running count, across warps from a prefix in
-// warp order, and across chunks from per-digit running offsets.
-__global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint32_t* __restrict__ kin,
-                                                                  const uint32_t* __restrict__ vin,
-                                                                  uint32_t* __restrict__ kout,
-                                                                  uint32_t* __restrict__ vout, int64_t n, int shift,
-                                                                  int64_t ntiles, const uint32_t* __restrict__ offs) {
-  constexpr int kWarps = kSortThreads / 32;
-  __shared__ uint32_t wcnt[kWarps][kRadix];
-  __shared__ uint32_t base[kRadix];
-  __shared__ uint32_t chunk_total[kRadix];
-  const int64_t t = blockIdx.x;
-  base[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + t];
+// one stable counting-sort pass over 8-bit digit `shift / 8`, tiles taken in order.  BULK: the
+// tile's input (the cell array in the first pass, else the keys and values) arrives by 1-D bulk
+// copies issued one tile ahead; otherwise it is read with plain loads.
+template <bool FIRST, bool BULK, class Src>
+__global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kernel(Src src, const uint32_t* __restrict__ kin,
+                                                                 const uint32_t* __restrict__ vin,
+                                                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                                 int64_t n, int shift, int64_t ntiles,
+                                                                 const uint32_t* __restrict__ digit_offset,
+                                                                 unsigned long long* __restrict__ look,
+                                                                 unsigned long long epoch, unsigned* __restrict__ tile_ctr,
+                                                                 int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  uint32_t* bufs = reinterpret_cast<uint32_t*>(sm);                                   // [2][2][kTile]
+  uint32_t (*wcnt)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(sm + 2 * kBufWords * 4);
+  uint32_t* lstart = reinterpret_cast<uint32_t*>(sm + 2 * kBufWords * 4 + kSortWarps * kRadix * 4);
+  uint32_t* gbase = lstart + kRadix;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(gbase + kRadix);
+  int64_t* s_next = reinterpret_cast<int64_t*>(bar + 2);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int c = 0; c < kChunks; ++c) {
-    const int64_t cstart = t * kBigTile + (int64_t)c * kTile;
-    if (cstart >= n) break;
-    for (int ww = 0; ww < kWarps; ++ww) wcnt[ww][threadIdx.x] = 0;
-    __syncthreads();
-    uint32_t key[kItems], val[kItems], rank[kItems];
-    const int64_t start = cstart + (int64_t)w * (kItems * 32);
-#pragma unroll
-    for (int r = 0; r < kItems; ++r) {
-      const int64_t i = start + r * 32 + lane;
-      key[r] = i < n ? kin[i] : 0u;
-      val[r] = i < n ? vin[i] : 0u;
+  const unsigned long long ep = epoch << 34;
+  // bulk copy of tile t's input into buffer b (sizes rounded up to 4 words: the arrays' capacity
+  // is a multiple of 64 slots, so the copy stays inside them)
+  auto issue = [&](int64_t t, int b) {
+    const int64_t cnt = min((int64_t)kTile, n - t * kTile);
+    const uint32_t bytes = (uint32_t)(((cnt + 3) & ~int64_t(3)) * 4);
+    uint32_t* dst = bufs + b * kBufWords;
+    ptx::mbar_expect_tx(&bar[b], FIRST ? bytes : 2 * bytes);
+    if constexpr (FIRST && BULK) {
+      ptx::bulk_load(dst, reinterpret_cast<const uint32_t*>(src.cell) + t * kTile, bytes, &bar[b]);
+    } else {
+      ptx::bulk_load(dst, kin + t * kTile, bytes, &bar[b]);
+      ptx::bulk_load(dst + kTile, vin + t * kTile, bytes, &bar[b]);
     }
+  };
+  if (threadIdx.x == 0) {
+    if (BULK) {
+      ptx::mbar_init(&bar[0], 1);
+      ptx::mbar_init(&bar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const int64_t t = (int64_t)atomicAdd(tile_ctr, 1u);
+    *s_next = t;
+    if constexpr (BULK) {
+      if (t < ntiles) issue(t, 0);
+    }
+  }
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int b = it & 1;
+    uint32_t* kbuf = bufs + b * kBufWords;
+    uint32_t* vbuf = kbuf + kTile;
+    const int64_t tile = *s_next;
+    for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww][threadIdx.x] = 0;
+    __syncthreads();  // everyone has read the tile number
+    if (tile >= ntiles) return;
+    if (threadIdx.x == 0) {
+      // take the next tile now and start its copy into the other buffer
+      const int64_t t2 = (int64_t)atomicAdd(tile_ctr, 1u);
+      *s_next = t2;
+      if constexpr (BULK) {
+        if (t2 < ntiles) issue(t2, b ^ 1);
+      }
+    }
+    if (BULK && !ptx::mbar_wait(&bar[b], (it >> 1) & 1)) atomicOr(err, 128);
+    // ---- load: warp w owns keys [w*512, (w+1)*512) of the tile in 16 rounds ----
+    uint32_t key[kItems], val[kItems], rank[kItems];
+    const int64_t start = tile * kTile + (int64_t)w * (kItems * 32);
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       const int64_t i = start + r * 32 + lane;
-      const bool valid = i < n;
+      const int li = w * (kItems * 32) + r * 32 + lane;
+      if constexpr (BULK && FIRST) {
+        key[r] = i < n ? src.of_cell((int32_t)kbuf[li]) : 0u;
+        val[r] = (uint32_t)i;
+      } else if constexpr (BULK) {
+        key[r] = kbuf[li];
+        val[r] = vbuf[li];
+      } else if constexpr (FIRST) {
+        key[r] = i < n ? src(i) : 0u;
+        val[r] = (uint32_t)i;
+      } else {
+        key[r] = i < n ? kin[i] : 0u;
+        val[r] = i < n ? vin[i] : 0u;
+      }
+    }
+    __syncthreads();  // the staged input is in registers: the buffer takes the output next
+    // ---- stable ranks inside the warp (one vote when all valid lanes hold the same digit) ----
+#pragma unroll
+    for (int r = 0; r < kItems; ++r) {
+      const bool valid = start + r * 32 + lane < n;
       const uint32_t dig = (key[r] >> shift) & 0xffu;
-      const unsigned peers = match_digit(dig, valid);
+      const unsigned vm = __ballot_sync(0xffffffffu, valid);
+      const uint32_t d0 = __shfl_sync(0xffffffffu, dig, vm ? __ffs(vm) - 1 : 0);
+      unsigned peers;
+      if (__all_sync(0xffffffffu, !valid || dig == d0))
+        peers = valid ? vm : ~vm;
+      else
+        peers = match_digit(dig, valid);
       uint32_t before = 0;
       if (valid) before = wcnt[w][dig];
       __syncwarp();
@@ -217,27 +269,87 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint32_t*
       rank[r] = valid ? before + __popc(peers & lt) : 0xffffffffu;
     }
     __syncthreads();
-    {
-      uint32_t acc = 0;
-      for (int ww = 0; ww < kWarps; ++ww) {
-        const uint32_t cc = wcnt[ww][threadIdx.x];
-        wcnt[ww][threadIdx.x] = acc;
-        acc += cc;
+    // ---- per digit: offsets of the warps inside the tile, the tile's count ----
+    const int d = threadIdx.x;
+    uint32_t tot = 0;
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+      const uint32_t c = wcnt[ww][d];
+      wcnt[ww][d] = tot;
+      tot += c;
+    }
+    unsigned long long* my = look + tile * kRadix + d;
+    store_look(my, ep | ((tile == 0 ? kLookPrefix : kLookAgg) << 32) | tot);
+    // ---- look back: the sum of this digit's counts over all earlier tiles ----
+    uint32_t excl = 0;
+    if (tile > 0) {
+      int64_t t = tile - 1;
+      uint64_t t0 = 0;
+      uint32_t polls = 0;
+      for (;;) {
+        const unsigned long long v = load_look(look + t * kRadix + d);
+        const unsigned long long kind = (v >> 32) & 3ull;
+        if ((v >> 34) == epoch && kind != 0) {
+          excl += (uint32_t)v;
+          if (kind == kLookPrefix || t == 0) break;
+          --t;
+          polls = 0;
+          continue;
+        }
+        if (polls == 0) t0 = sort_ns();
+        if (++polls >= kLookSpinLimit || ((polls & 31u) == 0 && sort_ns() - t0 > kLookWaitNs)) {
+          atomicOr(err, 64);  // gave up: the output is wrong, the host reports a timeout
+          break;
+        }
       }
-      chunk_total[threadIdx.x] = acc;
+      store_look(my, ep | (kLookPrefix << 32) | (excl + tot));
+    }
+    gbase[d] = digit_offset[d] + excl;
+    // ---- tile-local start of each digit (exclusive scan of the tile's counts) ----
+    lstart[d] = tot;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t c[8], s = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        c[k] = lstart[lane * 8 + k];
+        s += c[k];
+      }
+      uint32_t x = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t acc = x - s;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        lstart[lane * 8 + k] = acc;
+        acc += c[k];
+      }
     }
     __syncthreads();
+    // ---- the tile in digit order in shared memory, then out run by run ----
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       if (rank[r] != 0xffffffffu) {
         const uint32_t dig = (key[r] >> shift) & 0xffu;
-        const uint32_t dst = base[dig] + wcnt[w][dig] + rank[r];
-        kout[dst] = key[r];
-        vout[dst] = val[r];
+        const uint32_t lp = lstart[dig] + wcnt[w][dig] + rank[r];
+        kbuf[lp] = key[r];
+        vbuf[lp] = val[r];
       }
     }
     __syncthreads();
-    base[threadIdx.x] += chunk_total[threadIdx.x];
+    const int cnt = (int)min((int64_t)kTile, n - tile * kTile);
+    for (int lp = threadIdx.x; lp < cnt; lp += kSortThreads) {
+      const uint32_t k = kbuf[lp];
+      const uint32_t dig = (k >> shift) & 0xffu;
+      const uint32_t dst = gbase[dig] + (uint32_t)lp - lstart[dig];
+      kout[dst] = k;
+      vout[dst] = vbuf[lp];
+    }
+    // this buffer receives the tile after next by bulk copy: order the generic-proxy accesses of
+    // every thread before that async-proxy write
+    if constexpr (BULK) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
   }
 }
@@ -368,14 +480,73 @@ int grid_for(int64_t n, int max_blocks = 152 * 16) {
   return (int)b;
 }
 
-cudaError_t exclusive_scan(st_ctx* h, const uint32_t* in, uint32_t* out, int64_t m) {
-  int64_t nb = (m + kScanBlock - 1) / kScanBlock;
-  uint32_t* bsum = (uint32_t*)h->scan_aux.p;
-  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, h->stream>>>(in, m, bsum);
-  scan_blocksums_kernel<<<1, 1024, 0, h->stream>>>(bsum, nb);
-  scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, h->stream>>>(in, out, m, bsum);
-  h->launches += 3;
+
+template <bool FIRST, bool BULK, class Src>
+cudaError_t launch_pass(int64_t grid, cudaStream_t s, Src src, const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
+                        uint32_t* vout, int64_t n, int shift, int64_t ntiles, const uint32_t* offs,
+                        unsigned long long* look, uint32_t epoch, unsigned* tile_ctr, int* err) {
+  static bool attr = false;  // one per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<FIRST, BULK, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kPassSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  onesweep_kernel<FIRST, BULK, Src><<<(unsigned)grid, kSortThreads, kPassSmem, s>>>(
+      src, kin, vin, kout, vout, n, shift, ntiles, offs, look, epoch, tile_ctr, err);
   return cudaGetLastError();
+}
+
+// the passes of the stable sort of n keys of key_bits bits; the last pass writes kfinal / vfinal.
+// Bulk copies read whole 16-byte groups, so they serve only arrays that are 16-byte aligned with
+// capacity a multiple of 4 slots: the particle state's cell array (first pass, CellKeys) and,
+// with bulk_rest, every intermediate key/value array.
+template <class Src>
+cudaError_t radix_passes(Src src, int64_t n, int key_bits, uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
+                         uint32_t* kfinal, uint32_t* vfinal, uint32_t* totals, uint32_t* offs, unsigned* tile_ctr,
+                         unsigned long long* look, uint32_t* epoch, int* err, int sms, cudaStream_t s,
+                         int64_t* launches, bool bulk_rest) {
+  const int passes = (key_bits + 7) / 8;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
+  cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)kMaxPasses * kRadix * sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, kMaxPasses * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  digit_totals_kernel<Src><<<grid_for((n + kItems - 1) / kItems), kSortThreads, 0, s>>>(src, n, passes, totals);
+  digit_offsets_kernel<<<1, kRadix, 0, s>>>(totals, passes, offs);
+  *launches += 2;
+  int64_t grid = (int64_t)sms * kPassBlocksPerSM;
+  if (grid > ntiles) grid = ntiles;
+  const uint32_t* kin = nullptr;
+  const uint32_t* vin = nullptr;
+  for (int p = 0; p < passes; ++p) {
+    // ping-pong so that the last pass lands in the final buffers
+    const bool to_final = ((passes - 1 - p) % 2) == 0;
+    uint32_t* kout = to_final ? kfinal : (kfinal == ka ? kb : ka);
+    uint32_t* vout = to_final ? vfinal : (vfinal == va ? vb : va);
+    *epoch = (*epoch + 1) & ((1u << 30) - 1);
+    if (*epoch == 0) *epoch = 1;
+    if (p == 0) {
+      if constexpr (std::is_same<Src, CellKeys>::value)
+        e = launch_pass<true, true, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, ntiles, offs, look, *epoch,
+                                         tile_ctr, err);
+      else
+        e = launch_pass<true, false, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, ntiles, offs, look, *epoch,
+                                          tile_ctr, err);
+    } else if (bulk_rest) {
+      e = launch_pass<false, true, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, ntiles,
+                                              offs + p * kRadix, look, *epoch, tile_ctr + p, err);
+    } else {
+      e = launch_pass<false, false, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, ntiles,
+                                               offs + p * kRadix, look, *epoch, tile_ctr + p, err);
+    }
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    kin = kout;
+    vin = vout;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -384,9 +555,7 @@ st_status sort_particles(st_ctx* h) {
   const int64_t n = h->np;
   if (n == 0) return ST_OK;
   if (n >= (int64_t(1) << 32)) return set_error(h, ST_ERR_INVALID_ARG, "sorting needs fewer than 2^32 particles");
-  const int64_t ntiles = (n + kBigTile - 1) / kBigTile;
-  const int64_t hm = ntiles * kRadix;
-  const int64_t nb = (hm + kScanBlock - 1) / kScanBlock;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
   if (h->sort_cap < h->cap) {
     size_t kb = (size_t)h->cap * sizeof(uint32_t);
     for (int b = 0; b < 2; ++b) {
@@ -394,37 +563,44 @@ st_status sort_particles(st_ctx* h) {
     }
     h->sort_cap = h->cap;
   }
-  if (ensure(h, h->hist, (size_t)hm * 2 * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
-  if (ensure(h, h->scan_aux, (size_t)(nb + 1) * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
+  // look-back words: one per tile and digit, cleared once per allocation (the epoch tells passes apart)
+  const void* look_before = h->hist.p;
+  if (ensure(h, h->hist, (size_t)ntiles * kRadix * sizeof(unsigned long long)) != ST_OK) return ST_ERR_OOM;
+  if (ensure(h, h->scan_aux, (size_t)(2 * kMaxPasses * kRadix + kMaxPasses) * sizeof(uint32_t)) != ST_OK)
+    return ST_ERR_OOM;
   if (ensure(h, h->cell_start, ((size_t)h->nkeys + 1) * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
   if (ensure(h, h->state_alt, state_bytes(h->prec, h->cap)) != ST_OK) return ST_ERR_OOM;
   if (ensure(h, h->ids_alt, (size_t)h->cap * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
+  if (h->hist.p != look_before) {
+    // a new look-back buffer may hold anything: clear it so that no stale word carries an epoch
+    cudaError_t ce = cudaMemsetAsync(h->hist.p, 0, h->hist.bytes, h->stream);
+    if (ce != cudaSuccess) return cuda_check(h, ce, "clear look-back words");
+  }
 
   KeyGeo g = key_geo(h);
   uint32_t* k0 = (uint32_t*)h->keys[0].p;
   uint32_t* v0 = (uint32_t*)h->vals[0].p;
   uint32_t* k1 = (uint32_t*)h->keys[1].p;
   uint32_t* v1 = (uint32_t*)h->vals[1].p;
-  if (h->prec == ST_FP64)
-    keys_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(carve_f64(h->state.p, h->cap), n, g, k0, v0);
-  else
-    keys_mixed_kernel<<<grid_for(n), 256, 0, h->stream>>>((const int32_t*)h->state.p, n, g, k0, v0);
-  h->launches += 1;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_check(h, e, "sort keys");
-  uint32_t* hist = (uint32_t*)h->hist.p;
-  uint32_t* offs = hist + hm;
-  for (int shift = 0; shift < h->key_bits; shift += 8) {
-    upsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, h->stream>>>(k0, n, shift, ntiles, hist);
-    e = exclusive_scan(h, hist, offs, hm);
-    if (e != cudaSuccess) return cuda_check(h, e, "sort scan");
-    downsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, h->stream>>>(k0, v0, k1, v1, n, shift, ntiles, offs);
-    h->launches += 2;  // upsweep + downsweep
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_check(h, e, "sort pass");
-    std::swap(k0, k1);
-    std::swap(v0, v1);
+  uint32_t* totals = (uint32_t*)h->scan_aux.p;
+  uint32_t* offs = totals + kMaxPasses * kRadix;
+  unsigned* tile_ctr = (unsigned*)(offs + kMaxPasses * kRadix);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
+  if (sms <= 0) sms = 152;
+  cudaError_t e;
+  if (h->prec == ST_FP64) {
+    PositionKeys src{carve_f64(h->state.p, h->cap), g};
+    e = radix_passes(src, n, h->key_bits, k0, v0, k1, v1, k0, v0, totals, offs, tile_ctr,
+                     (unsigned long long*)h->hist.p, &h->sort_epoch, (int*)h->flags.p, sms, h->stream, &h->launches,
+                     true);
+  } else {
+    CellKeys src{(const int32_t*)h->state.p, g};
+    e = radix_passes(src, n, h->key_bits, k0, v0, k1, v1, k0, v0, totals, offs, tile_ctr,
+                     (unsigned long long*)h->hist.p, &h->sort_epoch, (int*)h->flags.p, sms, h->stream, &h->launches,
+                     true);
   }
+  if (e != cudaSuccess) return cuda_check(h, e, "sort passes");
   // k0/v0 now hold the sorted keys and the permutation
   if (h->prec == ST_FP64) {
     gather_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(carve_f64(h->state.p, h->cap),
@@ -472,42 +648,30 @@ namespace st {
 namespace {
 
 constexpr int64_t kStaticMaxN = int64_t(1) << 20;  // keys per call (matches the header's limit)
-constexpr int64_t kStaticTiles = kStaticMaxN / kBigTile;
-constexpr int64_t kStaticHist = kStaticTiles * kRadix;
-constexpr int64_t kStaticAux = (kStaticHist + kScanBlock - 1) / kScanBlock + 1;
-// layout: index seeds [N] | ping-pong keys [N] | ping-pong values [N] | histograms [H] | offsets [H] | scan aux
-constexpr size_t kStaticWords = (size_t)(3 * kStaticMaxN + 2 * kStaticHist + kStaticAux);
-
-__global__ void iota_kernel(uint32_t* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (uint32_t)i;
-}
-
-// exclusive scan with caller-provided block-sum storage `aux` ((m + 2047) / 2048 + 1 words)
-cudaError_t exclusive_scan_aux(const uint32_t* in, uint32_t* out, int64_t m, uint32_t* aux, cudaStream_t s) {
-  int64_t nb = (m + kScanBlock - 1) / kScanBlock;
-  scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, m, aux);
-  scan_blocksums_kernel<<<1, 1024, 0, s>>>(aux, nb);
-  scan_apply_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, m, aux);
-  return cudaGetLastError();
-}
+constexpr int64_t kStaticTiles = kStaticMaxN / kTile;
+// layout (32-bit words): ping-pong keys [N] | ping-pong values [N] | look-back words [2 T R] |
+// digit totals [P R] | digit offsets [P R] | tile counters [P] (+ padding to 8 bytes)
+constexpr size_t kStaticLook = 2 * (size_t)kStaticMaxN;
+constexpr size_t kStaticTotals = kStaticLook + 2 * (size_t)kStaticTiles * kRadix;
+constexpr size_t kStaticWords = kStaticTotals + 2 * (size_t)kMaxPasses * kRadix + kMaxPasses + 4;
 
 }  // namespace
-
 }  // namespace st
 
 // The scratch array.  Host code must not use its name as an address: on the host the name
 // refers to a host-side stand-in.  The device address comes from cudaGetSymbolAddress, once per
-// device, below.
+// device, below.  Device globals start zeroed, so no look-back word carries an epoch before use.
 static __device__ __align__(256) uint32_t g_sort_scratch[st::kStaticWords];
 
 namespace {
 std::mutex g_scratch_mu;
 constexpr int kMaxDevices = 64;
 uint32_t* g_scratch_addr[kMaxDevices] = {};
+uint32_t g_scratch_epoch[kMaxDevices] = {};
 
-// Device address of g_sort_scratch on the current device (looked up on the first call per device).
-cudaError_t scratch_address(uint32_t** out) {
+// Device address of g_sort_scratch on the current device (looked up on the first call per device)
+// and that device's look-back epoch counter.
+cudaError_t scratch_address(uint32_t** out, uint32_t** epoch) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -520,6 +684,7 @@ cudaError_t scratch_address(uint32_t** out) {
     g_scratch_addr[dev] = (uint32_t*)p;
   }
   *out = g_scratch_addr[dev];
+  *epoch = &g_scratch_epoch[dev];
   return cudaSuccess;
 }
 }  // namespace
@@ -532,33 +697,33 @@ extern "C" st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int ke
   if (n == 0) return ST_OK;
   if (!keys || !sorted_keys || !perm) return ST_ERR_INVALID_ARG;
   uint32_t* base = nullptr;
-  if (scratch_address(&base) != cudaSuccess) {
+  uint32_t* epoch = nullptr;
+  if (scratch_address(&base, &epoch) != cudaSuccess) {
     cudaGetLastError();
     return ST_ERR_CUDA;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t* seed = base;
-  uint32_t* sk = base + kStaticMaxN;
-  uint32_t* sv = base + 2 * kStaticMaxN;
-  uint32_t* hist = base + 3 * kStaticMaxN;
-  uint32_t* offs = hist + kStaticHist;
-  uint32_t* aux = offs + kStaticHist;
-  const int64_t ntiles = (n + kBigTile - 1) / kBigTile;
-  const int passes = (key_bits + 7) / 8;
-  iota_kernel<<<grid_for(n), 256, 0, s>>>(seed, n);
-  // alternate between the caller's outputs and the scratch pair so that the last pass lands in the outputs
-  const uint32_t* kin = keys;
-  const uint32_t* vin = seed;
-  for (int p = 0; p < passes; ++p) {
-    bool to_out = ((passes - 1 - p) % 2) == 0;
-    uint32_t* kout = to_out ? sorted_keys : sk;
-    uint32_t* vout = to_out ? perm : sv;
-    upsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, 8 * p, ntiles, hist);
-    if (exclusive_scan_aux(hist, offs, ntiles * kRadix, aux, s) != cudaSuccess) return ST_ERR_CUDA;
-    downsweep_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * p, ntiles, offs);
-    if (cudaGetLastError() != cudaSuccess) return ST_ERR_CUDA;
-    kin = kout;
-    vin = vout;
+  uint32_t* sk = base;
+  uint32_t* sv = base + kStaticMaxN;
+  unsigned long long* look = (unsigned long long*)(base + kStaticLook);
+  uint32_t* totals = base + kStaticTotals;
+  uint32_t* offs = totals + kMaxPasses * kRadix;
+  unsigned* tile_ctr = offs + kMaxPasses * kRadix;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 152;
+  int64_t launches = 0;
+  // a look-back wait that gives up cannot be reported here: the timeout flag lives in a handle;
+  // it writes to a word of the scratch instead
+  int* err = (int*)(tile_ctr + kMaxPasses);
+  uint32_t ep;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    ep = *epoch;
+    *epoch = (ep + 8) & ((1u << 30) - 1);
   }
-  return ST_OK;
+  cudaError_t e = radix_passes(ArrayKeys{keys}, n, key_bits, sk, sv, sorted_keys, perm, sorted_keys, perm, totals, offs,
+                               tile_ctr, look, &ep, err, sms, s, &launches, false);
+  return e == cudaSuccess ? ST_OK : ST_ERR_CUDA;
 }

@@ -72,6 +72,7 @@ struct st_ctx {
   int key_bits = 0;
   st::Buf keys[2], vals[2], hist, scan_aux, cell_start;  // cell_start uint32[nkeys + 1]
   int64_t sort_cap = 0;
+  uint32_t sort_epoch = 0;   // tags the look-back words of each sort pass (no clearing between passes)
 
   // source accumulator: carry-save words [3][ncell][kAccWords] (int64), units of 2^-acc_E
   st::Buf acc;
