@@ -85,6 +85,11 @@ def lib():
             L.orc_invariants.argtypes, L.orc_invariants.restype = [pg, i64, pd, pd, pd, pd], None
             L.orc_adjoint.argtypes = [pg, pd, i64, pd, pd, pd, i32, d, pd, pd, pd, pd]
             L.orc_adjoint.restype = C.c_int
+            L.orc_ecm_estimate.argtypes, L.orc_ecm_estimate.restype = [i32, i64, pd, pd, pd, pd], None
+            L.orc_fluid_update.argtypes = [pg, pd, pd, d, d, d, i32]
+            L.orc_fluid_update.restype = C.c_int
+            L.orc_couple.argtypes = [pg, pd, i64, pd, pd, pd, i32, i32, d, d, d, i32, i32, pd]
+            L.orc_couple.restype = C.c_int
             _lib = L
     return _lib
 
@@ -215,3 +220,44 @@ def adjoint(G: Grid, U, pos0, vel0, d, nsteps: int, dt: float, lam):
     if rc != 0:
         raise ValueError(f"orc_adjoint failed ({rc})")
     return gd, ga.value, gU
+
+
+EXTRAPOLATORS = {"zero": 0, "const": 1, "lin": 2}
+
+
+def ecm_estimate(extrap: str, s1=None, s2=None, s3=None, m=None) -> np.ndarray:
+    """S_est^n from S^{n-1}, S^{n-2}, S^{n-3} (None = before the first interval)."""
+    arrs = [None if a is None else _f64(a).reshape(-1) for a in (s1, s2, s3)]
+    if m is None:
+        m = next(a.shape[0] for a in arrs if a is not None)
+    out = np.zeros(m)
+    lib().orc_ecm_estimate(EXTRAPOLATORS[extrap], m, *[_pd(a) if a is not None else None for a in arrs], _pd(out))
+    return out
+
+
+def fluid_update(G: Grid, U, S, rho_f: float, nu: float, dtc: float, sweeps: int) -> np.ndarray:
+    """One coupling interval's fluid update of U [.., 3] (copied) with the impulse S [3, ncell]."""
+    shape = np.shape(U)
+    U = _f64(U).reshape(-1).copy()
+    S = _f64(S).reshape(-1) if S is not None else None
+    rc = lib().orc_fluid_update(C.byref(G), _pd(U), _pd(S) if S is not None else None, float(rho_f), float(nu),
+                                float(dtc), int(sweeps))
+    if rc != 0:
+        raise ValueError(f"orc_fluid_update failed ({rc})")
+    return U.reshape(shape)
+
+
+def couple(G: Grid, U, pos, vel, d, nint: int, K: int, dt: float, rho_f: float, nu: float, sweeps: int,
+           extrap: str = "zero"):
+    """Asynchronous coupled run; returns (U, pos, vel, pending [3, ncell]) (inputs copied)."""
+    shape = np.shape(U)
+    U = _f64(U).reshape(-1).copy()
+    pos = _f64(pos).reshape(3, -1).copy()
+    vel = _f64(vel).reshape(3, -1).copy()
+    d = _f64(d).reshape(-1)
+    pending = np.zeros((3, ncell(G)))
+    rc = lib().orc_couple(C.byref(G), _pd(U), d.shape[0], _pd(pos), _pd(vel), _pd(d), int(nint), int(K), float(dt),
+                          float(rho_f), float(nu), int(sweeps), EXTRAPOLATORS[extrap], _pd(pending))
+    if rc != 0:
+        raise ValueError(f"orc_couple failed ({rc})")
+    return U.reshape(shape), pos, vel, pending

@@ -373,3 +373,131 @@ int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos
   free(tc);
   return 0;
 }
+
+/* Extrapolation of S^m from the two sources before it (Sec. 2.4, Eqs. 14a-c). */
+static double ecm_extrapolate(int32_t extrap, const double* prev1, const double* prev2, int64_t i) {
+  double a = prev1 ? prev1[i] : 0.0;
+  double b = prev2 ? prev2[i] : 0.0;
+  if (extrap == 1) return a;
+  if (extrap == 2) return 2.0 * a - b;
+  return 0.0;
+}
+
+/* Sec. 2.4, Eqs. 12-13 with the reading stated in the header. */
+void orc_ecm_estimate(int32_t extrap, int64_t m, const double* s1, const double* s2,
+                      const double* s3, double* out) {
+  for (int64_t i = 0; i < m; ++i) {
+    double last = s1 ? s1[i] : 0.0;
+    double ext_prev = ecm_extrapolate(extrap, s2, s3, i); /* estimate of S^{n-1} */
+    double ext_now = ecm_extrapolate(extrap, s1, s2, i);  /* estimate of S^n */
+    out[i] = last - ext_prev + ext_now;
+  }
+}
+
+int orc_fluid_update(const orc_grid* G, double* U, const double* S, double rho_f, double nu,
+                     double dtc, int32_t sweeps) {
+  if (!grid_ok(G) || !(rho_f > 0.0) || nu < 0.0 || sweeps < 0) return -1;
+  int64_t nc = ncell_of(G);
+  double h[3] = {cell_size(G, 0), cell_size(G, 1), cell_size(G, 2)};
+  double V = h[0] * h[1] * h[2];
+  double lam[3];
+  double lsum = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    lam[ax] = nu * dtc / (h[ax] * h[ax]);
+    lsum = lsum + lam[ax];
+  }
+  double* ustar = (double*)malloc((size_t)nc * 3 * sizeof(double));
+  double* next = (double*)malloc((size_t)nc * 3 * sizeof(double));
+  if (!ustar || !next) {
+    free(ustar);
+    free(next);
+    return -2;
+  }
+  /* explicit momentum source: the impulse S spread over the fluid mass of the cell */
+  for (int64_t c = 0; c < nc; ++c)
+    for (int q = 0; q < 3; ++q) {
+      double add = S ? S[q * nc + c] / (rho_f * V) : 0.0;
+      ustar[3 * c + q] = U[3 * c + q] + add;
+      U[3 * c + q] = ustar[3 * c + q];
+    }
+  /* Jacobi: u_new = (u* + sum_ax lam_ax (u_old(+ax) + u_old(-ax))) / (1 + 2 sum lam) */
+  for (int32_t it = 0; it < sweeps; ++it) {
+    for (int32_t k = 0; k < G->n[2]; ++k)
+      for (int32_t j = 0; j < G->n[1]; ++j)
+        for (int32_t i = 0; i < G->n[0]; ++i) {
+          int64_t c = linear_cell(G, i, j, k);
+          int64_t nb[3][2] = {
+              {linear_cell(G, wrap_index(i - 1, G->n[0]), j, k), linear_cell(G, wrap_index(i + 1, G->n[0]), j, k)},
+              {linear_cell(G, i, wrap_index(j - 1, G->n[1]), k), linear_cell(G, i, wrap_index(j + 1, G->n[1]), k)},
+              {linear_cell(G, i, j, wrap_index(k - 1, G->n[2])), linear_cell(G, i, j, wrap_index(k + 1, G->n[2]))}};
+          for (int q = 0; q < 3; ++q) {
+            double acc = ustar[3 * c + q];
+            for (int ax = 0; ax < 3; ++ax)
+              acc = acc + lam[ax] * (U[3 * nb[ax][0] + q] + U[3 * nb[ax][1] + q]);
+            next[3 * c + q] = acc / (1.0 + 2.0 * lsum);
+          }
+        }
+    memcpy(U, next, (size_t)nc * 3 * sizeof(double));
+  }
+  free(ustar);
+  free(next);
+  return 0;
+}
+
+int orc_couple(const orc_grid* G, double* U, int64_t n, double* pos, double* vel, const double* d,
+               int32_t nint, int32_t K, double dt, double rho_f, double nu, int32_t sweeps,
+               int32_t extrap, double* pending) {
+  if (!grid_ok(G) || n < 0 || nint < 0 || K < 1 || !(dt > 0.0) || extrap < 0 || extrap > 2) return -1;
+  int64_t m = 3 * ncell_of(G);
+  /* the sources of the last three intervals, S^{n-1}, S^{n-2}, S^{n-3} */
+  double* hist[3];
+  double* cur = (double*)calloc((size_t)m, sizeof(double));
+  double* est = (double*)calloc((size_t)m, sizeof(double));
+  int ok = cur && est;
+  for (int k = 0; k < 3; ++k) {
+    hist[k] = (double*)calloc((size_t)m, sizeof(double));
+    ok = ok && hist[k];
+  }
+  if (!ok) {
+    free(cur);
+    free(est);
+    for (int k = 0; k < 3; ++k) free(hist[k]);
+    return -2;
+  }
+  int32_t have = 0; /* intervals completed so far */
+  for (int32_t it = 0; it < nint; ++it) {
+    /* the estimate for interval it uses only the sources of earlier intervals */
+    orc_ecm_estimate(extrap, m, have >= 1 ? hist[0] : NULL, have >= 2 ? hist[1] : NULL,
+                     have >= 3 ? hist[2] : NULL, est);
+    /* particles: K steps in the frozen field u^it, depositing S^it */
+    memset(cur, 0, (size_t)m * sizeof(double));
+    int r = orc_run(G, U, n, pos, vel, d, K, dt, cur, NULL, NULL);
+    /* fluid: u^{it+1} from u^it and the estimate (independent of S^it, so the order of the two
+     * halves does not matter) */
+    if (r == 0) r = orc_fluid_update(G, U, est, rho_f, nu, (double)K * dt, sweeps);
+    if (r != 0) {
+      free(cur);
+      free(est);
+      for (int k = 0; k < 3; ++k) free(hist[k]);
+      return r;
+    }
+    double* oldest = hist[2];
+    hist[2] = hist[1];
+    hist[1] = hist[0];
+    hist[0] = oldest;
+    memcpy(hist[0], cur, (size_t)m * sizeof(double));
+    have = have + 1;
+  }
+  if (pending) {
+    /* sum of S^n minus sum of S_est^n over the intervals run: S^{N-1} - S_ext^{N-1} */
+    for (int64_t i = 0; i < m; ++i) {
+      double last = have >= 1 ? hist[0][i] : 0.0;
+      double ext_last = ecm_extrapolate(extrap, have >= 2 ? hist[1] : NULL, have >= 3 ? hist[2] : NULL, i);
+      pending[i] = last - ext_last;
+    }
+  }
+  free(cur);
+  free(est);
+  for (int k = 0; k < 3; ++k) free(hist[k]);
+  return 0;
+}

@@ -24,7 +24,13 @@
  *     (chunks organised as structures of arrays, Sec. 2.2);
  *   - global invariants (particle count, momentum, summed source, mass);
  *   - the hand-derived adjoint of the step for a loss on the time-summed
- *     source field.
+ *     source field;
+ *   - the asynchronous two-way coupling of Sec. 2.3 on one device: the
+ *     particles advance in a frozen fluid field while the fluid is updated
+ *     from the sources of the previous coupling interval, estimated by the
+ *     extrapolator-corrector method of Sec. 2.4 (Eqs. 12-14); the fluid
+ *     update is an explicit momentum source followed by Jacobi sweeps of an
+ *     implicit periodic diffusion step.
  *
  * Pins (tests/test_oracle_pins.py): closed-form and ODE-integrated
  * uniform-flow solutions, terminal velocity, exact reproduction of
@@ -112,6 +118,39 @@ void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const doubl
 int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
                 const double* vel0, const double* d, int32_t nsteps, double dt,
                 const double* lam, double* grad_d, double* grad_alpha, double* gradU);
+
+/* Extrapolator-corrector estimate of the source of coupling interval n
+ * (Sec. 2.4, Eqs. 12-14): S_est^n = S^{n-1} - S_ext^{n-1} + S_ext^n, where
+ * S_ext^m extrapolates S^m from the sources before it: extrap 0 = zero (0),
+ * 1 = constant (S^{m-1}), 2 = linear (2 S^{m-1} - S^{m-2}).  Reading: the
+ * corrector removes the extrapolated part of the previous estimate; removing
+ * the whole previous estimate, as printed, is not conservative over time.
+ * s1, s2, s3 = S^{n-1}, S^{n-2}, S^{n-3} (NULL for an interval before the
+ * first); m values each. */
+void orc_ecm_estimate(int32_t extrap, int64_t m, const double* s1, const double* s2,
+                      const double* s3, double* out);
+
+/* Fluid update of one coupling interval of length dtc: u* = U + S / (rho_f V)
+ * in every cell (S[3][ncell], the impulse given to the fluid; V the cell
+ * volume), then `sweeps` Jacobi sweeps of the implicit diffusion step
+ * (I - nu dtc Lap) u = u* with the 7-point periodic Laplacian, starting from
+ * u*.  U[c][3] is updated in place.  Returns 0, or -1 / -2 on bad arguments
+ * or allocation failure. */
+int orc_fluid_update(const orc_grid* G, double* U, const double* S, double rho_f, double nu,
+                     double dtc, int32_t sweeps);
+
+/* Asynchronous two-way coupling (Sec. 2.3) of nint intervals of K particle
+ * steps of dt: in interval n the particles advance K steps in the frozen
+ * field u^n and deposit S^n, while the fluid becomes
+ * u^{n+1} = F(u^n, S_est^n) (orc_fluid_update with the estimate of
+ * orc_ecm_estimate, which uses only S^{n-1}, S^{n-2}, S^{n-3}).  U, pos and
+ * vel are updated in place.  pending[3][ncell] receives the sources
+ * deposited but not yet given to the fluid, S^{N-1} - S_ext^{N-1}, so that
+ * particle momentum + fluid momentum + pending - gravity impulse is
+ * conserved.  Returns 0, -1 on bad arguments, -2 on allocation failure. */
+int orc_couple(const orc_grid* G, double* U, int64_t n, double* pos, double* vel, const double* d,
+               int32_t nint, int32_t K, double dt, double rho_f, double nu, int32_t sweeps,
+               int32_t extrap, double* pending);
 
 #ifdef __cplusplus
 }
