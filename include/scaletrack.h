@@ -214,6 +214,45 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
 st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device, double* grad_d,
                               double* grad_alpha, double* grad_U, int on_device);
 
+/* Two-way coupling parameters (Sec. 2.3 and 2.4): fluid density rho_f > 0
+ * (kg/m^3, the cell's fluid mass is rho_f V), kinematic viscosity nu >= 0 of
+ * the implicit diffusion step, Jacobi sweeps per interval (>= 0), particle
+ * steps per coupling interval K (>= 1), and the extrapolator of the
+ * extrapolator-corrector estimate (Eqs. 12-14): 0 zero, 1 constant, 2 linear.
+ * Defaults: 1.2, 1e-3, 10, 5, 0.  Errors: INVALID_ARG, NONFINITE. */
+st_status st_couple_params(st_handle h, double rho_f, double nu, int sweeps, int steps_per_interval,
+                           int extrapolator);
+
+/* Run nintervals coupling intervals of the asynchronous two-way coupling
+ * (Sec. 2.3) on this GPU.  In interval n the particles take K steps of dt in
+ * the frozen current field u^n (as st_step, on the handle's stream) while a
+ * second stream computes the next field: u* = u^n + S_est^n / (rho_f V) per
+ * cell, then the Jacobi sweeps of (I - nu K dt Lap) u = u* (7-point periodic
+ * Laplacian, from u*).  S_est^n = S^{n-1} - S_ext^{n-1} + S_ext^n is the
+ * estimate of the interval's source from the sources of earlier intervals
+ * (reading of Sec. 2.4: the corrector removes the previous extrapolated part,
+ * which keeps the fluid's total intake equal to the particles' output up to
+ * the last, pending, interval).  At the interval's end the particles' source
+ * S^n leaves the accumulator (so st_get_sources reads only what later
+ * st_step calls deposit) and the new field becomes current.  The first
+ * interval after st_set_fluid has no source history.  Returns after the last
+ * interval's fluid update has been queued; the particle work may still run.
+ * Errors: INVALID_ARG (nintervals < 0, dt <= 0), NONFINITE, STATE (no
+ * fluid), OOM, CUDA, TIMEOUT. */
+st_status st_couple_run(st_handle h, int nintervals, double dt);
+
+/* The current fluid field as FP64 out[k][j][i][3] (the layout of st_set_fluid;
+ * device or host pointer per on_device; synchronises the handle's stream).
+ * Errors: INVALID_ARG, OOM, CUDA. */
+st_status st_get_fluid(st_handle h, double* out, int on_device);
+
+/* Sources given by the particles but not yet received by the fluid,
+ * out[3][ncell] FP64: S^{N-1} - S_ext^{N-1} of the last coupling interval
+ * plus what the accumulator holds now, so that particle momentum + rho_f V
+ * sum(u) + sum(pending) - gravity impulse is conserved.  Synchronises the
+ * handle's stream.  Errors: INVALID_ARG, OOM, CUDA. */
+st_status st_get_pending_sources(st_handle h, double* out, int on_device);
+
 /* Number of CUDA kernels this handle has launched since it was created (a
  * diagnostic for profiling: every kernel of the library counts once per
  * launch). */

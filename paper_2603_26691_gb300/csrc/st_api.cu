@@ -63,13 +63,7 @@ st_status ensure(st_ctx* h, Buf& b, size_t bytes) {
 
 using namespace st;
 
-#define ST_TRY(expr)                     \
-  do {                                   \
-    st_status _s = (expr);               \
-    if (_s != ST_OK) return _s;          \
-  } while (0)
 
-#define ST_CUDA(h, expr) ST_TRY(cuda_check((h), (expr), #expr))
 
 static bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
@@ -168,9 +162,16 @@ void st_destroy(st_handle h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt, &h->keys[0], &h->keys[1],
-                 &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start, &h->acc, &h->red};
+  if (h->stream2) cudaStreamSynchronize(h->stream2);
+  Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt,
+                 &h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start,
+                 &h->acc, &h->red, &h->src_hist[0], &h->src_hist[1], &h->src_hist[2], &h->src_hist[3],
+                 &h->src_est, &h->fl_cur, &h->fl_next, &h->fl_star, &h->fl_tmp, &h->fluid_pad_next, &h->umax_dev};
   for (Buf* b : bufs) dev_free(h, *b);
+  if (h->umax_host) cudaFreeHost(h->umax_host);
+  if (h->ev_main) cudaEventDestroy(h->ev_main);
+  if (h->ev_fluid) cudaEventDestroy(h->ev_fluid);
+  if (h->stream2) cudaStreamDestroy(h->stream2);
   delete h;
 }
 
@@ -235,6 +236,8 @@ st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device) {
   h->umax = umax;
   h->fluid_set = true;
   h->adj_ready = false;
+  h->fl_valid = false;   // a coupled run starts from this field, with no source history
+  h->couple_done = 0;
   return ST_OK;
 }
 
@@ -426,8 +429,9 @@ static st_status prepare_accumulator(st_handle h, double dt, double adds_now, in
   return ST_OK;
 }
 
-st_status st_step(st_handle h, int nsteps, double dt) {
-  ST_TRY(check_handle(h));
+extern "C++" {
+namespace st {
+st_status run_steps(st_ctx* h, int nsteps, double dt) {
   if (nsteps < 0) return set_error(h, ST_ERR_INVALID_ARG, "nsteps < 0");
   if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
   if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");
@@ -461,6 +465,13 @@ st_status st_step(st_handle h, int nsteps, double dt) {
     h->steps_since_sort += 1;
   }
   return ST_OK;
+}
+}  // namespace st
+}  // extern "C++"
+
+st_status st_step(st_handle h, int nsteps, double dt) {
+  ST_TRY(check_handle(h));
+  return run_steps(h, nsteps, dt);
 }
 
 st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {

@@ -88,6 +88,19 @@ struct st_ctx {
   int adj_nsteps = 0, adj_every = 0;
   double adj_dt = 0.0;
   bool adj_ready = false;
+  // two-way coupling (st_couple_*): fluid master fields, source history, second stream
+  double rho_f = 1.2, nu = 1e-3;
+  int sweeps = 10, couple_K = 5, extrap = 0;
+  int64_t couple_done = 0;   // coupling intervals whose source is in the history ring
+  bool fl_valid = false;     // fl_cur holds the current field (mixed handles)
+  st::Buf src_hist[4];       // S of the last intervals, FP64 [3][ncell]; interval n in slot n % 4
+  st::Buf src_est;           // FP64 [3][ncell]
+  st::Buf fl_cur, fl_next, fl_star, fl_tmp;  // fluid fields, float4 (mixed) or D4 (FP64) per cell
+  st::Buf fluid_pad_next;    // mixed: the padded field of the next interval
+  st::Buf umax_dev;          // max |u| of the next field (bits of a non-negative double)
+  double* umax_host = nullptr;  // pinned
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_main = nullptr, ev_fluid = nullptr;
   int64_t launches = 0;      // kernels launched by this handle
   std::string err;
 };
@@ -99,6 +112,14 @@ st_status set_error(st_ctx* h, st_status s, const std::string& msg);
 st_status cuda_check(st_ctx* h, cudaError_t e, const char* what);
 st_status dev_alloc(st_ctx* h, Buf& b, size_t bytes);
 void dev_free(st_ctx* h, Buf& b);
+
+#define ST_TRY(expr)                     \
+  do {                                   \
+    st_status _s = (expr);               \
+    if (_s != ST_OK) return _s;          \
+  } while (0)
+
+#define ST_CUDA(h, expr) ST_TRY(cuda_check((h), (expr), #expr))
 st_status ensure(st_ctx* h, Buf& b, size_t bytes);  // grow-only
 
 // carve the state block
@@ -304,6 +325,8 @@ bool tma_step_supported(const st_ctx* h);                               // step_
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p);      // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
 cudaError_t launch_normalize_acc(st_ctx* h);
+// the particle steps of st_step (sort when due, accumulator bookkeeping, step kernel)
+st_status run_steps(st_ctx* h, int nsteps, double dt);
 // word-capacity bookkeeping of the carry-save accumulator, on the device: a counter (in the flags
 // buffer) bounds the digits added to any word since the last carry propagation; before each step
 // the propagation runs if the counter plus the step's worst case could overflow a word.  `add` is

@@ -208,6 +208,38 @@ class Sim:
     def reorder(self):
         self._chk(self.lib.st_reorder(self.h), "st_reorder")
 
+    # -- asynchronous two-way coupling -------------------------------------------------------
+    EXTRAPOLATORS = {"zero": 0, "const": 1, "lin": 2}
+
+    def couple_params(self, rho_f: float = 1.2, nu: float = 1e-3, sweeps: int = 10, steps_per_interval: int = 5,
+                      extrapolator: str = "zero"):
+        self._chk(self.lib.st_couple_params(self.h, float(rho_f), float(nu), int(sweeps), int(steps_per_interval),
+                                            self.EXTRAPOLATORS[extrapolator]), "st_couple_params")
+
+    def couple_run(self, nintervals: int, dt: float):
+        self._chk(self.lib.st_couple_run(self.h, int(nintervals), float(dt)), "st_couple_run")
+
+    def fluid(self, host: bool = True):
+        """Current fluid field [nz, ny, nx, 3] float64 (numpy if host, else a device tensor)."""
+        shape = (self.grid[2], self.grid[1], self.grid[0], 3)
+        if host:
+            a = np.empty(shape)
+            self._chk(self.lib.st_get_fluid(self.h, C.c_void_p(a.ctypes.data), 0), "st_get_fluid")
+            return a
+        out = torch.empty(shape, dtype=torch.float64, device=self.device)
+        self._chk(self.lib.st_get_fluid(self.h, C.c_void_p(out.data_ptr()), 1), "st_get_fluid")
+        return out
+
+    def pending_sources(self, host: bool = True):
+        """Sources not yet received by the fluid [3, ncell] float64."""
+        if host:
+            a = np.empty((3, self.ncell))
+            self._chk(self.lib.st_get_pending_sources(self.h, C.c_void_p(a.ctypes.data), 0), "st_get_pending_sources")
+            return a
+        out = torch.empty((3, self.ncell), dtype=torch.float64, device=self.device)
+        self._chk(self.lib.st_get_pending_sources(self.h, C.c_void_p(out.data_ptr()), 1), "st_get_pending_sources")
+        return out
+
     def synchronize(self):
         self._chk(self.lib.st_synchronize(self.h), "st_synchronize")
 
