@@ -210,6 +210,65 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
     return ev
 
 
+def run_coupled(args, workload):
+    """The asynchronous two-way coupling workload: K particle steps per coupling interval in a frozen
+    field while the fluid update (estimated source + Jacobi sweeps) runs on a second stream.  One JSON
+    line: coupled particle-steps/s, beside the same particles' uncoupled step time."""
+    import torch
+
+    ws, rank, local = _dist()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    n = args.n or workload.n
+    K = workload.extra["fluid_every"]
+    U32 = workload.make_field().astype(np.float32)
+    sim = setup_sim(workload, n, U32, workload.precision, device)
+    warm = max(1, -(-args.warmup // K))
+    timed = max(1, args.steps // K)
+    R = workload.reorder_every
+    # the same particles stepped without the fluid update first: sorted, warm-up steps, then the
+    # timed steps with a sort every R steps counted from that sort (as the coupled run below)
+    sim.reorder()
+    timed_steps(sim, warm * K, workload.dt, 0, 0)
+    ev = timed_steps(sim, K * timed, workload.dt, R, warm * K)
+    torch.cuda.synchronize()
+    plain_ms = sum(e0.elapsed_time(e2) for (e0, e1, e2, _) in ev)
+    # the coupled run: sorted again, then the library sorts every R steps itself
+    sim.reorder()
+    sim.set_params(reorder_every=R)
+    sim.couple_params(rho_f=1.2, nu=workload.extra["nu"], sweeps=10, steps_per_interval=K, extrapolator="zero")
+    sim.couple_run(warm, workload.dt)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    launches0 = sim.kernel_launches
+    a.record()
+    sim.couple_run(timed, workload.dt)
+    b.record()
+    torch.cuda.synchronize()
+    launches = sim.kernel_launches - launches0
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    sim.close()
+    steps = K * timed
+    line = {"metric": "particle-steps/s, asynchronous two-way coupling (fluid update on a second stream)",
+            "value": n * steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm * K,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload.name, "grid": workload.grid, "particles_per_gpu": n,
+                       "chunk_edge": workload.chunk_edge, "steps_per_interval": K, "nu": workload.extra["nu"],
+                       "jacobi_sweeps": 10, "rho_f": 1.2, "extrapolator": "zero", "dt": workload.dt,
+                       "reorder_every": workload.reorder_every},
+            "uncoupled_ms_per_step": plain_ms / steps,
+            "coupling_overhead": ms / plain_ms - 1.0,
+            "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,6 +296,8 @@ def main():
         workload = dataclasses.replace(workload, grid=args.grid)
     if args.impl == "reference":
         return run_reference(args, workload)
+    if workload.extra and workload.extra.get("fluid_every"):
+        return run_coupled(args, workload)
 
     import torch
 

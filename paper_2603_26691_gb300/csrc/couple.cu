@@ -70,53 +70,50 @@ __global__ void source_add_kernel(const V* __restrict__ u, const double* __restr
   }
 }
 
-// one Jacobi sweep: out = (u* + sum_q lam_q (in(-q) + in(+q))) / (1 + 2 sum lam), periodic
+// one Jacobi sweep: out = (u* + sum_q lam_q (in(-q) + in(+q))) / (1 + 2 sum lam), periodic; one
+// thread per cell of a row, rows on grid y (j) and z (k): no integer division
 template <typename V, typename R>
 __global__ void jacobi_kernel(const V* __restrict__ ustar, const V* __restrict__ in, V* __restrict__ out, int nx,
                               int ny, int nz, R lx, R ly, R lz, R inv_den) {
-  const int64_t ncell = (int64_t)nx * ny * nz;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
-    const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
-    const int64_t xm = i > 0 ? c - sx : c + (nx - 1) * sx, xp = i < nx - 1 ? c + sx : c - (nx - 1) * sx;
-    const int64_t ym = j > 0 ? c - sy : c + (ny - 1) * sy, yp = j < ny - 1 ? c + sy : c - (ny - 1) * sy;
-    const int64_t zm = k > 0 ? c - sz : c + (nz - 1) * sz, zp = k < nz - 1 ? c + sz : c - (nz - 1) * sz;
-    const V s = ustar[c], a = in[xm], b = in[xp], e = in[ym], f = in[yp], g = in[zm], hh = in[zp];
-    R r[3];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= nx) return;
+  const int64_t row = (int64_t)nx * (j + (int64_t)ny * k);
+  const int64_t c = row + i;
+  const int64_t sy = nx, sz = (int64_t)nx * ny;
+  const int64_t xm = row + (i > 0 ? i - 1 : nx - 1), xp = row + (i < nx - 1 ? i + 1 : 0);
+  const int64_t ym = j > 0 ? c - sy : c + (int64_t)(ny - 1) * sy, yp = j < ny - 1 ? c + sy : c - (int64_t)(ny - 1) * sy;
+  const int64_t zm = k > 0 ? c - sz : c + (int64_t)(nz - 1) * sz, zp = k < nz - 1 ? c + sz : c - (int64_t)(nz - 1) * sz;
+  const V s = ustar[c], a = in[xm], b = in[xp], e = in[ym], f = in[yp], g = in[zm], hh = in[zp];
+  R r[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      R acc = comp(s, q);
-      acc = acc + lx * (comp(a, q) + comp(b, q));
-      acc = acc + ly * (comp(e, q) + comp(f, q));
-      acc = acc + lz * (comp(g, q) + comp(hh, q));
-      r[q] = acc * inv_den;
-    }
-    out[c] = make3(r[0], r[1], r[2], (const V*)nullptr);
+  for (int q = 0; q < 3; ++q) {
+    R acc = comp(s, q);
+    acc = acc + lx * (comp(a, q) + comp(b, q));
+    acc = acc + ly * (comp(e, q) + comp(f, q));
+    acc = acc + lz * (comp(g, q) + comp(hh, q));
+    r[q] = acc * inv_den;
   }
+  out[c] = make3(r[0], r[1], r[2], (const V*)nullptr);
 }
 
-// padded FP32 field (P ghost layers, periodic) from the unpadded one
+// padded FP32 field (P ghost layers, periodic) from the unpadded one; grid y, z = padded rows
 __global__ void pad_kernel(const float4* __restrict__ u, float4* __restrict__ out, int nx, int ny, int nz, int P) {
-  const int64_t px = nx + 2 * P, py = ny + 2 * P, pz = nz + 2 * P;
-  const int64_t total = px * py * pz;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int a = (int)(t % px), b = (int)((t / px) % py), c = (int)(t / (px * py));
-    int i = (a - P) % nx, j = (b - P) % ny, k = (c - P) % nz;
-    i += i < 0 ? nx : 0;
-    j += j < 0 ? ny : 0;
-    k += k < 0 ? nz : 0;
-    out[t] = u[i + (int64_t)nx * (j + (int64_t)ny * k)];
-  }
+  const int px = nx + 2 * P, py = ny + 2 * P;
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y, c = blockIdx.z;
+  if (a >= px) return;
+  int i = a - P, j = b - P, k = c - P;
+  if (i < 0 || i >= nx) i = ((i % nx) + nx) % nx;  // ghost layers (the grid may be thinner than P)
+  if (j < 0 || j >= ny) j = ((j % ny) + ny) % ny;
+  if (k < 0 || k >= nz) k = ((k % nz) + nz) % nz;
+  out[a + (int64_t)px * (b + (int64_t)py * c)] = u[i + (int64_t)nx * (j + (int64_t)ny * k)];
 }
 
-// the interior of the padded field
+// the interior of the padded field; grid y, z = rows
 __global__ void unpad_kernel(const float4* __restrict__ in, float4* __restrict__ u, int nx, int ny, int nz, int P) {
-  const int64_t ncell = (int64_t)nx * ny * nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+  if (i >= nx) return;
   const int64_t px = nx + 2 * P, pxy = px * (ny + 2 * P);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
-    u[c] = in[(i + P) + px * (j + P) + pxy * (k + P)];
-  }
+  u[i + (int64_t)nx * (j + (int64_t)ny * k)] = in[(i + P) + px * (j + P) + pxy * (k + P)];
 }
 
 // max |component| over the field, as the bits of a non-negative double (ordered like the values)
@@ -176,9 +173,9 @@ void* current_field(st_ctx* h) {
   if (!mixed(h)) return h->fluid.p;
   if (!h->fl_valid) {
     const Geometry& G = h->geo;
-    unpad_kernel<<<cgrid(G.ncell), kCoupleThreads, 0, h->stream>>>((const float4*)h->fluid_pad.p,
-                                                                    (float4*)h->fl_cur.p, G.n[0], G.n[1], G.n[2],
-                                                                    kFluidPad);
+    const dim3 grid((G.n[0] + 127) / 128, G.n[1], G.n[2]);
+    unpad_kernel<<<grid, 128, 0, h->stream>>>((const float4*)h->fluid_pad.p, (float4*)h->fl_cur.p, G.n[0], G.n[1],
+                                              G.n[2], kFluidPad);
     h->launches += 1;
     h->fl_valid = true;
   }
@@ -216,16 +213,17 @@ cudaError_t launch_fluid_update(st_ctx* h, const V* cur, double dt) {
     const V* in = (const V*)h->fl_star.p;
     for (int k = 0; k < h->sweeps; ++k) {
       V* out = ((h->sweeps - 1 - k) % 2 == 0) ? (V*)h->fl_next.p : (V*)h->fl_tmp.p;
-      jacobi_kernel<V, R><<<cgrid(nc), kCoupleThreads, 0, s>>>((const V*)h->fl_star.p, in, out, G.n[0], G.n[1],
-                                                               G.n[2], (R)lam[0], (R)lam[1], (R)lam[2], inv_den);
+      const dim3 grid((G.n[0] + 127) / 128, G.n[1], G.n[2]);
+      jacobi_kernel<V, R><<<grid, 128, 0, s>>>((const V*)h->fl_star.p, in, out, G.n[0], G.n[1], G.n[2], (R)lam[0],
+                                                (R)lam[1], (R)lam[2], inv_den);
       in = out;
       ++launches;
     }
   }
   if (mixed(h)) {
-    const int64_t tot = (int64_t)(G.n[0] + 2 * kFluidPad) * (G.n[1] + 2 * kFluidPad) * (G.n[2] + 2 * kFluidPad);
-    pad_kernel<<<cgrid(tot), kCoupleThreads, 0, s>>>((const float4*)h->fl_next.p, (float4*)h->fluid_pad_next.p,
-                                                     G.n[0], G.n[1], G.n[2], kFluidPad);
+    const dim3 grid((G.n[0] + 2 * kFluidPad + 127) / 128, G.n[1] + 2 * kFluidPad, G.n[2] + 2 * kFluidPad);
+    pad_kernel<<<grid, 128, 0, s>>>((const float4*)h->fl_next.p, (float4*)h->fluid_pad_next.p, G.n[0], G.n[1],
+                                    G.n[2], kFluidPad);
     ++launches;
   }
   cudaMemsetAsync(h->umax_dev.p, 0, 8, s);
