@@ -336,6 +336,7 @@ cudaError_t launch_acc_maybe_normalize(st_ctx* h, double worst, double add);
 cudaError_t reset_acc_counter(st_ctx* h);
 constexpr size_t kAccCounterOffset = 64;   // bytes into the flags buffer: uint64 counter
 constexpr size_t kAccFlagOffset = 72;      // int: 1 if the last check propagated carries
+constexpr size_t kUnitCounterOffset = 80;  // uint32: next unit of the sorted-step kernel
 cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]);
 cudaError_t launch_particle_sums(st_ctx* h, double out[4]);  // P_x, P_y, P_z, M

@@ -97,6 +97,7 @@ struct TmaArgs {
   const uint32_t* __restrict__ cell_start;
   int* __restrict__ err;
   unsigned long long* __restrict__ acc_ctr;  // digits added to any accumulator word (global commits)
+  unsigned* __restrict__ unit_ctr;           // next unit to hand out (zeroed before the launch)
   int64_t ncell;
   int nx, ny, nz;
   int nunits;                         // units of kU^3 cells in key order
@@ -287,6 +288,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
   uint64_t* tile_empty = tile_full + 2;      // [2]        consumers done with a fluid tile
   uint64_t* dep_done = tile_empty + 2;       // [1]        every consumer warp finished a unit's deposits
   uint64_t* flush_done = dep_done + 1;       // [1]        deposit tile flushed and cleared
+  volatile int* unit_slot = reinterpret_cast<volatile int*>(flush_done + 1);  // [kFluidBufs] unit of a tile
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -310,7 +312,11 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
     if (lane == 0) {
       int loaded = 0;    // non-empty units whose fluid tile was issued
       int64_t gt = 0;    // particle stages issued
-      for (int u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+      // units are handed out one at a time from a global counter, so a CTA that starts late (its SM
+      // busy with other work) simply takes fewer units
+      for (;;) {
+        const int u = (int)atomicAdd(a.unit_ctr, 1u);
+        if (u >= a.nunits) break;
         const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
         const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
         if (E <= S) continue;
@@ -319,6 +325,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           atomicOr(a.err, 1);
           return;
         }
+        unit_slot[buf] = u;  // published to the consumers by the tile barrier's arrive
         int ox, oy, oz;
         unit_origin(a, u, ox, oy, oz);
         mbar_expect_tx(&tile_full[buf], kFluidBytes);
@@ -344,6 +351,16 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           ++gt;
         }
       }
+      // no more units: a tile phase without a copy, unit -1
+      {
+        const int buf = loaded % kFluidBufs;
+        if (loaded >= kFluidBufs && !mbar_wait(&tile_empty[buf], ((loaded / kFluidBufs) - 1) & 1)) {
+          atomicOr(a.err, 1);
+          return;
+        }
+        unit_slot[buf] = -1;
+        mbar_arrive(&tile_full[buf]);
+      }
       // let the last copies land before the CTA can exit
       const int64_t first = gt > kStages ? gt - kStages : 0;
       for (int64_t k = first; k < gt; ++k) mbar_wait(&empty[k % kStages], (k / kStages) & 1);
@@ -357,15 +374,16 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
   const int px = a.nx + 2 * kG, pxy = (a.nx + 2 * kG) * (a.ny + 2 * kG);
   int loaded = 0;
   int64_t gt = 0;
-  for (int u = blockIdx.x; u < a.nunits; u += gridDim.x) {
-    const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
-    const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
-    if (E <= S) continue;
+  for (;;) {
     const int buf = loaded % kFluidBufs;
     if (!mbar_wait(&tile_full[buf], (loaded / kFluidBufs) & 1)) {
       atomicOr(a.err, 4);
       return;
     }
+    const int u = unit_slot[buf];
+    if (u < 0) break;
+    const int64_t S = a.cell_start[(int64_t)u * (kU * kU * kU)];
+    const int64_t E = a.cell_start[(int64_t)(u + 1) * (kU * kU * kU)];
     const float4* tile = fluid + buf * (kTE * kTE * kTE);
     int uo[3];
     unit_origin(a, u, uo[0], uo[1], uo[2]);
@@ -751,6 +769,11 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
   a.cell_start = (const uint32_t*)h->cell_start.p;
   a.err = (int*)h->flags.p;
   a.acc_ctr = (unsigned long long*)((char*)h->flags.p + kAccCounterOffset);
+  a.unit_ctr = (unsigned*)((char*)h->flags.p + kUnitCounterOffset);
+  {
+    cudaError_t e = cudaMemsetAsync(a.unit_ctr, 0, sizeof(unsigned), h->stream);
+    if (e != cudaSuccess) return e;
+  }
   a.ncell = h->geo.ncell;
   a.nx = nx;
   a.ny = ny;
