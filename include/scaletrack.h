@@ -180,6 +180,16 @@ st_status st_get_cells(st_handle h, int64_t first, int64_t count, int32_t* cells
  * order).  Errors: STATE if never sorted.  Synchronises. */
 st_status st_get_cell_counts(st_handle h, int64_t* counts, int on_device);
 
+/* Bounding boxes of the chunks (Sec. 2.2): a chunk is the set of particles in
+ * the key range of its B^3 block of cells as of the last reorder, and its box
+ * is the min and max of their current positions, each unwrapped to the
+ * periodic image nearest the chunk's centre.  out[chunk][6] FP64 = {xmin,
+ * ymin, zmin, xmax, ymax, zmax}, chunks numbered x fastest (the major part of
+ * the ordering key); an empty chunk gets +inf for the minima and -inf for the
+ * maxima.  Synchronises the handle's stream.  Errors: INVALID_ARG, STATE (not
+ * sorted since particles were added or cleared), OOM, CUDA. */
+st_status st_chunk_bounds(st_handle h, double* out, int on_device);
+
 /* Global invariants in FP64: out = {particle count, P_x, P_y, P_z, S_x, S_y,
  * S_z, M} with P = sum_p m_p v_p, S = sum over cells of the accumulated
  * source and M = sum_p m_p.  With no fluid forcing beyond drag,

@@ -86,6 +86,7 @@ def lib():
             L.orc_adjoint.argtypes = [pg, pd, i64, pd, pd, pd, i32, d, pd, pd, pd, pd]
             L.orc_adjoint.restype = C.c_int
             L.orc_ecm_estimate.argtypes, L.orc_ecm_estimate.restype = [i32, i64, pd, pd, pd, pd], None
+            L.orc_chunk_bounds.argtypes, L.orc_chunk_bounds.restype = [pg, i64, pd, pd, pd], i64
             L.orc_fluid_update.argtypes = [pg, pd, pd, d, d, d, i32]
             L.orc_fluid_update.restype = C.c_int
             L.orc_couple.argtypes = [pg, pd, i64, pd, pd, pd, i32, i32, d, d, d, i32, i32, pd]
@@ -261,3 +262,17 @@ def couple(G: Grid, U, pos, vel, d, nint: int, K: int, dt: float, rho_f: float, 
     if rc != 0:
         raise ValueError(f"orc_couple failed ({rc})")
     return U.reshape(shape), pos, vel, pending
+
+
+def chunk_bounds(G: Grid, pos_sort, pos_now) -> np.ndarray:
+    """Per-chunk boxes [nchunk, 6] = (min xyz, max xyz) of the current positions of each chunk's
+    particles (membership from pos_sort), unwrapped to the image nearest the chunk centre."""
+    pos_sort = _f64(pos_sort).reshape(3, -1)
+    pos_now = _f64(pos_now).reshape(3, -1)
+    B = int(G.chunk_edge)
+    nch = int(np.prod([(int(G.n[q]) + B - 1) // B for q in range(3)]))
+    out = np.zeros((nch, 6))
+    r = lib().orc_chunk_bounds(C.byref(G), pos_sort.shape[1], _pd(pos_sort), _pd(pos_now), _pd(out))
+    if r < 0:
+        raise ValueError("orc_chunk_bounds failed")
+    return out

@@ -501,3 +501,36 @@ int orc_couple(const orc_grid* G, double* U, int64_t n, double* pos, double* vel
   for (int k = 0; k < 3; ++k) free(hist[k]);
   return 0;
 }
+
+int64_t orc_chunk_bounds(const orc_grid* G, int64_t n, const double* pos_sort, const double* pos_now,
+                         double* out) {
+  if (!grid_ok(G) || n < 0 || G->chunk_edge < 1) return -1;
+  int32_t B = G->chunk_edge;
+  int32_t nc[3];
+  for (int ax = 0; ax < 3; ++ax) nc[ax] = (G->n[ax] + B - 1) / B;
+  int64_t nchunk = (int64_t)nc[0] * nc[1] * nc[2];
+  for (int64_t c = 0; c < nchunk; ++c)
+    for (int ax = 0; ax < 3; ++ax) {
+      out[6 * c + ax] = INFINITY;
+      out[6 * c + 3 + ax] = -INFINITY;
+    }
+  for (int64_t p = 0; p < n; ++p) {
+    double xs[3] = {pos_sort[p], pos_sort[n + p], pos_sort[2 * n + p]};
+    int32_t idx[3];
+    orc_cell(G, xs, idx);
+    int32_t ch[3] = {idx[0] / B, idx[1] / B, idx[2] / B};
+    int64_t c = ch[0] + (int64_t)nc[0] * (ch[1] + (int64_t)nc[1] * ch[2]);
+    for (int ax = 0; ax < 3; ++ax) {
+      double h = cell_size(G, ax);
+      double centre = ((double)ch[ax] * B + 0.5 * B) * h;
+      double x = orc_wrap(pos_now[ax * n + p], G->L[ax]);
+      /* nearest periodic image of x to the centre */
+      double dx = x - centre;
+      dx = dx - G->L[ax] * floor(dx / G->L[ax] + 0.5);
+      double xu = centre + dx;
+      if (xu < out[6 * c + ax]) out[6 * c + ax] = xu;
+      if (xu > out[6 * c + 3 + ax]) out[6 * c + 3 + ax] = xu;
+    }
+  }
+  return nchunk;
+}

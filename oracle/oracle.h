@@ -119,6 +119,16 @@ int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos
                 const double* vel0, const double* d, int32_t nsteps, double dt,
                 const double* lam, double* grad_d, double* grad_alpha, double* gradU);
 
+/* Bounding boxes of the chunks (Sec. 2.2): a chunk is the set of particles whose
+ * cell, at the time of the last ordering (pos_sort[3][n]), lies in its B^3 block
+ * of cells (numbered x fastest, as in orc_key); its box is the min and max of
+ * the current positions pos_now[3][n], each unwrapped to the periodic image
+ * nearest the chunk's centre.  out[chunk][6] = {xmin, ymin, zmin, xmax, ymax,
+ * zmax}; an empty chunk gets {+inf, +inf, +inf, -inf, -inf, -inf}.  Returns
+ * the number of chunks, or -1 on bad arguments. */
+int64_t orc_chunk_bounds(const orc_grid* G, int64_t n, const double* pos_sort, const double* pos_now,
+                         double* out);
+
 /* Extrapolator-corrector estimate of the source of coupling interval n
  * (Sec. 2.4, Eqs. 12-14): S_est^n = S^{n-1} - S_ext^{n-1} + S_ext^n, where
  * S_ext^m extrapolates S^m from the sources before it: extrap 0 = zero (0),

@@ -65,6 +65,7 @@ SIGNATURES = {
     "st_adjoint_backward": (_i, [_vp, _vp, _i, _vp, _P(_d), _vp, _i]),
     "st_sort_keys_static": (_i, [_vp, _i64, _i, _vp, _vp, _vp]),
     "st_gen_particles": (_i, [_vp, _u64, _i64, _i64, _P(_d), _d, _vp, _i, _vp, _vp, _vp, _vp]),
+    "st_chunk_bounds": (_i, [_vp, _vp, _i]),
     "st_couple_params": (_i, [_vp, _d, _d, _i, _i, _i]),
     "st_couple_run": (_i, [_vp, _i, _d]),
     "st_get_fluid": (_i, [_vp, _vp, _i]),

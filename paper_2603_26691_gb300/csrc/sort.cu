@@ -13,6 +13,7 @@
 //
 // Waits on other blocks are bounded: a look-back that gives up sets a device flag (reported as
 // ST_ERR_TIMEOUT) and carries on, so no block can hang the grid.
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -459,6 +460,61 @@ __global__ void cell_counts_kernel(const uint32_t* __restrict__ start, KeyGeo g,
   }
 }
 
+// Bounding box of every chunk's particles (the particles of the chunk's key range in the sorted
+// storage), each current position unwrapped to the periodic image nearest the chunk's centre:
+// out[c][6] = {min x, y, z, max x, y, z}; +inf / -inf for an empty chunk.  One block per chunk at a
+// time; min and max do not depend on the order of the reduction.
+template <bool MIXED>
+__global__ void __launch_bounds__(256) chunk_bounds_kernel(MixedState ms, F64State fs,
+                                                          const uint32_t* __restrict__ start, KeyGeo g, double L0,
+                                                          double L1, double L2, double h0, double h1, double h2,
+                                                          int64_t nchunk, double* __restrict__ out) {
+  __shared__ double red[6][8];
+  const double L[3] = {L0, L1, L2}, h[3] = {h0, h1, h2};
+  const int64_t per = (int64_t)1 << (3 * g.logB);
+  for (int64_t c = blockIdx.x; c < nchunk; c += gridDim.x) {
+    const int cc[3] = {(int)(c % g.ncx), (int)((c / g.ncx) % g.ncy), (int)(c / ((int64_t)g.ncx * g.ncy))};
+    double centre[3];
+    for (int q = 0; q < 3; ++q) centre[q] = __dmul_rn((double)cc[q] * g.B + 0.5 * g.B, h[q]);
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    const int64_t S = start[c * per], E = start[(c + 1) * per];
+    for (int64_t p = S + threadIdx.x; p < E; p += blockDim.x) {
+      double x[3];
+      if (MIXED) {
+        const int32_t cl = ms.cell[p];
+        const int idx[3] = {cell_i(cl), cell_j(cl), cell_k(cl)};
+        for (int q = 0; q < 3; ++q) x[q] = __dmul_rn(__dadd_rn((double)idx[q], (double)ms.xi[q][p]), h[q]);
+      } else {
+        for (int q = 0; q < 3; ++q) x[q] = fs.x[q][p];
+      }
+      for (int q = 0; q < 3; ++q) {
+        double dx = __dsub_rn(x[q], centre[q]);
+        dx = __dsub_rn(dx, __dmul_rn(L[q], floor(__dadd_rn(__ddiv_rn(dx, L[q]), 0.5))));
+        const double xu = __dadd_rn(centre[q], dx);
+        lo[q] = fmin(lo[q], xu);
+        hi[q] = fmax(hi[q], xu);
+      }
+    }
+    double v[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+    for (int o = 16; o > 0; o >>= 1)
+      for (int k = 0; k < 6; ++k) {
+        const double t = __shfl_down_sync(0xffffffffu, v[k], o);
+        v[k] = k < 3 ? fmin(v[k], t) : fmax(v[k], t);
+      }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+      for (int k = 0; k < 6; ++k) red[k][w] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+      const int k = threadIdx.x;
+      double r = red[k][0];
+      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) r = k < 3 ? fmin(r, red[k][ww]) : fmax(r, red[k][ww]);
+      out[6 * c + k] = r;
+    }
+    __syncthreads();
+  }
+}
+
 KeyGeo key_geo(const st_ctx* h) {
   KeyGeo g;
   for (int q = 0; q < 3; ++q) {
@@ -624,6 +680,23 @@ st_status sort_particles(st_ctx* h) {
   std::swap(h->state, h->state_alt);
   std::swap(h->ids, h->ids_alt);
   return ST_OK;
+}
+
+cudaError_t launch_chunk_bounds(st_ctx* h, double* out) {
+  KeyGeo g = key_geo(h);
+  const int64_t nchunk = (int64_t)g.ncx * g.ncy * ((h->geo.n[2] + g.B - 1) / g.B);
+  const int grid = (int)std::min<int64_t>(nchunk, 152 * 8);
+  const Geometry& G = h->geo;
+  if (h->prec == ST_FP64)
+    chunk_bounds_kernel<false><<<grid, 256, 0, h->stream>>>(MixedState{}, carve_f64(h->state.p, h->cap),
+                                                            (const uint32_t*)h->cell_start.p, g, G.L[0], G.L[1],
+                                                            G.L[2], G.h[0], G.h[1], G.h[2], nchunk, out);
+  else
+    chunk_bounds_kernel<true><<<grid, 256, 0, h->stream>>>(carve_mixed(h->state.p, h->cap, h->prec == ST_MIXED_BF16V),
+                                                           F64State{}, (const uint32_t*)h->cell_start.p, g, G.L[0],
+                                                           G.L[1], G.L[2], G.h[0], G.h[1], G.h[2], nchunk, out);
+  h->launches += 1;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts) {

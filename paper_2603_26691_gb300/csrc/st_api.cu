@@ -553,6 +553,27 @@ st_status st_get_cells(st_handle h, int64_t first, int64_t count, int32_t* cells
   return cuda_check(h, e, "get cells");
 }
 
+st_status st_chunk_bounds(st_handle h, double* out, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!out) return set_error(h, ST_ERR_INVALID_ARG, "out is NULL");
+  if (!h->sorted) return set_error(h, ST_ERR_STATE, "particles not sorted since the last change");
+  const int B = h->geo.B;
+  const int64_t nchunk =
+      (int64_t)((h->geo.n[0] + B - 1) / B) * ((h->geo.n[1] + B - 1) / B) * ((h->geo.n[2] + B - 1) / B);
+  const size_t bytes = (size_t)nchunk * 6 * sizeof(double);
+  Buf tmp;
+  double* dst = out;
+  if (!on_device) {
+    ST_TRY(dev_alloc(h, tmp, bytes));
+    dst = (double*)tmp.p;
+  }
+  cudaError_t e = launch_chunk_bounds(h, dst);
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(h, tmp);
+  return cuda_check(h, e, "chunk bounds");
+}
+
 st_status st_get_cell_counts(st_handle h, int64_t* counts, int on_device) {
   ST_TRY(check_handle(h));
   if (!counts) return set_error(h, ST_ERR_INVALID_ARG, "counts is NULL");

@@ -352,6 +352,7 @@ cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, c
                        double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
                        uint32_t* ids);
 st_status sort_particles(st_ctx* h);                                       // sort.cu
-cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);              // sort.cu
+cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);
+cudaError_t launch_chunk_bounds(st_ctx* h, double* out);              // sort.cu
 
 }  // namespace st

@@ -77,6 +77,7 @@ class Sim:
             self._alloc_fns = (_lib.ALLOC_FN(_a), _lib.FREE_FN(_f))
             self._alloc = _lib.Allocator(self._alloc_fns[0], self._alloc_fns[1], None)
         h = C.c_void_p()
+        self.chunk_edge = int(chunk_edge)
         st = self.lib.st_create_grid(*self.grid, *self.box, int(chunk_edge), _lib.PRECISIONS[precision],
                                      C.byref(self._alloc) if self._alloc is not None else None,
                                      C.c_void_p(self.stream.cuda_stream), C.byref(h))
@@ -283,6 +284,14 @@ class Sim:
         out = np.empty(self.ncell, dtype=np.int64)
         self._chk(self.lib.st_get_cell_counts(self.h, C.c_void_p(out.ctypes.data), 0), "st_get_cell_counts")
         return out
+
+    def chunk_bounds(self) -> np.ndarray:
+        """Per-chunk boxes [nchunk, 6] (min xyz, max xyz) of the chunks' current positions."""
+        B = self.chunk_edge
+        nch = int(np.prod([(g + B - 1) // B for g in self.grid]))
+        a = np.empty((nch, 6))
+        self._chk(self.lib.st_chunk_bounds(self.h, C.c_void_p(a.ctypes.data), 0), "st_chunk_bounds")
+        return a
 
     def invariants(self) -> np.ndarray:
         out = (C.c_double * 8)()

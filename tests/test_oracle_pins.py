@@ -341,3 +341,28 @@ def test_adjoint_dot_product_with_random_direction(oracle_mod):
     fd = (F(eps) - F(-eps)) / (2 * eps)
     ip = float((gd * dd).sum() + ga * da + (gU.reshape(U.shape) * dU).sum())
     assert abs(fd - ip) <= 1e-6 * abs(fd)
+
+
+def test_chunk_bounds_hand_example_and_properties(oracle_mod):
+    """Chunk boxes (Sec. 2.2): a hand-worked example on a 16^3 grid with 8^3-cell chunks (box 1, h =
+    1/16, chunk centres at 0.25 / 0.75), including a particle that crossed the periodic face and is
+    unwrapped to the image nearest its chunk's centre; and, for particles that have not moved, every
+    box lies inside its chunk's block of cells and does not depend on the particles' order."""
+    G = oracle_mod.make_grid(16, chunk_edge=8)
+    sort_pos = np.array([[0.01, 0.30, 0.90], [0.01, 0.20, 0.90], [0.01, 0.10, 0.95]])
+    now_pos = np.array([[0.99, 0.35, 0.02], [0.01, 0.20, 0.90], [0.01, 0.10, 0.95]])
+    b = oracle_mod.chunk_bounds(G, sort_pos, now_pos)
+    # chunk 0 holds particles 0 and 1: particle 0 moved from x = 0.01 across the face to 0.99,
+    # which is x = -0.01 next to the chunk (centre 0.25)
+    assert np.allclose(b[0], [-0.01, 0.01, 0.01, 0.35, 0.20, 0.10], atol=1e-15)
+    # chunk (1, 1, 1) = 1 + 2 (1 + 2 * 1) = 7 holds particle 2, at x = 0.02 -> 1.02 beside centre 0.75
+    assert np.allclose(b[7], [1.02, 0.90, 0.95, 1.02, 0.90, 0.95], atol=1e-15)
+    assert np.all(np.isinf(b[[1, 2, 3, 4, 5, 6]]))
+    rng = np.random.default_rng(9)
+    pos = rng.uniform(0, 1, size=(3, 500))
+    bb = oracle_mod.chunk_bounds(G, pos, pos)
+    perm = rng.permutation(500)
+    assert np.array_equal(bb, oracle_mod.chunk_bounds(G, pos[:, perm], pos[:, perm]))
+    for c in range(8):
+        lo = np.array([c % 2, (c // 2) % 2, c // 4]) * 0.5
+        assert np.all(bb[c, :3] >= lo) and np.all(bb[c, 3:] <= lo + 0.5)
