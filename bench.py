@@ -41,8 +41,8 @@ STEP_BYTES = {"mixed_f32": 32 + 28, "mixed_bf16": 26 + 22, "fp64": 56 + 48}
 STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
                            "step_mixed_tma.cu")
 MEASURED_TRAFFIC = {
-    # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches (fresh to 3 steps of drift), 64.17-64.27 B
-    ("ca8491dd11374c3356b14772fd4d585588c5381b10129fab5ff51a5965303886", "fourier256_mixed_1e9"): 64.21,
+    # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches (fresh to 3 steps of drift), 64.07-64.15 B
+    ("af9f9494f100f87ef717ef93d913b30bbbec87fd38b8695ad6856848a77c5df2", "fourier256_mixed_1e9"): 64.10,
 }
 
 
@@ -369,6 +369,16 @@ def main():
                 "algorithmic_bytes_per_particle_step": STEP_BYTES[precision], "peak_kind": peak_kind,
                 "step_kernel_ms": step_avg}
 
+    # per-chunk bounding boxes of the sorted state (on demand: one read of cells and offsets)
+    sim.reorder()
+    cb0 = torch.cuda.Event(enable_timing=True)
+    cb1 = torch.cuda.Event(enable_timing=True)
+    cb0.record()
+    sim.chunk_bounds()
+    cb1.record()
+    torch.cuda.synchronize()
+    chunk_bounds_ms = cb0.elapsed_time(cb1)
+
     # end to end through the C ABI with host buffers: each step receives the fluid field from
     # pinned host memory and returns the per-cell sources to pinned host memory
     Uh = torch.from_numpy(U32).pin_memory()
@@ -428,7 +438,8 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "breakdown": {"step_kernel_ms_avg": step_avg, "sort_ms_avg": (sum(sort_ms) / len(sort_ms)) if sort_ms else None,
-                          "sorts_in_timed_region": len(sort_ms)},
+                          "sorts_in_timed_region": len(sort_ms),
+                          "chunk_bounds_ms": chunk_bounds_ms},
             "fp64_step": fp64}
     if rank == 0:
         print(json.dumps(line), flush=True)

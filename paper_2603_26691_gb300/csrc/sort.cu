@@ -463,53 +463,93 @@ __global__ void cell_counts_kernel(const uint32_t* __restrict__ start, KeyGeo g,
 // Bounding box of every chunk's particles (the particles of the chunk's key range in the sorted
 // storage), each current position unwrapped to the periodic image nearest the chunk's centre:
 // out[c][6] = {min x, y, z, max x, y, z}; +inf / -inf for an empty chunk.  One block per chunk at a
-// time; min and max do not depend on the order of the reduction.
+// time.  The extreme particles are found with exact integer keys - per axis the cell's offset from
+// the chunk (moved by one box length when the cell is more than half a box from the chunk's
+// centre) in the high half and the bits of the non-negative in-cell offset (mixed) in the low
+// half, or the unwrapped FP64 position ordered as an integer (FP64 state) - and for the mixed
+// state only the winners' positions are unwrapped in FP64, with the oracle's formula: min and max
+// do not depend on the order of the reduction, and the FP64 work is per chunk, not per particle.
+__device__ __forceinline__ long long ordered_bits(double x) {  // integer order = double order
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b);
+}
+__device__ __forceinline__ double from_ordered_bits(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (long long)(0x8000000000000000ull - (unsigned long long)k));
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(256) chunk_bounds_kernel(MixedState ms, F64State fs,
                                                           const uint32_t* __restrict__ start, KeyGeo g, double L0,
                                                           double L1, double L2, double h0, double h1, double h2,
                                                           int64_t nchunk, double* __restrict__ out) {
-  __shared__ double red[6][8];
+  __shared__ long long red[6][8];
   const double L[3] = {L0, L1, L2}, h[3] = {h0, h1, h2};
   const int64_t per = (int64_t)1 << (3 * g.logB);
+  const long long kMax = 0x7fffffffffffffffll, kMin = -kMax - 1;
   for (int64_t c = blockIdx.x; c < nchunk; c += gridDim.x) {
     const int cc[3] = {(int)(c % g.ncx), (int)((c / g.ncx) % g.ncy), (int)(c / ((int64_t)g.ncx * g.ncy))};
-    double centre[3];
-    for (int q = 0; q < 3; ++q) centre[q] = __dmul_rn((double)cc[q] * g.B + 0.5 * g.B, h[q]);
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    long long lo[3] = {kMax, kMax, kMax}, hi[3] = {kMin, kMin, kMin};
     const int64_t S = start[c * per], E = start[(c + 1) * per];
     for (int64_t p = S + threadIdx.x; p < E; p += blockDim.x) {
-      double x[3];
+      int idx[3];
       if (MIXED) {
         const int32_t cl = ms.cell[p];
-        const int idx[3] = {cell_i(cl), cell_j(cl), cell_k(cl)};
-        for (int q = 0; q < 3; ++q) x[q] = __dmul_rn(__dadd_rn((double)idx[q], (double)ms.xi[q][p]), h[q]);
-      } else {
-        for (int q = 0; q < 3; ++q) x[q] = fs.x[q][p];
+        idx[0] = cell_i(cl);
+        idx[1] = cell_j(cl);
+        idx[2] = cell_k(cl);
       }
+#pragma unroll
       for (int q = 0; q < 3; ++q) {
-        double dx = __dsub_rn(x[q], centre[q]);
-        dx = __dsub_rn(dx, __dmul_rn(L[q], floor(__dadd_rn(__ddiv_rn(dx, L[q]), 0.5))));
-        const double xu = __dadd_rn(centre[q], dx);
-        lo[q] = fmin(lo[q], xu);
-        hi[q] = fmax(hi[q], xu);
+        long long key;
+        if (MIXED) {
+          // offset of the cell from the chunk's first cell, moved to the image nearest the centre
+          int r = idx[q] - cc[q] * g.B;
+          if (2 * r - g.B >= g.n[q]) r -= g.n[q];
+          else if (2 * r - g.B < -g.n[q]) r += g.n[q];
+          key = ((long long)(r + (1 << 20)) << 32) | (long long)__float_as_uint(ms.xi[q][p]);
+        } else {
+          // FP64 positions: the unwrapped position itself, with the oracle's arithmetic
+          const double cen = __dmul_rn((double)cc[q] * g.B + 0.5 * g.B, h[q]);
+          double dx = __dsub_rn(fs.x[q][p], cen);
+          dx = __dsub_rn(dx, __dmul_rn(L[q], floor(__dadd_rn(__ddiv_rn(dx, L[q]), 0.5))));
+          key = ordered_bits(__dadd_rn(cen, dx));
+        }
+        lo[q] = min(lo[q], key);
+        hi[q] = max(hi[q], key);
       }
     }
-    double v[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+    long long v[6] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
     for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
       for (int k = 0; k < 6; ++k) {
-        const double t = __shfl_down_sync(0xffffffffu, v[k], o);
-        v[k] = k < 3 ? fmin(v[k], t) : fmax(v[k], t);
+        const long long t = __shfl_down_sync(0xffffffffu, v[k], o);
+        v[k] = k < 3 ? min(v[k], t) : max(v[k], t);
       }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
       for (int k = 0; k < 6; ++k) red[k][w] = v[k];
     __syncthreads();
     if (threadIdx.x < 6) {
-      const int k = threadIdx.x;
-      double r = red[k][0];
-      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) r = k < 3 ? fmin(r, red[k][ww]) : fmax(r, red[k][ww]);
-      out[6 * c + k] = r;
+      const int k = threadIdx.x, q = k % 3;
+      long long r = red[k][0];
+      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) r = k < 3 ? min(r, red[k][ww]) : max(r, red[k][ww]);
+      double res;
+      if (E <= S) {
+        res = k < 3 ? INFINITY : -INFINITY;
+      } else if (MIXED) {
+        // the winner's position, unwrapped with the oracle's arithmetic
+        int i = (int)((r >> 32) - (1 << 20)) + cc[q] * g.B;
+        i = i < 0 ? i + g.n[q] : (i >= g.n[q] ? i - g.n[q] : i);
+        const double x =
+            __dmul_rn(__dadd_rn((double)i, (double)__uint_as_float((unsigned)(r & 0xffffffffll))), h[q]);
+        const double centre = __dmul_rn((double)cc[q] * g.B + 0.5 * g.B, h[q]);
+        double dx = __dsub_rn(x, centre);
+        dx = __dsub_rn(dx, __dmul_rn(L[q], floor(__dadd_rn(__ddiv_rn(dx, L[q]), 0.5))));
+        res = __dadd_rn(centre, dx);
+      } else {
+        res = from_ordered_bits(r);
+      }
+      out[6 * c + k] = res;
     }
     __syncthreads();
   }
