@@ -68,21 +68,6 @@ __device__ __forceinline__ void tma_load_tile(void* dst, const CUtensorMap* map,
       : "memory");
 }
 
-// 1 - e^{-x} for x >= 0: its degree-5 Taylor polynomial in Horner form for x < 1/8 (truncation
-// below 5e-8 relative), else 1 - 2^(-x log2 e); *e = e^{-x}
-__device__ __forceinline__ float one_minus_exp(float x, float* e) {
-  float ex;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(-1.4426950408889634f * x));
-  float s = fmaf(x, 1.0f / 120.0f, -1.0f / 24.0f);
-  s = fmaf(x, s, 1.0f / 6.0f);
-  s = fmaf(x, s, -0.5f);
-  s = fmaf(x, s, 1.0f);
-  const float small = x * s;
-  const float big = 1.0f - ex;
-  const float r = x < 0.125f ? small : big;
-  *e = x < 0.125f ? 1.0f - r : ex;
-  return r;
-}
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -181,9 +166,37 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+__device__ __forceinline__ unsigned long long add_rm2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long dup2(float a) { return pack2(a, a); }
 // lerp c0 + w (c1 - c0) on the (x, y) pair
 __device__ __forceinline__ unsigned long long lerp2(unsigned long long w, unsigned long long c0, unsigned long long c1) {
   return fma2(w, sub2(c1, c0), c0);
+}
+
+// 1 - e^{-x} for a pair of arguments x >= 0 (*E = e^{-x}): the degree-5 Taylor polynomial in
+// Horner form for x < 1/8 (truncation below 5e-8 relative), else 1 - 2^(-x log2 e); the polynomial
+// as pair operations, the exponentials and the choice per lane
+__device__ __forceinline__ unsigned long long one_minus_exp2(unsigned long long X, unsigned long long* E) {
+  float x0, x1, a0, a1;
+  unpack2(mul2(X, dup2(-1.4426950408889634f)), a0, a1);
+  float ex0, ex1;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex0) : "f"(a0));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex1) : "f"(a1));
+  unsigned long long S = fma2(X, dup2(1.0f / 120.0f), dup2(-1.0f / 24.0f));
+  S = fma2(X, S, dup2(1.0f / 6.0f));
+  S = fma2(X, S, dup2(-0.5f));
+  S = fma2(X, S, dup2(1.0f));
+  float s0, s1;
+  unpack2(mul2(X, S), s0, s1);
+  unpack2(X, x0, x1);
+  const float r0 = x0 < 0.125f ? s0 : 1.0f - ex0;
+  const float r1 = x1 < 0.125f ? s1 : 1.0f - ex1;
+  *E = pack2(x0 < 0.125f ? 1.0f - r0 : ex0, x1 < 0.125f ? 1.0f - r1 : ex1);
+  return pack2(r0, r1);
 }
 
 // trilinear interpolation of the 8 corner velocities (corner c_xyz, x fastest) at weights f: the
@@ -458,17 +471,23 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         own[j] = (j >= lo) && (j < hi);
         if (!own[j]) cell[j] = ucell;
       }
-      // ---- per particle: start cell relative to the unit, deposit key, fluid gather, drag and
-      // gravity (exponential integrator), relocation, exchanged momentum.  A start cell within kR
-      // cells of the unit (the deposit tile) has its whole stencil inside the fluid tile; the rest
-      // ("far" particles, rare) read the padded field and commit to the global accumulator.
+      // ---- per particle: start cell relative to the unit, deposit key, fluid gather; then drag and
+      // gravity (exponential integrator), relocation and exchanged momentum for two particles at
+      // a time as FP32 register pairs.  A start cell within kR cells of the unit (the deposit tile)
+      // has its whole stencil inside the fluid tile; the rest ("far" particles, rare) read the
+      // padded field and commit to the global accumulator.
       int key[4];
       float J[4][3];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int ci[3] = {cell_i(cell[j]), cell_j(cell[j]), cell_k(cell[j])};
-        float up[3];
-        {
+      for (int jp = 0; jp < 4; jp += 2) {
+        int ci[2][3];
+        float up[2][3];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int j = jp + e;
+          ci[e][0] = cell_i(cell[j]);
+          ci[e][1] = cell_j(cell[j]);
+          ci[e][2] = cell_k(cell[j]);
           int rc[3], rb[3];
           float f[3];
           bool in_dep = true;
@@ -477,7 +496,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
             const float o = xi[q][j];
             const bool hi2 = o >= 0.5f;
             f[q] = o + (hi2 ? -0.5f : 0.5f);
-            int r = ci[q] - uo[q];  // periodic offset from the unit origin, valid within the tile
+            int r = ci[e][q] - uo[q];  // periodic offset from the unit origin, valid within the tile
             if (PW2) {
               r = ((r + kR) & (n3[q] - 1)) - kR;
             } else {
@@ -491,69 +510,89 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           const int tofs = in_dep ? (rb[0] + kG) + kTE * ((rb[1] + kG) + kTE * (rb[2] + kG)) : 0;
           key[j] = !own[j]                ? -1
                    : (in_dep && use_tile) ? (rc[0] + kR) + kDE * ((rc[1] + kR) + kDE * (rc[2] + kR))
-                                          : kDepositCells + ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
-          const float4* b = tile + tofs;
-          trilerp(b[0], b[1], b[kTE], b[kTE + 1], b[kTE * kTE], b[kTE * kTE + 1], b[kTE * kTE + kTE],
-                  b[kTE * kTE + kTE + 1], f[0], f[1], f[2], up);
+                                          : kDepositCells + ci[e][0] + a.nx * (ci[e][1] + a.ny * ci[e][2]);
+          const float4* bb = tile + tofs;
+          trilerp(bb[0], bb[1], bb[kTE], bb[kTE + 1], bb[kTE * kTE], bb[kTE * kTE + 1], bb[kTE * kTE + kTE],
+                  bb[kTE * kTE + kTE + 1], f[0], f[1], f[2], up[e]);
           if (__builtin_expect(!in_dep, 0)) {
             const float3 g = gather_padded(a.Up, px, pxy, cell[j], xi[0][j], xi[1][j], xi[2][j]);
-            up[0] = g.x;
-            up[1] = g.y;
-            up[2] = g.z;
+            up[e][0] = g.x;
+            up[e][1] = g.y;
+            up[e][2] = g.z;
           }
         }
-        const float d = dv[j];
-        const float dd = d * d;
-        const float adt = a.cadt * rcp_approx(dd);
-        float Ee;
-        const float E1 = one_minus_exp(adt, &Ee);
-        const float inv_a = dd * a.inv_ca;
-        const float Q = E1 * inv_a;
-        const float m = a.mcoef * dd * d;
-        float oraw[3];
-        int ii[3];
-        bool bad = false;
+        // the integrator on the pair
+        const unsigned long long D = pack2(dv[jp], dv[jp + 1]);
+        const unsigned long long DD = mul2(D, D);
+        float dd0, dd1;
+        unpack2(DD, dd0, dd1);
+        const unsigned long long ADT = mul2(dup2(a.cadt), pack2(rcp_approx(dd0), rcp_approx(dd1)));
+        unsigned long long EE;
+        const unsigned long long E1 = one_minus_exp2(ADT, &EE);
+        const unsigned long long INV_A = mul2(DD, dup2(a.inv_ca));
+        const unsigned long long Q = mul2(E1, INV_A);
+        const unsigned long long M = mul2(mul2(dup2(a.mcoef), DD), D);
+        float oraw[2][3];
+        int ii[2][3];
+        bool bad[2] = {false, false};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          const float wt = fmaf(a.g[q], inv_a, up[q]);
-          const float dvw = v[q][j] - wt;
-          float vn = fmaf(dvw, Ee, wt);
+          const unsigned long long WT = fma2(dup2(a.g[q]), INV_A, pack2(up[0][q], up[1][q]));
+          const unsigned long long V = pack2(v[q][jp], v[q][jp + 1]);
+          const unsigned long long DVW = sub2(V, WT);
+          float vn[2];
+          unpack2(fma2(DVW, EE, WT), vn[0], vn[1]);
           if (BF16) {
-            // the stored (rounded) velocity change, so that the deposit balances the particles' momentum
-            vn = __bfloat162float(__float2bfloat16_rn(vn));
-            J[j][q] = -m * ((vn - v[q][j]) - a.gdt[q]);
+            // the stored (rounded) velocity change, so that the deposit balances the particles'
+            // momentum
+            float m0, m1;
+            unpack2(M, m0, m1);
+            vn[0] = __bfloat162float(__float2bfloat16_rn(vn[0]));
+            vn[1] = __bfloat162float(__float2bfloat16_rn(vn[1]));
+            J[jp][q] = -m0 * ((vn[0] - v[q][jp]) - a.gdt[q]);
+            J[jp + 1][q] = -m1 * ((vn[1] - v[q][jp + 1]) - a.gdt[q]);
           } else {
             // v' - v = -(v - w) (1 - E), without the cancellation of subtracting the rounded v'
-            J[j][q] = m * fmaf(dvw, E1, a.gdt[q]);
+            unpack2(mul2(M, fma2(DVW, E1, dup2(a.gdt[q]))), J[jp][q], J[jp + 1][q]);
           }
-          const float dxv = fmaf(wt, a.dt, dvw * Q);
-          const float o = fmaf(dxv, a.inv_h[q], xi[q][j]);
-          oraw[q] = o;
+          const unsigned long long DXV = fma2(WT, dup2(a.dt), mul2(DVW, Q));
+          const unsigned long long O = fma2(DXV, dup2(a.inv_h[q]), pack2(xi[q][jp], xi[q][jp + 1]));
           // whole cells carried: floor(o) from an add of 1.5 * 2^23 rounded toward -inf (exact for
           // |o| < 2^22), so no conversion instructions; the offset o - floor(o) lies in [0, 1]
-          const float t = __fadd_rd(o, 12582912.0f);
-          int k = (int)((unsigned)ci[q] + (unsigned)(__float_as_int(t) - 0x4B400000));
-          if (PW2) {
-            k &= n3[q] - 1;  // any whole-cell move of fewer than 2^22 cells
-            bad = bad || !(fabsf(o) < 4194304.0f);
-          } else {
-            if (k >= n3[q]) k -= n3[q];
-            else if (k < 0) k += n3[q];
-            bad = bad || !(fabsf(o) < 4194304.0f) || ((unsigned)k >= (unsigned)n3[q]);
-          }
-          ii[q] = k;
-          xi[q][j] = fminf(o - (t - 12582912.0f), 0.99999994f);
-          v[q][j] = vn;
-        }
-        if (__builtin_expect(bad, 0)) {
+          const unsigned long long T = add_rm2(O, dup2(12582912.0f));
+          float o[2], t[2], x[2];
+          unpack2(O, o[0], o[1]);
+          unpack2(T, t[0], t[1]);
+          unpack2(sub2(O, sub2(T, dup2(12582912.0f))), x[0], x[1]);
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const Relocated rl = relocate_general(oraw[q], ci[q], n3[q]);
-            ii[q] = rl.cell;
-            xi[q][j] = rl.offset;
+          for (int e = 0; e < 2; ++e) {
+            oraw[e][q] = o[e];
+            int k = (int)((unsigned)ci[e][q] + (unsigned)(__float_as_int(t[e]) - 0x4B400000));
+            if (PW2) {
+              k &= n3[q] - 1;  // any whole-cell move of fewer than 2^22 cells
+              bad[e] = bad[e] || !(fabsf(o[e]) < 4194304.0f);
+            } else {
+              if (k >= n3[q]) k -= n3[q];
+              else if (k < 0) k += n3[q];
+              bad[e] = bad[e] || !(fabsf(o[e]) < 4194304.0f) || ((unsigned)k >= (unsigned)n3[q]);
+            }
+            ii[e][q] = k;
+            xi[q][jp + e] = fminf(x[e], 0.99999994f);
+            v[q][jp + e] = vn[e];
           }
         }
-        cell[j] = pack_cell(ii[0], ii[1], ii[2]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          if (__builtin_expect(bad[e], 0)) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              const Relocated rl = relocate_general(oraw[e][q], ci[e][q], n3[q]);
+              ii[e][q] = rl.cell;
+              xi[q][jp + e] = rl.offset;
+            }
+          }
+          cell[jp + e] = pack_cell(ii[e][0], ii[e][1], ii[e][2]);
+        }
       }
       // ---- store the owned particles (128-bit when the lane owns all four) ----
       const bool all_own = own[0] && own[1] && own[2] && own[3];
