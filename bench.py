@@ -42,7 +42,7 @@ STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_26
                            "step_mixed_tma.cu")
 MEASURED_TRAFFIC = {
     # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches (fresh to 3 steps of drift), 64.07-64.15 B
-    ("af9f9494f100f87ef717ef93d913b30bbbec87fd38b8695ad6856848a77c5df2", "fourier256_mixed_1e9"): 64.10,
+    ("b97ae7cb91ca8c10d2c7e0bc45542fab569327300ae5d92059e5f57d7fafc00f", "fourier256_mixed_1e9"): 64.10,
 }
 
 
