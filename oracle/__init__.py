@@ -42,11 +42,20 @@ def build(force: bool = False) -> str:
 class Grid(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("chunk_edge", C.c_int32), ("L", C.c_double * 3),
                 ("rho_p", C.c_double), ("mu", C.c_double), ("g", C.c_double * 3),
-                ("alpha", C.c_double), ("mult", C.c_double)]
+                ("alpha", C.c_double), ("mult", C.c_double), ("gather", C.c_int32),
+                ("integrator", C.c_int32), ("drag", C.c_int32), ("deposit", C.c_int32),
+                ("rho_f", C.c_double)]
+
+
+GATHERS = {"trilinear": 0, "ngp": 1}
+INTEGRATORS = {"exponential": 0, "semi_implicit": 1}
+DRAGS = {"stokes": 0, "schiller_naumann": 1}
+DEPOSITS = {"cell": 0, "cic": 1}
 
 
 def make_grid(n, L=(1.0, 1.0, 1.0), chunk_edge=8, rho_p=1000.0, mu=1.8e-5,
-              g=(0.0, 0.0, -9.81), alpha=1.0, mult=1.0) -> Grid:
+              g=(0.0, 0.0, -9.81), alpha=1.0, mult=1.0, gather="trilinear", integrator="exponential",
+              drag="stokes", deposit="cell", rho_f=1.2) -> Grid:
     if isinstance(n, int):
         n = (n, n, n)
     G = Grid()
@@ -56,6 +65,9 @@ def make_grid(n, L=(1.0, 1.0, 1.0), chunk_edge=8, rho_p=1000.0, mu=1.8e-5,
     G.rho_p, G.mu = float(rho_p), float(mu)
     G.g[:] = [float(v) for v in g]
     G.alpha, G.mult = float(alpha), float(mult)
+    G.gather, G.integrator = GATHERS[gather], INTEGRATORS[integrator]
+    G.drag, G.deposit = DRAGS[drag], DEPOSITS[deposit]
+    G.rho_f = float(rho_f)
     return G
 
 
@@ -75,6 +87,8 @@ def lib():
             L.orc_gather.argtypes, L.orc_gather.restype = [pg, pd, pd, pd], None
             L.orc_advance.argtypes, L.orc_advance.restype = [pg, d, pd, d, pd, pd], None
             L.orc_mass.argtypes, L.orc_mass.restype = [pg, d], d
+            L.orc_drag_factor.argtypes, L.orc_drag_factor.restype = [pg, d], d
+            L.orc_deposit.argtypes, L.orc_deposit.restype = [pg, pd, pd, pd], None
             L.orc_particle_step.argtypes = [pg, pd, d, d, pd, pd, pi64, pd]
             L.orc_particle_step.restype = None
             L.orc_run.argtypes = [pg, pd, i64, pd, pd, pd, i32, d, pd, pi64, pi64]
@@ -139,6 +153,19 @@ def advance(G: Grid, d: float, up, dt: float, x, v):
 
 def mass(G: Grid, d: float) -> float:
     return lib().orc_mass(C.byref(G), float(d))
+
+
+def drag_factor(G: Grid, re: float) -> float:
+    return lib().orc_drag_factor(C.byref(G), float(re))
+
+
+def deposit(G: Grid, x, J, src=None) -> np.ndarray:
+    """Add one particle's impulse J at start position x into src [3, ncell] (a copy)."""
+    x = _f64(x, (3,))
+    J = _f64(J, (3,))
+    src = np.zeros((3, ncell(G))) if src is None else _f64(src).reshape(3, -1).copy()
+    lib().orc_deposit(C.byref(G), _pd(x), _pd(J), _pd(src))
+    return src
 
 
 def run(G: Grid, U, pos, vel, d, nsteps: int, dt: float, src=None, trace=False, frozen=None):

@@ -53,8 +53,10 @@ static int32_t wrap_index(int32_t i, int32_t n) {
 /* Trilinear interpolation of cell-centred values (centres at (i + 1/2) h):
  * s = x / h - 1/2, i0 = floor(s), f = s - i0; the value is the sum over the
  * eight corners (i0 + di, j0 + dj, k0 + dk), indices taken periodically, of
- * the corner value times prod over axes of (f if the offset is 1 else 1 - f). */
-void orc_gather(const orc_grid* G, const double* U, const double x[3], double up[3]) {
+ * the corner value times prod over axes of (f if the offset is 1 else 1 - f).
+ * The stencil (corner cells and weights) is shared with the cloud-in-cell
+ * deposit, which is this map transposed. */
+static void trilinear_stencil(const orc_grid* G, const double x[3], int64_t cells[8], double w[8]) {
   int32_t i0[3];
   double f[3];
   for (int ax = 0; ax < 3; ++ax) {
@@ -63,28 +65,77 @@ void orc_gather(const orc_grid* G, const double* U, const double x[3], double up
     i0[ax] = (int32_t)fl;
     f[ax] = s - fl;
   }
-  up[0] = up[1] = up[2] = 0.0;
+  int c = 0;
   for (int dk = 0; dk < 2; ++dk)
     for (int dj = 0; dj < 2; ++dj)
       for (int di = 0; di < 2; ++di) {
-        double w = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
-        int64_t c = linear_cell(G, wrap_index(i0[0] + di, G->n[0]), wrap_index(i0[1] + dj, G->n[1]),
-                                wrap_index(i0[2] + dk, G->n[2]));
-        for (int q = 0; q < 3; ++q) up[q] = up[q] + w * U[3 * c + q];
+        w[c] = (di ? f[0] : 1.0 - f[0]) * (dj ? f[1] : 1.0 - f[1]) * (dk ? f[2] : 1.0 - f[2]);
+        cells[c] = linear_cell(G, wrap_index(i0[0] + di, G->n[0]), wrap_index(i0[1] + dj, G->n[1]),
+                               wrap_index(i0[2] + dk, G->n[2]));
+        c = c + 1;
       }
 }
 
-/* Newton's second law (Sec. 2.1, Eqs. 9-10) with Stokes drag and gravity:
- *   dx/dt = v,  dv/dt = alpha (u_p - v) / tau + g,  tau = rho_p d^2 / (18 mu).
- * With a = alpha / tau and u_p frozen over the step the solution is exact:
+/* Nearest grid point (Sec. 2.5): the particle takes the value of the cell it
+ * is in. */
+void orc_gather(const orc_grid* G, const double* U, const double x[3], double up[3]) {
+  if (G->gather == 1) {
+    int32_t idx[3];
+    orc_cell(G, x, idx);
+    int64_t c = linear_cell(G, idx[0], idx[1], idx[2]);
+    for (int q = 0; q < 3; ++q) up[q] = U[3 * c + q];
+    return;
+  }
+  int64_t cells[8];
+  double w[8];
+  trilinear_stencil(G, x, cells, w);
+  up[0] = up[1] = up[2] = 0.0;
+  for (int c = 0; c < 8; ++c)
+    for (int q = 0; q < 3; ++q) up[q] = up[q] + w[c] * U[3 * cells[c] + q];
+}
+
+/* Drag correlation of Schiller and Naumann (cited in Sec. 2.1):
+ *   C_D = 24 / Re (1 + 0.15 Re^0.687) for Re <= 1000, C_D = 0.44 above,
+ * with the drag force 1/2 rho_f C_D (pi d^2 / 4) |u - v| (u - v).  Divided by
+ * the mass rho_p pi d^3 / 6 this is (18 mu / (rho_p d^2)) (C_D Re / 24)
+ * (u - v), i.e. Stokes drag times f = C_D Re / 24. */
+double orc_drag_factor(const orc_grid* G, double re) {
+  if (G->drag != 1) return 1.0;
+  if (re <= 0.0) return 1.0;
+  double cd = re <= 1000.0 ? 24.0 / re * (1.0 + 0.15 * pow(re, 0.687)) : 0.44;
+  return cd * re / 24.0;
+}
+
+/* Newton's second law (Sec. 2.1, Eqs. 9-10) with drag and gravity:
+ *   dx/dt = v,  dv/dt = alpha f (u_p - v) / tau + g,  tau = rho_p d^2 / (18 mu),
+ * f the drag factor from the relative velocity at the start of the step
+ * (Re = rho_f |u_p - v| d / mu), held over the step with u_p.
+ * Exponential integrator: with a = alpha f / tau the solution is exact,
  *   w_t = u_p + g / a            (the velocity v relaxes towards)
  *   v'  = w_t + (v - w_t) e^{-a dt}
  *   x'  = x + w_t dt + (v - w_t) (1 - e^{-a dt}) / a
- * and 1 - e^{-a dt} is taken as -expm1(-a dt). */
+ * and 1 - e^{-a dt} is taken as -expm1(-a dt).
+ * Semi-implicit Euler (Sec. 2.5): the drag implicit in the new velocity, the
+ * position advanced with it,
+ *   v'  = (v + dt (a u_p + g)) / (1 + a dt),   x' = x + dt v'. */
 void orc_advance(const orc_grid* G, double d, const double up[3], double dt, double x[3],
                  double v[3]) {
   double tau = G->rho_p * d * d / (18.0 * G->mu);
-  double a = G->alpha / tau;
+  double f = 1.0;
+  if (G->drag == 1) {
+    double r0 = up[0] - v[0], r1 = up[1] - v[1], r2 = up[2] - v[2];
+    double re = G->rho_f * sqrt(r0 * r0 + r1 * r1 + r2 * r2) * d / G->mu;
+    f = orc_drag_factor(G, re);
+  }
+  double a = G->alpha * f / tau;
+  if (G->integrator == 1) {
+    for (int ax = 0; ax < 3; ++ax) {
+      double vn = (v[ax] + dt * (a * up[ax] + G->g[ax])) / (1.0 + a * dt);
+      x[ax] = x[ax] + dt * vn;
+      v[ax] = vn;
+    }
+    return;
+  }
   double E = exp(-a * dt);
   double E1 = -expm1(-a * dt);
   for (int ax = 0; ax < 3; ++ax) {
@@ -94,6 +145,25 @@ void orc_advance(const orc_grid* G, double d, const double up[3], double dt, dou
     x[ax] = x[ax] + dx;
     v[ax] = vn;
   }
+}
+
+/* Deposit of one particle's impulse: the cell containing the particle at the
+ * start of the step (Sec. 2.5), or the eight cells of its trilinear stencil
+ * with the gather's weights (cloud in cell). */
+void orc_deposit(const orc_grid* G, const double x[3], const double J[3], double* src) {
+  int64_t nc = ncell_of(G);
+  if (G->deposit == 1) {
+    int64_t cells[8];
+    double w[8];
+    trilinear_stencil(G, x, cells, w);
+    for (int c = 0; c < 8; ++c)
+      for (int ax = 0; ax < 3; ++ax) src[ax * nc + cells[c]] = src[ax * nc + cells[c]] + w[c] * J[ax];
+    return;
+  }
+  int32_t idx[3];
+  orc_cell(G, x, idx);
+  int64_t c0 = linear_cell(G, idx[0], idx[1], idx[2]);
+  for (int ax = 0; ax < 3; ++ax) src[ax * nc + c0] = src[ax * nc + c0] + J[ax];
 }
 
 /* Mass of a spherical particle, times the parcel multiplicity (Sec. 3.2
@@ -128,13 +198,21 @@ static int grid_ok(const orc_grid* G) {
   for (int ax = 0; ax < 3; ++ax) {
     if (G->n[ax] <= 0 || !(G->L[ax] > 0.0)) return 0;
   }
+  if (G->gather < 0 || G->gather > 1 || G->integrator < 0 || G->integrator > 1 || G->drag < 0 ||
+      G->drag > 1 || G->deposit < 0 || G->deposit > 1 || !(G->rho_f >= 0.0))
+    return 0;
   return G->rho_p > 0.0 && G->mu > 0.0 && G->alpha > 0.0;
+}
+
+static int default_physics(const orc_grid* G) {
+  return G->gather == 0 && G->integrator == 0 && G->drag == 0 && G->deposit == 0;
 }
 
 int orc_run(const orc_grid* G, const double* U, int64_t n, double* pos, double* vel,
             const double* d, int32_t nsteps, double dt, double* src, int64_t* trace,
             const int64_t* frozen) {
   if (!grid_ok(G) || n < 0 || nsteps < 0) return -1;
+  if (frozen && G->deposit != 0) return -1;
   int64_t nc = ncell_of(G);
   for (int32_t s = 0; s < nsteps; ++s) {
     for (int64_t p = 0; p < n; ++p) {
@@ -145,7 +223,10 @@ int orc_run(const orc_grid* G, const double* U, int64_t n, double* pos, double* 
       orc_particle_step(G, U, dt, d[p], x, v, &c0, J);
       if (frozen) c0 = frozen[(int64_t)s * n + p];
       if (trace) trace[(int64_t)s * n + p] = c0;
-      if (src) {
+      if (src && G->deposit == 1) {
+        double x0[3] = {pos[p], pos[n + p], pos[2 * n + p]};
+        orc_deposit(G, x0, J, src);
+      } else if (src) {
         for (int ax = 0; ax < 3; ++ax) src[ax * nc + c0] = src[ax * nc + c0] + J[ax];
       }
       pos[p] = x[0];
@@ -245,7 +326,7 @@ void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const doubl
 int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
                 const double* vel0, const double* d, int32_t nsteps, double dt,
                 const double* lam, double* grad_d, double* grad_alpha, double* gradU) {
-  if (!grid_ok(G) || n < 0 || nsteps < 0) return -1;
+  if (!grid_ok(G) || !default_physics(G) || n < 0 || nsteps < 0) return -1;
   int64_t nc = ncell_of(G);
   for (int64_t c = 0; c < 3 * nc; ++c) gradU[c] = 0.0;
   *grad_alpha = 0.0;

@@ -32,6 +32,12 @@
  *     update is an explicit momentum source followed by Jacobi sweeps of an
  *     implicit periodic diffusion step.
  *
+ * Physics variants, selected in orc_grid: the nearest-grid-point gather and
+ * semi-implicit Euler integrator the paper itself uses (Sec. 2.5), the
+ * Schiller-Naumann drag correlation it cites (Sec. 2.1), and a cloud-in-cell
+ * deposit (the transpose of the trilinear gather).  Pinned in
+ * tests/test_physics_pins.py.
+ *
  * Pins (tests/test_oracle_pins.py): closed-form and ODE-integrated
  * uniform-flow solutions, terminal velocity, exact reproduction of
  * trilinear functions, the momentum balance, brute-force deposit and sort
@@ -59,6 +65,13 @@ typedef struct {
   double g[3];         /* gravitational acceleration */
   double alpha;        /* drag scale multiplying the Stokes drag */
   double mult;         /* parcel multiplicity w (particles per parcel) */
+  /* Physics variants (all 0 = trilinear gather, exponential integrator, Stokes drag, deposit
+   * into the containing cell at the start of the step). */
+  int32_t gather;      /* 0 trilinear on cell centres; 1 nearest grid point (Sec. 2.5) */
+  int32_t integrator;  /* 0 exponential; 1 semi-implicit Euler (Sec. 2.5) */
+  int32_t drag;        /* 0 Stokes; 1 Schiller-Naumann correlation (Sec. 2.1) */
+  int32_t deposit;     /* 0 containing cell; 1 cloud-in-cell (transpose of the trilinear gather) */
+  double rho_f;        /* fluid density in the particle Reynolds number (Schiller-Naumann only) */
 } orc_grid;
 
 /* Periodic wrap of one coordinate into [0, L). */
@@ -67,13 +80,25 @@ double orc_wrap(double x, double L);
 /* Cell index (i, j, k) of a wrapped position. */
 void orc_cell(const orc_grid* G, const double x[3], int32_t idx[3]);
 
-/* Trilinear interpolation of the cell-centred field U[c][3] at x. */
+/* The fluid velocity seen at x: trilinear interpolation of the cell-centred
+ * field U[c][3], or (gather = 1) the value of the cell that holds x. */
 void orc_gather(const orc_grid* G, const double* U, const double x[3], double up[3]);
 
-/* One exponential-integrator step of a particle of diameter d that sees the
- * frozen fluid velocity up: updates v and x in place (x not wrapped). */
+/* Drag factor f = C_D Re / 24 of the Schiller-Naumann correlation at
+ * particle Reynolds number Re (1 for Stokes drag at any Re). */
+double orc_drag_factor(const orc_grid* G, double re);
+
+/* One step of a particle of diameter d that sees the frozen fluid velocity
+ * up: updates v and x in place (x not wrapped), by the exponential
+ * integrator or (integrator = 1) semi-implicit Euler, with the drag factor
+ * evaluated from the relative velocity at the start of the step. */
 void orc_advance(const orc_grid* G, double d, const double up[3], double dt,
                  double x[3], double v[3]);
+
+/* Add the impulse J of a particle at x (its start-of-step position) to
+ * src[3][ncell]: whole into the cell that holds x, or (deposit = 1) spread
+ * over the eight cells of its trilinear stencil with the gather's weights. */
+void orc_deposit(const orc_grid* G, const double x[3], const double J[3], double* src);
 
 /* Particle mass (parcel multiplicity included). */
 double orc_mass(const orc_grid* G, double d);
@@ -88,7 +113,9 @@ void orc_particle_step(const orc_grid* G, const double* U, double dt, double d,
  * order.  If trace != NULL it records the deposit cell of every particle and
  * step (trace[s*n + p]); if frozen != NULL the deposit cells are taken from
  * it instead of being computed (finite differences with the cell sequence
- * held fixed).  Returns 0, or -1 on bad arguments. */
+ * held fixed).  trace and frozen concern the containing-cell deposit; with
+ * the cloud-in-cell deposit frozen must be NULL.  Returns 0, or -1 on bad
+ * arguments. */
 int orc_run(const orc_grid* G, const double* U, int64_t n, double* pos, double* vel,
             const double* d, int32_t nsteps, double dt, double* src,
             int64_t* trace, const int64_t* frozen);
@@ -114,7 +141,9 @@ void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const doubl
  * dL/dU (gradU[c][3], same layout as U).  Deposit cells are treated as
  * locally constant (the derivative that exists almost everywhere).  The
  * forward trajectory is stored whole (no checkpointing).  pos0/vel0 are
- * not modified.  Returns 0, -1 on bad arguments, -2 on allocation failure. */
+ * not modified.  Default physics only (trilinear, exponential, Stokes,
+ * containing-cell deposit).  Returns 0, -1 on bad arguments or other
+ * physics, -2 on allocation failure. */
 int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
                 const double* vel0, const double* d, int32_t nsteps, double dt,
                 const double* lam, double* grad_d, double* grad_alpha, double* gradU);
