@@ -189,6 +189,17 @@ def setup_sim(workload, n, U32, precision, device, batch=50_000_000):
     return sim
 
 
+# physics variants timed beside the default step: the paper's own choices (nearest-grid-point
+# gather, semi-implicit Euler, Schiller-Naumann drag, containing-cell deposit) and the
+# cloud-in-cell deposit
+VARIANTS = {
+    "paper_ngp_semi_implicit_schiller_naumann": dict(gather="ngp", integrator="semi_implicit",
+                                                     drag="schiller_naumann", deposit="cell"),
+    "schiller_naumann": dict(drag="schiller_naumann"),
+    "cic_deposit": dict(deposit="cic"),
+}
+
+
 def timed_steps(sim, steps, dt, reorder_every, step_index0):
     """Run `steps` steps with the sort every `reorder_every` steps; per-kernel CUDA events."""
     import torch
@@ -285,6 +296,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=3, help="steps per physics variant (0 = skip)")
     args = ap.parse_args()
 
     from paper_2603_26691_gb300 import inputs
@@ -400,6 +412,22 @@ def main():
     e2e = {"value": n * ws * E / e_el if E > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(U32.nbytes),
            "d2h_bytes_per_step": int(src_h.numel() * 8), "steps": E,
            "what": "per step: fluid field H2D from pinned host, step (sort when due), sources D2H to pinned host"}
+
+    # physics variants on the same particles, sorted, through the general mixed step kernel
+    variants = None
+    if args.variant_steps > 0:
+        variants = {}
+        for name, ph in VARIANTS.items():
+            sim.set_physics(**ph)
+            sim.reorder()
+            sim.step(1, dt)
+            ev = timed_steps(sim, args.variant_steps, dt, 0, 1)
+            torch.cuda.synchronize()
+            ms = sum(e1.elapsed_time(e2) for (e0, e1, e2, _) in ev) / len(ev)
+            variants[name] = {"physics": ph, "step_kernel_ms": ms, "particle_steps_per_s": n / (ms * 1e-3),
+                              "hbm_frac_of_algorithmic": STEP_BYTES[precision] * n / (ms * 1e-3) / 1e9 / peak,
+                              "kernel": "step_mixed_kernel"}
+        sim.set_physics()
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -440,7 +468,7 @@ def main():
             "breakdown": {"step_kernel_ms_avg": step_avg, "sort_ms_avg": (sum(sort_ms) / len(sort_ms)) if sort_ms else None,
                           "sorts_in_timed_region": len(sort_ms),
                           "chunk_bounds_ms": chunk_bounds_ms},
-            "fp64_step": fp64}
+            "fp64_step": fp64, "physics_variants": variants}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

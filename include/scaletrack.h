@@ -120,6 +120,30 @@ st_status st_synchronize(st_handle h);
 st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3], double drag_scale,
                         double multiplicity, int reorder_every);
 
+/* Physics variants.  The defaults (all 0) are the step described at the top
+ * of this file.  The alternatives are the choices the paper itself makes:
+ *   ST_GATHER_NGP: nearest grid point (Sec. 2.5) - the particle takes the
+ *     value of the cell it is in;
+ *   ST_INTEGRATOR_SEMI_IMPLICIT: semi-implicit Euler (Sec. 2.5), drag
+ *     implicit in the new velocity and the position advanced with it,
+ *       v' = (v + dt (a u_p + g)) / (1 + a dt),  x' = x + dt v';
+ *   ST_DRAG_SCHILLER_NAUMANN: the drag correlation cited in Sec. 2.1,
+ *     a = drag_scale f(Re) / tau with f = C_D Re / 24 = 1 + 0.15 Re^0.687
+ *     for Re <= 1000 and 0.44 Re / 24 above, Re = rho_f |u_p - v| d / mu
+ *     from the velocities at the start of the step (held over the step);
+ *   ST_DEPOSIT_CIC: cloud in cell - J spread over the eight cells of the
+ *     particle's trilinear stencil at the start of the step, with the
+ *     trilinear weights (the transpose of the trilinear gather).
+ * rho_f > 0 is the fluid density used in Re (only read by the
+ * Schiller-Naumann drag).  The sorted-order fast step kernel implements the
+ * defaults; other settings run the general step kernels.  The adjoint
+ * (st_adjoint_*) needs the defaults.  Errors: INVALID_ARG, NONFINITE. */
+enum { ST_GATHER_TRILINEAR = 0, ST_GATHER_NGP = 1 };
+enum { ST_INTEGRATOR_EXPONENTIAL = 0, ST_INTEGRATOR_SEMI_IMPLICIT = 1 };
+enum { ST_DRAG_STOKES = 0, ST_DRAG_SCHILLER_NAUMANN = 1 };
+enum { ST_DEPOSIT_CELL = 0, ST_DEPOSIT_CIC = 1 };
+st_status st_set_physics(st_handle h, int gather, int integrator, int drag, int deposit, double rho_f);
+
 /* Copy in the cell-centred fluid velocity u[k][j][i][3] (dtype
  * ST_DTYPE_F32 or ST_DTYPE_F64) - the Eulerian state of Sec. 2.3 that the
  * Lagrangian step reads.  FP64 handles keep it in FP64, mixed handles in

@@ -208,6 +208,22 @@ st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3],
   return ST_OK;
 }
 
+st_status st_set_physics(st_handle h, int gather, int integrator, int drag, int deposit, double rho_f) {
+  ST_TRY(check_handle(h));
+  if (!std::isfinite(rho_f)) return set_error(h, ST_ERR_NONFINITE, "rho_f is not finite");
+  if (gather < 0 || gather > 1 || integrator < 0 || integrator > 1 || drag < 0 || drag > 1 || deposit < 0 ||
+      deposit > 1)
+    return set_error(h, ST_ERR_INVALID_ARG, "unknown gather, integrator, drag or deposit");
+  if (!(rho_f > 0)) return set_error(h, ST_ERR_INVALID_ARG, "rho_f must be > 0");
+  h->phys_gather = gather;
+  h->phys_integrator = integrator;
+  h->phys_drag = drag;
+  h->phys_deposit = deposit;
+  h->rho_f_drag = rho_f;
+  h->adj_ready = false;
+  return ST_OK;
+}
+
 st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device) {
   ST_TRY(check_handle(h));
   if (!u) return set_error(h, ST_ERR_INVALID_ARG, "u is NULL");
@@ -390,6 +406,15 @@ st_status st_reorder(st_handle h) {
   return ST_OK;
 }
 
+// Contributions one particle can make to one cell in one step: one, except that the cloud-in-cell
+// stencil's two corners along an axis of a single cell are the same cell.
+static double deposits_per_cell(const st_ctx* h) {
+  if (h->phys_deposit != ST_DEPOSIT_CIC) return 1.0;
+  double f = 1.0;
+  for (int q = 0; q < 3; ++q) f *= h->geo.n[q] == 1 ? 2.0 : 1.0;
+  return f;
+}
+
 // Choose the fixed-point exponent so that a committed run at its bound maps to
 // at most 2^96 and the accumulated integer stays below 2^125.
 static st_status prepare_accumulator(st_handle h, double dt, double adds_now, int* E_out) {
@@ -424,7 +449,8 @@ static st_status prepare_accumulator(st_handle h, double dt, double adds_now, in
   h->acc_empty = false;
   // each word takes at most one digit per contribution; a step adds at most one contribution per
   // particle to any cell, plus one per neighbouring unit's tile flush (at most 8)
-  ST_TRY(cuda_check(h, launch_acc_maybe_normalize(h, (double)h->np + 8.0, adds_now), "normalise accumulator"));
+  ST_TRY(cuda_check(h, launch_acc_maybe_normalize(h, deposits_per_cell(h) * (double)h->np + 8.0, adds_now),
+                    "normalise accumulator"));
   *E_out = E;
   return ST_OK;
 }
@@ -444,9 +470,9 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     }
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
-    const bool tma = h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
+    const bool tma = h->prec != ST_FP64 && h->sorted && default_physics(h) && tma_step_supported(h);
     int E = 0;
-    ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : (double)h->np + 8.0, &E));
+    ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : deposits_per_cell(h) * (double)h->np + 8.0, &E));
     StepParams p;
     p.dt = dt;
     p.ca = 18.0 * h->mu * h->alpha / h->rho_p;
@@ -454,6 +480,11 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
     p.E = E;
     p.scale = std::ldexp(1.0, E);
+    p.ngp = h->phys_gather == ST_GATHER_NGP;
+    p.semi = h->phys_integrator == ST_INTEGRATOR_SEMI_IMPLICIT;
+    p.sn = h->phys_drag == ST_DRAG_SCHILLER_NAUMANN;
+    p.cic = h->phys_deposit == ST_DEPOSIT_CIC;
+    p.re_coef = h->rho_f_drag / h->mu;
     cudaError_t e;
     if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
@@ -627,6 +658,8 @@ st_status st_clear_particles(st_handle h) {
 st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every) {
   ST_TRY(check_handle(h));
   if (h->prec != ST_FP64) return set_error(h, ST_ERR_STATE, "the adjoint needs an FP64 handle");
+  if (!default_physics(h))
+    return set_error(h, ST_ERR_STATE, "the adjoint needs the default physics (trilinear, exponential, Stokes, cell)");
   if (nsteps < 1 || checkpoint_every < 1) return set_error(h, ST_ERR_INVALID_ARG, "nsteps and checkpoint_every must be >= 1");
   if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
   if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");

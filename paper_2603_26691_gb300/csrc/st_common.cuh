@@ -50,6 +50,10 @@ struct st_ctx {
   // physical parameters
   double rho_p = 1000.0, mu = 1.8e-5, g[3] = {0.0, 0.0, -9.81}, alpha = 1.0, mult = 1.0;
   int reorder_every = 10;
+  // physics variants (st_set_physics): gather, integrator, drag law, deposit; all 0 by default
+  int phys_gather = ST_GATHER_TRILINEAR, phys_integrator = ST_INTEGRATOR_EXPONENTIAL;
+  int phys_drag = ST_DRAG_STOKES, phys_deposit = ST_DEPOSIT_CELL;
+  double rho_f_drag = 1.2;  // fluid density in the particle Reynolds number
 
   // fluid: FP64 handles D4[ncell] (x, y, z, 0); mixed handles float4[ncell]
   st::Buf fluid;
@@ -295,7 +299,17 @@ struct StepParams {
   double g[3];
   double scale;    // 2^E for the FP64 path
   int E;           // for the FP32 path
+  // physics variants (nonzero = nearest grid point, semi-implicit Euler, Schiller-Naumann,
+  // cloud-in-cell deposit) and rho_f / mu for the particle Reynolds number
+  int ngp = 0, semi = 0, sn = 0, cic = 0;
+  double re_coef = 0.0;
 };
+
+// every physics switch at its default (the sorted TMA step kernel implements only this)
+inline bool default_physics(const st_ctx* h) {
+  return h->phys_gather == ST_GATHER_TRILINEAR && h->phys_integrator == ST_INTEGRATOR_EXPONENTIAL &&
+         h->phys_drag == ST_DRAG_STOKES && h->phys_deposit == ST_DEPOSIT_CELL;
+}
 
 cudaError_t launch_step_f64(st_ctx* h, const StepParams& p);
 // the FP64 step on an explicit state; acc == nullptr skips the deposit (adjoint recomputation)

@@ -2,7 +2,9 @@
 // per warp.  Gather -> exponential integrator -> wrap/relocate -> impulse,
 // then a warp-segmented reduction of the impulses over runs of equal
 // start-of-step cell in storage order, committed to the exact fixed-point
-// source accumulator.  GB300's FP64 rate is low, so this kernel is bound by
+// source accumulator.  The physics variants (nearest-grid-point gather,
+// semi-implicit Euler, Schiller-Naumann drag, cloud-in-cell deposit) are
+// uniform branches on the step's parameters.  GB300's FP64 rate is low, so this kernel is bound by
 // FP64 arithmetic rather than by HBM.
 #include "st_common.cuh"
 
@@ -39,15 +41,47 @@ __device__ __forceinline__ void lerp3(D4 a, D4 b, double f, double r[3]) {
   r[2] = fma(f, b.z - a.z, a.z);
 }
 
+// Schiller-Naumann drag factor f = C_D Re / 24: 1 + 0.15 Re^0.687 up to Re = 1000, 0.44 Re / 24 above
+__device__ __forceinline__ double sn_factor(double re) {
+  return re <= 1000.0 ? 1.0 + 0.15 * pow(re, 0.687) : (0.44 / 24.0) * re;
+}
+
+// Warp-segmented sum of J over runs of equal key (lanes in storage order), one commit per run.
+__device__ __forceinline__ void deposit_runs(const F64Args& a, int lane, int key, double j0, double j1, double j2) {
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = (lane == 0) || (prev != key);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned above = lane == 31 ? 0u : (heads & ~((2u << lane) - 1u));
+  const int end = above ? (__ffs(above) - 2) : 31;
+  for (int off = 1; off < 32; off <<= 1) {
+    double t0 = __shfl_down_sync(0xffffffffu, j0, off);
+    double t1 = __shfl_down_sync(0xffffffffu, j1, off);
+    double t2 = __shfl_down_sync(0xffffffffu, j2, off);
+    if (lane + off <= end) {
+      j0 += t0;
+      j1 += t1;
+      j2 += t2;
+    }
+  }
+  if (a.acc && head && key >= 0) {
+    acc_add_f64(a.acc + kAccWords * key, j0, a.p.E);
+    acc_add_f64(a.acc + kAccWords * (a.ncell + key), j1, a.p.E);
+    acc_add_f64(a.acc + kAccWords * (2 * a.ncell + key), j2, a.p.E);
+  }
+}
+
 __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int n3[3] = {a.nx, a.ny, a.nz};
+  const int64_t row = a.nx, slab = (int64_t)a.nx * a.ny;
   for (int64_t base = warp * 32; base < a.n; base += nwarp * 32) {
     const int64_t p = base + lane;
     int key = -1;
     double J[3] = {0.0, 0.0, 0.0};
+    int i0[3] = {0, 0, 0}, i1[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
     if (p < a.n) {
       double x[3], v[3];
       for (int q = 0; q < 3; ++q) {
@@ -56,8 +90,7 @@ __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
       }
       const double d = a.s.d[p];
       // start-of-step cell and trilinear stencil on cell centres
-      int c0[3], i0[3], i1[3];
-      double f[3];
+      int c0[3];
       for (int q = 0; q < 3; ++q) {
         double sx = x[q] * a.inv_h[q];
         int i = (int)floor(sx);
@@ -70,60 +103,78 @@ __global__ void __launch_bounds__(256) step_f64_kernel(const F64Args a) {
         i1[q] = ii + 1 >= n3[q] ? ii + 1 - n3[q] : ii + 1;
       }
       key = c0[0] + a.nx * (c0[1] + a.ny * c0[2]);
-      const int64_t row = a.nx, slab = (int64_t)a.nx * a.ny;
-      D4 U000 = ld_cell(a.U, i0[0] + row * i0[1] + slab * i0[2]);
-      D4 U100 = ld_cell(a.U, i1[0] + row * i0[1] + slab * i0[2]);
-      D4 U010 = ld_cell(a.U, i0[0] + row * i1[1] + slab * i0[2]);
-      D4 U110 = ld_cell(a.U, i1[0] + row * i1[1] + slab * i0[2]);
-      D4 U001 = ld_cell(a.U, i0[0] + row * i0[1] + slab * i1[2]);
-      D4 U101 = ld_cell(a.U, i1[0] + row * i0[1] + slab * i1[2]);
-      D4 U011 = ld_cell(a.U, i0[0] + row * i1[1] + slab * i1[2]);
-      D4 U111 = ld_cell(a.U, i1[0] + row * i1[1] + slab * i1[2]);
-      double r00[3], r10[3], r01[3], r11[3], r0[3], r1[3], up[3];
-      lerp3(U000, U100, f[0], r00);
-      lerp3(U010, U110, f[0], r10);
-      lerp3(U001, U101, f[0], r01);
-      lerp3(U011, U111, f[0], r11);
-      for (int q = 0; q < 3; ++q) {
-        r0[q] = fma(f[1], r10[q] - r00[q], r00[q]);
-        r1[q] = fma(f[1], r11[q] - r01[q], r01[q]);
-        up[q] = fma(f[2], r1[q] - r0[q], r0[q]);
+      double up[3];
+      if (a.p.ngp) {
+        // nearest grid point: the value of the cell holding the particle
+        const D4 Uc = ld_cell(a.U, key);
+        up[0] = Uc.x;
+        up[1] = Uc.y;
+        up[2] = Uc.z;
+      } else {
+        D4 U000 = ld_cell(a.U, i0[0] + row * i0[1] + slab * i0[2]);
+        D4 U100 = ld_cell(a.U, i1[0] + row * i0[1] + slab * i0[2]);
+        D4 U010 = ld_cell(a.U, i0[0] + row * i1[1] + slab * i0[2]);
+        D4 U110 = ld_cell(a.U, i1[0] + row * i1[1] + slab * i0[2]);
+        D4 U001 = ld_cell(a.U, i0[0] + row * i0[1] + slab * i1[2]);
+        D4 U101 = ld_cell(a.U, i1[0] + row * i0[1] + slab * i1[2]);
+        D4 U011 = ld_cell(a.U, i0[0] + row * i1[1] + slab * i1[2]);
+        D4 U111 = ld_cell(a.U, i1[0] + row * i1[1] + slab * i1[2]);
+        double r00[3], r10[3], r01[3], r11[3];
+        lerp3(U000, U100, f[0], r00);
+        lerp3(U010, U110, f[0], r10);
+        lerp3(U001, U101, f[0], r01);
+        lerp3(U011, U111, f[0], r11);
+        for (int q = 0; q < 3; ++q) {
+          const double r0 = fma(f[1], r10[q] - r00[q], r00[q]);
+          const double r1 = fma(f[1], r11[q] - r01[q], r01[q]);
+          up[q] = fma(f[2], r1 - r0, r0);
+        }
       }
-      // Stokes drag + gravity, exponential integrator
+      // drag rate a = alpha f(Re) / tau, f = 1 for Stokes drag
       const double dd = d * d;
-      const double ra = a.p.ca / dd;  // a = alpha / tau
+      double ra = a.p.ca / dd;
+      if (a.p.sn) {
+        const double r0 = up[0] - v[0], r1 = up[1] - v[1], r2 = up[2] - v[2];
+        ra *= sn_factor(a.p.re_coef * sqrt(r0 * r0 + r1 * r1 + r2 * r2) * d);
+      }
       const double adt = ra * a.p.dt;
-      const double E = exp(-adt);
-      const double E1 = -expm1(-adt);
-      const double Qd = E1 / ra;
       const double m = a.p.mcoef * dd * d;
-      for (int q = 0; q < 3; ++q) {
-        const double wt = up[q] + a.p.g[q] / ra;
-        const double vn = wt + (v[q] - wt) * E;
-        const double xn = x[q] + (wt * a.p.dt + (v[q] - wt) * Qd);
-        J[q] = -m * ((vn - v[q]) - a.p.g[q] * a.p.dt);
-        a.s.x[q][p] = wrap_pos(xn, a.L[q], a.invL[q]);
-        a.s.v[q][p] = vn;
+      if (a.p.semi) {
+        // semi-implicit Euler: v' = (v + dt (a u_p + g)) / (1 + a dt), x' = x + dt v'
+        const double den = 1.0 + adt;
+        for (int q = 0; q < 3; ++q) {
+          const double vn = (v[q] + a.p.dt * (ra * up[q] + a.p.g[q])) / den;
+          const double xn = x[q] + a.p.dt * vn;
+          J[q] = -m * ((vn - v[q]) - a.p.g[q] * a.p.dt);
+          a.s.x[q][p] = wrap_pos(xn, a.L[q], a.invL[q]);
+          a.s.v[q][p] = vn;
+        }
+      } else {
+        // exponential integrator
+        const double E = exp(-adt);
+        const double E1 = -expm1(-adt);
+        const double Qd = E1 / ra;
+        for (int q = 0; q < 3; ++q) {
+          const double wt = up[q] + a.p.g[q] / ra;
+          const double vn = wt + (v[q] - wt) * E;
+          const double xn = x[q] + (wt * a.p.dt + (v[q] - wt) * Qd);
+          J[q] = -m * ((vn - v[q]) - a.p.g[q] * a.p.dt);
+          a.s.x[q][p] = wrap_pos(xn, a.L[q], a.invL[q]);
+          a.s.v[q][p] = vn;
+        }
       }
     }
-    // warp-segmented reduction over runs of equal start cell (lanes in storage order)
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const bool head = (lane == 0) || (prev != key);
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const unsigned above = lane == 31 ? 0u : (heads & ~((2u << lane) - 1u));
-    const int end = above ? (__ffs(above) - 2) : 31;
-    for (int off = 1; off < 32; off <<= 1) {
-      double t0 = __shfl_down_sync(0xffffffffu, J[0], off);
-      double t1 = __shfl_down_sync(0xffffffffu, J[1], off);
-      double t2 = __shfl_down_sync(0xffffffffu, J[2], off);
-      if (lane + off <= end) {
-        J[0] += t0;
-        J[1] += t1;
-        J[2] += t2;
+    if (!a.p.cic) {
+      deposit_runs(a, lane, key, J[0], J[1], J[2]);
+    } else {
+      // cloud in cell: the eight cells of the start-of-step trilinear stencil, each its own pass of
+      // runs over the warp (sorted particles share corners, so runs stay long)
+      for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        const double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+        const int kc = key < 0 ? -1 : (dx ? i1[0] : i0[0]) + a.nx * ((dy ? i1[1] : i0[1]) + a.ny * (dz ? i1[2] : i0[2]));
+        deposit_runs(a, lane, kc, w * J[0], w * J[1], w * J[2]);
       }
-    }
-    if (a.acc && head && key >= 0) {
-      for (int q = 0; q < 3; ++q) acc_add_f64(a.acc + kAccWords * (q * a.ncell + key), J[q], a.p.E);
     }
   }
 }

@@ -5,6 +5,9 @@
 // particles.  Impulses are reduced over runs of equal start-of-step cell in
 // storage order (lane-local suffix sums, then a segmented suffix scan across
 // lanes) and each run is committed once to the exact fixed-point accumulator.
+// The physics variants (nearest-grid-point gather, semi-implicit Euler,
+// Schiller-Naumann drag) are uniform branches; the cloud-in-cell deposit is a
+// template instance that runs the run-sum once per stencil corner.
 #include "st_common.cuh"
 
 namespace st {
@@ -21,6 +24,8 @@ struct MixedArgs {
   float dt, cadt, inv_ca, mcoef;
   float g[3], gdt[3];
   int E;
+  int ngp, semi, sn;  // nearest-grid-point gather, semi-implicit Euler, Schiller-Naumann drag
+  float re_coef;      // rho_f / mu
 };
 
 __device__ __forceinline__ void lerp3(float4 a, float4 b, float f, float r[3]) {
@@ -90,7 +95,70 @@ __device__ __noinline__ int relocate_far(float& o, int ci, int n) {
   return (int)(k < 0 ? k + n : k);
 }
 
-template <bool BF16>
+// Sums J over runs of equal key in the warp's 128 particles (4 consecutive per lane) and commits
+// each run once to the fixed-point accumulator: lane-local suffix sums, then a segmented suffix
+// scan across lanes.  Negative keys are skipped.
+__device__ __forceinline__ void deposit_runs(const MixedArgs& a, int lane, const int key[4], const float J[4][3]) {
+  // lane-local suffix sums S_j over the run that starts at j
+  float S[4][3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) S[3][q] = J[3][q];
+#pragma unroll
+  for (int j = 2; j >= 0; --j) {
+    const bool same = key[j] == key[j + 1];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[j][q] = J[j][q] + (same ? S[j + 1][q] : 0.0f);
+  }
+  // first element of the run that ends the lane (the lane's tail run)
+  const int tail = (key[2] != key[3]) ? 3 : (key[1] != key[2]) ? 2 : (key[0] != key[1]) ? 1 : 0;
+  const bool all_same = tail == 0;
+  // link to the next lane: its leading run continues this lane's trailing run
+  const int nk0 = __shfl_down_sync(0xffffffffu, key[0], 1);
+  const int nall = __shfl_down_sync(0xffffffffu, (int)all_same, 1);
+  float A[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) A[q] = __shfl_down_sync(0xffffffffu, S[0][q], 1);
+  const bool link = (lane < 31) && (nk0 == key[3]) && (key[3] >= 0);
+  int B = (link && nall) ? 1 : 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) A[q] = link ? A[q] : 0.0f;
+  // segmented suffix scan R_l = A_l + B_l R_{l+1}
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    float t0 = __shfl_down_sync(0xffffffffu, A[0], off);
+    float t1 = __shfl_down_sync(0xffffffffu, A[1], off);
+    float t2 = __shfl_down_sync(0xffffffffu, A[2], off);
+    int tb = __shfl_down_sync(0xffffffffu, B, off);
+    if (lane + off > 31) {
+      tb = 0;
+      t0 = t1 = t2 = 0.0f;
+    }
+    if (B) {
+      A[0] += t0;
+      A[1] += t1;
+      A[2] += t2;
+    }
+    B = B & tb;
+  }
+  const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
+  const bool head_lane = (lane == 0) || (pk3 != key[0]);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool start = (j == 0) ? head_lane : (key[j] != key[j - 1]);
+    if (start && key[j] >= 0) {
+      const bool to_end = j == tail;  // only the tail run continues into the next lane
+      commit(a, key[j], S[j][0] + (to_end ? A[0] : 0.0f), S[j][1] + (to_end ? A[1] : 0.0f),
+             S[j][2] + (to_end ? A[2] : 0.0f));
+    }
+  }
+}
+
+// Schiller-Naumann drag factor f = C_D Re / 24: 1 + 0.15 Re^0.687 up to Re = 1000, 0.44 Re / 24 above
+__device__ __forceinline__ float sn_factor(float re) {
+  return re <= 1000.0f ? fmaf(0.15f, powf(re, 0.687f), 1.0f) : (0.44f / 24.0f) * re;
+}
+
+template <bool BF16, bool CIC>
 __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -101,6 +169,9 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
     int key[4] = {-1, -1, -1, -1};
     float J[4][3];
     for (int j = 0; j < 4; ++j) J[j][0] = J[j][1] = J[j][2] = 0.0f;
+    // cloud-in-cell deposit: the start-of-step stencil's lower corner (periodic) and weights
+    int sb[CIC ? 4 : 1][3];
+    float sf[CIC ? 4 : 1][3];
     {
       // pull the next iteration's particle lines towards L2 while this one computes
       const int64_t pn = p0 + nwarp * 128;
@@ -145,36 +216,65 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
             const bool hi = o >= 0.5f;
             i0[q] = ci[q] - (hi ? 0 : 1) + kFluidPad;
             f[q] = o + (hi ? -0.5f : 0.5f);
+            if (CIC) {
+              const int lo = i0[q] - kFluidPad;
+              sb[CIC ? j : 0][q] = lo < 0 ? lo + n3[q] : lo;
+              sf[CIC ? j : 0][q] = f[q];
+            }
           }
           const int64_t row = a.nx + 2 * kFluidPad, slab = row * (a.ny + 2 * kFluidPad);
-          const float4* b = a.U + i0[0] + row * i0[1] + slab * i0[2];
-          const float4 U000 = __ldg(b);
-          const float4 U100 = __ldg(b + 1);
-          const float4 U010 = __ldg(b + row);
-          const float4 U110 = __ldg(b + row + 1);
-          const float4 U001 = __ldg(b + slab);
-          const float4 U101 = __ldg(b + slab + 1);
-          const float4 U011 = __ldg(b + slab + row);
-          const float4 U111 = __ldg(b + slab + row + 1);
-          float r00[3], r10[3], r01[3], r11[3], up[3];
-          lerp3(U000, U100, f[0], r00);
-          lerp3(U010, U110, f[0], r10);
-          lerp3(U001, U101, f[0], r01);
-          lerp3(U011, U111, f[0], r11);
+          float up[3];
+          if (a.ngp) {
+            // nearest grid point: the value of the cell holding the particle
+            const float4 Uc = __ldg(a.U + (ci[0] + kFluidPad) + row * (ci[1] + kFluidPad) + slab * (ci[2] + kFluidPad));
+            up[0] = Uc.x;
+            up[1] = Uc.y;
+            up[2] = Uc.z;
+          } else {
+            const float4* b = a.U + i0[0] + row * i0[1] + slab * i0[2];
+            const float4 U000 = __ldg(b);
+            const float4 U100 = __ldg(b + 1);
+            const float4 U010 = __ldg(b + row);
+            const float4 U110 = __ldg(b + row + 1);
+            const float4 U001 = __ldg(b + slab);
+            const float4 U101 = __ldg(b + slab + 1);
+            const float4 U011 = __ldg(b + slab + row);
+            const float4 U111 = __ldg(b + slab + row + 1);
+            float r00[3], r10[3], r01[3], r11[3];
+            lerp3(U000, U100, f[0], r00);
+            lerp3(U010, U110, f[0], r10);
+            lerp3(U001, U101, f[0], r01);
+            lerp3(U011, U111, f[0], r11);
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const float r0 = fmaf(f[1], r10[q] - r00[q], r00[q]);
-            const float r1 = fmaf(f[1], r11[q] - r01[q], r01[q]);
-            up[q] = fmaf(f[2], r1 - r0, r0);
+            for (int q = 0; q < 3; ++q) {
+              const float r0 = fmaf(f[1], r10[q] - r00[q], r00[q]);
+              const float r1 = fmaf(f[1], r11[q] - r01[q], r01[q]);
+              up[q] = fmaf(f[2], r1 - r0, r0);
+            }
           }
-          // exponential integrator for Stokes drag + gravity
+          // drag rate a = alpha f(Re) / tau (f = 1 for Stokes drag); both integrators take the form
+          // v' = w + (v - w) E, x' = x + w dt + (v - w) Q with w = u_p + g / a:
+          //   exponential:         E = e^{-a dt},       Q = (1 - E) / a
+          //   semi-implicit Euler: E = 1 / (1 + a dt),  Q = E dt  (x' = x + dt v')
           const float d = dv[j];
           const float dd = d * d;
-          const float adt = a.cadt / dd;       // a dt
-          const float E1 = -expm1f(-adt);      // 1 - e^{-a dt}
-          const float E = 1.0f - E1;
-          const float inv_a = dd * a.inv_ca;   // 1 / a
-          const float Q = E1 * inv_a;
+          float adt = a.cadt / dd;       // a dt
+          float inv_a = dd * a.inv_ca;   // 1 / a
+          if (a.sn) {
+            const float r0 = up[0] - v[0][j], r1 = up[1] - v[1][j], r2 = up[2] - v[2][j];
+            const float fac = sn_factor(a.re_coef * sqrtf(fmaf(r0, r0, fmaf(r1, r1, r2 * r2))) * d);
+            adt *= fac;
+            inv_a /= fac;
+          }
+          float E, Q;
+          if (a.semi) {
+            E = 1.0f / (1.0f + adt);
+            Q = E * a.dt;
+          } else {
+            const float E1 = -expm1f(-adt);  // 1 - e^{-a dt}
+            E = 1.0f - E1;
+            Q = E1 * inv_a;
+          }
           const float m = a.mcoef * dd * d;
           int cn[3];
 #pragma unroll
@@ -216,57 +316,30 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
         __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
       for (int q = 0; q < 3; ++q) store_v<BF16>(a, q, p0, v[q]);
     }
-    // ---- deposit: runs of equal start cell over the warp's 128 particles ----
-    // lane-local suffix sums S_j over the run that starts at j
-    float S[4][3];
+    // ---- deposit: runs of equal key over the warp's 128 particles ----
+    if (!CIC) {
+      deposit_runs(a, lane, key, J);
+    } else {
+      // cloud in cell: one pass of runs per stencil corner (sorted particles share corners)
+#pragma unroll 1
+      for (int c = 0; c < 8; ++c) {
+        const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        int kc[4];
+        float Jc[4][3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) S[3][q] = J[3][q];
+        for (int j = 0; j < 4; ++j) {
+          const float* fj = sf[CIC ? j : 0];
+          const int* bj = sb[CIC ? j : 0];
+          const float w = (dx ? fj[0] : 1.0f - fj[0]) * (dy ? fj[1] : 1.0f - fj[1]) * (dz ? fj[2] : 1.0f - fj[2]);
+          int ix = bj[0] + dx, iy = bj[1] + dy, iz = bj[2] + dz;
+          ix = ix >= a.nx ? ix - a.nx : ix;
+          iy = iy >= a.ny ? iy - a.ny : iy;
+          iz = iz >= a.nz ? iz - a.nz : iz;
+          kc[j] = key[j] < 0 ? -1 : ix + a.nx * (iy + a.ny * iz);
 #pragma unroll
-    for (int j = 2; j >= 0; --j) {
-      const bool same = key[j] == key[j + 1];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) S[j][q] = J[j][q] + (same ? S[j + 1][q] : 0.0f);
-    }
-    // first element of the run that ends the lane (the lane's tail run)
-    const int tail = (key[2] != key[3]) ? 3 : (key[1] != key[2]) ? 2 : (key[0] != key[1]) ? 1 : 0;
-    const bool all_same = tail == 0;
-    // link to the next lane: its leading run continues this lane's trailing run
-    const int nk0 = __shfl_down_sync(0xffffffffu, key[0], 1);
-    const int nall = __shfl_down_sync(0xffffffffu, (int)all_same, 1);
-    float A[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) A[q] = __shfl_down_sync(0xffffffffu, S[0][q], 1);
-    const bool link = (lane < 31) && (nk0 == key[3]) && (key[3] >= 0);
-    int B = (link && nall) ? 1 : 0;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) A[q] = link ? A[q] : 0.0f;
-    // segmented suffix scan R_l = A_l + B_l R_{l+1}
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      float t0 = __shfl_down_sync(0xffffffffu, A[0], off);
-      float t1 = __shfl_down_sync(0xffffffffu, A[1], off);
-      float t2 = __shfl_down_sync(0xffffffffu, A[2], off);
-      int tb = __shfl_down_sync(0xffffffffu, B, off);
-      if (lane + off > 31) {
-        tb = 0;
-        t0 = t1 = t2 = 0.0f;
-      }
-      if (B) {
-        A[0] += t0;
-        A[1] += t1;
-        A[2] += t2;
-      }
-      B = B & tb;
-    }
-    const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
-    const bool head_lane = (lane == 0) || (pk3 != key[0]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const bool start = (j == 0) ? head_lane : (key[j] != key[j - 1]);
-      if (start && key[j] >= 0) {
-        const bool to_end = j == tail;  // only the tail run continues into the next lane
-        commit(a, key[j], S[j][0] + (to_end ? A[0] : 0.0f), S[j][1] + (to_end ? A[1] : 0.0f),
-               S[j][2] + (to_end ? A[2] : 0.0f));
+          for (int q = 0; q < 3; ++q) Jc[j][q] = w * J[j][q];
+        }
+        deposit_runs(a, lane, kc, Jc);
       }
     }
   }
@@ -295,14 +368,17 @@ cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p) {
   a.inv_ca = (float)(1.0 / p.ca);
   a.mcoef = (float)p.mcoef;
   a.E = p.E;
+  a.ngp = p.ngp;
+  a.semi = p.semi;
+  a.sn = p.sn;
+  a.re_coef = (float)p.re_coef;
   int64_t warps = (h->np + 127) / 128;
   int64_t blocks = (warps * 32 + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  if (bf)
-    step_mixed_kernel<true><<<(int)blocks, 256, 0, h->stream>>>(a);
-  else
-    step_mixed_kernel<false><<<(int)blocks, 256, 0, h->stream>>>(a);
+  void (*kern)(const MixedArgs) = bf ? (p.cic ? step_mixed_kernel<true, true> : step_mixed_kernel<true, false>)
+                                     : (p.cic ? step_mixed_kernel<false, true> : step_mixed_kernel<false, false>);
+  kern<<<(int)blocks, 256, 0, h->stream>>>(a);
   h->launches += 1;
   return cudaGetLastError();
 }

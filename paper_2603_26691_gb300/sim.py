@@ -117,6 +117,19 @@ class Sim:
         self._chk(self.lib.st_set_params(self.h, float(rho_p), float(mu), garr, float(drag_scale),
                                          float(multiplicity), int(reorder_every)), "st_set_params")
 
+    GATHERS = {"trilinear": 0, "ngp": 1}
+    INTEGRATORS = {"exponential": 0, "semi_implicit": 1}
+    DRAGS = {"stokes": 0, "schiller_naumann": 1}
+    DEPOSITS = {"cell": 0, "cic": 1}
+
+    def set_physics(self, gather="trilinear", integrator="exponential", drag="stokes", deposit="cell", rho_f=1.2):
+        """Physics variants: nearest-grid-point gather, semi-implicit Euler, Schiller-Naumann drag
+        (rho_f: fluid density in the particle Reynolds number), cloud-in-cell deposit."""
+        self.physics = dict(gather=gather, integrator=integrator, drag=drag, deposit=deposit, rho_f=rho_f)
+        self._chk(self.lib.st_set_physics(self.h, self.GATHERS[gather], self.INTEGRATORS[integrator],
+                                          self.DRAGS[drag], self.DEPOSITS[deposit], float(rho_f)),
+                  "st_set_physics")
+
     def set_fluid(self, U):
         """Cell-centred velocity [nz, ny, nx, 3] (float32 or float64; numpy or torch)."""
         if isinstance(U, torch.Tensor):
