@@ -42,7 +42,7 @@ STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_26
                            "step_mixed_tma.cu")
 MEASURED_TRAFFIC = {
     # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches (fresh to 3 steps of drift), 64.07-64.15 B
-    ("b97ae7cb91ca8c10d2c7e0bc45542fab569327300ae5d92059e5f57d7fafc00f", "fourier256_mixed_1e9"): 64.10,
+    ("c77ed6b09a92278f43f98ab4db8acd4a5f11f778c3ef783f761ce5d9b96b2721", "fourier256_mixed_1e9"): 64.10,
 }
 
 

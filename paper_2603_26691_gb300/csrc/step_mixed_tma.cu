@@ -48,6 +48,7 @@ constexpr int kR = 2;                      // deposit halo
 constexpr int kDE = kU + 2 * kR;           // deposit tile edge (12)
 constexpr int kDepositCells = kDE * kDE * kDE;  // 1728
 constexpr int kScanLanes = 8;              // runs are chained across at most this many lanes
+constexpr int kDirectRecords = 16;         // more run records than this per warp: commit in place
 constexpr int kDigits = 3;                 // 15-bit digits per value in the shared deposit tile
 constexpr int kDigitBits = 15;
 constexpr int kDepShift = 51;              // shared tile units = global units * 2^kDepShift
@@ -284,6 +285,20 @@ __device__ __forceinline__ void dep_add3(int* w, float r0, float r1, float r2, f
     if (d0[q]) atomicAdd(wq, d0[q]);
     if (d1[q]) atomicAdd(wq + kDepositCells, d1[q]);
     if (d2[q]) atomicAdd(wq + 2 * kDepositCells, d2[q]);
+  }
+}
+
+// one run record: into the shared deposit tile, or (start cell outside the tile, rare) straight to
+// the global accumulator, counted for the carry-propagation decision
+__device__ __forceinline__ void commit_record(const TmaArgs& a, int* dep, int kk, float r0, float r1, float r2) {
+  if (__builtin_expect(kk < kDepositCells, 1)) {
+    dep_add3(dep + kk, r0, r1, r2, a.s1, a.s2);
+  } else {
+    const int64_t c = kk - kDepositCells;
+    acc_add_f32(a.acc + kAccWords * c, r0, a.E);
+    acc_add_f32(a.acc + kAccWords * (a.ncell + c), r1, a.E);
+    acc_add_f32(a.acc + kAccWords * (2 * a.ncell + c), r2, a.E);
+    atomicAdd(a.acc_ctr, 1ull);
   }
 }
 
@@ -667,48 +682,61 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
       }
       const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
       const bool head_lane = (glane == 0) || (pk3 != key[0]);
-      // the run sums, one {J, key} record per run, packed in (j, lane) order into the warp's own
-      // (already consumed) part of the stage: J in the cell and first two offset arrays, the key
-      // in the third; then each lane takes one record at a time, so a step with few runs costs
-      // one pass.  The stage goes back to the producer after this.
-      int* rj0 = reinterpret_cast<int*>(const_cast<unsigned char*>(src)) + warp * 128;
-      int* rj1 = rj0 + kT;
-      int* rj2 = rj0 + 2 * kT;
-      int* rk = rj0 + 3 * kT;
-      const unsigned lt_mask = (1u << lane) - 1u;
+      // the run sums, one {J, key} record per run.  Few runs (after a sort): the records are packed
+      // in (j, lane) order into the warp's own (already consumed) part of the stage - J in the cell
+      // and first two offset arrays, the key in the third - and each lane takes one record at a
+      // time, so the whole deposit is one pass.  Many runs (particles drifted away from their
+      // sort-time cells): each lane commits its runs where they are, one pass per particle slot,
+      // without the round trip through shared memory.
+      bool starts[4];
+      unsigned hms[4];
       int nh = 0;
-      __syncwarp();
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const bool start = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
-        const unsigned hm = __ballot_sync(0xffffffffu, start);
-        if (start) {
-          const bool to_end = j == tail;
-          const int slot = nh + __popc(hm & lt_mask);
-          rj0[slot] = __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f));
-          rj1[slot] = __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f));
-          rj2[slot] = __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f));
-          rk[slot] = key[j];
-        }
-        nh += __popc(hm);
+        starts[j] = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
+        hms[j] = __ballot_sync(0xffffffffu, starts[j]);
+        nh += __popc(hms[j]);
       }
-      __syncwarp();
-      for (int e = lane; e < nh; e += 32) {
-        const int kk = rk[e];
-        const float r0 = __int_as_float(rj0[e]), r1 = __int_as_float(rj1[e]), r2 = __int_as_float(rj2[e]);
-        if (__builtin_expect(kk < kDepositCells, 1)) {
-          dep_add3(dep + kk, r0, r1, r2, a.s1, a.s2);
-        } else {  // start cell outside the deposit tile (rare): straight to the global accumulator
-          const int64_t c = kk - kDepositCells;
-          acc_add_f32(a.acc + kAccWords * c, r0, a.E);
-          acc_add_f32(a.acc + kAccWords * (a.ncell + c), r1, a.E);
-          acc_add_f32(a.acc + kAccWords * (2 * a.ncell + c), r2, a.E);
-          atomicAdd(a.acc_ctr, 1ull);
+      const bool direct = nh > kDirectRecords;
+      if (direct) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (starts[j]) {
+            const bool to_end = j == tail;
+            const float r0 = Sx[j][0] + (to_end ? R[0] : 0.0f);
+            const float r1 = Sx[j][1] + (to_end ? R[1] : 0.0f);
+            const float r2 = Sx[j][2] + (to_end ? R[2] : 0.0f);
+            commit_record(a, dep, key[j], r0, r1, r2);
+          }
         }
+      } else {
+        int* rj0 = reinterpret_cast<int*>(const_cast<unsigned char*>(src)) + warp * 128;
+        int* rj1 = rj0 + kT;
+        int* rj2 = rj0 + 2 * kT;
+        int* rk = rj0 + 3 * kT;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        int base = 0;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (starts[j]) {
+            const bool to_end = j == tail;
+            const int slot = base + __popc(hms[j] & lt_mask);
+            rj0[slot] = __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f));
+            rj1[slot] = __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f));
+            rj2[slot] = __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f));
+            rk[slot] = key[j];
+          }
+          base += __popc(hms[j]);
+        }
+        __syncwarp();
+        for (int e = lane; e < nh; e += 32) {
+          commit_record(a, dep, rk[e], __int_as_float(rj0[e]), __int_as_float(rj1[e]), __int_as_float(rj2[e]));
+        }
+        // the records were written through the generic proxy; order them before the producer's
+        // next bulk copy into this stage
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      // the records were written through the generic proxy; order them before the producer's next
-      // bulk copy into this stage
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
     }
