@@ -377,7 +377,9 @@ def main():
         if m is not None:
             traffic = m * n
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "step_mixed_tma_kernel" if precision != "fp64" else "step_f64_kernel",
+                "traffic": traffic,
+                # the same kernel's measured DRAM bytes (ncu, this source) at the measured rate
+                "frac_of_measured_traffic": (traffic / (step_avg * 1e-3) / 1e9 / peak) if traffic else None, "kernel": "step_mixed_tma_kernel" if precision != "fp64" else "step_f64_kernel",
                 "algorithmic_bytes_per_particle_step": STEP_BYTES[precision], "peak_kind": peak_kind,
                 "step_kernel_ms": step_avg}
 
