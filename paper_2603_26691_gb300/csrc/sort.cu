@@ -372,6 +372,65 @@ __global__ void gather_f64_kernel(F64State src, F64State dst, const uint32_t* __
 // mixed-precision payload gather, 4 consecutive outputs per thread: one 16-byte load of the
 // permutation, then every gathered load of the 4 particles in flight at once, then 128-bit
 // (64-bit for BF16 velocities) coalesced stores
+// The payload gather from 32-byte particle records {cell, offsets | velocity, diameter} (written
+// by the step before the sort): one 256-bit load, one sector, per particle instead of one sector per
+// array.  FP32 velocity.
+__global__ void gather_records_kernel(const float4* __restrict__ rec, MixedState dst, const uint32_t* __restrict__ sid,
+                                      uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
+  const int64_t n4 = n >> 2;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 pp = __ldg(reinterpret_cast<const uint4*>(perm) + g);
+    const uint32_t p[4] = {pp.x, pp.y, pp.z, pp.w};
+    ptx::Rec32 r[4];
+    uint32_t id[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      r[k] = ptx::ld_rec32(rec + 2 * (int64_t)p[k]);
+      id[k] = __ldg(sid + p[k]);
+    }
+    const int64_t o = g << 2;
+    __stcs(reinterpret_cast<int4*>(dst.cell + o), make_int4(__float_as_int(r[0].c), __float_as_int(r[1].c),
+                                                             __float_as_int(r[2].c), __float_as_int(r[3].c)));
+    __stcs(reinterpret_cast<float4*>(dst.xi[0] + o), make_float4(r[0].x0, r[1].x0, r[2].x0, r[3].x0));
+    __stcs(reinterpret_cast<float4*>(dst.xi[1] + o), make_float4(r[0].x1, r[1].x1, r[2].x1, r[3].x1));
+    __stcs(reinterpret_cast<float4*>(dst.xi[2] + o), make_float4(r[0].x2, r[1].x2, r[2].x2, r[3].x2));
+    __stcs(reinterpret_cast<float4*>((float*)dst.v[0] + o), make_float4(r[0].v0, r[1].v0, r[2].v0, r[3].v0));
+    __stcs(reinterpret_cast<float4*>((float*)dst.v[1] + o), make_float4(r[0].v1, r[1].v1, r[2].v1, r[3].v1));
+    __stcs(reinterpret_cast<float4*>((float*)dst.v[2] + o), make_float4(r[0].v2, r[1].v2, r[2].v2, r[3].v2));
+    __stcs(reinterpret_cast<float4*>(dst.d + o), make_float4(r[0].d, r[1].d, r[2].d, r[3].d));
+    __stcs(reinterpret_cast<uint4*>(did + o), make_uint4(id[0], id[1], id[2], id[3]));
+  }
+  // ragged tail
+  for (int64_t i = (n4 << 2) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pi = perm[i];
+    const ptx::Rec32 r = ptx::ld_rec32(rec + 2 * pi);
+    dst.cell[i] = __float_as_int(r.c);
+    dst.xi[0][i] = r.x0;
+    dst.xi[1][i] = r.x1;
+    dst.xi[2][i] = r.x2;
+    ((float*)dst.v[0])[i] = r.v0;
+    ((float*)dst.v[1])[i] = r.v1;
+    ((float*)dst.v[2])[i] = r.v2;
+    dst.d[i] = r.d;
+    did[i] = sid[pi];
+  }
+}
+
+// Records back to the structure of arrays in place of a sort (the cells are already there).
+__global__ void records_to_soa_kernel(const float4* __restrict__ rec, MixedState dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 a = rec[2 * i], b = rec[2 * i + 1];
+    dst.xi[0][i] = a.y;
+    dst.xi[1][i] = a.z;
+    dst.xi[2][i] = a.w;
+    ((float*)dst.v[0])[i] = b.x;
+    ((float*)dst.v[1])[i] = b.y;
+    ((float*)dst.v[2])[i] = b.z;
+    dst.d[i] = b.w;
+  }
+}
+
 template <bool BF16>
 __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32_t* __restrict__ sid,
                                     uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
@@ -702,6 +761,12 @@ st_status sort_particles(st_ctx* h) {
     gather_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(carve_f64(h->state.p, h->cap),
                                                           carve_f64(h->state_alt.p, h->cap), (const uint32_t*)h->ids.p,
                                                           (uint32_t*)h->ids_alt.p, v0, n);
+  } else if (h->records_pending) {
+    // the step before this sort left the state as records in state_alt: gather them back into
+    // the (stale) structure of arrays; only the ids change buffers
+    gather_records_kernel<<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
+        (const float4*)h->state_alt.p, carve_mixed(h->state.p, h->cap, false), (const uint32_t*)h->ids.p,
+        (uint32_t*)h->ids_alt.p, v0, n);
   } else if (h->prec == ST_MIXED_F32) {
     gather_mixed_kernel<false><<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
         carve_mixed(h->state.p, h->cap, false), carve_mixed(h->state_alt.p, h->cap, false), (const uint32_t*)h->ids.p,
@@ -717,9 +782,21 @@ st_status sort_particles(st_ctx* h) {
   h->launches += 3;  // gather + cell starts (two kernels)
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(h, e, "sort gather");
-  std::swap(h->state, h->state_alt);
+  if (h->records_pending)
+    h->records_pending = false;
+  else
+    std::swap(h->state, h->state_alt);
   std::swap(h->ids, h->ids_alt);
   return ST_OK;
+}
+
+st_status materialize_state(st_ctx* h) {
+  if (!h->records_pending) return ST_OK;
+  records_to_soa_kernel<<<grid_for(h->np), 256, 0, h->stream>>>((const float4*)h->state_alt.p,
+                                                                 carve_mixed(h->state.p, h->cap, false), h->np);
+  h->launches += 1;
+  h->records_pending = false;
+  return cuda_check(h, cudaGetLastError(), "records to arrays");
 }
 
 cudaError_t launch_chunk_bounds(st_ctx* h, double* out) {

@@ -259,6 +259,7 @@ st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device) {
 
 static st_status grow(st_handle h, int64_t need) {
   if (need <= h->cap) return ST_OK;
+  ST_TRY(materialize_state(h));
   int64_t cap = h->cap ? h->cap : 1024;
   while (cap < need) cap = cap + cap / 2 + 64;
   cap = (cap + 63) & ~int64_t(63);
@@ -319,6 +320,7 @@ st_status st_add_particles(st_handle h, int64_t n, const double* xyz, const doub
   if (n == 0) return ST_OK;
   if (!xyz || !d) return set_error(h, ST_ERR_INVALID_ARG, "xyz and d are required");
   if (h->np + n > (int64_t(1) << 34)) return set_error(h, ST_ERR_INVALID_ARG, "too many particles");
+  ST_TRY(materialize_state(h));
   // stage host data on the device
   Buf tx, tv, td, ti;
   const double *dx = xyz, *dv = vel, *dd = d;
@@ -467,6 +469,8 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     if (h->np == 0) break;
     if (h->reorder_every > 0 && (!h->sorted || h->steps_since_sort >= h->reorder_every)) {
       ST_TRY(st_reorder(h));
+    } else {
+      ST_TRY(materialize_state(h));
     }
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
@@ -488,8 +492,14 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     cudaError_t e;
     if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
-    else if (tma)
-      e = launch_step_mixed_tma(h, p);
+    else if (tma) {
+      // a sort is due before the next step: write the state as records for its gather
+      const bool records = h->prec == ST_MIXED_F32 && h->reorder_every > 0 &&
+                           h->steps_since_sort + 1 >= h->reorder_every &&
+                           h->state_alt.bytes >= state_bytes(h->prec, h->cap);
+      e = launch_step_mixed_tma(h, p, records);
+      if (e == cudaSuccess && records) h->records_pending = true;
+    }
     else
       e = launch_step_mixed(h, p);
     ST_TRY(cuda_check(h, e, "step kernel"));
@@ -533,6 +543,7 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
 st_status st_get_particles(st_handle h, int64_t first, int64_t count, double* xyz, double* vel, double* d,
                            uint32_t* ids, int on_device) {
   ST_TRY(check_handle(h));
+  ST_TRY(materialize_state(h));
   if (first < 0 || count < 0 || first + count > h->np) return set_error(h, ST_ERR_INVALID_ARG, "range out of bounds");
   if (count == 0) return ST_OK;
   Buf tx, tv, td, ti;
@@ -586,6 +597,7 @@ st_status st_get_cells(st_handle h, int64_t first, int64_t count, int32_t* cells
 
 st_status st_chunk_bounds(st_handle h, double* out, int on_device) {
   ST_TRY(check_handle(h));
+  ST_TRY(materialize_state(h));
   if (!out) return set_error(h, ST_ERR_INVALID_ARG, "out is NULL");
   if (!h->sorted) return set_error(h, ST_ERR_STATE, "particles not sorted since the last change");
   const int B = h->geo.B;
@@ -630,6 +642,7 @@ st_status st_get_cell_counts(st_handle h, int64_t* counts, int on_device) {
 
 st_status st_invariants(st_handle h, double out[8]) {
   ST_TRY(check_handle(h));
+  ST_TRY(materialize_state(h));
   if (!out) return set_error(h, ST_ERR_INVALID_ARG, "out is NULL");
   double pm[4] = {0, 0, 0, 0}, s3[3] = {0, 0, 0};
   cudaError_t e = cudaSuccess;
@@ -647,6 +660,7 @@ st_status st_invariants(st_handle h, double out[8]) {
 st_status st_clear_particles(st_handle h) {
   ST_TRY(check_handle(h));
   h->np = 0;
+  h->records_pending = false;
   h->sorted = false;
   h->steps_since_sort = 0;
   h->dmax = 0.0;

@@ -77,6 +77,11 @@ struct st_ctx {
   st::Buf keys[2], vals[2], hist, scan_aux, cell_start;  // cell_start uint32[nkeys + 1]
   int64_t sort_cap = 0;
   uint32_t sort_epoch = 0;   // tags the look-back words of each sort pass (no clearing between passes)
+  // The step just before a due sort (FP32 velocity, sorted step kernel) writes the new state as
+  // 32-byte records {cell, offsets | velocity, diameter} into state_alt and only the cells into
+  // `state`; the sort gathers from the records.  Until then the offsets, velocities and
+  // diameters in `state` are stale: every other reader calls materialize_state first.
+  bool records_pending = false;
 
   // source accumulator: carry-save words [3][ncell][kAccWords] (int64), units of 2^-acc_E
   st::Buf acc;
@@ -336,7 +341,9 @@ cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s);
 cudaError_t launch_wide_to_f64(st_ctx* h, const long long* Uw, double* out, int64_t m);
 cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p);
 bool tma_step_supported(const st_ctx* h);                               // step_mixed_tma.cu
-cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p);      // step_mixed_tma.cu
+// records = true (FP32 velocity only): the new state goes out as 32-byte records into state_alt
+// (plus the cells into the structure of arrays) for the sort that follows; see records_pending
+cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records);  // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
 cudaError_t launch_normalize_acc(st_ctx* h);
 // the particle steps of st_step (sort when due, accumulator bookkeeping, step kernel)
@@ -366,6 +373,8 @@ cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, c
                        double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
                        uint32_t* ids);
 st_status sort_particles(st_ctx* h);                                       // sort.cu
+// the structure of arrays current again if the last step left records for a sort (no-op otherwise)
+st_status materialize_state(st_ctx* h);                                    // sort.cu
 cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);
 cudaError_t launch_chunk_bounds(st_ctx* h, double* out);              // sort.cu
 

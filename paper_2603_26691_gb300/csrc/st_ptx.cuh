@@ -55,5 +55,23 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                "l"(src), "r"(bytes), "r"(sptr(bar))
                : "memory");
 }
+// One 32-byte particle record {cell bits, offsets | velocity, diameter} as a single 256-bit
+// global access (sm_100 and later; the address must be 32-byte aligned): one sector per particle.
+struct Rec32 {
+  float c, x0, x1, x2, v0, v1, v2, d;
+};
+__device__ __forceinline__ void st_rec32(void* p, const Rec32& r) {
+  asm volatile("st.global.L1::no_allocate.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(r.c),
+               "f"(r.x0), "f"(r.x1), "f"(r.x2), "f"(r.v0), "f"(r.v1), "f"(r.v2), "f"(r.d)
+               : "memory");
+}
+__device__ __forceinline__ Rec32 ld_rec32(const void* p) {
+  Rec32 r;
+  asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(r.c), "=f"(r.x0), "=f"(r.x1), "=f"(r.x2), "=f"(r.v0), "=f"(r.v1), "=f"(r.v2), "=f"(r.d)
+               : "l"(p));
+  return r;
+}
+
 }  // namespace ptx
 }  // namespace st

@@ -93,6 +93,7 @@ struct TmaArgs {
   float g[3], gdt[3];
   int E;                              // global accumulator exponent
   float s1, s2;                       // s1 * s2 = 2^(E - kDepShift): global units -> deposit-tile units
+  float4* __restrict__ rec;           // record output: two float4 per particle (see st_common.cuh)
 };
 
 // de-interleave 3 bits per level (local x bit lowest)
@@ -302,7 +303,7 @@ __device__ __forceinline__ void commit_record(const TmaArgs& a, int* dep, int kk
   }
 }
 
-template <bool BF16, bool PW2>
+template <bool BF16, bool PW2, bool REC>
 __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const __grid_constant__ TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -611,7 +612,22 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
       }
       // ---- store the owned particles (128-bit when the lane owns all four) ----
       const bool all_own = own[0] && own[1] && own[2] && own[3];
-      if (all_own) {
+      if (REC) {
+        // the step before a sort: the cells to the structure of arrays (the sort's keys), the whole
+        // state as 32-byte records {cell, offsets | velocity, diameter}, one 256-bit store per
+        // particle (a full sector; the sort's gather then reads one sector per particle).  The
+        // diameters are read again from the stage.
+        const float4 d4 = *reinterpret_cast<const float4*>(src + 7 * kT * 4 + L * 4);
+        const float dj[4] = {d4.x, d4.y, d4.z, d4.w};
+        if (all_own) __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (!own[j]) continue;
+          if (!all_own) a.s.cell[p0 + j] = cell[j];
+          st_rec32(a.rec + 2 * (p0 + j),
+                   Rec32{__int_as_float(cell[j]), xi[0][j], xi[1][j], xi[2][j], v[0][j], v[1][j], v[2][j], dj[j]});
+        }
+      } else if (all_own) {
         __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
         for (int q = 0; q < 3; ++q)
           __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
@@ -803,15 +819,17 @@ bool tma_step_supported(const st_ctx* h) {
   return h->fluid_pad.p != nullptr;
 }
 
-cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
+cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) {
   const bool bf = h->prec == ST_MIXED_BF16V;
+  if (records && bf) return cudaErrorInvalidValue;
   bool pw2 = true;
   for (int q = 0; q < 3; ++q) pw2 = pw2 && (h->geo.n[q] & (h->geo.n[q] - 1)) == 0;
   void (*kern)(const CUtensorMap, const TmaArgs) =
-      bf ? (pw2 ? step_mixed_tma_kernel<true, true> : step_mixed_tma_kernel<true, false>)
-         : (pw2 ? step_mixed_tma_kernel<false, true> : step_mixed_tma_kernel<false, false>);
-  static bool attr_set[4] = {false, false, false, false};
-  const int variant = 2 * (int)bf + (int)pw2;
+      records ? (pw2 ? step_mixed_tma_kernel<false, true, true> : step_mixed_tma_kernel<false, false, true>)
+      : bf    ? (pw2 ? step_mixed_tma_kernel<true, true, false> : step_mixed_tma_kernel<true, false, false>)
+              : (pw2 ? step_mixed_tma_kernel<false, true, false> : step_mixed_tma_kernel<false, false, false>);
+  static bool attr_set[6] = {false, false, false, false, false, false};
+  const int variant = records ? 4 + (int)pw2 : 2 * (int)bf + (int)pw2;
   if (!attr_set[variant]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
@@ -831,6 +849,7 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p) {
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   TmaArgs a;
   a.s = carve_mixed(h->state.p, h->cap, bf);
+  a.rec = records ? (float4*)h->state_alt.p : nullptr;
   a.Up = (const float4*)h->fluid_pad.p;
   a.acc = (long long*)h->acc.p;
   a.cell_start = (const uint32_t*)h->cell_start.p;

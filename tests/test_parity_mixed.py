@@ -192,3 +192,44 @@ def test_mixed_moves_longer_than_the_box(Sim, N):
     assert (np.abs(g["vel"] - ovel[:, order]) / (np.abs(ovel[:, order]) + 1.0)).max() <= 1e-5
     assert np.linalg.norm(g["src"] - osrc) <= 1e-5 * np.linalg.norm(osrc)
     assert g["inv"][0] == n
+
+
+def test_reads_between_the_pre_sort_step_and_the_sort(Sim):
+    # the step just before a due sort leaves the state as records for the sort's gather; reading
+    # particles, invariants or chunk boxes, adding particles, or stepping without the sort in
+    # between turns them back into arrays first, and the sort from records gives the same result
+    N, n, dt = 32, 30_001, 5e-4
+    U = _f32(inputs.random_fourier(N, seed=13))
+    pos, vel, d, _ = inputs.particles(515, 0, n, vmax=0.5)
+    G = oracle.make_grid(N)
+    sim = Sim(N, precision="mixed_f32")
+    sim.set_params(reorder_every=5)
+    sim.set_fluid(U.astype(np.float32))
+    sim.add_particles(pos, d, vel)
+    sim.step(5, dt)  # sorts before step 0; step 4 leaves records (a sort is due before step 5)
+    opos, ovel, osrc, _ = oracle.run(G, U, pos, vel, d, 5, dt)
+    inv = sim.invariants()
+    p5, v5, d5, ids5 = sim.particles()
+    o5 = ids5.astype(np.int64)
+    assert np.abs(min_image(p5, opos[:, o5])).max() * N <= 1e-5
+    assert (np.abs(v5 - ovel[:, o5]) / (np.abs(ovel[:, o5]) + 1.0)).max() <= 1e-5
+    m = np.array([oracle.mass(G, x) for x in d5])
+    assert abs(inv[7] - m.sum()) <= 1e-6 * m.sum()
+    # more particles while records may be pending, then 5 steps (the sort gathers from records)
+    pos2, vel2, d2, _ = inputs.particles(516, n, 999, vmax=0.5)
+    sim.step(4, dt)
+    sim.add_particles(pos2, d2, vel2)
+    sim.step(6, dt)
+    g = dict(src=sim.sources(host=True))
+    g["pos"], g["vel"], g["d"], g["ids"] = sim.particles()
+    sim.close()
+    # oracle: the first n particles 15 steps, the added ones 6
+    P1, V1, S1, _ = oracle.run(G, U, pos, vel, d, 9, dt)
+    allp = np.concatenate([P1, pos2], axis=1)
+    allv = np.concatenate([V1, vel2], axis=1)
+    alld = np.concatenate([d, d2])
+    P2, V2, S2, _ = oracle.run(G, U, allp, allv, alld, 6, dt, src=S1)
+    order = g["ids"].astype(np.int64)
+    assert np.abs(min_image(g["pos"], P2[:, order])).max() * N <= 1e-5
+    assert (np.abs(g["vel"] - V2[:, order]) / (np.abs(V2[:, order]) + 1.0)).max() <= 1e-5
+    assert np.linalg.norm(g["src"] - S2) <= 1e-5 * np.linalg.norm(S2)
