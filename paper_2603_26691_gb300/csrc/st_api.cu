@@ -474,7 +474,8 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     }
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
-    const bool tma = h->prec != ST_FP64 && h->sorted && default_physics(h) && tma_step_supported(h);
+    // the sorted step kernel takes every physics variant but the cloud-in-cell deposit
+    const bool tma = h->prec != ST_FP64 && h->sorted && h->phys_deposit == ST_DEPOSIT_CELL && tma_step_supported(h);
     int E = 0;
     ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : deposits_per_cell(h) * (double)h->np + 8.0, &E));
     StepParams p;
@@ -494,7 +495,7 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
       e = launch_step_f64(h, p);
     else if (tma) {
       // a sort is due before the next step: write the state as records for its gather
-      const bool records = h->prec == ST_MIXED_F32 && h->reorder_every > 0 &&
+      const bool records = h->prec == ST_MIXED_F32 && default_physics(h) && h->reorder_every > 0 &&
                            h->steps_since_sort + 1 >= h->reorder_every &&
                            h->state_alt.bytes >= state_bytes(h->prec, h->cap);
       e = launch_step_mixed_tma(h, p, records);

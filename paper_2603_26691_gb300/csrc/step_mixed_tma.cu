@@ -94,6 +94,8 @@ struct TmaArgs {
   int E;                              // global accumulator exponent
   float s1, s2;                       // s1 * s2 = 2^(E - kDepShift): global units -> deposit-tile units
   float4* __restrict__ rec;           // record output: two float4 per particle (see st_common.cuh)
+  int ngp, semi, sn;                  // physics variants (the PHYS instance): nearest grid point,
+  float re_coef;                      // semi-implicit Euler, Schiller-Naumann drag (Re = re_coef |u-v| d)
 };
 
 // de-interleave 3 bits per level (local x bit lowest)
@@ -242,6 +244,22 @@ __device__ __noinline__ float3 gather_padded(const float4* __restrict__ Up, int 
   return make_float3(up[0], up[1], up[2]);
 }
 
+// nearest-grid-point value of a particle outside its unit's tile, from the ghost-padded field
+__device__ __noinline__ float3 ngp_padded(const float4* __restrict__ Up, int px, int pxy, int cell) {
+  const float4 u = __ldg(Up + (cell_i(cell) + kG) + (int64_t)px * (cell_j(cell) + kG) + (int64_t)pxy * (cell_k(cell) + kG));
+  return make_float3(u.x, u.y, u.z);
+}
+
+// Schiller-Naumann drag factor f = C_D Re / 24: 1 + 0.15 Re^0.687 up to Re = 1000 (the power from
+// the hardware base-2 logarithm and exponential), 0.44 Re / 24 above
+__device__ __forceinline__ float sn_factor(float re) {
+  float l, p;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(re));
+  const float y = 0.687f * l;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p) : "f"(y));
+  return re <= 1000.0f ? fmaf(0.15f, p, 1.0f) : (0.44f / 24.0f) * re;
+}
+
 // add round(r_q * 2^Es), q = 0, 1, 2, to the shared deposit-tile values of one cell, each kept as
 // three signed digits in int32 words (w[0] + 2^15 w[kDepositCells] + 2^30 w[2 kDepositCells], the
 // components kDigits kDepositCells words apart); s1 * s2 = 2^Es.  Each scaled value t
@@ -303,7 +321,7 @@ __device__ __forceinline__ void commit_record(const TmaArgs& a, int* dep, int kk
   }
 }
 
-template <bool BF16, bool PW2, bool REC>
+template <bool BF16, bool PW2, bool REC, bool PHYS>
 __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const __grid_constant__ TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -527,14 +545,28 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           key[j] = !own[j]                ? -1
                    : (in_dep && use_tile) ? (rc[0] + kR) + kDE * ((rc[1] + kR) + kDE * (rc[2] + kR))
                                           : kDepositCells + ci[e][0] + a.nx * (ci[e][1] + a.ny * ci[e][2]);
-          const float4* bb = tile + tofs;
-          trilerp(bb[0], bb[1], bb[kTE], bb[kTE + 1], bb[kTE * kTE], bb[kTE * kTE + 1], bb[kTE * kTE + kTE],
-                  bb[kTE * kTE + kTE + 1], f[0], f[1], f[2], up[e]);
-          if (__builtin_expect(!in_dep, 0)) {
-            const float3 g = gather_padded(a.Up, px, pxy, cell[j], xi[0][j], xi[1][j], xi[2][j]);
-            up[e][0] = g.x;
-            up[e][1] = g.y;
-            up[e][2] = g.z;
+          if (PHYS && a.ngp) {
+            // nearest grid point: the value of the start cell (inside the tile when in_dep)
+            const float4 c = tile[in_dep ? (rc[0] + kG) + kTE * ((rc[1] + kG) + kTE * (rc[2] + kG)) : 0];
+            up[e][0] = c.x;
+            up[e][1] = c.y;
+            up[e][2] = c.z;
+            if (__builtin_expect(!in_dep, 0)) {
+              const float3 g = ngp_padded(a.Up, px, pxy, cell[j]);
+              up[e][0] = g.x;
+              up[e][1] = g.y;
+              up[e][2] = g.z;
+            }
+          } else {
+            const float4* bb = tile + tofs;
+            trilerp(bb[0], bb[1], bb[kTE], bb[kTE + 1], bb[kTE * kTE], bb[kTE * kTE + 1], bb[kTE * kTE + kTE],
+                    bb[kTE * kTE + kTE + 1], f[0], f[1], f[2], up[e]);
+            if (__builtin_expect(!in_dep, 0)) {
+              const float3 g = gather_padded(a.Up, px, pxy, cell[j], xi[0][j], xi[1][j], xi[2][j]);
+              up[e][0] = g.x;
+              up[e][1] = g.y;
+              up[e][2] = g.z;
+            }
           }
         }
         // the integrator on the pair
@@ -542,11 +574,40 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         const unsigned long long DD = mul2(D, D);
         float dd0, dd1;
         unpack2(DD, dd0, dd1);
-        const unsigned long long ADT = mul2(dup2(a.cadt), pack2(rcp_approx(dd0), rcp_approx(dd1)));
-        unsigned long long EE;
-        const unsigned long long E1 = one_minus_exp2(ADT, &EE);
-        const unsigned long long INV_A = mul2(DD, dup2(a.inv_ca));
-        const unsigned long long Q = mul2(E1, INV_A);
+        unsigned long long ADT = mul2(dup2(a.cadt), pack2(rcp_approx(dd0), rcp_approx(dd1)));
+        unsigned long long INV_A = mul2(DD, dup2(a.inv_ca));
+        unsigned long long EE, E1, Q;
+        if (PHYS) {
+          // drag rate a = alpha f(Re) / tau (f = 1 for Stokes drag), f from the start-of-step
+          // relative velocity; both integrators take the form v' = w + (v - w) E,
+          // x' = x + w dt + (v - w) Q with w = u_p + g / a:
+          //   exponential:         E = e^{-a dt},       Q = (1 - E) / a
+          //   semi-implicit Euler: E = 1 / (1 + a dt),  Q = E dt  (x' = x + dt v')
+          if (a.sn) {
+            float fac[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const float r0 = up[e][0] - v[0][jp + e], r1 = up[e][1] - v[1][jp + e], r2 = up[e][2] - v[2][jp + e];
+              fac[e] = sn_factor(a.re_coef * sqrtf(fmaf(r0, r0, fmaf(r1, r1, r2 * r2))) * dv[jp + e]);
+            }
+            ADT = mul2(ADT, pack2(fac[0], fac[1]));
+            INV_A = mul2(INV_A, pack2(1.0f / fac[0], 1.0f / fac[1]));
+          }
+          if (a.semi) {
+            float x0, x1;
+            unpack2(ADT, x0, x1);
+            const float e0 = 1.0f / (1.0f + x0), e1 = 1.0f / (1.0f + x1);
+            EE = pack2(e0, e1);
+            E1 = pack2(x0 * e0, x1 * e1);  // 1 - E = a dt / (1 + a dt)
+            Q = mul2(EE, dup2(a.dt));
+          } else {
+            E1 = one_minus_exp2(ADT, &EE);
+            Q = mul2(E1, INV_A);
+          }
+        } else {
+          E1 = one_minus_exp2(ADT, &EE);
+          Q = mul2(E1, INV_A);
+        }
         const unsigned long long M = mul2(mul2(dup2(a.mcoef), DD), D);
         float oraw[2][3];
         int ii[2][3];
@@ -821,15 +882,20 @@ bool tma_step_supported(const st_ctx* h) {
 
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) {
   const bool bf = h->prec == ST_MIXED_BF16V;
-  if (records && bf) return cudaErrorInvalidValue;
+  const bool phys = p.ngp || p.semi || p.sn;
+  if (p.cic || (records && (bf || phys))) return cudaErrorInvalidValue;
   bool pw2 = true;
   for (int q = 0; q < 3; ++q) pw2 = pw2 && (h->geo.n[q] & (h->geo.n[q] - 1)) == 0;
-  void (*kern)(const CUtensorMap, const TmaArgs) =
-      records ? (pw2 ? step_mixed_tma_kernel<false, true, true> : step_mixed_tma_kernel<false, false, true>)
-      : bf    ? (pw2 ? step_mixed_tma_kernel<true, true, false> : step_mixed_tma_kernel<true, false, false>)
-              : (pw2 ? step_mixed_tma_kernel<false, true, false> : step_mixed_tma_kernel<false, false, false>);
-  static bool attr_set[6] = {false, false, false, false, false, false};
-  const int variant = records ? 4 + (int)pw2 : 2 * (int)bf + (int)pw2;
+  using Kern = void (*)(const CUtensorMap, const TmaArgs);
+  static const Kern table[10] = {
+      step_mixed_tma_kernel<false, false, false, false>, step_mixed_tma_kernel<false, true, false, false>,
+      step_mixed_tma_kernel<false, false, false, true>,  step_mixed_tma_kernel<false, true, false, true>,
+      step_mixed_tma_kernel<true, false, false, false>,  step_mixed_tma_kernel<true, true, false, false>,
+      step_mixed_tma_kernel<true, false, false, true>,   step_mixed_tma_kernel<true, true, false, true>,
+      step_mixed_tma_kernel<false, false, true, false>,  step_mixed_tma_kernel<false, true, true, false>};
+  static bool attr_set[10] = {};
+  const int variant = records ? 8 + (int)pw2 : 4 * (int)bf + 2 * (int)phys + (int)pw2;
+  const Kern kern = table[variant];
   if (!attr_set[variant]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
@@ -850,6 +916,10 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) 
   TmaArgs a;
   a.s = carve_mixed(h->state.p, h->cap, bf);
   a.rec = records ? (float4*)h->state_alt.p : nullptr;
+  a.ngp = p.ngp;
+  a.semi = p.semi;
+  a.sn = p.sn;
+  a.re_coef = (float)p.re_coef;
   a.Up = (const float4*)h->fluid_pad.p;
   a.acc = (long long*)h->acc.p;
   a.cell_start = (const uint32_t*)h->cell_start.p;

@@ -42,14 +42,18 @@ def _oracle(N, U, pos, vel, d, steps, dt, combo, band):
     p, v = pos.copy(), vel.copy()
     src = np.zeros((3, N ** 3))
     near = np.zeros(p.shape[1], dtype=bool)
+    first = np.full(p.shape[1], steps)  # the first step that starts within the band of a face
     trace = []
-    for _ in range(steps):
-        near |= face_distance(p, (N, N, N)) < band
+    for s in range(steps):
+        now = face_distance(p, (N, N, N)) < band
+        first[now & ~near] = s
+        near |= now
         p, v, src, tr = oracle.run(G, U, p, v, d, 1, dt, src=src, trace=True)
         trace.append(tr[0])
     trace = np.array(trace)
+    after = np.arange(steps)[:, None] >= first[None, :]  # deposits from that step on
     bad = np.zeros((N, N, N), dtype=bool)
-    for c in np.unique(trace[:, near]):
+    for c in np.unique(trace[after]):
         i, j, k = c % N, (c // N) % N, c // (N * N)
         for a, b, e in itertools.product((-1, 0, 1), repeat=3):
             bad[(k + e) % N, (j + b) % N, (i + a) % N] = True
@@ -57,7 +61,7 @@ def _oracle(N, U, pos, vel, d, steps, dt, combo, band):
 
 
 def _gpu(Sim, prec, N, U, pos, vel, d, steps, dt, combo, reorder_every):
-    sim = Sim(N, precision=prec)
+    sim = Sim(N, precision=prec, chunk_edge=8)
     sim.set_params(reorder_every=reorder_every)
     sim.set_physics(**_phys(combo), rho_f=1.2)
     sim.set_fluid(U if prec == "fp64" else U.astype(np.float32))
@@ -91,12 +95,26 @@ def _check(g, o, N, pos_tol, vel_tol, src_l2, src_max):
 CASE = dict(N=12, n=4097, steps=9, dt=1e-3)
 
 
-def _inputs(seed):
-    c = CASE
+def _inputs(seed, c=CASE):
     U = (inputs.taylor_green(c["N"]) + inputs.random_fourier(c["N"], rms=0.3, seed=seed)).astype(np.float32)
     U = U.astype(np.float64)  # the FP32-rounded field for both sides
     pos, vel, d, _ = inputs.particles(seed, 0, c["n"], vmax=0.5)
     return U, pos, vel, d
+
+
+# grids the sorted-particle (TMA) step kernel takes: edges multiples of the 8-cell unit, at least 14
+# cells; power-of-two and other edges run different instances
+TMA_COMBOS = [c for c in COMBOS if c[3] == "cell" and c != DEFAULT]
+
+
+@pytest.mark.parametrize("N", [32, 24])
+@pytest.mark.parametrize("combo", TMA_COMBOS, ids=["-".join(c[:3]) for c in TMA_COMBOS])
+def test_sorted_step_kernel_variant_within_bounds(Sim, combo, N):
+    c = dict(N=N, n=20_011, steps=9, dt=1e-3)
+    U, pos, vel, d = _inputs(35, c)
+    o = _oracle(N, U, pos, vel, d, c["steps"], c["dt"], combo, band=2e-5)
+    g = _gpu(Sim, "mixed_f32", N, U, pos, vel, d, c["steps"], c["dt"], combo, reorder_every=4)
+    _check(g, o, N, 1e-5, 1e-5, 1e-5, 1e-4)
 
 
 @pytest.mark.parametrize("combo", COMBOS, ids=["-".join(c) for c in COMBOS])
