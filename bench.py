@@ -225,6 +225,118 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
     return ev
 
 
+# FP64 operations per particle of one adjoint step launch (adjoint_step_kernel) and of one FP64
+# step launch, from ncu instruction counters (2 x DFMA + DADD + DMUL, thread instructions) on the
+# adjoint workload; keyed by the SHA-256 of the kernel source, absent (null) once it changes
+MEASURED_FP64_OPS = {
+    # profiles/adjoint_tgf64_1e7.md: 245.0 DFMA + 59.8 DADD + 108.0 DMUL per particle; FP64 pipe 84.5 % busy
+    ("ec1e65882226f5e3119b27f77982eb078dea8786c6779c14c1a4340fb960fb2e", "adjoint_step_kernel"): 657.8,
+}
+MEASURED_FP64_PIPE = {("ec1e65882226f5e3119b27f77982eb078dea8786c6779c14c1a4340fb960fb2e", "adjoint_step_kernel"): 0.845}
+ADJOINT_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
+                              "adjoint.cu")
+FP64_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, the nominal figure (no measured FP64 peak on this machine)
+
+
+def run_adjoint(args, workload):
+    """The adjoint workload: FP64 forward with checkpoints, then the backward sweep (recomputation of
+    each segment and the adjoint step), for a loss on the time-summed source field.  One JSON line:
+    forward+backward particle-steps/s, with the library's kernel timers."""
+    import hashlib
+
+    import torch
+
+    ws, rank, local = _dist()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    n = args.n or workload.n
+    U = workload.make_field()
+    U32 = U.astype(np.float32)
+    sim = setup_sim(workload, n, U32, "fp64", device)
+    sim.set_params(reorder_every=0)
+    steps, ck, dt = workload.steps, workload.extra["checkpoint"], workload.dt
+    gen = torch.Generator(device=device)
+    gen.manual_seed(7)
+    lam = torch.randn((3, sim.ncell), generator=gen, dtype=torch.float64, device=device)
+    # warm-up: W short forward/backward runs of one checkpoint segment
+    for _ in range(max(args.warmup, 1)):
+        sim.adjoint_forward(ck, dt, ck)
+        sim.adjoint_backward(lam)
+    torch.cuda.synchronize()
+    sim.timers(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = sim.kernel_launches
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t2 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    sim.adjoint_forward(steps, dt, ck)
+    t1.record()
+    gd, ga, gU = sim.adjoint_backward(lam)
+    t2.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = sim.kernel_launches - launches0
+    tm = sim.timers()
+    sim.timers(False)
+    fwd_ms, bwd_ms = t0.elapsed_time(t1), t1.elapsed_time(t2)
+    total_ms = fwd_ms + bwd_ms
+    value = n * steps / (total_ms * 1e-3)
+    adj_ms, adj_n = tm["adjoint"]
+    stp_ms, stp_n = tm["step"]
+    with open(ADJOINT_SOURCE, "rb") as f:
+        src_hash = hashlib.sha256(f.read()).hexdigest()
+    ops = MEASURED_FP64_OPS.get((src_hash, "adjoint_step_kernel"))
+    adj_avg = adj_ms / max(adj_n, 1)
+    achieved = ops * n / (adj_avg * 1e-3) / 1e9 if ops else None
+    roofline = {"bound": "alu", "kernel": "adjoint_step_kernel", "unit": "GFLOP/s (FP64)", "peak": FP64_NOMINAL_GFLOPS,
+                "peak_kind": "nominal GB300 dense FP64 (no measured FP64 peak)", "achieved": achieved,
+                "frac": achieved / FP64_NOMINAL_GFLOPS if achieved else None, "traffic": None,
+                "fp64_ops_per_particle": ops, "launches": adj_n, "ms_per_launch": adj_avg,
+                "fp64_pipe_busy_ncu": MEASURED_FP64_PIPE.get((src_hash, "adjoint_step_kernel")),
+                "step_f64_kernel": {"launches": stp_n, "ms_per_launch": stp_ms / max(stp_n, 1)}}
+    # end to end through the public API with host buffers: lam from host memory, the gradients to host
+    lam_h = lam.cpu().numpy()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    sim.adjoint_forward(steps, dt, ck)
+    hgd, hga, hgU = sim.adjoint_backward(lam_h)
+    e_el = time.perf_counter() - e0
+    e2e = {"value": n * steps / e_el, "unit": "particle-steps/s", "h2d_bytes_per_step": int(lam_h.nbytes),
+           "d2h_bytes_per_step": int(hgd.nbytes + hgU.nbytes), "steps": 1,
+           "what": "one forward (checkpointed) + backward run, lam from host, dL/dd and dL/dU to host"}
+    sim.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        from paper_2603_26691_gb300 import inputs
+
+        ns = 200_000  # about 9 s of oracle time (~4.7e6 particle-steps/s)
+        G = oracle.make_grid(workload.grid, chunk_edge=workload.chunk_edge)
+        pos, vel, d, _ = inputs.particles(workload.seed, 0, ns)
+        c0 = time.perf_counter()
+        oracle.adjoint(G, U, pos, vel, d, steps, dt, lam_h)
+        c_el = time.perf_counter() - c0
+        cpu = {"value": ns * steps / c_el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ns} particles x {steps} steps, forward and adjoint (single thread), {c_el:.1f} s"}
+    line = {"metric": "adjoint particle-steps/s (forward with checkpoints + backward with recomputation)",
+            "value": value, "unit": "particle-steps/s", "n_gpus": ws, "steps": steps, "warmup": max(args.warmup, 1),
+            "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload.name, "grid": workload.grid, "particles_per_gpu": n, "dt": dt,
+                       "checkpoint_every": ck, "field": "Taylor-Green + 10% random Fourier, FP32-rounded",
+                       "l2": "no flush: 56 B x particles of state per step, far larger than L2",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "breakdown": {"forward_ms": fwd_ms, "backward_ms": bwd_ms, "timers": tm,
+                          "grad_alpha": ga, "grad_d_norm": float(torch.linalg.vector_norm(gd).item())}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_coupled(args, workload):
     """The asynchronous two-way coupling workload: K particle steps per coupling interval in a frozen
     field while the fluid update (estimated source + Jacobi sweeps) runs on a second stream.  One JSON
@@ -312,6 +424,8 @@ def main():
         workload = dataclasses.replace(workload, grid=args.grid)
     if args.impl == "reference":
         return run_reference(args, workload)
+    if workload.extra and workload.extra.get("checkpoint"):
+        return run_adjoint(args, workload)
     if workload.extra and workload.extra.get("fluid_every"):
         return run_coupled(args, workload)
 

@@ -340,6 +340,18 @@ st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t co
 st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
                               uint32_t* perm, void* stream);
 
+/* Kernel timers: CUDA events recorded around the library's own launches, on the stream each runs
+ * on, summed per kind.  ST_TIMER_STEP: every particle step kernel (st_step, the adjoint's forward
+ * steps and recomputation); ST_TIMER_SORT: a whole reorder (all of its kernels);
+ * ST_TIMER_ADJOINT: the adjoint step kernel of st_adjoint_backward; ST_TIMER_FLUID: the coupled
+ * fluid update on the second stream (st_couple_run).  st_timers_enable(h, 1) clears and starts
+ * recording, 0 stops it.  st_timers_read synchronises, writes the summed milliseconds and the
+ * number of timed launches per kind (arrays of ST_TIMER_COUNT), and clears them if `reset`.
+ * Recording costs two events per timed launch.  Errors: INVALID_ARG, CUDA. */
+enum { ST_TIMER_STEP = 0, ST_TIMER_SORT = 1, ST_TIMER_ADJOINT = 2, ST_TIMER_FLUID = 3, ST_TIMER_COUNT = 4 };
+st_status st_timers_enable(st_handle h, int on);
+st_status st_timers_read(st_handle h, double* ms, int64_t* launches, int reset);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,8 @@ SIGNATURES = {
     "st_synchronize": (_i, [_vp]),
     "st_set_params": (_i, [_vp, _d, _d, _P(_d), _d, _d, _i]),
     "st_set_physics": (_i, [_vp, _i, _i, _i, _i, _d]),
+    "st_timers_enable": (_i, [_vp, _i]),
+    "st_timers_read": (_i, [_vp, _P(_d), _P(_i64), _i]),
     "st_set_fluid": (_i, [_vp, _vp, _i, _i]),
     "st_reserve": (_i, [_vp, _i64]),
     "st_add_particles": (_i, [_vp, _i64, _vp, _vp, _vp, _vp, _i]),

@@ -268,8 +268,10 @@ st_status st_couple_run(st_handle h, int nintervals, double dt) {
     // read too
     ST_CUDA(h, cudaEventRecord(h->ev_main, h->stream));
     ST_CUDA(h, cudaStreamWaitEvent(h->stream2, h->ev_main, 0));
+    timer_begin(h, ST_TIMER_FLUID, h->stream2);
     cudaError_t e = mixed(h) ? launch_fluid_update<float4, float>(h, (const float4*)cur, dt)
                              : launch_fluid_update<D4, double>(h, (const D4*)cur, dt);
+    timer_end(h, ST_TIMER_FLUID, h->stream2);
     ST_TRY(cuda_check(h, e, "fluid update"));
     ST_CUDA(h, cudaEventRecord(h->ev_fluid, h->stream2));
     // the particles of this interval in the current field

@@ -172,6 +172,12 @@ void st_destroy(st_handle h) {
   if (h->ev_main) cudaEventDestroy(h->ev_main);
   if (h->ev_fluid) cudaEventDestroy(h->ev_fluid);
   if (h->stream2) cudaStreamDestroy(h->stream2);
+  for (int k = 0; k < ST_TIMER_COUNT; ++k)
+    for (auto& pr : h->ev_pending[k]) {
+      cudaEventDestroy(pr.first);
+      if (pr.second) cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
 }
 
@@ -205,6 +211,80 @@ st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3],
   h->mult = multiplicity;
   h->reorder_every = reorder_every;
   h->adj_ready = false;
+  return ST_OK;
+}
+
+extern "C++" {
+namespace st {
+static cudaEvent_t timer_event(st_ctx* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+void timer_begin(st_ctx* h, int k, cudaStream_t s) {
+  if (!h->timing) return;
+  cudaEvent_t e = timer_event(h);
+  if (!e) return;
+  cudaEventRecord(e, s);
+  h->ev_pending[k].push_back({e, nullptr});
+}
+void timer_end(st_ctx* h, int k, cudaStream_t s) {
+  if (!h->timing || h->ev_pending[k].empty() || h->ev_pending[k].back().second) return;
+  cudaEvent_t e = timer_event(h);
+  if (!e) return;
+  cudaEventRecord(e, s);
+  h->ev_pending[k].back().second = e;
+}
+static cudaError_t timers_fold(st_ctx* h) {
+  for (int k = 0; k < ST_TIMER_COUNT; ++k) {
+    for (auto& pr : h->ev_pending[k]) {
+      if (pr.second) {
+        cudaError_t e = cudaEventSynchronize(pr.second);
+        if (e != cudaSuccess) return e;
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+        if (e != cudaSuccess) return e;
+        h->timer_ms[k] += ms;
+        h->timer_count[k] += 1;
+        h->ev_pool.push_back(pr.second);
+      }
+      h->ev_pool.push_back(pr.first);
+    }
+    h->ev_pending[k].clear();
+  }
+  return cudaSuccess;
+}
+}  // namespace st
+}  // extern "C++"
+
+st_status st_timers_enable(st_handle h, int on) {
+  ST_TRY(check_handle(h));
+  ST_TRY(cuda_check(h, timers_fold(h), "timers"));
+  for (int k = 0; k < ST_TIMER_COUNT; ++k) {
+    h->timer_ms[k] = 0.0;
+    h->timer_count[k] = 0;
+  }
+  h->timing = on != 0;
+  return ST_OK;
+}
+
+st_status st_timers_read(st_handle h, double* ms, int64_t* launches, int reset) {
+  ST_TRY(check_handle(h));
+  if (!ms || !launches) return set_error(h, ST_ERR_INVALID_ARG, "ms and launches are required");
+  ST_TRY(cuda_check(h, timers_fold(h), "timers"));
+  for (int k = 0; k < ST_TIMER_COUNT; ++k) {
+    ms[k] = h->timer_ms[k];
+    launches[k] = h->timer_count[k];
+    if (reset) {
+      h->timer_ms[k] = 0.0;
+      h->timer_count[k] = 0;
+    }
+  }
   return ST_OK;
 }
 
@@ -401,7 +481,10 @@ st_status st_num_particles(st_handle h, int64_t* n) {
 
 st_status st_reorder(st_handle h) {
   ST_TRY(check_handle(h));
-  ST_TRY(sort_particles(h));
+  timer_begin(h, ST_TIMER_SORT, h->stream);
+  const st_status ss = sort_particles(h);
+  timer_end(h, ST_TIMER_SORT, h->stream);
+  ST_TRY(ss);
   h->adj_ready = false;
   h->sorted = true;
   h->steps_since_sort = 0;
@@ -491,6 +574,7 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     p.cic = h->phys_deposit == ST_DEPOSIT_CIC;
     p.re_coef = h->rho_f_drag / h->mu;
     cudaError_t e;
+    timer_begin(h, ST_TIMER_STEP, h->stream);
     if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
     else if (tma) {
@@ -503,6 +587,7 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     }
     else
       e = launch_step_mixed(h, p);
+    timer_end(h, ST_TIMER_STEP, h->stream);
     ST_TRY(cuda_check(h, e, "step kernel"));
     h->steps_since_sort += 1;
   }
@@ -705,7 +790,10 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
     for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
     p.E = E;
     p.scale = std::ldexp(1.0, E);
-    ST_TRY(cuda_check(h, launch_step_f64(h, p), "adjoint forward step"));
+    timer_begin(h, ST_TIMER_STEP, h->stream);
+    const cudaError_t fe = launch_step_f64(h, p);
+    timer_end(h, ST_TIMER_STEP, h->stream);
+    ST_TRY(cuda_check(h, fe, "adjoint forward step"));
   }
   h->adj_nsteps = nsteps;
   h->adj_every = checkpoint_every;
@@ -772,7 +860,11 @@ st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device,
     for (int k = s0; k < s1 && e == cudaSuccess; ++k) {
       double* slot = (double*)tape.p + (size_t)(k - s0) * 6 * n;
       e = cudaMemcpyAsync(slot, W, (size_t)6 * n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
-      if (e == cudaSuccess && k + 1 < s1) e = launch_step_f64_state(h, ws, nullptr, p);
+      if (e == cudaSuccess && k + 1 < s1) {
+        timer_begin(h, ST_TIMER_STEP, h->stream);
+        e = launch_step_f64_state(h, ws, nullptr, p);
+        timer_end(h, ST_TIMER_STEP, h->stream);
+      }
     }
     // reverse sweep
     for (int k = s1 - 1; k >= s0 && e == cudaSuccess; --k) {
@@ -790,7 +882,9 @@ st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device,
       a.lam = dlam;
       a.Uw = (long long*)Uw.p;
       a.dt = h->adj_dt;
+      timer_begin(h, ST_TIMER_ADJOINT, h->stream);
       e = launch_adjoint_step(h, a);
+      timer_end(h, ST_TIMER_ADJOINT, h->stream);
     }
   }
   // outputs

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/scaletrack.h"
 
@@ -82,6 +84,13 @@ struct st_ctx {
   // `state`; the sort gathers from the records.  Until then the offsets, velocities and
   // diameters in `state` are stale: every other reader calls materialize_state first.
   bool records_pending = false;
+
+  // kernel timers (st_timers_*): pending event pairs per kind, folded into sums on read
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[ST_TIMER_COUNT];
+  double timer_ms[ST_TIMER_COUNT] = {0, 0, 0, 0};
+  int64_t timer_count[ST_TIMER_COUNT] = {0, 0, 0, 0};
 
   // source accumulator: carry-save words [3][ncell][kAccWords] (int64), units of 2^-acc_E
   st::Buf acc;
@@ -375,6 +384,10 @@ cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, c
 st_status sort_particles(st_ctx* h);                                       // sort.cu
 // the structure of arrays current again if the last step left records for a sort (no-op otherwise)
 st_status materialize_state(st_ctx* h);                                    // sort.cu
+// timer marks around a launch of kind k on stream s (no-ops unless st_timers_enable is on); the
+// end mark pairs with the last begin of the same kind
+void timer_begin(st_ctx* h, int k, cudaStream_t s);                        // st_api.cu
+void timer_end(st_ctx* h, int k, cudaStream_t s);                          // st_api.cu
 cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);
 cudaError_t launch_chunk_bounds(st_ctx* h, double* out);              // sort.cu
 

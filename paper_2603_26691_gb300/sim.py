@@ -130,6 +130,19 @@ class Sim:
                                           self.DRAGS[drag], self.DEPOSITS[deposit], float(rho_f)),
                   "st_set_physics")
 
+    TIMERS = ("step", "sort", "adjoint", "fluid")
+
+    def timers(self, on=None, reset=False):
+        """Library kernel timers: timers(True) clears and starts, timers(False) stops; timers() returns
+        {kind: (ms, launches)} (synchronises)."""
+        if on is not None:
+            self._chk(self.lib.st_timers_enable(self.h, int(bool(on))), "st_timers_enable")
+            return None
+        ms = (C.c_double * 4)()
+        cnt = (C.c_int64 * 4)()
+        self._chk(self.lib.st_timers_read(self.h, ms, cnt, int(reset)), "st_timers_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(self.TIMERS)}
+
     def set_fluid(self, U):
         """Cell-centred velocity [nz, ny, nx, 3] (float32 or float64; numpy or torch)."""
         if isinstance(U, torch.Tensor):

@@ -1,0 +1,38 @@
+"""The library's kernel timers (st_timers_*): CUDA events around its own launches, per kind."""
+import numpy as np
+import pytest
+
+from paper_2603_26691_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_timers_count_and_time_the_launches():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2603_26691_gb300.sim import Sim
+
+    N = 16
+    sim = Sim(N, precision="fp64")
+    sim.set_params(reorder_every=3)
+    sim.set_fluid(inputs.taylor_green(N))
+    pos, vel, d, _ = inputs.particles(3, 0, 5000)
+    sim.add_particles(pos, d, vel)
+    sim.step(2, 1e-3)  # not timed
+    sim.timers(True)
+    sim.step(7, 1e-3)  # sorts before steps 3 and 6 of the handle's count (steps_since_sort 3)
+    t = sim.timers()
+    assert t["step"][1] == 7 and t["step"][0] > 0.0
+    assert t["sort"][1] == 2 and t["sort"][0] > 0.0
+    assert t["adjoint"] == (0.0, 0) and t["fluid"] == (0.0, 0)
+    sim.adjoint_forward(6, 1e-3, 4)
+    sim.adjoint_backward(np.ones((3, N ** 3)))
+    t = sim.timers(reset=True)
+    assert t["adjoint"][1] == 6
+    assert t["step"][1] == 7 + 6 + 4  # the forward's six steps, then 3 + 1 recomputed in two segments
+    assert sim.timers()["step"] == (0.0, 0)
+    sim.timers(False)
+    sim.step(1, 1e-3)
+    assert sim.timers()["step"] == (0.0, 0)
+    sim.close()
