@@ -42,8 +42,9 @@ STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_26
                            "step_mixed_tma.cu")
 MEASURED_TRAFFIC = {
     # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches of the plain instance (fresh to 3 steps of
-    # drift), 64.07-64.15 B
-    ("680c1a7dedce94f10000793f00ec6123913bfcf90608c081eb949ebaab873ffd", "fourier256_mixed_1e9"): 64.10,
+    # drift), 64.07-64.15 B (FP32 velocity) and 52.07-52.15 B (BF16 velocity)
+    ("7bd1329b51673b25c0eeab937e4cb8e0c8f211f0772b88a766f5ac58c8920118", "fourier256_mixed_1e9"): 64.10,
+    ("7bd1329b51673b25c0eeab937e4cb8e0c8f211f0772b88a766f5ac58c8920118", "fourier256_bf16v_1e9"): 52.10,
 }
 
 
@@ -232,7 +233,24 @@ MEASURED_FP64_OPS = {
     # profiles/adjoint_tgf64_1e7.md: 245.0 DFMA + 59.8 DADD + 108.0 DMUL per particle; FP64 pipe 84.5 % busy
     ("ec1e65882226f5e3119b27f77982eb078dea8786c6779c14c1a4340fb960fb2e", "adjoint_step_kernel"): 657.8,
 }
-MEASURED_FP64_PIPE = {("ec1e65882226f5e3119b27f77982eb078dea8786c6779c14c1a4340fb960fb2e", "adjoint_step_kernel"): 0.845}
+MEASURED_FP64_PIPE = {("ec1e65882226f5e3119b27f77982eb078dea8786c6779c14c1a4340fb960fb2e", "adjoint_step_kernel"): 0.845,
+                      ("a27e98c87a227e349133c8367bb24f80eafc62ff237b75b17965b7ebee0312de", "step_f64_kernel"): 0.866}
+# step_f64_kernel: 110 DFMA + 62 DADD + 24 DMUL per particle (2e6 particles on 128^3, ncu)
+MEASURED_FP64_OPS[("a27e98c87a227e349133c8367bb24f80eafc62ff237b75b17965b7ebee0312de", "step_f64_kernel")] = 306.0
+F64_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc", "step_f64.cu")
+
+
+def fp64_step_roofline(n, ms):
+    """The FP64 step kernel against GB300's FP64 rate (its operation count from ncu, by source)."""
+    import hashlib
+
+    with open(F64_SOURCE, "rb") as f:
+        key = (hashlib.sha256(f.read()).hexdigest(), "step_f64_kernel")
+    ops = MEASURED_FP64_OPS.get(key)
+    ach = ops * n / (ms * 1e-3) / 1e9 if ops else None
+    return {"bound": "alu", "unit": "GFLOP/s (FP64)", "fp64_ops_per_particle": ops, "achieved": ach,
+            "peak": FP64_NOMINAL_GFLOPS, "peak_kind": "nominal GB300 dense FP64",
+            "frac": ach / FP64_NOMINAL_GFLOPS if ach else None, "fp64_pipe_busy_ncu": MEASURED_FP64_PIPE.get(key)}
 ADJOINT_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
                               "adjoint.cu")
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, the nominal figure (no measured FP64 peak on this pool)
@@ -483,11 +501,12 @@ def main():
     value = n * ws * K / (t_max * 1e-3)
 
     peak, peak_kind = _peaks()
-    # the step just before each sort (FP32 velocity) runs the record-writing instance of the step
-    # kernel (its output as 32-byte records for the sort's gather: 32 B read, 36 B written); the
-    # others run the plain instance, the dominant kernel that the roofline below is for
-    rec_step = [precision == "mixed_f32" and reorder_every > 0 and (W + i + 1) % reorder_every == 0
+    # the step just before each sort runs the record-writing instance of the step kernel (its
+    # output as 32-byte records for the sort's gather: the state read, 36 B written); the others
+    # run the plain instance, the dominant kernel that the roofline below is for
+    rec_step = [precision != "fp64" and reorder_every > 0 and (W + i + 1) % reorder_every == 0
                 for i in range(K)]
+    rec_bytes = {"mixed_f32": 68, "mixed_bf16": 62}.get(precision)  # read the state, write cells + records
     plain_ms = [t for t, r in zip(step_ms, rec_step) if not r] or step_ms
     rec_ms = [t for t, r in zip(step_ms, rec_step) if r]
     step_all_avg = sum(step_ms) / len(step_ms)
@@ -514,8 +533,13 @@ def main():
                               "frac": bytes_per_launch / (step_all_avg * 1e-3) / 1e9 / peak},
                 "record_steps": {"launches": len(rec_ms),
                                  "step_kernel_ms_avg": (sum(rec_ms) / len(rec_ms)) if rec_ms else None,
-                                 "bytes_per_particle": 68,
-                                 "frac": (68 * n / (sum(rec_ms) / len(rec_ms) * 1e-3) / 1e9 / peak) if rec_ms else None}}
+                                 "bytes_per_particle": rec_bytes,
+                                 "frac": (rec_bytes * n / (sum(rec_ms) / len(rec_ms) * 1e-3) / 1e9 / peak)
+                                 if rec_ms else None}}
+
+    if precision == "fp64":  # the FP64 step is bound by FP64 arithmetic, not by HBM
+        roofline = dict(fp64_step_roofline(n, step_avg), kernel="step_f64_kernel", launches=len(step_ms),
+                        step_kernel_ms=step_avg, hbm_frac_of_algorithmic=achieved / peak)
 
     # per-chunk bounding boxes of the sorted state (on demand: one read of cells and offsets)
     sim.reorder()
@@ -585,7 +609,7 @@ def main():
         fp64 = {"particles": fp64_n, "step_kernel_ms": ms64, "particle_steps_per_s": rate64,
                 "mixed_step_kernel_particle_steps_per_s": n / (step_avg * 1e-3),
                 "speedup_mixed_over_fp64_step_kernel": (n / (step_avg * 1e-3)) / rate64,
-                "bound": "alu (FP64)"}
+                "bound": "alu (FP64)", "roofline": fp64_step_roofline(fp64_n, ms64)}
         s64.close()
         del s64
         torch.cuda.empty_cache()

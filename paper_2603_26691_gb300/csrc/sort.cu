@@ -374,7 +374,28 @@ __global__ void gather_f64_kernel(F64State src, F64State dst, const uint32_t* __
 // (64-bit for BF16 velocities) coalesced stores
 // The payload gather from 32-byte particle records {cell, offsets | velocity, diameter} (written
 // by the step before the sort): one 256-bit load, one sector, per particle instead of one sector per
-// array.  FP32 velocity.
+// array.  BF16 handles' velocities are BF16-exact in the records.
+template <bool BF16>
+__device__ __forceinline__ void store_v4(void* v, int64_t o, float a, float b, float c, float d) {
+  if (BF16) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    uint2 r;
+    r.x = *reinterpret_cast<unsigned*>(&lo);
+    r.y = *reinterpret_cast<unsigned*>(&hi);
+    __stcs(reinterpret_cast<uint2*>((__nv_bfloat16*)v + o), r);
+  } else {
+    __stcs(reinterpret_cast<float4*>((float*)v + o), make_float4(a, b, c, d));
+  }
+}
+template <bool BF16>
+__device__ __forceinline__ void store_v1(void* v, int64_t i, float a) {
+  if (BF16)
+    ((__nv_bfloat16*)v)[i] = __float2bfloat16_rn(a);
+  else
+    ((float*)v)[i] = a;
+}
+
+template <bool BF16>
 __global__ void gather_records_kernel(const float4* __restrict__ rec, MixedState dst, const uint32_t* __restrict__ sid,
                                       uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
   const int64_t n4 = n >> 2;
@@ -394,9 +415,9 @@ __global__ void gather_records_kernel(const float4* __restrict__ rec, MixedState
     __stcs(reinterpret_cast<float4*>(dst.xi[0] + o), make_float4(r[0].x0, r[1].x0, r[2].x0, r[3].x0));
     __stcs(reinterpret_cast<float4*>(dst.xi[1] + o), make_float4(r[0].x1, r[1].x1, r[2].x1, r[3].x1));
     __stcs(reinterpret_cast<float4*>(dst.xi[2] + o), make_float4(r[0].x2, r[1].x2, r[2].x2, r[3].x2));
-    __stcs(reinterpret_cast<float4*>((float*)dst.v[0] + o), make_float4(r[0].v0, r[1].v0, r[2].v0, r[3].v0));
-    __stcs(reinterpret_cast<float4*>((float*)dst.v[1] + o), make_float4(r[0].v1, r[1].v1, r[2].v1, r[3].v1));
-    __stcs(reinterpret_cast<float4*>((float*)dst.v[2] + o), make_float4(r[0].v2, r[1].v2, r[2].v2, r[3].v2));
+    store_v4<BF16>(dst.v[0], o, r[0].v0, r[1].v0, r[2].v0, r[3].v0);
+    store_v4<BF16>(dst.v[1], o, r[0].v1, r[1].v1, r[2].v1, r[3].v1);
+    store_v4<BF16>(dst.v[2], o, r[0].v2, r[1].v2, r[2].v2, r[3].v2);
     __stcs(reinterpret_cast<float4*>(dst.d + o), make_float4(r[0].d, r[1].d, r[2].d, r[3].d));
     __stcs(reinterpret_cast<uint4*>(did + o), make_uint4(id[0], id[1], id[2], id[3]));
   }
@@ -409,24 +430,25 @@ __global__ void gather_records_kernel(const float4* __restrict__ rec, MixedState
     dst.xi[0][i] = r.x0;
     dst.xi[1][i] = r.x1;
     dst.xi[2][i] = r.x2;
-    ((float*)dst.v[0])[i] = r.v0;
-    ((float*)dst.v[1])[i] = r.v1;
-    ((float*)dst.v[2])[i] = r.v2;
+    store_v1<BF16>(dst.v[0], i, r.v0);
+    store_v1<BF16>(dst.v[1], i, r.v1);
+    store_v1<BF16>(dst.v[2], i, r.v2);
     dst.d[i] = r.d;
     did[i] = sid[pi];
   }
 }
 
 // Records back to the structure of arrays in place of a sort (the cells are already there).
+template <bool BF16>
 __global__ void records_to_soa_kernel(const float4* __restrict__ rec, MixedState dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float4 a = rec[2 * i], b = rec[2 * i + 1];
     dst.xi[0][i] = a.y;
     dst.xi[1][i] = a.z;
     dst.xi[2][i] = a.w;
-    ((float*)dst.v[0])[i] = b.x;
-    ((float*)dst.v[1])[i] = b.y;
-    ((float*)dst.v[2])[i] = b.z;
+    store_v1<BF16>(dst.v[0], i, b.x);
+    store_v1<BF16>(dst.v[1], i, b.y);
+    store_v1<BF16>(dst.v[2], i, b.z);
     dst.d[i] = b.w;
   }
 }
@@ -724,7 +746,7 @@ st_status sort_particles(st_ctx* h) {
   if (ensure(h, h->scan_aux, (size_t)(2 * kMaxPasses * kRadix + kMaxPasses) * sizeof(uint32_t)) != ST_OK)
     return ST_ERR_OOM;
   if (ensure(h, h->cell_start, ((size_t)h->nkeys + 1) * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
-  if (ensure(h, h->state_alt, state_bytes(h->prec, h->cap)) != ST_OK) return ST_ERR_OOM;
+  if (ensure(h, h->state_alt, state_alt_bytes(h->prec, h->cap)) != ST_OK) return ST_ERR_OOM;
   if (ensure(h, h->ids_alt, (size_t)h->cap * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
   if (h->hist.p != look_before) {
     // a new look-back buffer may hold anything: clear it so that no stale word carries an epoch
@@ -764,8 +786,9 @@ st_status sort_particles(st_ctx* h) {
   } else if (h->records_pending) {
     // the step before this sort left the state as records in state_alt: gather them back into
     // the (stale) structure of arrays; only the ids change buffers
-    gather_records_kernel<<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
-        (const float4*)h->state_alt.p, carve_mixed(h->state.p, h->cap, false), (const uint32_t*)h->ids.p,
+    const bool bf = h->prec == ST_MIXED_BF16V;
+    (bf ? gather_records_kernel<true> : gather_records_kernel<false>)<<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
+        (const float4*)h->state_alt.p, carve_mixed(h->state.p, h->cap, bf), (const uint32_t*)h->ids.p,
         (uint32_t*)h->ids_alt.p, v0, n);
   } else if (h->prec == ST_MIXED_F32) {
     gather_mixed_kernel<false><<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
@@ -792,8 +815,9 @@ st_status sort_particles(st_ctx* h) {
 
 st_status materialize_state(st_ctx* h) {
   if (!h->records_pending) return ST_OK;
-  records_to_soa_kernel<<<grid_for(h->np), 256, 0, h->stream>>>((const float4*)h->state_alt.p,
-                                                                 carve_mixed(h->state.p, h->cap, false), h->np);
+  const bool bf = h->prec == ST_MIXED_BF16V;
+  (bf ? records_to_soa_kernel<true> : records_to_soa_kernel<false>)<<<grid_for(h->np), 256, 0, h->stream>>>(
+      (const float4*)h->state_alt.p, carve_mixed(h->state.p, h->cap, bf), h->np);
   h->launches += 1;
   h->records_pending = false;
   return cuda_check(h, cudaGetLastError(), "records to arrays");

@@ -579,9 +579,9 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
       e = launch_step_f64(h, p);
     else if (tma) {
       // a sort is due before the next step: write the state as records for its gather
-      const bool records = h->prec == ST_MIXED_F32 && default_physics(h) && h->reorder_every > 0 &&
+      const bool records = default_physics(h) && h->reorder_every > 0 &&
                            h->steps_since_sort + 1 >= h->reorder_every &&
-                           h->state_alt.bytes >= state_bytes(h->prec, h->cap);
+                           h->state_alt.bytes >= (size_t)h->cap * 32;
       e = launch_step_mixed_tma(h, p, records);
       if (e == cudaSuccess && records) h->records_pending = true;
     }

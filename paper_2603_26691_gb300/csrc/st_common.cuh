@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
 #include <vector>
@@ -79,7 +80,7 @@ struct st_ctx {
   st::Buf keys[2], vals[2], hist, scan_aux, cell_start;  // cell_start uint32[nkeys + 1]
   int64_t sort_cap = 0;
   uint32_t sort_epoch = 0;   // tags the look-back words of each sort pass (no clearing between passes)
-  // The step just before a due sort (FP32 velocity, sorted step kernel) writes the new state as
+  // The step just before a due sort (mixed handles, sorted step kernel) writes the new state as
   // 32-byte records {cell, offsets | velocity, diameter} into state_alt and only the cells into
   // `state`; the sort gathers from the records.  Until then the offsets, velocities and
   // diameters in `state` are stale: every other reader calls materialize_state first.
@@ -159,6 +160,12 @@ struct MixedState {
   void* v[3];  // float* or __nv_bfloat16*
   float* d;
 };
+
+// the sort's spare buffer: room for the state, and on mixed handles for 32-byte particle records
+inline size_t state_alt_bytes(int prec, int64_t cap) {
+  const size_t b = state_bytes(prec, cap);
+  return prec == ST_FP64 ? b : std::max(b, (size_t)cap * 32);
+}
 
 inline F64State carve_f64(void* base, int64_t cap) {
   F64State s;
@@ -350,8 +357,9 @@ cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s);
 cudaError_t launch_wide_to_f64(st_ctx* h, const long long* Uw, double* out, int64_t m);
 cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p);
 bool tma_step_supported(const st_ctx* h);                               // step_mixed_tma.cu
-// records = true (FP32 velocity only): the new state goes out as 32-byte records into state_alt
-// (plus the cells into the structure of arrays) for the sort that follows; see records_pending
+// records = true (mixed handles, default physics): the new state goes out as 32-byte records into
+// state_alt (plus the cells into the structure of arrays) for the sort that follows; see
+// records_pending
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records);  // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
 cudaError_t launch_normalize_acc(st_ctx* h);

@@ -677,8 +677,10 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         // the step before a sort: the cells to the structure of arrays (the sort's keys), the whole
         // state as 32-byte records {cell, offsets | velocity, diameter}, one 256-bit store per
         // particle (a full sector; the sort's gather then reads one sector per particle).  The
-        // diameters are read again from the stage.
-        const float4 d4 = *reinterpret_cast<const float4*>(src + 7 * kT * 4 + L * 4);
+        // diameters are read again from the stage.  BF16 handles store the (BF16-exact) velocities
+        // as FP32 in the record.
+        const float4 d4 =
+            *reinterpret_cast<const float4*>(src + (BF16 ? 4 * kT * 4 + 3 * kT * 2 : 7 * kT * 4) + L * 4);
         const float dj[4] = {d4.x, d4.y, d4.z, d4.w};
         if (all_own) __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
 #pragma unroll
@@ -883,18 +885,19 @@ bool tma_step_supported(const st_ctx* h) {
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) {
   const bool bf = h->prec == ST_MIXED_BF16V;
   const bool phys = p.ngp || p.semi || p.sn;
-  if (p.cic || (records && (bf || phys))) return cudaErrorInvalidValue;
+  if (p.cic || (records && phys)) return cudaErrorInvalidValue;
   bool pw2 = true;
   for (int q = 0; q < 3; ++q) pw2 = pw2 && (h->geo.n[q] & (h->geo.n[q] - 1)) == 0;
   using Kern = void (*)(const CUtensorMap, const TmaArgs);
-  static const Kern table[10] = {
+  static const Kern table[12] = {
       step_mixed_tma_kernel<false, false, false, false>, step_mixed_tma_kernel<false, true, false, false>,
       step_mixed_tma_kernel<false, false, false, true>,  step_mixed_tma_kernel<false, true, false, true>,
       step_mixed_tma_kernel<true, false, false, false>,  step_mixed_tma_kernel<true, true, false, false>,
       step_mixed_tma_kernel<true, false, false, true>,   step_mixed_tma_kernel<true, true, false, true>,
-      step_mixed_tma_kernel<false, false, true, false>,  step_mixed_tma_kernel<false, true, true, false>};
-  static bool attr_set[10] = {};
-  const int variant = records ? 8 + (int)pw2 : 4 * (int)bf + 2 * (int)phys + (int)pw2;
+      step_mixed_tma_kernel<false, false, true, false>,  step_mixed_tma_kernel<false, true, true, false>,
+      step_mixed_tma_kernel<true, false, true, false>,   step_mixed_tma_kernel<true, true, true, false>};
+  static bool attr_set[12] = {};
+  const int variant = records ? 8 + 2 * (int)bf + (int)pw2 : 4 * (int)bf + 2 * (int)phys + (int)pw2;
   const Kern kern = table[variant];
   if (!attr_set[variant]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
