@@ -369,9 +369,6 @@ __global__ void gather_f64_kernel(F64State src, F64State dst, const uint32_t* __
   }
 }
 
-// mixed-precision payload gather, 4 consecutive outputs per thread: one 16-byte load of the
-// permutation, then every gathered load of the 4 particles in flight at once, then 128-bit
-// (64-bit for BF16 velocities) coalesced stores
 // The payload gather from 32-byte particle records {cell, offsets | velocity, diameter} (written
 // by the step before the sort): one 256-bit load, one sector, per particle instead of one sector per
 // array.  BF16 handles' velocities are BF16-exact in the records.
@@ -453,6 +450,9 @@ __global__ void records_to_soa_kernel(const float4* __restrict__ rec, MixedState
   }
 }
 
+// mixed-precision payload gather, 4 consecutive outputs per thread: one 16-byte load of the
+// permutation, then every gathered load of the 4 particles in flight at once, then 128-bit
+// (64-bit for BF16 velocities) coalesced stores
 template <bool BF16>
 __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32_t* __restrict__ sid,
                                     uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {

@@ -665,6 +665,7 @@ st_status st_get_particles(st_handle h, int64_t first, int64_t count, double* xy
 
 st_status st_get_cells(st_handle h, int64_t first, int64_t count, int32_t* cells, int on_device) {
   ST_TRY(check_handle(h));
+  ST_TRY(materialize_state(h));
   if (!cells) return set_error(h, ST_ERR_INVALID_ARG, "cells is NULL");
   if (first < 0 || count < 0 || first + count > h->np) return set_error(h, ST_ERR_INVALID_ARG, "range out of bounds");
   if (count == 0) return ST_OK;
