@@ -574,7 +574,7 @@ def main():
            "what": "per step: fluid field H2D from pinned host, step (sort when due), sources D2H to pinned host"}
 
     # physics variants on the same particles, sorted: the sorted-particle step kernel's physics
-    # instance (containing-cell deposit) or the general mixed kernel (cloud-in-cell deposit)
+    # instance
     variants = None
     if args.variant_steps > 0:
         variants = {}
@@ -587,8 +587,7 @@ def main():
             ms = sum(e1.elapsed_time(e2) for (e0, e1, e2, _) in ev) / len(ev)
             variants[name] = {"physics": ph, "step_kernel_ms": ms, "particle_steps_per_s": n / (ms * 1e-3),
                               "hbm_frac_of_algorithmic": STEP_BYTES[precision] * n / (ms * 1e-3) / 1e9 / peak,
-                              "kernel": ("step_mixed_tma_kernel (physics instance)" if ph.get("deposit", "cell") == "cell"
-                                         else "step_mixed_kernel")}
+                              "kernel": "step_mixed_tma_kernel (physics instance)"}
         sim.set_physics()
     sim.close()
     del sim

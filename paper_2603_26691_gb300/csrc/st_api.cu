@@ -557,8 +557,7 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     }
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
-    // the sorted step kernel takes every physics variant but the cloud-in-cell deposit
-    const bool tma = h->prec != ST_FP64 && h->sorted && h->phys_deposit == ST_DEPOSIT_CELL && tma_step_supported(h);
+    const bool tma = h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
     int E = 0;
     ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : deposits_per_cell(h) * (double)h->np + 8.0, &E));
     StepParams p;

@@ -94,8 +94,9 @@ struct TmaArgs {
   int E;                              // global accumulator exponent
   float s1, s2;                       // s1 * s2 = 2^(E - kDepShift): global units -> deposit-tile units
   float4* __restrict__ rec;           // record output: two float4 per particle (see st_common.cuh)
-  int ngp, semi, sn;                  // physics variants (the PHYS instance): nearest grid point,
-  float re_coef;                      // semi-implicit Euler, Schiller-Naumann drag (Re = re_coef |u-v| d)
+  int ngp, semi, sn, cic;             // physics variants (the PHYS instance): nearest grid point,
+  float re_coef;                      // semi-implicit Euler, Schiller-Naumann drag (Re = re_coef |u-v| d),
+                                      // cloud-in-cell deposit
 };
 
 // de-interleave 3 bits per level (local x bit lowest)
@@ -720,101 +721,167 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           }
         }
       }
-      // ---- deposit: runs of equal start cell over the warp's 128 particles (lane-local suffix sums,
-      // then a segmented suffix scan across lanes chains runs that span lanes) ----
-      float Sx[4][3];
+      // ---- deposit: runs of equal key over the warp's 128 particles (lane-local suffix sums, then a
+      // segmented suffix scan across lanes chains runs that span lanes).  compact = false keeps
+      // the stage untouched (the records are committed where they are formed) ----
+      auto deposit = [&](const int (&key)[4], const float (&J)[4][3], bool compact) {
+        float Sx[4][3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) Sx[3][q] = J[3][q];
+        for (int q = 0; q < 3; ++q) Sx[3][q] = J[3][q];
 #pragma unroll
-      for (int j = 2; j >= 0; --j) {
-        const bool same = key[j] == key[j + 1];
+        for (int j = 2; j >= 0; --j) {
+          const bool same = key[j] == key[j + 1];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) Sx[j][q] = J[j][q] + (same ? Sx[j + 1][q] : 0.0f);
-      }
-      const int tail = (key[2] != key[3]) ? 3 : (key[1] != key[2]) ? 2 : (key[0] != key[1]) ? 1 : 0;
-      const int nk0 = __shfl_down_sync(0xffffffffu, key[0], 1);
-      const int nall = __shfl_down_sync(0xffffffffu, (int)(tail == 0), 1);
-      float R[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) R[q] = __shfl_down_sync(0xffffffffu, Sx[0][q], 1);
-      const int glane = lane & (kScanLanes - 1);
-      const bool link = (glane < kScanLanes - 1) && (nk0 == key[3]) && (key[3] >= 0);
-      int Bl = (link && nall) ? 1 : 0;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) R[q] = link ? R[q] : 0.0f;
-#pragma unroll
-      for (int off = 1; off < kScanLanes; off <<= 1) {
-        float t0v = __shfl_down_sync(0xffffffffu, R[0], off);
-        float t1v = __shfl_down_sync(0xffffffffu, R[1], off);
-        float t2v = __shfl_down_sync(0xffffffffu, R[2], off);
-        int tb = __shfl_down_sync(0xffffffffu, Bl, off);
-        if (glane + off > kScanLanes - 1) {
-          tb = 0;
-          t0v = t1v = t2v = 0.0f;
+          for (int q = 0; q < 3; ++q) Sx[j][q] = J[j][q] + (same ? Sx[j + 1][q] : 0.0f);
         }
-        if (Bl) {
-          R[0] += t0v;
-          R[1] += t1v;
-          R[2] += t2v;
-        }
-        Bl &= tb;
-      }
-      const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
-      const bool head_lane = (glane == 0) || (pk3 != key[0]);
-      // the run sums, one {J, key} record per run.  Few runs (after a sort): the records are packed
-      // in (j, lane) order into the warp's own (already consumed) part of the stage - J in the cell
-      // and first two offset arrays, the key in the third - and each lane takes one record at a
-      // time, so the whole deposit is one pass.  Many runs (particles drifted away from their
-      // sort-time cells): each lane commits its runs where they are, one pass per particle slot,
-      // without the round trip through shared memory.
-      bool starts[4];
-      unsigned hms[4];
-      int nh = 0;
+        const int tail = (key[2] != key[3]) ? 3 : (key[1] != key[2]) ? 2 : (key[0] != key[1]) ? 1 : 0;
+        const int nk0 = __shfl_down_sync(0xffffffffu, key[0], 1);
+        const int nall = __shfl_down_sync(0xffffffffu, (int)(tail == 0), 1);
+        float R[3];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        starts[j] = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
-        hms[j] = __ballot_sync(0xffffffffu, starts[j]);
-        nh += __popc(hms[j]);
-      }
-      const bool direct = nh > kDirectRecords;
-      if (direct) {
+        for (int q = 0; q < 3; ++q) R[q] = __shfl_down_sync(0xffffffffu, Sx[0][q], 1);
+        const int glane = lane & (kScanLanes - 1);
+        const bool link = (glane < kScanLanes - 1) && (nk0 == key[3]) && (key[3] >= 0);
+        int Bl = (link && nall) ? 1 : 0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) R[q] = link ? R[q] : 0.0f;
+#pragma unroll
+        for (int off = 1; off < kScanLanes; off <<= 1) {
+          float t0v = __shfl_down_sync(0xffffffffu, R[0], off);
+          float t1v = __shfl_down_sync(0xffffffffu, R[1], off);
+          float t2v = __shfl_down_sync(0xffffffffu, R[2], off);
+          int tb = __shfl_down_sync(0xffffffffu, Bl, off);
+          if (glane + off > kScanLanes - 1) {
+            tb = 0;
+            t0v = t1v = t2v = 0.0f;
+          }
+          if (Bl) {
+            R[0] += t0v;
+            R[1] += t1v;
+            R[2] += t2v;
+          }
+          Bl &= tb;
+        }
+        const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
+        const bool head_lane = (glane == 0) || (pk3 != key[0]);
+        // the run sums, one {J, key} record per run.  Few runs (after a sort): the records are packed
+        // in (j, lane) order into the warp's own (already consumed) part of the stage - J in the cell
+        // and first two offset arrays, the key in the third - and each lane takes one record at a
+        // time, so the whole deposit is one pass.  Many runs (particles drifted away from their
+        // sort-time cells): each lane commits its runs where they are, one pass per particle slot,
+        // without the round trip through shared memory.
+        bool starts[4];
+        unsigned hms[4];
+        int nh = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (starts[j]) {
-            const bool to_end = j == tail;
-            const float r0 = Sx[j][0] + (to_end ? R[0] : 0.0f);
-            const float r1 = Sx[j][1] + (to_end ? R[1] : 0.0f);
-            const float r2 = Sx[j][2] + (to_end ? R[2] : 0.0f);
-            commit_record(a, dep, key[j], r0, r1, r2);
-          }
+          starts[j] = ((j == 0) ? head_lane : (key[j] != key[j - 1])) && key[j] >= 0;
+          hms[j] = __ballot_sync(0xffffffffu, starts[j]);
+          nh += __popc(hms[j]);
         }
+        const bool direct = !compact || nh > kDirectRecords;
+        if (direct) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (starts[j]) {
+              const bool to_end = j == tail;
+              const float r0 = Sx[j][0] + (to_end ? R[0] : 0.0f);
+              const float r1 = Sx[j][1] + (to_end ? R[1] : 0.0f);
+              const float r2 = Sx[j][2] + (to_end ? R[2] : 0.0f);
+              commit_record(a, dep, key[j], r0, r1, r2);
+            }
+          }
+        } else {
+          int* rj0 = reinterpret_cast<int*>(const_cast<unsigned char*>(src)) + warp * 128;
+          int* rj1 = rj0 + kT;
+          int* rj2 = rj0 + 2 * kT;
+          int* rk = rj0 + 3 * kT;
+          const unsigned lt_mask = (1u << lane) - 1u;
+          int base = 0;
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (starts[j]) {
+              const bool to_end = j == tail;
+              const int slot = base + __popc(hms[j] & lt_mask);
+              rj0[slot] = __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f));
+              rj1[slot] = __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f));
+              rj2[slot] = __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f));
+              rk[slot] = key[j];
+            }
+            base += __popc(hms[j]);
+          }
+          __syncwarp();
+          for (int e = lane; e < nh; e += 32) {
+            commit_record(a, dep, rk[e], __int_as_float(rj0[e]), __int_as_float(rj1[e]), __int_as_float(rj2[e]));
+          }
+          // the records were written through the generic proxy; order them before the producer's
+          // next bulk copy into this stage
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+      };
+      if (!(PHYS && a.cic)) {
+        deposit(key, J, true);
       } else {
-        int* rj0 = reinterpret_cast<int*>(const_cast<unsigned char*>(src)) + warp * 128;
-        int* rj1 = rj0 + kT;
-        int* rj2 = rj0 + 2 * kT;
-        int* rk = rj0 + 3 * kT;
-        const unsigned lt_mask = (1u << lane) - 1u;
-        int base = 0;
-        __syncwarp();
+        // cloud in cell: J spread over the eight cells of the start-of-step trilinear stencil with
+        // its weights, one pass of runs per corner.  The start cells and offsets are read again
+        // from the stage (still intact: every pass commits in place).  Corners inside the deposit
+        // tile go there; the rest (start cells at the tile's edge or outside it, rare) go to the
+        // global accumulator.
+        const int4 c4 = *reinterpret_cast<const int4*>(src + L * 4);
+        const int cs[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          const int dl[3] = {c & 1, (c >> 1) & 1, c >> 2};
+          int kc[4];
+          float Jc[4][3];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (starts[j]) {
-            const bool to_end = j == tail;
-            const int slot = base + __popc(hms[j] & lt_mask);
-            rj0[slot] = __float_as_int(Sx[j][0] + (to_end ? R[0] : 0.0f));
-            rj1[slot] = __float_as_int(Sx[j][1] + (to_end ? R[1] : 0.0f));
-            rj2[slot] = __float_as_int(Sx[j][2] + (to_end ? R[2] : 0.0f));
-            rk[slot] = key[j];
+          for (int q = 0; q < 3; ++q) {
+            const float4 o4 = *reinterpret_cast<const float4*>(src + (1 + q) * kT * 4 + L * 4);
+            const float oj[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const bool lo = oj[j] < 0.5f;
+              const float f = oj[j] + (lo ? 0.5f : -0.5f);
+              const float w = dl[q] ? f : 1.0f - f;
+              if (q == 0) {
+                Jc[j][0] = w;
+              } else {
+                Jc[j][0] *= w;
+              }
+              // corner index along this axis relative to the start cell: -1, 0 or +1
+              const int off = dl[q] - (lo ? 1 : 0);
+              if (q == 0) kc[j] = off + 1;
+              else if (q == 1) kc[j] += 3 * (off + 1);
+              else kc[j] += 9 * (off + 1);
+            }
           }
-          base += __popc(hms[j]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float w = Jc[j][0];
+            Jc[j][0] = w * J[j][0];
+            Jc[j][1] = w * J[j][1];
+            Jc[j][2] = w * J[j][2];
+            const int ox = kc[j] % 3 - 1, oy = (kc[j] / 3) % 3 - 1, oz = kc[j] / 9 - 1;
+            int k = -1;
+            if (key[j] >= 0 && key[j] < kDepositCells) {
+              const int kz = key[j] / (kDE * kDE), rem = key[j] - kz * (kDE * kDE);
+              const int ky = rem / kDE, kx = rem - ky * kDE;
+              const int bx = kx + ox, by = ky + oy, bz = kz + oz;
+              if ((unsigned)bx < (unsigned)kDE && (unsigned)by < (unsigned)kDE && (unsigned)bz < (unsigned)kDE)
+                k = bx + kDE * (by + kDE * bz);
+            }
+            if (k < 0 && key[j] >= 0) {  // the global accumulator, periodic corner index
+              int gx = cell_i(cs[j]) + ox, gy = cell_j(cs[j]) + oy, gz = cell_k(cs[j]) + oz;
+              gx = gx < 0 ? gx + n3[0] : (gx >= n3[0] ? gx - n3[0] : gx);
+              gy = gy < 0 ? gy + n3[1] : (gy >= n3[1] ? gy - n3[1] : gy);
+              gz = gz < 0 ? gz + n3[2] : (gz >= n3[2] ? gz - n3[2] : gz);
+              k = kDepositCells + gx + a.nx * (gy + a.ny * gz);
+            }
+            kc[j] = k;
+          }
+          deposit(kc, Jc, false);
         }
-        __syncwarp();
-        for (int e = lane; e < nh; e += 32) {
-          commit_record(a, dep, rk[e], __int_as_float(rj0[e]), __int_as_float(rj1[e]), __int_as_float(rj2[e]));
-        }
-        // the records were written through the generic proxy; order them before the producer's
-        // next bulk copy into this stage
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
@@ -884,8 +951,8 @@ bool tma_step_supported(const st_ctx* h) {
 
 cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) {
   const bool bf = h->prec == ST_MIXED_BF16V;
-  const bool phys = p.ngp || p.semi || p.sn;
-  if (p.cic || (records && phys)) return cudaErrorInvalidValue;
+  const bool phys = p.ngp || p.semi || p.sn || p.cic;
+  if (records && phys) return cudaErrorInvalidValue;
   bool pw2 = true;
   for (int q = 0; q < 3; ++q) pw2 = pw2 && (h->geo.n[q] & (h->geo.n[q] - 1)) == 0;
   using Kern = void (*)(const CUtensorMap, const TmaArgs);
@@ -922,6 +989,7 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) 
   a.ngp = p.ngp;
   a.semi = p.semi;
   a.sn = p.sn;
+  a.cic = p.cic;
   a.re_coef = (float)p.re_coef;
   a.Up = (const float4*)h->fluid_pad.p;
   a.acc = (long long*)h->acc.p;

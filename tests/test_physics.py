@@ -104,11 +104,11 @@ def _inputs(seed, c=CASE):
 
 # grids the sorted-particle (TMA) step kernel takes: edges multiples of the 8-cell unit, at least 14
 # cells; power-of-two and other edges run different instances
-TMA_COMBOS = [c for c in COMBOS if c[3] == "cell" and c != DEFAULT]
+TMA_COMBOS = [c for c in COMBOS if c != DEFAULT]
 
 
 @pytest.mark.parametrize("N", [32, 24])
-@pytest.mark.parametrize("combo", TMA_COMBOS, ids=["-".join(c[:3]) for c in TMA_COMBOS])
+@pytest.mark.parametrize("combo", TMA_COMBOS, ids=["-".join(c) for c in TMA_COMBOS])
 def test_sorted_step_kernel_variant_within_bounds(Sim, combo, N):
     c = dict(N=N, n=20_011, steps=9, dt=1e-3)
     U, pos, vel, d = _inputs(35, c)
