@@ -67,20 +67,6 @@ struct ArrayKeys {  // keys given by the caller
   __device__ __forceinline__ uint32_t operator()(int64_t i) const { return k[i]; }
 };
 
-// lanes of the warp holding the same 8-bit digit (and the same validity): the intersection of one
-// ballot per digit bit, a fixed cost whatever the number of distinct digits in the warp
-__device__ __forceinline__ unsigned match_digit(uint32_t dig, bool valid) {
-  unsigned m = __ballot_sync(0xffffffffu, valid);
-  m = valid ? m : ~m;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const bool bit = (dig >> b) & 1u;
-    const unsigned bb = __ballot_sync(0xffffffffu, bit);
-    m &= bit ? bb : ~bb;
-  }
-  return m;
-}
-
 __device__ __forceinline__ uint64_t sort_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -257,11 +243,12 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
       const uint32_t dig = (key[r] >> shift) & 0xffu;
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       const uint32_t d0 = __shfl_sync(0xffffffffu, dig, vm ? __ffs(vm) - 1 : 0);
+      // lanes holding the same digit (invalid lanes match only each other)
       unsigned peers;
       if (__all_sync(0xffffffffu, !valid || dig == d0))
         peers = valid ? vm : ~vm;
       else
-        peers = match_digit(dig, valid);
+        peers = __match_any_sync(0xffffffffu, valid ? dig : 0x100u);
       uint32_t before = 0;
       if (valid) before = wcnt[w][dig];
       __syncwarp();
