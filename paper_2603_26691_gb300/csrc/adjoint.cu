@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
     }
     const double dd = d * d;
     const double ra = a.ca / dd;
-    const double E = exp(-ra * a.dt);
     const double E1 = -expm1(-ra * a.dt);
+    const double E = 1.0 - E1;  // e^{-a dt} as the complement of expm1, as in the forward step
     const double Q = E1 / ra;
     const double m = a.mcoef * dd * d;
     double wt[3], vn[3];
