@@ -745,22 +745,25 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         int Bl = (link && nall) ? 1 : 0;
 #pragma unroll
         for (int q = 0; q < 3; ++q) R[q] = link ? R[q] : 0.0f;
+        // the scan only matters where a run passes through a whole lane (often nowhere after drift)
+        if (__any_sync(0xffffffffu, Bl)) {
 #pragma unroll
-        for (int off = 1; off < kScanLanes; off <<= 1) {
-          float t0v = __shfl_down_sync(0xffffffffu, R[0], off);
-          float t1v = __shfl_down_sync(0xffffffffu, R[1], off);
-          float t2v = __shfl_down_sync(0xffffffffu, R[2], off);
-          int tb = __shfl_down_sync(0xffffffffu, Bl, off);
-          if (glane + off > kScanLanes - 1) {
-            tb = 0;
-            t0v = t1v = t2v = 0.0f;
+          for (int off = 1; off < kScanLanes; off <<= 1) {
+            float t0v = __shfl_down_sync(0xffffffffu, R[0], off);
+            float t1v = __shfl_down_sync(0xffffffffu, R[1], off);
+            float t2v = __shfl_down_sync(0xffffffffu, R[2], off);
+            int tb = __shfl_down_sync(0xffffffffu, Bl, off);
+            if (glane + off > kScanLanes - 1) {
+              tb = 0;
+              t0v = t1v = t2v = 0.0f;
+            }
+            if (Bl) {
+              R[0] += t0v;
+              R[1] += t1v;
+              R[2] += t2v;
+            }
+            Bl &= tb;
           }
-          if (Bl) {
-            R[0] += t0v;
-            R[1] += t1v;
-            R[2] += t2v;
-          }
-          Bl &= tb;
         }
         const int pk3 = __shfl_up_sync(0xffffffffu, key[3], 1);
         const bool head_lane = (glane == 0) || (pk3 != key[0]);
