@@ -44,7 +44,7 @@ MEASURED_TRAFFIC = {
     # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches of the plain instance (fresh to 3 steps of
     # drift), 64.07-64.15 B (FP32 velocity; the BF16-velocity instance measured 52.07-52.15 B before the
     # cloud-in-cell deposit joined the physics instance)
-    ("1883bbde2b0000b64dd18aaccbb3bc1a538891293108598ed93f5da5f6912c86", "fourier256_mixed_1e9"): 64.10,
+    ("2fc1c88f45bb45b2724b215a4285936b4a474300d83ab593db9287cb2007a271", "fourier256_mixed_1e9"): 64.10,
 }
 
 

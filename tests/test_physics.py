@@ -216,3 +216,17 @@ def test_set_physics_rejects_bad_arguments_and_the_adjoint_needs_defaults(Sim):
     sim.set_physics()
     assert lib.st_adjoint_forward(h, 4, 1e-3, 2) == _lib.ST_OK
     sim.close()
+
+
+@pytest.mark.parametrize("combo", [("trilinear", "exponential", "stokes", "cic"),
+                                   ("ngp", "semi_implicit", "schiller_naumann", "cic")], ids=["cic", "paper-cic"])
+def test_sorted_kernel_cic_far_from_the_sort_time_unit(Sim, combo):
+    # one sort, then 60 steps in a fast flow: many start cells leave their unit's deposit tile,
+    # so the cloud-in-cell corners go through the global accumulator as well as the tile
+    N, n, steps, dt = 32, 20_011, 60, 1e-3
+    c = dict(N=N, n=n)
+    U, pos, vel, d = _inputs(36, c)
+    U = U * 4.0  # particles follow the flow: several cells in 60 ms
+    o = _oracle(N, U, pos, vel, d, steps, dt, combo, band=2e-5)
+    g = _gpu(Sim, "mixed_f32", N, U, pos, vel, d, steps, dt, combo, reorder_every=1000)
+    _check(g, o, N, 1e-5, 1e-5, 1e-5, 1e-4)
