@@ -358,7 +358,7 @@ def run_adjoint(args, workload):
 
 def run_coupled(args, workload):
     """The asynchronous two-way coupling workload: K particle steps per coupling interval in a frozen
-    field while the fluid update (estimated source + Jacobi sweeps) runs on a second stream.  One JSON
+    field, each interval's fluid update (estimated source + Jacobi sweeps) ahead of its steps.  One JSON
     line: coupled particle-steps/s, beside the same particles' uncoupled step time."""
     import torch
 
@@ -400,7 +400,7 @@ def run_coupled(args, workload):
     ms = a.elapsed_time(b)
     sim.close()
     steps = K * timed
-    line = {"metric": "particle-steps/s, asynchronous two-way coupling (fluid update on a second stream)",
+    line = {"metric": "particle-steps/s, asynchronous two-way coupling (fluid update from lagged sources)",
             "value": n * steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warm * K,
             "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",

@@ -259,18 +259,20 @@ st_status st_couple_params(st_handle h, double rho_f, double nu, int sweeps, int
 
 /* Run nintervals coupling intervals of the asynchronous two-way coupling
  * (Sec. 2.3) on this GPU.  In interval n the particles take K steps of dt in
- * the frozen current field u^n (as st_step, on the handle's stream) while a
- * second stream computes the next field: u* = u^n + S_est^n / (rho_f V) per
- * cell, then the Jacobi sweeps of (I - nu K dt Lap) u = u* (7-point periodic
- * Laplacian, from u*).  S_est^n = S^{n-1} - S_ext^{n-1} + S_ext^n is the
+ * the frozen current field u^n (as st_step); the next field, computed from
+ * u^n and the sources of earlier intervals only, is u* = u^n + S_est^n /
+ * (rho_f V) per cell, then the Jacobi sweeps of (I - nu K dt Lap) u = u*
+ * (7-point periodic Laplacian, from u*).  Both run on the handle's stream,
+ * the fluid update ahead of the interval's steps: the lag of one interval
+ * (the asynchrony of Sec. 2.3) is in the data, not in the scheduling.  S_est^n = S^{n-1} - S_ext^{n-1} + S_ext^n is the
  * estimate of the interval's source from the sources of earlier intervals
  * (reading of Sec. 2.4: the corrector removes the previous extrapolated part,
  * which keeps the fluid's total intake equal to the particles' output up to
  * the last, pending, interval).  At the interval's end the particles' source
  * S^n leaves the accumulator (so st_get_sources reads only what later
  * st_step calls deposit) and the new field becomes current.  The first
- * interval after st_set_fluid has no source history.  Returns after the last
- * interval's fluid update has been queued; the particle work may still run.
+ * interval after st_set_fluid has no source history.  Returns once the last
+ * interval's fluid update has finished; its particle steps may still run.
  * Errors: INVALID_ARG (nintervals < 0, dt <= 0), NONFINITE, STATE (no
  * fluid), OOM, CUDA, TIMEOUT. */
 st_status st_couple_run(st_handle h, int nintervals, double dt);
@@ -344,7 +346,7 @@ st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int key_bits, uin
  * on, summed per kind.  ST_TIMER_STEP: every particle step kernel (st_step, the adjoint's forward
  * steps and recomputation); ST_TIMER_SORT: a whole reorder (all of its kernels);
  * ST_TIMER_ADJOINT: the adjoint step kernel of st_adjoint_backward; ST_TIMER_FLUID: the coupled
- * fluid update on the second stream (st_couple_run).  st_timers_enable(h, 1) clears and starts
+ * fluid update of st_couple_run.  st_timers_enable(h, 1) clears and starts
  * recording, 0 stops it.  st_timers_read synchronises, writes the summed milliseconds and the
  * number of timed launches per kind (arrays of ST_TIMER_COUNT), and clears them if `reset`.
  * Recording costs two events per timed launch.  Errors: INVALID_ARG, CUDA. */

@@ -1,13 +1,15 @@
 // Asynchronous two-way coupling on one GPU (Sec. 2.3) with the extrapolator-corrector estimate of
 // the Lagrangian source (Sec. 2.4, Eqs. 12-14).
 //
-// A coupling interval is K particle steps in a frozen fluid field u^n.  While the particles run
-// on the handle's stream, a second stream computes the next field
+// A coupling interval is K particle steps in a frozen fluid field u^n.  The next field
 //   u* = u^n + S_est^n / (rho_f V),   then `sweeps` Jacobi sweeps of (I - nu dtc Lap) u = u*
 // (7-point periodic Laplacian, dtc = K dt, starting from u*), where
 //   S_est^n = S^{n-1} - S_ext^{n-1} + S_ext^n
 // uses only the sources of earlier intervals (zero, constant or linear extrapolation of S^m from
-// S^{m-1}, S^{m-2}).  At the end of the interval the particles' source S^n moves from the exact
+// S^{m-1}, S^{m-2}), so it is computed before the interval's particle steps, in the same stream:
+// on one GPU the persistent step kernel needs whole SMs, and fluid kernels running beside it cost
+// it far more time than they take on their own.  At the end of the interval the particles' source
+// S^n moves from the exact
 // accumulator into a ring of the last four intervals' sources (FP64), the fields are swapped,
 // and the next interval begins.  Jacobi sweeps are averages with positive weights, so they keep
 // sum_c u_c (the fluid momentum) and never raise max |u|; max |u| of each new field is read back
@@ -161,8 +163,6 @@ st_status couple_resources(st_ctx* h) {
   }
   if (h->umax_dev.bytes < 8) ST_TRY(dev_alloc(h, h->umax_dev, 8));
   if (!h->umax_host) ST_CUDA(h, cudaMallocHost((void**)&h->umax_host, sizeof(double)));
-  if (!h->stream2) ST_CUDA(h, cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
-  if (!h->ev_main) ST_CUDA(h, cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming));
   if (!h->ev_fluid) ST_CUDA(h, cudaEventCreateWithFlags(&h->ev_fluid, cudaEventDisableTiming));
   return ST_OK;
 }
@@ -186,12 +186,12 @@ const double* hist_slot(const st_ctx* h, int64_t interval) {
   return interval >= 0 && interval < h->couple_done ? (const double*)h->src_hist[interval % 4].p : nullptr;
 }
 
-// fluid update of the current interval on stream2: fl_next = F(current, estimate)
+// fluid update of the current interval, on the handle's stream: fl_next = F(current, estimate)
 template <typename V, typename R>
 cudaError_t launch_fluid_update(st_ctx* h, const V* cur, double dt) {
   const Geometry& G = h->geo;
   const int64_t nc = G.ncell, m = 3 * nc;
-  cudaStream_t s = h->stream2;
+  cudaStream_t s = h->stream;
   const int64_t n = h->couple_done;
   ecm_kernel<<<cgrid(m), kCoupleThreads, 0, s>>>(h->extrap, hist_slot(h, n - 1), hist_slot(h, n - 2),
                                                  hist_slot(h, n - 3), (double*)h->src_est.p, m);
@@ -263,17 +263,14 @@ st_status st_couple_run(st_handle h, int nintervals, double dt) {
   ST_TRY(couple_resources(h));
   for (int it = 0; it < nintervals; ++it) {
     void* cur = current_field(h);
-    // the fluid update starts once everything queued so far (the previous interval's source in
-    // the ring, the previous swap) is done; it reads the current field, which the particles only
-    // read too
-    ST_CUDA(h, cudaEventRecord(h->ev_main, h->stream));
-    ST_CUDA(h, cudaStreamWaitEvent(h->stream2, h->ev_main, 0));
-    timer_begin(h, ST_TIMER_FLUID, h->stream2);
+    // the next field from the current one and the sources of earlier intervals (the previous
+    // interval's source is already in the ring); the particles then read the current field only
+    timer_begin(h, ST_TIMER_FLUID, h->stream);
     cudaError_t e = mixed(h) ? launch_fluid_update<float4, float>(h, (const float4*)cur, dt)
                              : launch_fluid_update<D4, double>(h, (const D4*)cur, dt);
-    timer_end(h, ST_TIMER_FLUID, h->stream2);
+    timer_end(h, ST_TIMER_FLUID, h->stream);
     ST_TRY(cuda_check(h, e, "fluid update"));
-    ST_CUDA(h, cudaEventRecord(h->ev_fluid, h->stream2));
+    ST_CUDA(h, cudaEventRecord(h->ev_fluid, h->stream));
     // the particles of this interval in the current field
     ST_TRY(run_steps(h, h->couple_K, dt));
     // their source moves into the ring and the accumulator starts empty
@@ -283,8 +280,8 @@ st_status st_couple_run(st_handle h, int nintervals, double dt) {
     ST_CUDA(h, reset_acc_counter(h));
     h->acc_empty = true;
     h->acc_load = 0.0;
-    // the next interval runs in the new field
-    ST_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_fluid, 0));
+    // the next interval runs in the new field (its max |u|, read back, sets the next exponent; the
+    // fluid update finished ahead of this interval's steps, so the wait does not drain the stream)
     ST_CUDA(h, cudaEventSynchronize(h->ev_fluid));
     h->umax = *h->umax_host;
     if (mixed(h)) {

@@ -162,16 +162,13 @@ void st_destroy(st_handle h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
-  if (h->stream2) cudaStreamSynchronize(h->stream2);
   Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt,
                  &h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start,
                  &h->acc, &h->red, &h->src_hist[0], &h->src_hist[1], &h->src_hist[2], &h->src_hist[3],
                  &h->src_est, &h->fl_cur, &h->fl_next, &h->fl_star, &h->fl_tmp, &h->fluid_pad_next, &h->umax_dev};
   for (Buf* b : bufs) dev_free(h, *b);
   if (h->umax_host) cudaFreeHost(h->umax_host);
-  if (h->ev_main) cudaEventDestroy(h->ev_main);
   if (h->ev_fluid) cudaEventDestroy(h->ev_fluid);
-  if (h->stream2) cudaStreamDestroy(h->stream2);
   for (int k = 0; k < ST_TIMER_COUNT; ++k)
     for (auto& pr : h->ev_pending[k]) {
       cudaEventDestroy(pr.first);

@@ -107,7 +107,7 @@ struct st_ctx {
   int adj_nsteps = 0, adj_every = 0;
   double adj_dt = 0.0;
   bool adj_ready = false;
-  // two-way coupling (st_couple_*): fluid master fields, source history, second stream
+  // two-way coupling (st_couple_*): fluid master fields, source history
   double rho_f = 1.2, nu = 1e-3;
   int sweeps = 10, couple_K = 5, extrap = 0;
   int64_t couple_done = 0;   // coupling intervals whose source is in the history ring
@@ -118,8 +118,7 @@ struct st_ctx {
   st::Buf fluid_pad_next;    // mixed: the padded field of the next interval
   st::Buf umax_dev;          // max |u| of the next field (bits of a non-negative double)
   double* umax_host = nullptr;  // pinned
-  cudaStream_t stream2 = nullptr;
-  cudaEvent_t ev_main = nullptr, ev_fluid = nullptr;
+  cudaEvent_t ev_fluid = nullptr;  // the interval's fluid update done (its max |u| in umax_host)
   int64_t launches = 0;      // kernels launched by this handle
   std::string err;
 };

@@ -1,5 +1,5 @@
-"""Asynchronous two-way coupling on the GPU (particles on one stream, the fluid update with the
-extrapolator-corrector estimate on a second) against the FP64 oracle's orc_couple, and the global
+"""Asynchronous two-way coupling on the GPU (the fluid update from lagged sources with the
+extrapolator-corrector estimate, between the particle intervals) against the FP64 oracle's orc_couple, and the global
 momentum budget (particles + fluid + pending sources - gravity impulse) at small and full size."""
 import numpy as np
 import pytest
@@ -96,7 +96,7 @@ def test_mixed_coupled_run_within_bounds(Sim, prec):
 
 def test_coupled_fourier256_2e9_momentum_budget(Sim):
     """The coupled workload: 256^3 FP32 Fourier field, 2e9 mixed-precision particles in 32^3-cell
-    chunks, fluid update every 5 steps on the second stream (nu = 1e-3, 10 Jacobi sweeps,
+    chunks, fluid update every 5 steps from lagged sources (nu = 1e-3, 10 Jacobi sweeps,
     rho_f = 1.2), 50 steps of 5e-4; the FP64 global momentum budget."""
     import torch
 
