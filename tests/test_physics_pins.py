@@ -228,3 +228,13 @@ def test_momentum_budget_of_every_physics_combination(gather, integrator, drag, 
     if deposit == "cell":
         # the containing-cell deposit only touches cells that held a particle at a step start
         assert np.count_nonzero(np.abs(src).sum(0)) <= min(N ** 3, 300 * steps)
+
+
+def test_schiller_naumann_drag_coefficient_at_stored_values():
+    import json
+    import os
+
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "pins.json")))["schiller_naumann_cd"]
+    G = oracle.make_grid(4, drag="schiller_naumann")
+    for re, cd in golden["re_and_cd"]:
+        assert abs(oracle.drag_factor(G, re) * 24.0 / re - cd) <= 1e-13 * cd, (re, cd)
