@@ -282,6 +282,16 @@ class Sim:
         self._chk(self.lib.st_get_sources(self.h, C.c_void_p(out.data_ptr()), int(reset), 1), "st_get_sources")
         return out
 
+    def source_density(self, elapsed: float, reset: bool = False, host: bool = False):
+        """The momentum source of Sec. 2.1, Eq. 11, as a rate density: the accumulated impulse per cell
+        divided by the cell volume and by the time it was accumulated over (`elapsed`, in s) [3, ncell]."""
+        if not elapsed > 0:
+            raise ValueError("elapsed must be > 0")
+        vol = 1.0
+        for b, g in zip(self.box, self.grid):
+            vol *= b / g
+        return self.sources(reset=reset, host=host) / (vol * elapsed)
+
     def particles(self, first: int = 0, count: int | None = None, host: bool = True):
         """(pos [3, count], vel [3, count], d [count], ids [count]) in storage order."""
         if count is None:

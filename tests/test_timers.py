@@ -36,3 +36,21 @@ def test_timers_count_and_time_the_launches():
     sim.step(1, 1e-3)
     assert sim.timers()["step"] == (0.0, 0)
     sim.close()
+
+
+def test_source_density_is_impulse_over_volume_and_time():
+    import torch
+
+    from paper_2603_26691_gb300.sim import Sim
+
+    N, steps, dt = (8, 6, 4), 5, 1e-3
+    sim = Sim(N, box=(1.0, 0.5, 2.0), precision="fp64")
+    sim.set_fluid(np.zeros((4, 6, 8, 3)))
+    pos, vel, d, _ = inputs.particles(9, 0, 2000, L=(1.0, 0.5, 2.0), vmax=1.0)
+    sim.add_particles(pos, d, vel)
+    sim.step(steps, dt)
+    J = sim.sources(host=True)
+    S = sim.source_density(steps * dt, host=True)
+    V = (1.0 / 8) * (0.5 / 6) * (2.0 / 4)
+    assert np.array_equal(S, J / (V * steps * dt))
+    sim.close()
