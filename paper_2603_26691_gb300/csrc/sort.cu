@@ -94,8 +94,34 @@ __global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int
        base += nthreads * kItems) {
     uint32_t k[kItems];
     const int m = (int)min((int64_t)kItems, n - base);
+    if constexpr (std::is_same<Src, CellKeys>::value || std::is_same<Src, ArrayKeys>::value) {
+      // a thread's 16 consecutive words as four 16-byte loads (the arrays are 256-byte aligned)
+      const uint32_t* w;
+      if constexpr (std::is_same<Src, CellKeys>::value)
+        w = reinterpret_cast<const uint32_t*>(src.cell);
+      else
+        w = src.k;
+      if (m == kItems) {
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) k[r] = r < m ? src(base + r) : 0u;
+        for (int r = 0; r < kItems; r += 4) {
+          const uint4 q = __ldg(reinterpret_cast<const uint4*>(w + base + r));
+          const uint32_t v4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if constexpr (std::is_same<Src, CellKeys>::value)
+              k[r + e] = src.of_cell((int32_t)v4[e]);
+            else
+              k[r + e] = v4[e];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < kItems; ++r) k[r] = r < m ? src(base + r) : 0u;
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kItems; ++r) k[r] = r < m ? src(base + r) : 0u;
+    }
     for (int p = 0; p < passes; ++p) {
       const int sh = 8 * p;
       uint32_t cur = (k[0] >> sh) & 0xffu, run = 1;

@@ -592,12 +592,12 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
               fac[e] = sn_factor(a.re_coef * sqrtf(fmaf(r0, r0, fmaf(r1, r1, r2 * r2))) * dv[jp + e]);
             }
             ADT = mul2(ADT, pack2(fac[0], fac[1]));
-            INV_A = mul2(INV_A, pack2(1.0f / fac[0], 1.0f / fac[1]));
+            INV_A = mul2(INV_A, pack2(rcp_approx(fac[0]), rcp_approx(fac[1])));
           }
           if (a.semi) {
             float x0, x1;
             unpack2(ADT, x0, x1);
-            const float e0 = 1.0f / (1.0f + x0), e1 = 1.0f / (1.0f + x1);
+            const float e0 = rcp_approx(1.0f + x0), e1 = rcp_approx(1.0f + x1);
             EE = pack2(e0, e1);
             E1 = pack2(x0 * e0, x1 * e1);  // 1 - E = a dt / (1 + a dt)
             Q = mul2(EE, dup2(a.dt));
