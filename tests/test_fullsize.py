@@ -138,3 +138,56 @@ def test_fourier256_mixed_1e9_sampled(torch_cuda):
     sub.close()
     assert np.linalg.norm(gsrc - osrc) <= 1e-5 * np.linalg.norm(osrc)
     assert np.abs(gsrc - osrc).max() <= 1e-4 * np.abs(osrc).max()
+
+
+@pytest.mark.parametrize("physics", [dict(gather="ngp", integrator="semi_implicit", drag="schiller_naumann"),
+                                     dict(deposit="cic")], ids=["paper", "cic"])
+def test_fourier256_mixed_1e9_physics_variants_sampled(torch_cuda, physics):
+    """The bench workload with a physics variant, as bench.py times it (the sorted-particle kernel's
+    physics instance): a seeded 3e4-particle subsample against the oracle step by step (particles
+    within the FP32 position bound of a cell face at a step start may take the other cell, which
+    the nearest-grid-point gather turns into a velocity jump, and are left out), the momentum
+    balance of the full run, and (cloud in cell) the subsample's own per-cell sources."""
+    from paper_2603_26691_gb300.sim import Sim
+
+    torch = torch_cuda
+    w = inputs.WORKLOADS["fourier256_mixed_1e9"]
+    U = w.make_field()
+    N = w.grid
+    sim = Sim(N, precision="mixed_f32", chunk_edge=w.chunk_edge)
+    sim.set_params(reorder_every=w.reorder_every)
+    sim.set_physics(**physics)
+    sim.set_fluid(U.astype(np.float32))
+    _populate(sim, w, w.n)
+    inv0 = sim.invariants()
+    sim.step(w.steps, w.dt)
+    inv1 = sim.invariants()
+    sample = np.sort(np.random.default_rng(3).choice(w.n, 30_000, replace=False))
+    gpos, gvel, gd, gcell = _sample_state(torch, sim, sample)
+    sim.close()
+    torch.cuda.empty_cache()
+    assert inv1[0] == w.n
+    assert _balance(inv0, inv1, w.steps, w.dt) <= 1e-5
+    pos, vel, d, _ = inputs.particles_at(w.seed, sample)
+    G = oracle.make_grid(N, **physics)
+    p, v = pos.copy(), vel.copy()
+    near = np.zeros(p.shape[1], dtype=bool)
+    osrc = np.zeros((3, N ** 3))
+    for _ in range(w.steps):
+        near |= face_distance(p, (N, N, N)) < 1e-4
+        p, v, osrc, _ = oracle.run(G, U, p, v, d, 1, w.dt, src=osrc)
+    keep = ~near if physics.get("gather") == "ngp" else np.ones(p.shape[1], dtype=bool)
+    assert keep.mean() > 0.97
+    h = 1.0 / N
+    assert np.abs(min_image(gpos, p))[:, keep].max() <= 1e-5 * h
+    assert (np.abs(gvel - v) / (np.abs(v) + 1.0))[:, keep].max() <= 1e-5
+    if physics.get("deposit") == "cic":
+        sub = Sim(N, precision="mixed_f32", chunk_edge=w.chunk_edge)
+        sub.set_params(reorder_every=w.reorder_every)
+        sub.set_physics(**physics)
+        sub.set_fluid(U.astype(np.float32))
+        sub.add_particles(pos, d, vel)
+        sub.step(w.steps, w.dt)
+        gsrc = sub.sources(host=True)
+        sub.close()
+        assert np.linalg.norm(gsrc - osrc) <= 1e-5 * np.linalg.norm(osrc)
