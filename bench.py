@@ -230,14 +230,13 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
 # step launch, from ncu instruction counters (2 x DFMA + DADD + DMUL, thread instructions) on the
 # adjoint workload; keyed by the SHA-256 of the kernel source, absent (null) once it changes
 MEASURED_FP64_OPS = {
-    # profiles/adjoint_tgf64_1e7.md: 242 DFMA + 60.8 DADD + 109 DMUL per particle (mean of two
-    # launches; the exponential's data-dependent paths move it by +-2.5 %); FP64 pipe 84.6 % busy
-    ("753a71b009a03e1f6367557b509f3a4d4bb70b522bc3ca323f507061a6318b23", "adjoint_step_kernel"): 653.8,
-    # step_f64_kernel: 99 DFMA + 63 DADD + 24 DMUL per particle (2e6 particles on 128^3)
-    ("eaa6773e675d1dfb6d5805e1a891649ba387295816019d70d67045187bef34ee", "step_f64_kernel"): 285.0,
+    # profiles/adjoint_tgf64_1e7.md: 131 DFMA + 49.8 DADD + 94 DMUL per particle; FP64 pipe 82 % busy
+    ("e2da8aed14ed9415f4c54e78bc7b93a9c26a332e8e776e737d51a4a475c444a6", "adjoint_step_kernel"): 405.8,
+    # step_f64_kernel: 56 DFMA + 59 DADD + 19 DMUL per particle (2e6 particles on 128^3)
+    ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 190.0,
 }
-MEASURED_FP64_PIPE = {("753a71b009a03e1f6367557b509f3a4d4bb70b522bc3ca323f507061a6318b23", "adjoint_step_kernel"): 0.846,
-                      ("eaa6773e675d1dfb6d5805e1a891649ba387295816019d70d67045187bef34ee", "step_f64_kernel"): 0.866}
+MEASURED_FP64_PIPE = {("e2da8aed14ed9415f4c54e78bc7b93a9c26a332e8e776e737d51a4a475c444a6", "adjoint_step_kernel"): 0.820,
+                      ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 0.858}
 F64_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc", "step_f64.cu")
 
 

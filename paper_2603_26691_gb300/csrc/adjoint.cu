@@ -66,6 +66,7 @@ struct AdjArgs {
   int nx, ny, nz;
   double inv_h[3];
   double dt, ca, mcoef, alpha, g[3];
+  double inv_ca, inv_alpha;  // 1 / ca, 1 / alpha
 };
 
 __device__ __forceinline__ D4 ld_cell(const D4* __restrict__ U, int64_t c) {
@@ -117,14 +118,18 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
       up[2] += W[k] * Uc[k].z;
     }
     const double dd = d * d;
-    const double ra = a.ca / dd;
+    // the reciprocals once (GB300 divides in FP64 by iteration): 1/a, 1/a^2, 1/d
+    const double inv_ra = dd * a.inv_ca;
+    const double ra = 1.0 / inv_ra;
+    const double inv_ra2 = inv_ra * inv_ra;
+    const double inv_d = 1.0 / d;
     const double E1 = -expm1(-ra * a.dt);
     const double E = 1.0 - E1;  // e^{-a dt} as the complement of expm1, as in the forward step
-    const double Q = E1 / ra;
+    const double Q = E1 * inv_ra;
     const double m = a.mcoef * dd * d;
     double wt[3], vn[3];
     for (int q = 0; q < 3; ++q) {
-      wt[q] = up[q] + a.g[q] / ra;
+      wt[q] = up[q] + a.g[q] * inv_ra;
       vn[q] = wt[q] + (v[q] - wt[q]) * E;
     }
     // reverse sweep
@@ -140,13 +145,13 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
       Eb += vnb * v[q];
       Qb += xb[q] * (v[q] - wt[q]);
       ub[q] = wtb;
-      ab -= wtb * a.g[q] / (ra * ra);
+      ab -= wtb * a.g[q] * inv_ra2;
     }
-    E1b += Qb / ra;
-    ab -= Qb * E1 / (ra * ra);
+    E1b += Qb * inv_ra;
+    ab -= Qb * E1 * inv_ra2;
     ab += a.dt * E * (E1b - Eb);
-    alphab_sum += ab * ra / a.alpha;
-    double dbv = a.db[p] + ab * (-2.0 * ra / d) + mb * 3.0 * m / d;
+    alphab_sum += ab * ra * a.inv_alpha;
+    double dbv = a.db[p] + ab * (-2.0 * ra * inv_d) + mb * 3.0 * m * inv_d;
     a.db[p] = dbv;
     // transposed trilinear weights: dL/dU and dL/df
     double fb[3] = {0.0, 0.0, 0.0};
@@ -225,6 +230,8 @@ cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s) {
   a.ca = 18.0 * h->mu * h->alpha / h->rho_p;
   a.mcoef = h->mult * h->rho_p * 3.14159265358979323846 / 6.0;
   a.alpha = h->alpha;
+  a.inv_ca = 1.0 / a.ca;
+  a.inv_alpha = 1.0 / h->alpha;
   adjoint_step_kernel<<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
   h->launches += 1;
   return cudaGetLastError();
