@@ -230,12 +230,12 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
 # step launch, from ncu instruction counters (2 x DFMA + DADD + DMUL, thread instructions) on the
 # adjoint workload; keyed by the SHA-256 of the kernel source, absent (null) once it changes
 MEASURED_FP64_OPS = {
-    # profiles/adjoint_tgf64_1e7.md: 131 DFMA + 49.8 DADD + 94 DMUL per particle; FP64 pipe 82 % busy
-    ("e2da8aed14ed9415f4c54e78bc7b93a9c26a332e8e776e737d51a4a475c444a6", "adjoint_step_kernel"): 405.8,
+    # profiles/adjoint_tgf64_1e7.md: 116 DFMA + 46.8 DADD + 70 DMUL per particle; FP64 pipe 78 % busy
+    ("3cf9bcbbbab3e1f18cdc5c827cfd66f845e5342e29054642856750d30484b6f0", "adjoint_step_kernel"): 348.8,
     # step_f64_kernel: 56 DFMA + 59 DADD + 19 DMUL per particle (2e6 particles on 128^3)
     ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 190.0,
 }
-MEASURED_FP64_PIPE = {("e2da8aed14ed9415f4c54e78bc7b93a9c26a332e8e776e737d51a4a475c444a6", "adjoint_step_kernel"): 0.820,
+MEASURED_FP64_PIPE = {("3cf9bcbbbab3e1f18cdc5c827cfd66f845e5342e29054642856750d30484b6f0", "adjoint_step_kernel"): 0.779,
                       ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 0.858}
 F64_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc", "step_f64.cu")
 

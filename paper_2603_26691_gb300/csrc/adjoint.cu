@@ -153,21 +153,30 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
     alphab_sum += ab * ra * a.inv_alpha;
     double dbv = a.db[p] + ab * (-2.0 * ra * inv_d) + mb * 3.0 * m * inv_d;
     a.db[p] = dbv;
-    // transposed trilinear weights: dL/dU and dL/df
-    double fb[3] = {0.0, 0.0, 0.0};
+    // transposed trilinear weights: dL/dU (each corner's weight times ub) and dL/df, the
+    // derivative of the trilinear form of the corner values' dot products with ub, taken
+    // separably (differences along one axis, interpolated along the other two)
+    double dot[8];
     for (int k = 0; k < 8; ++k) {
-      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
-      const double wx = di ? f[0] : 1.0 - f[0];
-      const double wy = dj ? f[1] : 1.0 - f[1];
-      const double wz = dk ? f[2] : 1.0 - f[2];
-      const double dot = Uc[k].x * ub[0] + Uc[k].y * ub[1] + Uc[k].z * ub[2];
-      fb[0] += (di ? 1.0 : -1.0) * wy * wz * dot;
-      fb[1] += wx * (dj ? 1.0 : -1.0) * wz * dot;
-      fb[2] += wx * wy * (dk ? 1.0 : -1.0) * dot;
+      dot[k] = Uc[k].x * ub[0] + Uc[k].y * ub[1] + Uc[k].z * ub[2];
       long long* w = a.Uw + corner[k] * 3 * kWideWords;
       wide_add(w, W[k] * ub[0]);
       wide_add(w + kWideWords, W[k] * ub[1]);
       wide_add(w + 2 * kWideWords, W[k] * ub[2]);
+    }
+    // corner k = di + 2 dj + 4 dk; lerp(p, q, t) = p + t (q - p)
+    auto lerp = [](double p0, double p1, double t) { return p0 + t * (p1 - p0); };
+    double fb[3];
+    {
+      // d/df_x: x-differences at the four (dj, dk) edges, interpolated in y then z
+      const double e00 = dot[1] - dot[0], e10 = dot[3] - dot[2], e01 = dot[5] - dot[4], e11 = dot[7] - dot[6];
+      fb[0] = lerp(lerp(e00, e10, f[1]), lerp(e01, e11, f[1]), f[2]);
+      // d/df_y: y-differences, interpolated in x then z
+      const double g00 = dot[2] - dot[0], g10 = dot[3] - dot[1], g01 = dot[6] - dot[4], g11 = dot[7] - dot[5];
+      fb[1] = lerp(lerp(g00, g10, f[0]), lerp(g01, g11, f[0]), f[2]);
+      // d/df_z: z-differences, interpolated in x then y
+      const double h00 = dot[4] - dot[0], h10 = dot[5] - dot[1], h01 = dot[6] - dot[2], h11 = dot[7] - dot[3];
+      fb[2] = lerp(lerp(h00, h10, f[0]), lerp(h01, h11, f[0]), f[1]);
     }
     for (int q = 0; q < 3; ++q) {
       a.xb[q][p] = xb[q] + fb[q] * a.inv_h[q];
