@@ -168,12 +168,13 @@ def deposit(G: Grid, x, J, src=None) -> np.ndarray:
     return src
 
 
-def run(G: Grid, U, pos, vel, d, nsteps: int, dt: float, src=None, trace=False, frozen=None):
+def run(G: Grid, U, pos, vel, d, nsteps: int, dt: float, src=None, trace=False, frozen=None, inplace=False):
     """Advance particles nsteps in the frozen field U.
 
     pos, vel: [3, n] float64 (copied); d: [n].  Returns (pos, vel, src, trace)
-    with src [3, ncell] (accumulated onto the given src if any) and trace
-    [nsteps, n] int64 deposit cells when requested.
+    with src [3, ncell] (accumulated onto the given src if any; with inplace=True
+    the given src, a C-contiguous float64 [3, ncell] array, is added to directly
+    instead of a copy) and trace [nsteps, n] int64 deposit cells when requested.
     """
     U = _f64(U)
     pos = _f64(pos).reshape(3, -1).copy()
@@ -181,7 +182,12 @@ def run(G: Grid, U, pos, vel, d, nsteps: int, dt: float, src=None, trace=False, 
     d = _f64(d).reshape(-1)
     n = d.shape[0]
     nc = ncell(G)
-    src = np.zeros((3, nc)) if src is None else _f64(src).reshape(3, nc).copy()
+    if inplace:
+        if not (isinstance(src, np.ndarray) and src.dtype == np.float64 and src.flags.c_contiguous
+                and src.size == 3 * nc):
+            raise ValueError("inplace needs a C-contiguous float64 src of 3 * ncell values")
+    else:
+        src = np.zeros((3, nc)) if src is None else _f64(src).reshape(3, nc).copy()
     tr = np.zeros((max(nsteps, 0), n), dtype=np.int64) if trace else None
     fr = None
     if frozen is not None:
