@@ -135,9 +135,10 @@ st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3],
  *     particle's trilinear stencil at the start of the step, with the
  *     trilinear weights (the transpose of the trilinear gather).
  * rho_f > 0 is the fluid density used in Re (only read by the
- * Schiller-Naumann drag).  The sorted-order fast step kernel implements the
- * defaults; other settings run the general step kernels.  The adjoint
- * (st_adjoint_*) needs the defaults.  Errors: INVALID_ARG, NONFINITE. */
+ * Schiller-Naumann drag).  Every combination runs on the sorted-particle
+ * step kernel of mixed handles (a separate instance of it; the defaults keep
+ * their own) and on the general kernels.  The adjoint (st_adjoint_*) needs
+ * the defaults.  Errors: INVALID_ARG, NONFINITE. */
 enum { ST_GATHER_TRILINEAR = 0, ST_GATHER_NGP = 1 };
 enum { ST_INTEGRATOR_EXPONENTIAL = 0, ST_INTEGRATOR_SEMI_IMPLICIT = 1 };
 enum { ST_DRAG_STOKES = 0, ST_DRAG_SCHILLER_NAUMANN = 1 };
@@ -169,8 +170,11 @@ st_status st_num_particles(st_handle h, int64_t* n);
 /* Advance all particles nsteps steps of length dt > 0 through the current
  * fluid field (the fixed sub-steps per Eulerian step of Sec. 3.3), adding
  * each step's impulses to the per-cell source accumulator.  Runs the
- * counting sort first when it is due.  Asynchronous on the stream.
- * Errors: INVALID_ARG, STATE (no fluid set), OVERFLOW, CUDA. */
+ * counting sort first when it is due.  On mixed handles the step just before
+ * a due sort writes the new state as 32-byte particle records for that
+ * sort's gather; any other call that reads or changes the particles turns
+ * them back first, so this is not visible through the ABI.  Asynchronous on
+ * the stream.  Errors: INVALID_ARG, STATE (no fluid set), OVERFLOW, CUDA. */
 st_status st_step(st_handle h, int nsteps, double dt);
 
 /* Read the accumulated per-cell source: out[3][ncell] in FP64, the raw
