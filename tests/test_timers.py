@@ -54,3 +54,22 @@ def test_source_density_is_impulse_over_volume_and_time():
     V = (1.0 / 8) * (0.5 / 6) * (2.0 / 4)
     assert np.array_equal(S, J / (V * steps * dt))
     sim.close()
+
+
+def test_timers_count_the_coupled_fluid_updates():
+    from paper_2603_26691_gb300.sim import Sim
+
+    N = 16
+    sim = Sim(N, precision="mixed_f32")
+    sim.set_params(reorder_every=4)
+    sim.set_fluid(inputs.taylor_green(N).astype(np.float32))
+    pos, vel, d, _ = inputs.particles(4, 0, 20_000)
+    sim.add_particles(pos, d, vel)
+    sim.couple_params(steps_per_interval=3)
+    sim.timers(True)
+    sim.couple_run(5, 1e-3)
+    t = sim.timers()
+    assert t["fluid"][1] == 5 and t["fluid"][0] > 0.0
+    assert t["step"][1] == 15
+    assert t["sort"][1] == 4  # before steps 0, 4, 8, 12 of the handle's count
+    sim.close()
