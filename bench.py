@@ -241,17 +241,26 @@ MEASURED_FP64_PIPE = {("3cf9bcbbbab3e1f18cdc5c827cfd66f845e5342e29054642856750d3
 F64_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc", "step_f64.cu")
 
 
-def fp64_step_roofline(n, ms):
-    """The FP64 step kernel against GB300's FP64 rate (its operation count from ncu, by source)."""
+def fp64_peak(sim):
+    """This GPU's FP64 FMA rate, measured by the library's FMA-chain probe (else the nominal figure)."""
+    try:
+        return sim.probe_fma()[0], "measured (FP64 FMA-chain probe, st_probe_fma)"
+    except Exception:  # noqa: BLE001 - an older library without the probe
+        return FP64_NOMINAL_GFLOPS, "nominal GB300 dense FP64"
+
+
+def fp64_step_roofline(n, ms, peak=None, peak_kind=None):
+    """The FP64 step kernel against the FP64 rate (its operation count from ncu, by source)."""
     import hashlib
 
     with open(F64_SOURCE, "rb") as f:
         key = (hashlib.sha256(f.read()).hexdigest(), "step_f64_kernel")
     ops = MEASURED_FP64_OPS.get(key)
     ach = ops * n / (ms * 1e-3) / 1e9 if ops else None
+    peak = peak or FP64_NOMINAL_GFLOPS
     return {"bound": "alu", "unit": "GFLOP/s (FP64)", "fp64_ops_per_particle": ops, "achieved": ach,
-            "peak": FP64_NOMINAL_GFLOPS, "peak_kind": "nominal GB300 dense FP64",
-            "frac": ach / FP64_NOMINAL_GFLOPS if ach else None, "fp64_pipe_busy_ncu": MEASURED_FP64_PIPE.get(key)}
+            "peak": peak, "peak_kind": peak_kind or "nominal GB300 dense FP64",
+            "frac": ach / peak if ach else None, "fp64_pipe_busy_ncu": MEASURED_FP64_PIPE.get(key)}
 ADJOINT_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
                               "adjoint.cu")
 FP64_NOMINAL_GFLOPS = 1250.0  # GB300 dense FP64, the nominal figure (no measured FP64 peak on this pool)
@@ -310,9 +319,10 @@ def run_adjoint(args, workload):
     ops = MEASURED_FP64_OPS.get((src_hash, "adjoint_step_kernel"))
     adj_avg = adj_ms / max(adj_n, 1)
     achieved = ops * n / (adj_avg * 1e-3) / 1e9 if ops else None
-    roofline = {"bound": "alu", "kernel": "adjoint_step_kernel", "unit": "GFLOP/s (FP64)", "peak": FP64_NOMINAL_GFLOPS,
-                "peak_kind": "nominal GB300 dense FP64 (no measured FP64 peak)", "achieved": achieved,
-                "frac": achieved / FP64_NOMINAL_GFLOPS if achieved else None, "traffic": None,
+    p64, p64_kind = fp64_peak(sim)
+    roofline = {"bound": "alu", "kernel": "adjoint_step_kernel", "unit": "GFLOP/s (FP64)", "peak": p64,
+                "peak_kind": p64_kind, "achieved": achieved,
+                "frac": achieved / p64 if achieved else None, "traffic": None,
                 "fp64_ops_per_particle": ops, "launches": adj_n, "ms_per_launch": adj_avg,
                 "fp64_pipe_busy_ncu": MEASURED_FP64_PIPE.get((src_hash, "adjoint_step_kernel")),
                 "step_f64_kernel": {"launches": stp_n, "ms_per_launch": stp_ms / max(stp_n, 1)}}
@@ -539,7 +549,7 @@ def main():
                                  if rec_ms else None}}
 
     if precision == "fp64":  # the FP64 step is bound by FP64 arithmetic, not by HBM
-        roofline = dict(fp64_step_roofline(n, step_avg), kernel="step_f64_kernel", launches=len(step_ms),
+        roofline = dict(fp64_step_roofline(n, step_avg, *fp64_peak(sim)), kernel="step_f64_kernel", launches=len(step_ms),
                         step_kernel_ms=step_avg, hbm_frac_of_algorithmic=achieved / peak)
 
     # per-chunk bounding boxes of the sorted state (on demand: one read of cells and offsets)
@@ -605,11 +615,12 @@ def main():
         ev64 = timed_steps(s64, args.fp64_steps, dt, 0, 1)
         torch.cuda.synchronize()
         ms64 = sum(e1.elapsed_time(e2) for (e0, e1, e2, _) in ev64) / len(ev64)
+        p64, p64_kind = fp64_peak(s64)
         rate64 = fp64_n / (ms64 * 1e-3)
         fp64 = {"particles": fp64_n, "step_kernel_ms": ms64, "particle_steps_per_s": rate64,
                 "mixed_step_kernel_particle_steps_per_s": n / (step_avg * 1e-3),
                 "speedup_mixed_over_fp64_step_kernel": (n / (step_avg * 1e-3)) / rate64,
-                "bound": "alu (FP64)", "roofline": fp64_step_roofline(fp64_n, ms64)}
+                "bound": "alu (FP64)", "roofline": fp64_step_roofline(fp64_n, ms64, p64, p64_kind)}
         s64.close()
         del s64
         torch.cuda.empty_cache()

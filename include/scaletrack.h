@@ -358,6 +358,12 @@ enum { ST_TIMER_STEP = 0, ST_TIMER_SORT = 1, ST_TIMER_ADJOINT = 2, ST_TIMER_FLUI
 st_status st_timers_enable(st_handle h, int on);
 st_status st_timers_read(st_handle h, double* ms, int64_t* launches, int reset);
 
+/* The FP64 and FP32 fused multiply-add rates of this GPU, in GFLOP/s (2 flops per FMA),
+ * measured by short kernels of independent FMA chains with no memory traffic (about 0.1 s):
+ * the peak that the FP64 step and the adjoint, which are bound by FP64 arithmetic, are
+ * reported against.  Synchronises.  Errors: INVALID_ARG, OOM, CUDA. */
+st_status st_probe_fma(st_handle h, double* fp64_gflops, double* fp32_gflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,7 @@ SIGNATURES = {
     "st_set_params": (_i, [_vp, _d, _d, _P(_d), _d, _d, _i]),
     "st_set_physics": (_i, [_vp, _i, _i, _i, _i, _d]),
     "st_timers_enable": (_i, [_vp, _i]),
+    "st_probe_fma": (_i, [_vp, _P(_d), _P(_d)]),
     "st_timers_read": (_i, [_vp, _P(_d), _P(_i64), _i]),
     "st_set_fluid": (_i, [_vp, _vp, _i, _i]),
     "st_reserve": (_i, [_vp, _i64]),

@@ -912,6 +912,12 @@ st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device,
   return ST_OK;
 }
 
+st_status st_probe_fma(st_handle h, double* fp64_gflops, double* fp32_gflops) {
+  ST_TRY(check_handle(h));
+  if (!fp64_gflops || !fp32_gflops) return set_error(h, ST_ERR_INVALID_ARG, "output pointers are required");
+  return cuda_check(h, probe_fma_rates(h, fp64_gflops, fp32_gflops), "fma probe");
+}
+
 st_status st_kernel_launches(st_handle h, int64_t* count) {
   ST_TRY(check_handle(h));
   if (!count) return set_error(h, ST_ERR_INVALID_ARG, "count is NULL");

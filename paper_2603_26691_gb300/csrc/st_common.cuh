@@ -391,6 +391,8 @@ cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, c
 st_status sort_particles(st_ctx* h);                                       // sort.cu
 // the structure of arrays current again if the last step left records for a sort (no-op otherwise)
 st_status materialize_state(st_ctx* h);                                    // sort.cu
+// FP64 and FP32 FMA rates of this GPU (GFLOP/s), measured by FMA-chain kernels; synchronises
+cudaError_t probe_fma_rates(st_ctx* h, double* fp64_gflops, double* fp32_gflops);  // util.cu
 // timer marks around a launch of kind k on stream s (no-ops unless st_timers_enable is on); the
 // end mark pairs with the last begin of the same kind
 void timer_begin(st_ctx* h, int k, cudaStream_t s);                        // st_api.cu

@@ -579,4 +579,70 @@ cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, c
   return cudaGetLastError();
 }
 
+// Arithmetic-rate probes: eight (FP64) or sixteen (FP32) independent FMA chains per thread, no
+// memory traffic in the loop; the result is stored only if it equals an impossible value.
+__global__ void fma64_probe_kernel(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-9 + k * 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += x[k];
+  if (t == 12345.0) out[0] = t;
+}
+__global__ void fma32_probe_kernel(float* out, int iters, float a, float b) {
+  float x[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = threadIdx.x * 1e-6f + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = fmaf(x[k], a, b);
+  }
+  float t = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t += x[k];
+  if (t == 12345.0f) out[0] = t;
+}
+
+cudaError_t probe_fma_rates(st_ctx* h, double* fp64_gflops, double* fp32_gflops) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
+  if (sms <= 0) sms = 152;
+  const int blocks = sms * 8, threads = 256;
+  Buf tmp;
+  if (dev_alloc(h, tmp, 16) != ST_OK) return cudaErrorMemoryAllocation;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float ms = 0.0f;
+  const int it64 = 4000, it32 = 20000;
+  if (e == cudaSuccess) {
+    fma64_probe_kernel<<<blocks, threads, 0, h->stream>>>((double*)tmp.p, 50, 0.999999, 1e-7);  // warm-up
+    cudaEventRecord(e0, h->stream);
+    fma64_probe_kernel<<<blocks, threads, 0, h->stream>>>((double*)tmp.p, it64, 0.999999, 1e-7);
+    cudaEventRecord(e1, h->stream);
+    e = cudaEventSynchronize(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) *fp64_gflops = 2.0 * 8 * (double)it64 * blocks * threads / (ms * 1e-3) / 1e9;
+  if (e == cudaSuccess) {
+    fma32_probe_kernel<<<blocks, threads, 0, h->stream>>>((float*)tmp.p, 50, 0.999999f, 1e-7f);
+    cudaEventRecord(e0, h->stream);
+    fma32_probe_kernel<<<blocks, threads, 0, h->stream>>>((float*)tmp.p, it32, 0.999999f, 1e-7f);
+    cudaEventRecord(e1, h->stream);
+    e = cudaEventSynchronize(e1);
+  }
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e == cudaSuccess) *fp32_gflops = 2.0 * 16 * (double)it32 * blocks * threads / (ms * 1e-3) / 1e9;
+  h->launches += 4;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dev_free(h, tmp);
+  return e;
+}
+
 }  // namespace st

@@ -130,6 +130,12 @@ class Sim:
                                           self.DRAGS[drag], self.DEPOSITS[deposit], float(rho_f)),
                   "st_set_physics")
 
+    def probe_fma(self):
+        """(FP64, FP32) fused multiply-add rates of this GPU in GFLOP/s."""
+        a, b = C.c_double(), C.c_double()
+        self._chk(self.lib.st_probe_fma(self.h, C.byref(a), C.byref(b)), "st_probe_fma")
+        return a.value, b.value
+
     TIMERS = ("step", "sort", "adjoint", "fluid")
 
     def timers(self, on=None, reset=False):

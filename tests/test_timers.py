@@ -73,3 +73,13 @@ def test_timers_count_the_coupled_fluid_updates():
     assert t["step"][1] == 15
     assert t["sort"][1] == 4  # before steps 0, 4, 8, 12 of the handle's count
     sim.close()
+
+
+def test_fma_probe_rates_are_plausible():
+    from paper_2603_26691_gb300.sim import Sim
+
+    sim = Sim(8, precision="fp64")
+    f64, f32 = sim.probe_fma()
+    sim.close()
+    # GB300: dense FP64 about 1.25 TFLOP/s, FP32 FMA tens of TFLOP/s; the ratio is what matters here
+    assert 100.0 < f64 < 1e5 and f32 > 10.0 * f64, (f64, f32)
