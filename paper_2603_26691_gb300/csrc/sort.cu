@@ -32,6 +32,7 @@ constexpr int kRadix = 256;
 constexpr int kMaxPasses = 4;
 constexpr uint32_t kLookSpinLimit = 1u << 22;
 constexpr uint64_t kLookWaitNs = 1000000000ull;  // 1 s
+constexpr int kLookWindow = 4;  // look-back words read per round trip
 
 // look-back word: epoch (30 bits) | kind (2 bits: 1 = the tile's own count, 2 = inclusive
 // prefix) | count (32 bits).  A word whose epoch is not the pass's is empty.
@@ -51,6 +52,15 @@ struct CellKeys {  // mixed precision: the packed cell of each slot
     return chunk_key(cell_i(c), cell_j(c), cell_k(c), g.B, g.logB, g.ncx, g.ncy);
   }
   __device__ __forceinline__ uint32_t operator()(int64_t i) const { return of_cell(cell[i]); }
+  // the same key with the Morton spread of the local coordinates read from a 32-entry table
+  // (tab[v] = spread3(v)): three table reads instead of the shift-and-mask sequences
+  __device__ __forceinline__ uint32_t of_cell_tab(int32_t c, const uint32_t* tab) const {
+    const uint32_t i = (uint32_t)cell_i(c), j = (uint32_t)cell_j(c), k = (uint32_t)cell_k(c);
+    const uint32_t m = (uint32_t)g.B - 1u;
+    const uint32_t chunk = (i >> g.logB) + (uint32_t)g.ncx * ((j >> g.logB) + (uint32_t)g.ncy * (k >> g.logB));
+    const uint32_t morton = tab[(i & m) & 31u] | (tab[(j & m) & 31u] << 1) | (tab[(k & m) & 31u] << 2);
+    return (chunk << (3 * g.logB)) | morton;
+  }
 };
 struct PositionKeys {  // FP64: the cell of each position
   F64State s;
@@ -169,10 +179,11 @@ __global__ void digit_offsets_kernel(const uint32_t* __restrict__ totals, int pa
 
 // shared memory of a pass: two staging buffers (each a key-or-cell array and a value array of a
 // tile: the next tile lands in one while the current tile is ranked and written out through the
-// other), per-warp digit counts, digit starts, two mbarriers and the tile numbers
+// other), per-warp digit counts, digit starts, two mbarriers, the tile numbers and the Morton
+// spread table of the first pass
 constexpr int kBufWords = 2 * kTile;
 constexpr int kPassBlocksPerSM = 3;  // 3 x 75.8 KB of shared memory, 80 registers
-constexpr size_t kPassSmem = 2 * kBufWords * 4 + kSortWarps * kRadix * 4 + 2 * kRadix * 4 + 2 * 8 + 2 * 8;
+constexpr size_t kPassSmem = 2 * kBufWords * 4 + kSortWarps * kRadix * 4 + 2 * kRadix * 4 + 2 * 8 + 2 * 8 + 32 * 4;
 
 // one stable counting-sort pass over 8-bit digit `shift / 8`, tiles taken in order.  BULK: the
 // tile's input (the cell array in the first pass, else the keys and values) arrives by 1-D bulk
@@ -193,6 +204,8 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
   uint32_t* gbase = lstart + kRadix;
   uint64_t* bar = reinterpret_cast<uint64_t*>(gbase + kRadix);
   int64_t* s_next = reinterpret_cast<int64_t*>(bar + 2);
+  uint32_t* mtab = reinterpret_cast<uint32_t*>(s_next + 2);  // Morton spread table (first pass)
+  if (FIRST && threadIdx.x < 32) mtab[threadIdx.x] = spread3(threadIdx.x);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const unsigned long long ep = epoch << 34;
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
       const int64_t i = start + r * 32 + lane;
       const int li = w * (kItems * 32) + r * 32 + lane;
       if constexpr (BULK && FIRST) {
-        key[r] = i < n ? src.of_cell((int32_t)kbuf[li]) : 0u;
+        key[r] = i < n ? src.of_cell_tab((int32_t)kbuf[li], mtab) : 0u;
         val[r] = (uint32_t)i;
       } else if constexpr (BULK) {
         key[r] = kbuf[li];
@@ -283,7 +296,7 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
       rank[r] = valid ? before + __popc(peers & lt) : 0xffffffffu;
     }
     __syncthreads();
-    // ---- per digit: offsets of the warps inside the tile, the tile's count ----
+    // ---- per digit: offsets of the warps inside the tile, the tile's count (published) ----
     const int d = threadIdx.x;
     uint32_t tot = 0;
     for (int ww = 0; ww < kSortWarps; ++ww) {
@@ -293,31 +306,6 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
     }
     unsigned long long* my = look + tile * kRadix + d;
     store_look(my, ep | ((tile == 0 ? kLookPrefix : kLookAgg) << 32) | tot);
-    // ---- look back: the sum of this digit's counts over all earlier tiles ----
-    uint32_t excl = 0;
-    if (tile > 0) {
-      int64_t t = tile - 1;
-      uint64_t t0 = 0;
-      uint32_t polls = 0;
-      for (;;) {
-        const unsigned long long v = load_look(look + t * kRadix + d);
-        const unsigned long long kind = (v >> 32) & 3ull;
-        if ((v >> 34) == epoch && kind != 0) {
-          excl += (uint32_t)v;
-          if (kind == kLookPrefix || t == 0) break;
-          --t;
-          polls = 0;
-          continue;
-        }
-        if (polls == 0) t0 = sort_ns();
-        if (++polls >= kLookSpinLimit || ((polls & 31u) == 0 && sort_ns() - t0 > kLookWaitNs)) {
-          atomicOr(err, 64);  // gave up: the output is wrong, the host reports a timeout
-          break;
-        }
-      }
-      store_look(my, ep | (kLookPrefix << 32) | (excl + tot));
-    }
-    gbase[d] = digit_offset[d] + excl;
     // ---- tile-local start of each digit (exclusive scan of the tile's counts) ----
     lstart[d] = tot;
     __syncthreads();
@@ -342,7 +330,7 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
       }
     }
     __syncthreads();
-    // ---- the tile in digit order in shared memory, then out run by run ----
+    // ---- the tile in digit order in shared memory (needs only the tile's own counts) ----
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       if (rank[r] != 0xffffffffu) {
@@ -352,6 +340,47 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
         vbuf[lp] = val[r];
       }
     }
+    // ---- look back: the sum of this digit's counts over all earlier tiles.  The words of the
+    // kLookWindow tiles before the first unread one are loaded together (one round trip) and
+    // summed in order until a tile's inclusive prefix; a word not yet published ends the round
+    // and the next round starts at it.
+    uint32_t excl = 0;
+    if (tile > 0) {
+      int64_t t = tile - 1;
+      uint64_t t0 = 0;
+      uint32_t polls = 0;
+      for (;;) {
+        unsigned long long v[kLookWindow];
+#pragma unroll
+        for (int k = 0; k < kLookWindow; ++k) v[k] = t - k >= 0 ? load_look(look + (t - k) * kRadix + d) : 0ull;
+        int k = 0;
+        bool done = false;
+#pragma unroll
+        for (int q = 0; q < kLookWindow; ++q) {
+          if (k == q && !done && t - q >= 0) {
+            const unsigned long long kind = (v[q] >> 32) & 3ull;
+            if ((v[q] >> 34) == epoch && kind != 0) {
+              excl += (uint32_t)v[q];
+              ++k;
+              done = kind == kLookPrefix || t - q == 0;
+            }
+          }
+        }
+        if (done) break;
+        if (k > 0) {
+          t -= k;
+          polls = 0;
+          continue;
+        }
+        if (polls == 0) t0 = sort_ns();
+        if (++polls >= kLookSpinLimit || ((polls & 31u) == 0 && sort_ns() - t0 > kLookWaitNs)) {
+          atomicOr(err, 64);  // gave up: the output is wrong, the host reports a timeout
+          break;
+        }
+      }
+      store_look(my, ep | (kLookPrefix << 32) | (excl + tot));
+    }
+    gbase[d] = digit_offset[d] + excl;
     __syncthreads();
     const int cnt = (int)min((int64_t)kTile, n - tile * kTile);
     for (int lp = threadIdx.x; lp < cnt; lp += kSortThreads) {
@@ -527,11 +556,33 @@ __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32
 // start[k] = first sorted position with key >= k, for k in [0, nkeys]: position i writes the keys
 // in (key[i-1], key[i]] (one pass over the sorted keys; the keys after the last one are filled by
 // cell_start_tail_kernel)
+// start[k] = the first sorted position whose key is >= k, for every k up to the last key: each
+// thread takes four consecutive sorted keys (one 16-byte load; the key arrays are 256-byte
+// aligned) and the key before them
 __global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ start) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k1 = keys[i];
-    const int64_t k0 = i > 0 ? (int64_t)keys[i - 1] : -1;
-    for (int64_t k = k0 + 1; k <= k1; ++k) start[k] = (uint32_t)i;
+  const int64_t groups = (n + 3) >> 2;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = g << 2;
+    uint32_t k4[4];
+    if (i0 + 4 <= n) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(keys) + g);
+      k4[0] = q.x;
+      k4[1] = q.y;
+      k4[2] = q.z;
+      k4[3] = q.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) k4[e] = i0 + e < n ? keys[i0 + e] : 0u;
+    }
+    int64_t prev = i0 > 0 ? (int64_t)__ldg(keys + i0 - 1) : -1;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (i0 + e < n) {
+        const int64_t k1 = k4[e];
+        for (int64_t k = prev + 1; k <= k1; ++k) start[k] = (uint32_t)(i0 + e);
+        prev = k1;
+      }
+    }
   }
 }
 
@@ -812,7 +863,7 @@ st_status sort_particles(st_ctx* h) {
         carve_mixed(h->state.p, h->cap, true), carve_mixed(h->state_alt.p, h->cap, true), (const uint32_t*)h->ids.p,
         (uint32_t*)h->ids_alt.p, v0, n);
   }
-  cell_start_kernel<<<grid_for(n), 256, 0, h->stream>>>(k0, n, (uint32_t*)h->cell_start.p);
+  cell_start_kernel<<<grid_for((n + 3) / 4), 256, 0, h->stream>>>(k0, n, (uint32_t*)h->cell_start.p);
   cell_start_tail_kernel<<<grid_for((int64_t)h->nkeys + 1), 256, 0, h->stream>>>(k0, n, h->nkeys,
                                                                                    (uint32_t*)h->cell_start.p);
   h->launches += 3;  // gather + cell starts (two kernels)
