@@ -77,6 +77,13 @@ struct ArrayKeys {  // keys given by the caller
   __device__ __forceinline__ uint32_t operator()(int64_t i) const { return k[i]; }
 };
 
+// the digit of pass p: bits [8p, 8p + 8) of the key, cut at key_bits (keys are compared on their
+// low key_bits bits only)
+__host__ __device__ __forceinline__ uint32_t digit_mask(int key_bits, int p) {
+  const int b = key_bits - 8 * p;
+  return b >= 8 ? 0xffu : (b <= 0 ? 0u : (1u << b) - 1u);
+}
+
 __device__ __forceinline__ uint64_t sort_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -94,8 +101,9 @@ __device__ __forceinline__ unsigned long long load_look(const unsigned long long
 // every pass's digit totals in one read of the keys: each lane counts runs of equal digits over
 // 16 consecutive keys and adds each run once to the block's counts
 template <class Src>
-__global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int64_t n, int passes,
+__global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int64_t n, int key_bits,
                                                                      uint32_t* __restrict__ totals) {
+  const int passes = (key_bits + 7) / 8;
   __shared__ uint32_t cnt[kMaxPasses][kRadix];
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&cnt[0][0])[i] = 0;
   __syncthreads();
@@ -134,11 +142,12 @@ __global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int
     }
     for (int p = 0; p < passes; ++p) {
       const int sh = 8 * p;
-      uint32_t cur = (k[0] >> sh) & 0xffu, run = 1;
+      const uint32_t dm = digit_mask(key_bits, p);
+      uint32_t cur = (k[0] >> sh) & dm, run = 1;
 #pragma unroll
       for (int r = 1; r < kItems; ++r) {
         if (r >= m) break;
-        const uint32_t d = (k[r] >> sh) & 0xffu;
+        const uint32_t d = (k[r] >> sh) & dm;
         if (d == cur) {
           ++run;
         } else {
@@ -185,14 +194,14 @@ constexpr int kBufWords = 2 * kTile;
 constexpr int kPassBlocksPerSM = 3;  // 3 x 75.8 KB of shared memory, 80 registers
 constexpr size_t kPassSmem = 2 * kBufWords * 4 + kSortWarps * kRadix * 4 + 2 * kRadix * 4 + 2 * 8 + 2 * 8 + 32 * 4;
 
-// one stable counting-sort pass over 8-bit digit `shift / 8`, tiles taken in order.  BULK: the
-// tile's input (the cell array in the first pass, else the keys and values) arrives by 1-D bulk
-// copies issued one tile ahead; otherwise it is read with plain loads.
+// one stable counting-sort pass over digit `shift / 8` (8 bits, fewer in the last pass: dmask), tiles
+// taken in order.  BULK: the tile's input (the cell array in the first pass, else the keys and values)
+// arrives by 1-D bulk copies issued one tile ahead; otherwise it is read with plain loads.
 template <bool FIRST, bool BULK, class Src>
 __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kernel(Src src, const uint32_t* __restrict__ kin,
                                                                  const uint32_t* __restrict__ vin,
                                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                                 int64_t n, int shift, int64_t ntiles,
+                                                                 int64_t n, int shift, uint32_t dmask, int64_t ntiles,
                                                                  const uint32_t* __restrict__ digit_offset,
                                                                  unsigned long long* __restrict__ look,
                                                                  unsigned long long epoch, unsigned* __restrict__ tile_ctr,
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       const bool valid = start + r * 32 + lane < n;
-      const uint32_t dig = (key[r] >> shift) & 0xffu;
+      const uint32_t dig = (key[r] >> shift) & dmask;
       const unsigned vm = __ballot_sync(0xffffffffu, valid);
       const uint32_t d0 = __shfl_sync(0xffffffffu, dig, vm ? __ffs(vm) - 1 : 0);
       // lanes holding the same digit (invalid lanes match only each other)
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
       if (rank[r] != 0xffffffffu) {
-        const uint32_t dig = (key[r] >> shift) & 0xffu;
+        const uint32_t dig = (key[r] >> shift) & dmask;
         const uint32_t lp = lstart[dig] + wcnt[w][dig] + rank[r];
         kbuf[lp] = key[r];
         vbuf[lp] = val[r];
@@ -385,7 +394,7 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
     const int cnt = (int)min((int64_t)kTile, n - tile * kTile);
     for (int lp = threadIdx.x; lp < cnt; lp += kSortThreads) {
       const uint32_t k = kbuf[lp];
-      const uint32_t dig = (k >> shift) & 0xffu;
+      const uint32_t dig = (k >> shift) & dmask;
       const uint32_t dst = gbase[dig] + (uint32_t)lp - lstart[dig];
       kout[dst] = k;
       vout[dst] = vbuf[lp];
@@ -724,7 +733,7 @@ int grid_for(int64_t n, int max_blocks = 152 * 16) {
 
 template <bool FIRST, bool BULK, class Src>
 cudaError_t launch_pass(int64_t grid, cudaStream_t s, Src src, const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
-                        uint32_t* vout, int64_t n, int shift, int64_t ntiles, const uint32_t* offs,
+                        uint32_t* vout, int64_t n, int shift, uint32_t dmask, int64_t ntiles, const uint32_t* offs,
                         unsigned long long* look, uint32_t epoch, unsigned* tile_ctr, int* err) {
   static bool attr = false;  // one per instantiation
   if (!attr) {
@@ -734,7 +743,7 @@ cudaError_t launch_pass(int64_t grid, cudaStream_t s, Src src, const uint32_t* k
     attr = true;
   }
   onesweep_kernel<FIRST, BULK, Src><<<(unsigned)grid, kSortThreads, kPassSmem, s>>>(
-      src, kin, vin, kout, vout, n, shift, ntiles, offs, look, epoch, tile_ctr, err);
+      src, kin, vin, kout, vout, n, shift, dmask, ntiles, offs, look, epoch, tile_ctr, err);
   return cudaGetLastError();
 }
 
@@ -752,7 +761,7 @@ cudaError_t radix_passes(Src src, int64_t n, int key_bits, uint32_t* ka, uint32_
   cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)kMaxPasses * kRadix * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, kMaxPasses * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  digit_totals_kernel<Src><<<grid_for((n + kItems - 1) / kItems), kSortThreads, 0, s>>>(src, n, passes, totals);
+  digit_totals_kernel<Src><<<grid_for((n + kItems - 1) / kItems), kSortThreads, 0, s>>>(src, n, key_bits, totals);
   digit_offsets_kernel<<<1, kRadix, 0, s>>>(totals, passes, offs);
   *launches += 2;
   int64_t grid = (int64_t)sms * kPassBlocksPerSM;
@@ -766,18 +775,19 @@ cudaError_t radix_passes(Src src, int64_t n, int key_bits, uint32_t* ka, uint32_
     uint32_t* vout = to_final ? vfinal : (vfinal == va ? vb : va);
     *epoch = (*epoch + 1) & ((1u << 30) - 1);
     if (*epoch == 0) *epoch = 1;
+    const uint32_t dm = digit_mask(key_bits, p);
     if (p == 0) {
       if constexpr (std::is_same<Src, CellKeys>::value)
-        e = launch_pass<true, true, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, ntiles, offs, look, *epoch,
-                                         tile_ctr, err);
+        e = launch_pass<true, true, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, dm, ntiles, offs, look,
+                                         *epoch, tile_ctr, err);
       else
-        e = launch_pass<true, false, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, ntiles, offs, look, *epoch,
-                                          tile_ctr, err);
+        e = launch_pass<true, false, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, dm, ntiles, offs, look,
+                                          *epoch, tile_ctr, err);
     } else if (bulk_rest) {
-      e = launch_pass<false, true, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, ntiles,
+      e = launch_pass<false, true, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, dm, ntiles,
                                               offs + p * kRadix, look, *epoch, tile_ctr + p, err);
     } else {
-      e = launch_pass<false, false, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, ntiles,
+      e = launch_pass<false, false, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, dm, ntiles,
                                                offs + p * kRadix, look, *epoch, tile_ctr + p, err);
     }
     if (e != cudaSuccess) return e;
