@@ -2,11 +2,13 @@
 //
 // LSD radix sort of (key, slot) pairs with 8-bit digits.  One read of the keys counts every
 // pass's digit totals; then each pass is a single sweep: a block takes the next tile of 4096
-// keys in order, ranks them stably inside the tile (warp digit ballots, prefix counts combined
-// across warps in warp order), publishes its per-digit counts, adds the counts of all earlier
-// tiles by looking back over their published words (decoupled look-back; each word holds a
-// count and says whether it is the tile's own count or its inclusive prefix), and writes the
-// tile out digit-run by digit-run through shared memory so that the global writes coalesce.
+// keys in order, ranks them stably inside the tile (lanes of equal digit found with one
+// __match_any_sync per 32 keys, prefix counts combined across warps in warp order), publishes its
+// per-digit counts, places the tile in digit order in shared memory, adds the counts of all
+// earlier tiles by looking back over their published words (decoupled look-back, a few tiles'
+// words per round trip; each word holds a count and says whether it is the tile's own count or
+// its inclusive prefix), and writes the tile out digit-run by digit-run so that the global
+// writes coalesce.
 // The first pass computes the keys from the particle state on the fly and uses the storage
 // slot as the value.  The structure-of-arrays payload is then gathered once through the final
 // permutation.  Equal keys keep their storage order, so the permutation is unique.
