@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int
                                                                      uint32_t* __restrict__ totals) {
   const int passes = (key_bits + 7) / 8;
   __shared__ uint32_t cnt[kMaxPasses][kRadix];
+  __shared__ uint32_t mtab[32];  // Morton spread table for keys from cells
   for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += blockDim.x) (&cnt[0][0])[i] = 0;
+  if (threadIdx.x < 32) mtab[threadIdx.x] = spread3(threadIdx.x);
   __syncthreads();
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * kItems; base < n;
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             if constexpr (std::is_same<Src, CellKeys>::value)
-              k[r + e] = src.of_cell((int32_t)v4[e]);
+              k[r + e] = src.of_cell_tab((int32_t)v4[e], mtab);
             else
               k[r + e] = v4[e];
           }
