@@ -35,6 +35,7 @@ constexpr int kMaxPasses = 4;
 constexpr uint32_t kLookSpinLimit = 1u << 22;
 constexpr uint64_t kLookWaitNs = 1000000000ull;  // 1 s
 constexpr int kLookWindow = 4;  // look-back words read per round trip
+constexpr int kAttrDevices = 64;  // devices whose kernel attributes are tracked
 
 // look-back word: epoch (30 bits) | kind (2 bits: 1 = the tile's own count, 2 = inclusive
 // prefix) | count (32 bits).  A word whose epoch is not the pass's is empty.
@@ -739,12 +740,16 @@ template <bool FIRST, bool BULK, class Src>
 cudaError_t launch_pass(int64_t grid, cudaStream_t s, Src src, const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
                         uint32_t* vout, int64_t n, int shift, uint32_t dmask, int64_t ntiles, const uint32_t* offs,
                         unsigned long long* look, uint32_t epoch, unsigned* tile_ctr, int* err) {
-  static bool attr = false;  // one per instantiation
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(onesweep_kernel<FIRST, BULK, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kPassSmem);
+  static bool attr[kAttrDevices] = {};  // per instantiation and device (a kernel attribute is per device)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
+  if (!attr[dev]) {
+    e = cudaFuncSetAttribute(onesweep_kernel<FIRST, BULK, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPassSmem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr[dev] = true;
   }
   onesweep_kernel<FIRST, BULK, Src><<<(unsigned)grid, kSortThreads, kPassSmem, s>>>(
       src, kin, vin, kout, vout, n, shift, dmask, ntiles, offs, look, epoch, tile_ctr, err);

@@ -966,13 +966,15 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) 
       step_mixed_tma_kernel<true, false, false, true>,   step_mixed_tma_kernel<true, true, false, true>,
       step_mixed_tma_kernel<false, false, true, false>,  step_mixed_tma_kernel<false, true, true, false>,
       step_mixed_tma_kernel<true, false, true, false>,   step_mixed_tma_kernel<true, true, true, false>};
-  static bool attr_set[12] = {};
+  constexpr int kAttrDevices = 64;
+  static bool attr_set[kAttrDevices][12] = {};  // a kernel attribute is per device
   const int variant = records ? 8 + 2 * (int)bf + (int)pw2 : 4 * (int)bf + 2 * (int)phys + (int)pw2;
   const Kern kern = table[variant];
-  if (!attr_set[variant]) {
+  if (h->dev < 0 || h->dev >= kAttrDevices) return cudaErrorInvalidDevice;
+  if (!attr_set[h->dev][variant]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr_set[variant] = true;
+    attr_set[h->dev][variant] = true;
   }
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
