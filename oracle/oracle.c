@@ -204,10 +204,6 @@ static int grid_ok(const orc_grid* G) {
   return G->rho_p > 0.0 && G->mu > 0.0 && G->alpha > 0.0;
 }
 
-static int default_physics(const orc_grid* G) {
-  return G->gather == 0 && G->integrator == 0 && G->drag == 0 && G->deposit == 0;
-}
-
 int orc_run(const orc_grid* G, const double* U, int64_t n, double* pos, double* vel,
             const double* d, int32_t nsteps, double dt, double* src, int64_t* trace,
             const int64_t* frozen) {
@@ -326,7 +322,11 @@ void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const doubl
 int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
                 const double* vel0, const double* d, int32_t nsteps, double dt,
                 const double* lam, double* grad_d, double* grad_alpha, double* gradU) {
-  if (!grid_ok(G) || !default_physics(G) || n < 0 || nsteps < 0) return -1;
+  /* the default physics, or the default physics with the cloud-in-cell deposit */
+  const int cic = G->deposit == 1;
+  if (!grid_ok(G) || G->gather != 0 || G->integrator != 0 || G->drag != 0 || G->deposit > 1 || n < 0 ||
+      nsteps < 0)
+    return -1;
   int64_t nc = ncell_of(G);
   for (int64_t c = 0; c < 3 * nc; ++c) gradU[c] = 0.0;
   *grad_alpha = 0.0;
@@ -386,8 +386,38 @@ int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos
         wt[ax] = up[ax] + G->g[ax] / a;
         vn[ax] = wt[ax] + (vs[ax] - wt[ax]) * E;
       }
-      int64_t c0 = tc[s];
-      double Jb[3] = {lam[c0], lam[nc + c0], lam[2 * nc + c0]};
+      double Jb[3];
+      double fdep[3] = {0.0, 0.0, 0.0}; /* derivative of lam . (deposit) in the stencil fractions */
+      if (cic) {
+        /* J spread with the trilinear weights of the start position: its adjoint is the weighted
+         * sum of lam over the eight cells, and the weights' derivatives give lam . J terms */
+        double J[3];
+        for (int ax = 0; ax < 3; ++ax) J[ax] = -m * (vn[ax] - vs[ax] - G->g[ax] * dt);
+        Jb[0] = Jb[1] = Jb[2] = 0.0;
+        for (int dk = 0; dk < 2; ++dk)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              double wx = di ? f[0] : 1.0 - f[0];
+              double wy = dj ? f[1] : 1.0 - f[1];
+              double wz = dk ? f[2] : 1.0 - f[2];
+              double w = wx * wy * wz;
+              int64_t c = linear_cell(G, wrap_index(i0[0] + di, G->n[0]),
+                                      wrap_index(i0[1] + dj, G->n[1]), wrap_index(i0[2] + dk, G->n[2]));
+              double lj = 0.0;
+              for (int q = 0; q < 3; ++q) {
+                Jb[q] = Jb[q] + w * lam[q * nc + c];
+                lj = lj + lam[q * nc + c] * J[q];
+              }
+              fdep[0] = fdep[0] + (di ? 1.0 : -1.0) * wy * wz * lj;
+              fdep[1] = fdep[1] + wx * (dj ? 1.0 : -1.0) * wz * lj;
+              fdep[2] = fdep[2] + wx * wy * (dk ? 1.0 : -1.0) * lj;
+            }
+      } else {
+        int64_t c0 = tc[s];
+        Jb[0] = lam[c0];
+        Jb[1] = lam[nc + c0];
+        Jb[2] = lam[2 * nc + c0];
+      }
       /* J = -m (v' - v - g dt) */
       double mb = 0.0;
       double vnb[3], vsb[3];
@@ -442,7 +472,7 @@ int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos
             fb[2] = fb[2] + wx * wy * (dk ? 1.0 : -1.0) * dot;
           }
       for (int ax = 0; ax < 3; ++ax) {
-        xb[ax] = xsb[ax] + fb[ax] / h[ax];
+        xb[ax] = xsb[ax] + (fb[ax] + fdep[ax]) / h[ax];
         vb[ax] = vsb[ax];
       }
     }

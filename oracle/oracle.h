@@ -138,11 +138,13 @@ void orc_invariants(const orc_grid* G, int64_t n, const double* vel, const doubl
 
 /* Adjoint of orc_run for a loss L(Jtot) with Jtot the time-summed source:
  * given lam[3][ncell] = dL/dJtot, returns dL/dd_p, dL/dalpha and
- * dL/dU (gradU[c][3], same layout as U).  Deposit cells are treated as
- * locally constant (the derivative that exists almost everywhere).  The
- * forward trajectory is stored whole (no checkpointing).  pos0/vel0 are
- * not modified.  Default physics only (trilinear, exponential, Stokes,
- * containing-cell deposit).  Returns 0, -1 on bad arguments or other
+ * dL/dU (gradU[c][3], same layout as U).  With the containing-cell deposit
+ * the deposit cells are treated as locally constant (the derivative that
+ * exists almost everywhere); with the cloud-in-cell deposit the deposit
+ * weights are differentiated as well (they are continuous in the position).
+ * The forward trajectory is stored whole (no checkpointing).  pos0/vel0 are
+ * not modified.  Trilinear gather, exponential integrator and Stokes drag
+ * only, with either deposit.  Returns 0, -1 on bad arguments or other
  * physics, -2 on allocation failure. */
 int orc_adjoint(const orc_grid* G, const double* U, int64_t n, const double* pos0,
                 const double* vel0, const double* d, int32_t nsteps, double dt,

@@ -343,6 +343,80 @@ def test_adjoint_dot_product_with_random_direction(oracle_mod):
     assert abs(fd - ip) <= 1e-6 * abs(fd)
 
 
+# --- adjoint through the cloud-in-cell deposit: central differences with nothing held fixed ----
+
+def test_adjoint_cic_matches_central_finite_differences_unfrozen(oracle_mod):
+    """With the cloud-in-cell deposit the loss is continuous in the positions, so the adjoint, which
+    then differentiates the deposit weights as well, matches central differences of the full run
+    with no deposit cell held fixed."""
+    o = oracle_mod
+    G0, U, pos, vel, d, nsteps, dt = _adjoint_case(o)
+    G = o.make_grid(G0.n[0], alpha=0.9, deposit="cic")
+    _, _, src0, _ = o.run(G, U, pos, vel, d, nsteps, dt)
+    target = 0.7 * src0 + 1e-13 * np.random.default_rng(17).standard_normal(src0.shape)
+    lam = src0 - target
+    gd, ga, gU = o.adjoint(G, U, pos, vel, d, nsteps, dt, lam)
+    eps = 1e-4
+    for p in range(d.shape[0]):
+        dp, dm = d.copy(), d.copy()
+        dp[p] *= 1 + eps
+        dm[p] *= 1 - eps
+        fd = (_loss(o, G, U, pos, vel, dp, nsteps, dt, target, None)[0]
+              - _loss(o, G, U, pos, vel, dm, nsteps, dt, target, None)[0]) / (2 * eps * d[p])
+        assert abs(fd - gd[p]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gd).max())
+    Gp = o.make_grid(G.n[0], alpha=0.9 + eps, deposit="cic")
+    Gm = o.make_grid(G.n[0], alpha=0.9 - eps, deposit="cic")
+    fd = (_loss(o, Gp, U, pos, vel, d, nsteps, dt, target, None)[0]
+          - _loss(o, Gm, U, pos, vel, d, nsteps, dt, target, None)[0]) / (2 * eps)
+    assert abs(fd - ga) <= 1e-5 * abs(fd)
+    flat = np.argsort(-np.abs(gU).ravel())[:12]
+    for f in flat:
+        Up, Um = U.copy().reshape(-1), U.copy().reshape(-1)
+        Up[f] += eps
+        Um[f] -= eps
+        fd = (_loss(o, G, Up.reshape(U.shape), pos, vel, d, nsteps, dt, target, None)[0]
+              - _loss(o, G, Um.reshape(U.shape), pos, vel, d, nsteps, dt, target, None)[0]) / (2 * eps)
+        assert abs(fd - gU.ravel()[f]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gU).max())
+
+
+def test_adjoint_cic_dot_product_with_random_direction(oracle_mod):
+    """<grad, delta> equals the directional derivative of a linear functional of Jtot under the
+    cloud-in-cell deposit, with nothing held fixed."""
+    o = oracle_mod
+    _, U, pos, vel, d, nsteps, dt = _adjoint_case(o, n=5, npart=20, nsteps=6)
+    G = o.make_grid(5, alpha=0.9, deposit="cic")
+    rng = np.random.default_rng(18)
+    lam = rng.standard_normal((3, 5 ** 3))
+    gd, ga, gU = o.adjoint(G, U, pos, vel, d, nsteps, dt, lam)
+    dd = rng.standard_normal(d.shape) * d
+    dU = rng.standard_normal(U.shape)
+    da = 0.3
+    eps = 1e-5
+
+    def F(t):
+        Gt = o.make_grid(5, alpha=0.9 + t * da, deposit="cic")
+        _, _, src, _ = o.run(Gt, U + t * dU, pos, vel, d + t * dd, nsteps, dt)
+        return float((lam * src).sum())
+
+    fd = (F(eps) - F(-eps)) / (2 * eps)
+    ip = float((gd * dd).sum() + ga * da + (gU.reshape(U.shape) * dU).sum())
+    assert abs(fd - ip) <= 1e-6 * abs(fd)
+
+
+def test_adjoint_cic_differs_from_the_cell_deposit_adjoint(oracle_mod):
+    """The two deposits give different gradients for the same loss (the cloud-in-cell one is not
+    the cell one under another name), and other physics are refused."""
+    o = oracle_mod
+    G0, U, pos, vel, d, nsteps, dt = _adjoint_case(o)
+    G = o.make_grid(G0.n[0], alpha=0.9, deposit="cic")
+    lam = np.random.default_rng(19).standard_normal((3, G0.n[0] ** 3))
+    g_cic = o.adjoint(G, U, pos, vel, d, nsteps, dt, lam)[0]
+    g_cell = o.adjoint(G0, U, pos, vel, d, nsteps, dt, lam)[0]
+    assert np.abs(g_cic - g_cell).max() > 1e-3 * np.abs(g_cell).max()
+    with pytest.raises(ValueError):
+        o.adjoint(o.make_grid(G0.n[0], deposit="cic", drag="schiller_naumann"), U, pos, vel, d, nsteps, dt, lam)
+
+
 def test_chunk_bounds_hand_example_and_properties(oracle_mod):
     """Chunk boxes (Sec. 2.2): a hand-worked example on a 16^3 grid with 8^3-cell chunks (box 1, h =
     1/16, chunk centres at 0.25 / 0.75), including a particle that crossed the periodic face and is
