@@ -232,11 +232,12 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
 # adjoint workload; keyed by the SHA-256 of the kernel source, absent (null) once it changes
 MEASURED_FP64_OPS = {
     # profiles/adjoint_tgf64_1e7.md: 116 DFMA + 46.8 DADD + 70 DMUL per particle; FP64 pipe 78 % busy
-    ("3cf9bcbbbab3e1f18cdc5c827cfd66f845e5342e29054642856750d30484b6f0", "adjoint_step_kernel"): 348.8,
+    # (the cell-deposit instance adjoint_step_kernel<false>)
+    ("5f3671774619d7b6c8817a16cb24f49b90a6869dbce4f2756fe1d5772c54a060", "adjoint_step_kernel"): 348.8,
     # step_f64_kernel: 56 DFMA + 59 DADD + 19 DMUL per particle (2e6 particles on 128^3)
     ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 190.0,
 }
-MEASURED_FP64_PIPE = {("3cf9bcbbbab3e1f18cdc5c827cfd66f845e5342e29054642856750d30484b6f0", "adjoint_step_kernel"): 0.779,
+MEASURED_FP64_PIPE = {("5f3671774619d7b6c8817a16cb24f49b90a6869dbce4f2756fe1d5772c54a060", "adjoint_step_kernel"): 0.777,
                       ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 0.858}
 F64_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc", "step_f64.cu")
 

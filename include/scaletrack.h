@@ -233,11 +233,15 @@ st_status st_clear_particles(st_handle h);
  * velocities every checkpoint_every steps (6 x n x 8 bytes each).  With
  * Jtot the time-summed per-cell source, st_adjoint_backward then returns the
  * gradient of any loss L(Jtot).  The method has no adjoint in the paper; this
- * differentiates the step of Sec. 2.1 (Eqs. 9-11) as implemented here, with the
- * deposit cell held fixed (its derivative is zero almost everywhere).  FP64
- * handles only.  Changing particles, parameters or the fluid, or reordering,
+ * differentiates the step of Sec. 2.1 (Eqs. 9-11) as implemented here: with
+ * the cell deposit the deposit cell is held fixed (its derivative is zero
+ * almost everywhere); with the cloud-in-cell deposit (st_set_physics) its
+ * trilinear weights are differentiated as well.  FP64 handles with the
+ * trilinear gather, the exponential integrator and Stokes drag only.
+ * Changing particles, parameters, the physics or the fluid, or reordering,
  * invalidates the recorded run.
- * Errors: STATE (not FP64, no particles), INVALID_ARG, NONFINITE, OOM, CUDA. */
+ * Errors: STATE (not FP64, other physics, no particles), INVALID_ARG,
+ * NONFINITE, OOM, CUDA. */
 st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every);
 
 /* Reverse sweep of the last st_adjoint_forward run, segment by segment from

@@ -5,7 +5,8 @@ runs nsteps FP64 steps of the particles (initial positions pos0, velocities vel0
 diameters d) with drag scale alpha through the frozen fluid U, and returns the per-cell
 impulse summed over the run, J [3, ncell].  Its backward calls the library's adjoint
 (st_adjoint_backward): dL/dd per particle, dL/dalpha and dL/dU, with the deposit cell held
-fixed (its derivative is zero almost everywhere).  All arithmetic runs in the CUDA library.
+fixed under the cell deposit (its derivative is zero almost everywhere) and the deposit weights
+differentiated under the cloud-in-cell deposit.  All arithmetic runs in the CUDA library.
 """
 from __future__ import annotations
 

@@ -9,7 +9,10 @@
 //   v' = w E1 + v E;  x' = x + w (dt - Q) + v Q
 //   J = -m (v' - v - g dt),  m = mult rho_p pi d^3 / 6,  Jtot[c0] += J
 // with the deposit cell held fixed (its derivative is zero almost everywhere)
-// and the periodic wrap a translation.  Per particle it carries the adjoints
+// and the periodic wrap a translation.  With the cloud-in-cell deposit
+// (Jtot[corner] += W(f) J over the gather's stencil) the adjoint of J is the
+// W-weighted sum of lam over the corners, and the weights' derivatives add
+// lam_corner . J to the stencil-fraction adjoint beside the gather's term.  Per particle it carries the adjoints
 // of x and v between steps and accumulates dL/dd; dL/dalpha is reduced
 // per block in a fixed order; dL/dU is scattered through the transposed
 // trilinear weights into an exact carry-save fixed-point accumulator, so
@@ -75,6 +78,8 @@ __device__ __forceinline__ D4 ld_cell(const D4* __restrict__ U, int64_t c) {
   return D4{a.x, a.y, b.x, b.y};
 }
 
+// CIC: the cloud-in-cell deposit (else the containing cell)
+template <bool CIC>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs a) {
   const int n3[3] = {a.nx, a.ny, a.nz};
   double alphab_sum = 0.0;
@@ -133,7 +138,24 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
       vn[q] = wt[q] + (v[q] - wt[q]) * E;
     }
     // reverse sweep
-    const double Jb[3] = {a.lam[key], a.lam[a.ncell + key], a.lam[2 * a.ncell + key]};
+    double Jb[3];
+    double lj[CIC ? 8 : 1];  // cloud in cell: lam at each corner dotted with J
+    if constexpr (CIC) {
+      double J[3];
+      for (int q = 0; q < 3; ++q) J[q] = -m * (vn[q] - v[q] - a.g[q] * a.dt);
+      Jb[0] = Jb[1] = Jb[2] = 0.0;
+      for (int k = 0; k < 8; ++k) {
+        const double l0 = a.lam[corner[k]], l1 = a.lam[a.ncell + corner[k]], l2 = a.lam[2 * a.ncell + corner[k]];
+        Jb[0] += W[k] * l0;
+        Jb[1] += W[k] * l1;
+        Jb[2] += W[k] * l2;
+        lj[k] = l0 * J[0] + l1 * J[1] + l2 * J[2];
+      }
+    } else {
+      Jb[0] = a.lam[key];
+      Jb[1] = a.lam[a.ncell + key];
+      Jb[2] = a.lam[2 * a.ncell + key];
+    }
     double mb = 0.0, Eb = 0.0, E1b = 0.0, Qb = 0.0, ab = 0.0;
     double ub[3], vsb[3];
     for (int q = 0; q < 3; ++q) {
@@ -154,11 +176,13 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
     double dbv = a.db[p] + ab * (-2.0 * ra * inv_d) + mb * 3.0 * m * inv_d;
     a.db[p] = dbv;
     // transposed trilinear weights: dL/dU (each corner's weight times ub) and dL/df, the
-    // derivative of the trilinear form of the corner values' dot products with ub, taken
-    // separably (differences along one axis, interpolated along the other two)
+    // derivative of the trilinear form of the corner values' dot products with ub (plus, for the
+    // cloud-in-cell deposit, lam . J at the corner), taken separably (differences along one
+    // axis, interpolated along the other two)
     double dot[8];
     for (int k = 0; k < 8; ++k) {
       dot[k] = Uc[k].x * ub[0] + Uc[k].y * ub[1] + Uc[k].z * ub[2];
+      if constexpr (CIC) dot[k] += lj[k];
       long long* w = a.Uw + corner[k] * 3 * kWideWords;
       wide_add(w, W[k] * ub[0]);
       wide_add(w + kWideWords, W[k] * ub[1]);
@@ -241,7 +265,10 @@ cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s) {
   a.alpha = h->alpha;
   a.inv_ca = 1.0 / a.ca;
   a.inv_alpha = 1.0 / h->alpha;
-  adjoint_step_kernel<<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
+  if (h->phys_deposit == ST_DEPOSIT_CIC)
+    adjoint_step_kernel<true><<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
+  else
+    adjoint_step_kernel<false><<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
   h->launches += 1;
   return cudaGetLastError();
 }

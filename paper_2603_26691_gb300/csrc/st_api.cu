@@ -755,8 +755,10 @@ st_status st_clear_particles(st_handle h) {
 st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every) {
   ST_TRY(check_handle(h));
   if (h->prec != ST_FP64) return set_error(h, ST_ERR_STATE, "the adjoint needs an FP64 handle");
-  if (!default_physics(h))
-    return set_error(h, ST_ERR_STATE, "the adjoint needs the default physics (trilinear, exponential, Stokes, cell)");
+  if (h->phys_gather != ST_GATHER_TRILINEAR || h->phys_integrator != ST_INTEGRATOR_EXPONENTIAL ||
+      h->phys_drag != ST_DRAG_STOKES)
+    return set_error(h, ST_ERR_STATE,
+                     "the adjoint needs the trilinear gather, the exponential integrator and Stokes drag");
   if (nsteps < 1 || checkpoint_every < 1) return set_error(h, ST_ERR_INVALID_ARG, "nsteps and checkpoint_every must be >= 1");
   if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
   if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");
@@ -787,6 +789,7 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
     for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
     p.E = E;
     p.scale = std::ldexp(1.0, E);
+    p.cic = h->phys_deposit == ST_DEPOSIT_CIC;  // the other physics are the defaults here
     timer_begin(h, ST_TIMER_STEP, h->stream);
     const cudaError_t fe = launch_step_f64(h, p);
     timer_end(h, ST_TIMER_STEP, h->stream);

@@ -24,9 +24,10 @@ def _case(N=12, n=257, alpha=0.9):
     return N, U, pos, vel, d * 1.5, alpha
 
 
-def _gpu_grads(Sim, N, U, pos, vel, d, alpha, nsteps, dt, ck, lam):
+def _gpu_grads(Sim, N, U, pos, vel, d, alpha, nsteps, dt, ck, lam, deposit="cell"):
     sim = Sim(N, precision="fp64")
     sim.set_params(drag_scale=alpha, reorder_every=0)
+    sim.set_physics(deposit=deposit)
     sim.set_fluid(U)
     sim.add_particles(pos, d, vel)
     sim.adjoint_forward(nsteps, dt, ck)
@@ -80,6 +81,73 @@ def test_adjoint_matches_central_finite_differences(Sim):
         Um[f] -= eps
         fd = (loss(G, Up.reshape(U.shape), d) - loss(G, Um.reshape(U.shape), d)) / (2 * eps)
         assert abs(fd - gU.ravel()[f]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gU).max())
+
+
+@pytest.mark.parametrize("ck", [1, 7])
+def test_adjoint_cic_matches_oracle_adjoint(Sim, ck):
+    """The cloud-in-cell deposit's adjoint (deposit weights differentiated) against the oracle's."""
+    N, U, pos, vel, d, alpha = _case()
+    nsteps, dt = 23, 1e-3
+    lam = np.random.default_rng(15).standard_normal((3, N ** 3))
+    J, gd, ga, gU = _gpu_grads(Sim, N, U, pos, vel, d, alpha, nsteps, dt, ck, lam, deposit="cic")
+    G = oracle.make_grid(N, alpha=alpha, deposit="cic")
+    _, _, oJ, _ = oracle.run(G, U, pos, vel, d, nsteps, dt)
+    ogd, oga, ogU = oracle.adjoint(G, U, pos, vel, d, nsteps, dt, lam)
+    assert np.abs(J - oJ).max() <= 1e-10 * np.abs(oJ).max()
+    assert np.abs(gd - ogd).max() <= 1e-9 * np.abs(ogd).max()
+    assert abs(ga - oga) <= 1e-9 * abs(oga)
+    assert np.abs(gU - ogU).max() <= 1e-9 * np.abs(ogU).max()
+    # not the cell deposit's gradient under another name
+    cgd = oracle.adjoint(oracle.make_grid(N, alpha=alpha), U, pos, vel, d, nsteps, dt, lam)[0]
+    assert np.abs(gd - cgd).max() > 1e-3 * np.abs(cgd).max()
+
+
+def test_adjoint_cic_matches_central_finite_differences_unfrozen(Sim):
+    """With the cloud-in-cell deposit nothing is held fixed: the GPU gradient of
+    L = 1/2 |Jtot - Jtarget|^2 against central differences of the oracle's full run (eps 1e-4)."""
+    N, U, pos, vel, d, alpha = _case(N=10, n=40)
+    nsteps, dt = 20, 1e-3
+    G = oracle.make_grid(N, alpha=alpha, deposit="cic")
+    _, _, J0, _ = oracle.run(G, U, pos, vel, d, nsteps, dt)
+    _, _, Jt, _ = oracle.run(G, U, pos, vel, d * 1.05, nsteps, dt)
+    lam = J0 - Jt
+    _, gd, ga, gU = _gpu_grads(Sim, N, U, pos, vel, d, alpha, nsteps, dt, 6, lam, deposit="cic")
+
+    def loss(Gx, Ux, dx):
+        _, _, J, _ = oracle.run(Gx, Ux, pos, vel, dx, nsteps, dt)
+        return 0.5 * float(((J - Jt) ** 2).sum())
+
+    eps = 1e-4
+    for p in range(0, d.shape[0], 4):
+        dp, dm = d.copy(), d.copy()
+        dp[p] *= 1 + eps
+        dm[p] *= 1 - eps
+        fd = (loss(G, U, dp) - loss(G, U, dm)) / (2 * eps * d[p])
+        assert abs(fd - gd[p]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gd).max())
+    fd = (loss(oracle.make_grid(N, alpha=alpha + eps, deposit="cic"), U, d)
+          - loss(oracle.make_grid(N, alpha=alpha - eps, deposit="cic"), U, d)) / (2 * eps)
+    assert abs(fd - ga) <= 1e-5 * abs(fd)
+    for f in np.argsort(-np.abs(gU).ravel())[:8]:
+        Up, Um = U.copy().reshape(-1), U.copy().reshape(-1)
+        Up[f] += eps
+        Um[f] -= eps
+        fd = (loss(G, Up.reshape(U.shape), d) - loss(G, Um.reshape(U.shape), d)) / (2 * eps)
+        assert abs(fd - gU.ravel()[f]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(gU).max())
+
+
+def test_adjoint_refuses_physics_it_does_not_differentiate(Sim):
+    from paper_2603_26691_gb300._lib import StError
+
+    N, U, pos, vel, d, alpha = _case(N=8, n=33)
+    sim = Sim(N, precision="fp64")
+    sim.set_params(reorder_every=0)
+    sim.set_fluid(U)
+    sim.add_particles(pos, d, vel)
+    for ph in (dict(drag="schiller_naumann"), dict(gather="ngp"), dict(integrator="semi_implicit")):
+        sim.set_physics(**ph)
+        with pytest.raises(StError):
+            sim.adjoint_forward(3, 1e-3, 1)
+    sim.close()
 
 
 def test_autograd_function_quadratic_loss(Sim):

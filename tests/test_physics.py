@@ -199,7 +199,7 @@ def test_variant_momentum_budget_exact(Sim, combo):
         assert np.abs(bal).max() <= (1e-12 if prec == "fp64" else 1e-6) * scale
 
 
-def test_set_physics_rejects_bad_arguments_and_the_adjoint_needs_defaults(Sim):
+def test_set_physics_rejects_bad_arguments_and_the_adjoint_needs_its_physics(Sim):
     from paper_2603_26691_gb300 import _lib
 
     sim = Sim(8, precision="fp64")
@@ -211,8 +211,10 @@ def test_set_physics_rejects_bad_arguments_and_the_adjoint_needs_defaults(Sim):
     pos, vel, d, _ = inputs.particles(1, 0, 64)
     sim.set_fluid(inputs.taylor_green(8))
     sim.add_particles(pos, d, vel)
-    sim.set_physics(deposit="cic")
+    sim.set_physics(drag="schiller_naumann")
     assert lib.st_adjoint_forward(h, 4, 1e-3, 2) == _lib.ST_ERR_STATE
+    sim.set_physics(deposit="cic")  # the cloud-in-cell deposit is differentiated
+    assert lib.st_adjoint_forward(h, 4, 1e-3, 2) == _lib.ST_OK
     sim.set_physics()
     assert lib.st_adjoint_forward(h, 4, 1e-3, 2) == _lib.ST_OK
     sim.close()
