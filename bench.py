@@ -337,6 +337,24 @@ def run_adjoint(args, workload):
     e2e = {"value": n * steps / e_el, "unit": "particle-steps/s", "h2d_bytes_per_step": int(lam_h.nbytes),
            "d2h_bytes_per_step": int(hgd.nbytes + hgU.nbytes), "steps": 1,
            "what": "one forward (checkpointed) + backward run, lam from host, dL/dd and dL/dU to host"}
+    # the same run through the cloud-in-cell deposit (the adjoint step kernel's second instance,
+    # which differentiates the deposit weights too)
+    sim.set_physics(deposit="cic")
+    sim.timers(True)
+    c0e, c1e, c2e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0e.record()
+    sim.adjoint_forward(steps, dt, ck)
+    c1e.record()
+    sim.adjoint_backward(lam)
+    c2e.record()
+    torch.cuda.synchronize()
+    tmc = sim.timers()
+    sim.timers(False)
+    sim.set_physics()
+    cf_ms, cb_ms = c0e.elapsed_time(c1e), c1e.elapsed_time(c2e)
+    cic = {"forward_ms": cf_ms, "backward_ms": cb_ms, "particle_steps_per_s": n * steps / ((cf_ms + cb_ms) * 1e-3),
+           "adjoint_kernel_ms_per_launch": tmc["adjoint"][0] / max(tmc["adjoint"][1], 1),
+           "step_kernel_ms_per_launch": tmc["step"][0] / max(tmc["step"][1], 1)}
     sim.close()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -361,7 +379,8 @@ def run_adjoint(args, workload):
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "breakdown": {"forward_ms": fwd_ms, "backward_ms": bwd_ms, "timers": tm,
-                          "grad_alpha": ga, "grad_d_norm": float(torch.linalg.vector_norm(gd).item())}}
+                          "grad_alpha": ga, "grad_d_norm": float(torch.linalg.vector_norm(gd).item()),
+                          "cic_deposit": cic}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

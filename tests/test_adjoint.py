@@ -150,7 +150,8 @@ def test_adjoint_refuses_physics_it_does_not_differentiate(Sim):
     sim.close()
 
 
-def test_autograd_function_quadratic_loss(Sim):
+@pytest.mark.parametrize("deposit", ["cell", "cic"])
+def test_autograd_function_quadratic_loss(Sim, deposit):
     import torch
 
     from paper_2603_26691_gb300.autograd import lagrangian_sources
@@ -158,6 +159,7 @@ def test_autograd_function_quadratic_loss(Sim):
     N, U, pos, vel, d, alpha = _case(N=12, n=500)
     nsteps, dt = 25, 1e-3
     sim = Sim(N, precision="fp64")
+    sim.set_physics(deposit=deposit)
     dev = torch.device("cuda")
     dt_ = torch.tensor(d, device=dev, requires_grad=True)
     at = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
@@ -168,7 +170,7 @@ def test_autograd_function_quadratic_loss(Sim):
     L = 0.5 * ((J - Jt) ** 2).sum()
     L.backward()
     sim.close()
-    G = oracle.make_grid(N, alpha=alpha)
+    G = oracle.make_grid(N, alpha=alpha, deposit=deposit)
     _, _, oJ, _ = oracle.run(G, U, pos, vel, d, nsteps, dt)
     _, _, oJt, _ = oracle.run(G, U, pos, vel, d * 1.05, nsteps, dt)
     ogd, oga, ogU = oracle.adjoint(G, U, pos, vel, d, nsteps, dt, oJ - oJt)
