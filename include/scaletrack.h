@@ -138,7 +138,8 @@ st_status st_set_params(st_handle h, double rho_p, double mu, const double g[3],
  * Schiller-Naumann drag).  Every combination runs on the sorted-particle
  * step kernel of mixed handles (a separate instance of it; the defaults keep
  * their own) and on the general kernels.  The adjoint (st_adjoint_*) needs
- * the defaults.  Errors: INVALID_ARG, NONFINITE. */
+ * the default gather, integrator and drag, with either deposit.
+ * Errors: INVALID_ARG, NONFINITE. */
 enum { ST_GATHER_TRILINEAR = 0, ST_GATHER_NGP = 1 };
 enum { ST_INTEGRATOR_EXPONENTIAL = 0, ST_INTEGRATOR_SEMI_IMPLICIT = 1 };
 enum { ST_DRAG_STOKES = 0, ST_DRAG_SCHILLER_NAUMANN = 1 };
