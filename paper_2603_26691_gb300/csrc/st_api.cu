@@ -341,7 +341,9 @@ static st_status grow(st_handle h, int64_t need) {
   while (cap < need) cap = cap + cap / 2 + 64;
   cap = (cap + 63) & ~int64_t(63);
   Buf ns, ni;
-  ST_TRY(dev_alloc(h, ns, state_bytes(h->prec, cap)));
+  // sized like the sort's spare buffer (room for 32-byte particle records on mixed handles): the
+  // sort swaps the two, so either may be the one the step before a sort writes records into
+  ST_TRY(dev_alloc(h, ns, state_alt_bytes(h->prec, cap)));
   st_status s = dev_alloc(h, ni, (size_t)cap * sizeof(uint32_t));
   if (s != ST_OK) {
     dev_free(h, ns);
