@@ -44,7 +44,7 @@ MEASURED_TRAFFIC = {
     # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches of the plain instance (fresh to 3 steps of
     # drift), 64.07-64.15 B (FP32 velocity; the BF16-velocity instance measured 52.07-52.15 B before the
     # cloud-in-cell deposit joined the physics instance)
-    ("f38670b836ca987e7c5925e8aca1a41885eb15598c361c3ee6ae19a4429be906", "fourier256_mixed_1e9"): 64.10,
+    ("02954dbb200a46ce08d8b4d415a6188ed5cc14601c187adc5886aaba1a5a184e", "fourier256_mixed_1e9"): 64.10,
 }
 
 

@@ -827,7 +827,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         deposit(key, J, true);
       } else {
         // cloud in cell: J spread over the eight cells of the start-of-step trilinear stencil with
-        // its weights, one pass of runs per corner.  The start cells and offsets are read again
+        // its weights, one pass per corner.  The start cells and offsets are read again
         // from the stage (still intact: every pass commits in place).  Corners inside the deposit
         // tile go there; the rest (start cells at the tile's edge or outside it, rare) go to the
         // global accumulator.
@@ -883,7 +883,12 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
             }
             kc[j] = k;
           }
-          deposit(kc, Jc, false);
+          // each particle's corner straight into the tile: neighbouring particles of a cell sit in
+          // different half-cells and so rarely share a corner cell, and run sums would only add
+          // the cost of forming them
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (kc[j] >= 0) commit_record(a, dep, kc[j], Jc[j][0], Jc[j][1], Jc[j][2]);
         }
       }
       __syncwarp();
