@@ -47,6 +47,19 @@ class Grid(C.Structure):
                 ("rho_f", C.c_double)]
 
 
+class Micro(C.Structure):
+    _fields_ = [("D_v", C.c_double), ("kappa_f", C.c_double), ("cp_p", C.c_double), ("L", C.c_double),
+                ("Pr", C.c_double), ("d_min", C.c_double)]
+
+
+def make_micro(D_v=2.5e-5, kappa_f=0.025, cp_p=4186.0, L=2.5e6, Pr=0.71, d_min=1e-7) -> Micro:
+    """Droplet microphysics parameters (defaults: water droplets in air near 285 K)."""
+    M = Micro()
+    M.D_v, M.kappa_f, M.cp_p, M.L, M.Pr, M.d_min = (float(D_v), float(kappa_f), float(cp_p), float(L),
+                                                    float(Pr), float(d_min))
+    return M
+
+
 GATHERS = {"trilinear": 0, "ngp": 1}
 INTEGRATORS = {"exponential": 0, "semi_implicit": 1}
 DRAGS = {"stokes": 0, "schiller_naumann": 1}
@@ -105,6 +118,11 @@ def lib():
             L.orc_fluid_update.restype = C.c_int
             L.orc_couple.argtypes = [pg, pd, i64, pd, pd, pd, i32, i32, d, d, d, i32, i32, pd]
             L.orc_couple.restype = C.c_int
+            L.orc_rho_sat.argtypes, L.orc_rho_sat.restype = [d], d
+            L.orc_rho_sat_dT.argtypes, L.orc_rho_sat_dT.restype = [d], d
+            L.orc_nusselt.argtypes, L.orc_nusselt.restype = [_P(Micro), d], d
+            L.orc_micro_run.argtypes = [pg, _P(Micro), pd, pd, pd, i64, pd, pd, pd, pd, i32, d, pd, pd, pd]
+            L.orc_micro_run.restype = C.c_int
             _lib = L
     return _lib
 
@@ -309,3 +327,37 @@ def chunk_bounds(G: Grid, pos_sort, pos_now) -> np.ndarray:
     if r < 0:
         raise ValueError("orc_chunk_bounds failed")
     return out
+
+
+def rho_sat(T: float) -> float:
+    """Saturation vapour density over flat water (kg/m^3) at T (K)."""
+    return lib().orc_rho_sat(float(T))
+
+
+def rho_sat_dT(T: float) -> float:
+    """d rho_sat / dT (kg/(m^3 K)) at T (K)."""
+    return lib().orc_rho_sat_dT(float(T))
+
+
+def nusselt(M: Micro, re: float) -> float:
+    return lib().orc_nusselt(C.byref(M), float(re))
+
+
+def micro_run(G: Grid, M: Micro, U, Tf, rhov, pos, vel, d, Tp, nsteps: int, dt: float):
+    """Droplets with vapour mass and heat transfer: nsteps steps in the frozen fields U [.., 3], Tf and rhov
+    [ncell].  Returns (pos, vel, d, Tp, src [3, ncell], msrc [ncell], esrc [ncell]) (inputs copied)."""
+    U = _f64(U)
+    Tf = _f64(Tf).reshape(-1)
+    rhov = _f64(rhov).reshape(-1)
+    pos = _f64(pos).reshape(3, -1).copy()
+    vel = _f64(vel).reshape(3, -1).copy()
+    d = _f64(d).reshape(-1).copy()
+    Tp = _f64(Tp).reshape(-1).copy()
+    n = d.shape[0]
+    nc = ncell(G)
+    src, msrc, esrc = np.zeros((3, nc)), np.zeros(nc), np.zeros(nc)
+    rc = lib().orc_micro_run(C.byref(G), C.byref(M), _pd(U), _pd(Tf), _pd(rhov), n, _pd(pos), _pd(vel), _pd(d),
+                             _pd(Tp), int(nsteps), float(dt), _pd(src), _pd(msrc), _pd(esrc))
+    if rc != 0:
+        raise ValueError(f"orc_micro_run failed ({rc})")
+    return pos, vel, d, Tp, src, msrc, esrc

@@ -645,3 +645,150 @@ int64_t orc_chunk_bounds(const orc_grid* G, int64_t n, const double* pos_sort, c
   }
   return nchunk;
 }
+
+/* ---- droplet microphysics (Sec. 2.1): vapour mass transfer and heat transfer ---------------- */
+
+/* Saturation vapour density over a flat water surface at temperature T (K):
+ * rho_sat = e_s(T) / (R_v T) with the saturation vapour pressure of the Magnus
+ * form, e_s = 610.94 Pa exp(17.625 t / (t + 243.04 K)), t = T - 273.15 K (the
+ * coefficients Alduchov and Eskridge (1996) fitted over water), and the gas
+ * constant of water vapour R_v = 461.5 J/(kg K). */
+double orc_rho_sat(double T) {
+  double t = T - 273.15;
+  double es = 610.94 * exp(17.625 * t / (t + 243.04));
+  return es / (461.5 * T);
+}
+
+/* Nusselt number of a sphere at particle Reynolds number Re: the Ranz-Marshall
+ * correlation Nu = 2 + 0.6 Re^(1/2) Pr^(1/3) (the paper names the Nusselt
+ * number without a correlation). */
+double orc_nusselt(const orc_micro* M, double re) {
+  return 2.0 + 0.6 * sqrt(re) * pow(M->Pr, 1.0 / 3.0);
+}
+
+/* A cell-centred scalar field F[c] at x: trilinear (or, gather = 1, the
+ * containing cell's value), with the stencil of the velocity gather. */
+static double scalar_gather(const orc_grid* G, const double* F, const double x[3]) {
+  if (G->gather == 1) {
+    int32_t idx[3];
+    orc_cell(G, x, idx);
+    return F[linear_cell(G, idx[0], idx[1], idx[2])];
+  }
+  int64_t cells[8];
+  double w[8];
+  trilinear_stencil(G, x, cells, w);
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c) s = s + w[c] * F[cells[c]];
+  return s;
+}
+
+/* d rho_sat / dT at T (K): rho_sat (d ln e_s / dT - 1 / T) with d ln e_s / dT =
+ * 17.625 * 243.04 / (t + 243.04)^2 from the Magnus form above. */
+double orc_rho_sat_dT(double T) {
+  double t = T - 273.15;
+  double a = t + 243.04;
+  return orc_rho_sat(T) * (17.625 * 243.04 / (a * a) - 1.0 / T);
+}
+
+/* One step of one droplet with mass and heat transfer.  The rates come from the
+ * state at the start of the step (position x, velocity v, diameter d,
+ * temperature Tp) and the fluid values gathered at x (velocity u_p,
+ * temperature T_f, vapour density rho_v), held over the step:
+ *   - motion as orc_advance, with the drag of the start-of-step diameter;
+ *   - mass (Sec. 2.1): dm/dt = 2 pi D_v d rho_sat (S_f - S_p) with S_f =
+ *     rho_v / rho_sat(T_f) and S_p = rho_sat(Tp) / rho_sat(T_f) (a flat
+ *     surface at the droplet's temperature), i.e. dm/dt = B (rho_v -
+ *     rho_sat(Tp)), B = 2 pi D_v d; with m = rho_p pi d^3 / 6 per droplet
+ *     this is d(d^2)/dt = 8 D_v (rho_v - rho_sat(Tp)) / rho_p;
+ *   - heat (Sec. 2.1): m C_p dTp/dt = A (T_f - Tp) + L dm/dt, A = pi Nu kappa_f
+ *     d (reading: the latent heat of the condensed mass warms the droplet and
+ *     evaporation cools it; the printed equation has the opposite sign, which
+ *     would heat an evaporating droplet), Nu from the start-of-step slip
+ *     (Re = rho_f |u_p - v| d / mu);
+ *   - the step (the paper gives none): with d, A, B frozen and rho_sat
+ *     linearised about the start temperature T0, rho_sat(T) ~ r0 + s (T - T0),
+ *     the heat balance is linear, dT/dt = -k (T - T*) with
+ *       k = (A + L B s) / (m C_p),  T* = (A T_f + L B (rho_v - r0 + s T0)) / (A + L B s),
+ *     and is advanced exactly, T' = T* + (T0 - T*) e^{-k dt}; the d^2 law is
+ *     integrated along the same temperature path,
+ *       d'^2 = d^2 + (8 D_v / rho_p) [(rho_v - r0 + s T0) dt - s I],
+ *       I = int_0^dt T = T* dt + (T0 - T*) (1 - e^{-k dt}) / k.
+ *     This is exact when the droplet stays at the fluid temperature (the d^2
+ *     law) and when no vapour moves (the temperature's exponential relaxation),
+ *     and stable for steps much longer than the droplet's thermal time.  A
+ *     droplet that would shrink below d_min keeps d_min;
+ *   - what the fluid gains, into the start-of-step cell c0 (Sec. 2.1, Eq. 11
+ *     and the vapour and energy sources, with the sign of a gain for the
+ *     fluid): momentum J = -[(m' v' - m v) - m g dt], vapour mass -(m' - m),
+ *     energy -C_p (m' Tp' - m Tp).  Masses include the parcel multiplicity;
+ *     the per-droplet rates do not depend on it. */
+void orc_micro_particle_step(const orc_grid* G, const orc_micro* M, const double* U, const double* Tf,
+                             const double* rhov, double dt, double x[3], double v[3], double* d, double* Tp,
+                             int64_t* c0, double J[3], double* dmass, double* denergy) {
+  int32_t idx[3];
+  double up[3], vold[3];
+  orc_cell(G, x, idx);
+  *c0 = linear_cell(G, idx[0], idx[1], idx[2]);
+  orc_gather(G, U, x, up);
+  double tf = scalar_gather(G, Tf, x);
+  double rv = scalar_gather(G, rhov, x);
+  double d0 = *d, T0 = *Tp;
+  double r0 = up[0] - v[0], r1 = up[1] - v[1], r2 = up[2] - v[2];
+  double re = G->rho_f * sqrt(r0 * r0 + r1 * r1 + r2 * r2) * d0 / G->mu;
+  for (int ax = 0; ax < 3; ++ax) vold[ax] = v[ax];
+  orc_advance(G, d0, up, dt, x, v);
+  for (int ax = 0; ax < 3; ++ax) x[ax] = orc_wrap(x[ax], G->L[ax]);
+  /* the linear heat balance over the step */
+  double nu = orc_nusselt(M, re);
+  double md0 = G->rho_p * kPi * d0 * d0 * d0 / 6.0;
+  double A = kPi * nu * M->kappa_f * d0;
+  double B = 2.0 * kPi * M->D_v * d0;
+  double rs = orc_rho_sat(T0);
+  double sl = orc_rho_sat_dT(T0);
+  double excess = rv - rs + sl * T0;
+  double den = A + M->L * B * sl;
+  double k = den / (md0 * M->cp_p);
+  double Ts = (A * tf + M->L * B * excess) / den;
+  double e1 = -expm1(-k * dt);
+  double T1 = Ts + (T0 - Ts) * (1.0 - e1);
+  double I = Ts * dt + (T0 - Ts) * e1 / k;
+  /* the d^2 law along that temperature path */
+  double q = d0 * d0 + 8.0 * M->D_v * (excess * dt - sl * I) / G->rho_p;
+  double d1 = q > M->d_min * M->d_min ? sqrt(q) : M->d_min;
+  double m0 = orc_mass(G, d0), m1 = orc_mass(G, d1);
+  /* what the fluid gains */
+  for (int ax = 0; ax < 3; ++ax) J[ax] = -((m1 * v[ax] - m0 * vold[ax]) - m0 * G->g[ax] * dt);
+  *dmass = -(m1 - m0);
+  *denergy = -M->cp_p * (m1 * T1 - m0 * T0);
+  *d = d1;
+  *Tp = T1;
+}
+
+int orc_micro_run(const orc_grid* G, const orc_micro* M, const double* U, const double* Tf, const double* rhov,
+                  int64_t n, double* pos, double* vel, double* d, double* Tp, int32_t nsteps, double dt,
+                  double* src, double* msrc, double* esrc) {
+  if (!grid_ok(G) || !M || n < 0 || nsteps < 0 || G->deposit != 0) return -1;
+  if (!(M->D_v >= 0.0) || !(M->kappa_f > 0.0) || !(M->cp_p > 0.0) || !(M->Pr > 0.0) || !(M->d_min > 0.0))
+    return -1;
+  int64_t nc = ncell_of(G);
+  for (int32_t s = 0; s < nsteps; ++s) {
+    for (int64_t p = 0; p < n; ++p) {
+      double x[3] = {pos[p], pos[n + p], pos[2 * n + p]};
+      double v[3] = {vel[p], vel[n + p], vel[2 * n + p]};
+      int64_t c0;
+      double J[3], dm, de;
+      orc_micro_particle_step(G, M, U, Tf, rhov, dt, x, v, &d[p], &Tp[p], &c0, J, &dm, &de);
+      if (src)
+        for (int ax = 0; ax < 3; ++ax) src[ax * nc + c0] = src[ax * nc + c0] + J[ax];
+      if (msrc) msrc[c0] = msrc[c0] + dm;
+      if (esrc) esrc[c0] = esrc[c0] + de;
+      pos[p] = x[0];
+      pos[n + p] = x[1];
+      pos[2 * n + p] = x[2];
+      vel[p] = v[0];
+      vel[n + p] = v[1];
+      vel[2 * n + p] = v[2];
+    }
+  }
+  return 0;
+}

@@ -25,6 +25,9 @@
  *   - global invariants (particle count, momentum, summed source, mass);
  *   - the hand-derived adjoint of the step for a loss on the time-summed
  *     source field;
+ *   - droplet microphysics (Sec. 2.1): vapour mass transfer to or from a
+ *     droplet and its heat balance with the latent heat, and the vapour-mass
+ *     and energy sources they give the fluid;
  *   - the asynchronous two-way coupling of Sec. 2.3 on one device: the
  *     particles advance in a frozen fluid field while the fluid is updated
  *     from the sources of the previous coupling interval, estimated by the
@@ -192,6 +195,44 @@ int orc_fluid_update(const orc_grid* G, double* U, const double* S, double rho_f
 int orc_couple(const orc_grid* G, double* U, int64_t n, double* pos, double* vel, const double* d,
                int32_t nint, int32_t K, double dt, double rho_f, double nu, int32_t sweeps,
                int32_t extrap, double* pending);
+
+/* Droplet microphysics parameters (Sec. 2.1). */
+typedef struct {
+  double D_v;      /* diffusivity of water vapour in the fluid (m^2/s) */
+  double kappa_f;  /* thermal conductivity of the fluid (W/(m K)) */
+  double cp_p;     /* specific heat capacity of the droplet (J/(kg K)) */
+  double L;        /* latent heat of vaporization of water (J/kg) */
+  double Pr;       /* Prandtl number of the fluid (Nusselt correlation) */
+  double d_min;    /* diameter an evaporating droplet keeps at least (m) */
+} orc_micro;
+
+/* Saturation vapour density over flat water at T (K), kg/m^3 (Magnus form,
+ * Alduchov-Eskridge coefficients, ideal gas with R_v = 461.5 J/(kg K)). */
+double orc_rho_sat(double T);
+
+/* d rho_sat / dT at T (K), from the same form. */
+double orc_rho_sat_dT(double T);
+
+/* Nusselt number (Ranz-Marshall: 2 + 0.6 Re^(1/2) Pr^(1/3)). */
+double orc_nusselt(const orc_micro* M, double re);
+
+/* One step of one droplet with motion, vapour mass transfer and heat transfer
+ * (Sec. 2.1): x, v, d, Tp updated in place; c0 the start-of-step cell; J, dmass
+ * and denergy the momentum, vapour mass and energy the fluid gains.  The step
+ * is documented at its definition in oracle.c. */
+void orc_micro_particle_step(const orc_grid* G, const orc_micro* M, const double* U, const double* Tf,
+                             const double* rhov, double dt, double x[3], double v[3], double* d, double* Tp,
+                             int64_t* c0, double J[3], double* dmass, double* denergy);
+
+/* nsteps steps of n droplets with microphysics in the frozen fields U[c][3],
+ * Tf[c] (K) and rhov[c] (kg/m^3); pos, vel, d and Tp updated in place; the
+ * fluid's gains added, step-major in particle-index order, into src[3][ncell]
+ * (momentum), msrc[ncell] (vapour mass) and esrc[ncell] (energy), each into
+ * the start-of-step cell (any may be NULL).  The cell deposit only.  Returns
+ * 0, or -1 on bad arguments. */
+int orc_micro_run(const orc_grid* G, const orc_micro* M, const double* U, const double* Tf, const double* rhov,
+                  int64_t n, double* pos, double* vel, double* d, double* Tp, int32_t nsteps, double dt,
+                  double* src, double* msrc, double* esrc);
 
 #ifdef __cplusplus
 }
