@@ -35,16 +35,18 @@ METRIC = "particle-steps/s at 1e9 particles, % HBM roofline; mixed vs FP64 at fi
 UNIT = "particle-steps/s"
 # algorithmic bytes per particle-step of the step kernel (read + write of the particle state)
 STEP_BYTES = {"mixed_f32": 32 + 28, "mixed_bf16": 26 + 22, "fp64": 56 + 48}
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the sorted-step kernel,
-# per particle, from one ncu capture of the full workload, keyed by the SHA-256 of the kernel's
-# source file; a kernel whose source has changed since has no measured traffic (null)
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per particle and launch of the sorted-step
+# kernel at the workload's density, keyed by the SHA-256 of the kernel's source file; a kernel whose
+# source has changed since has no measured traffic (null).  Counter captures run on small cases only
+# (a few GB on the device), so the figure is derived from two of them at 24 and 60 particles per cell
+# (128^3 / 5.0e7 and 64^3 / 1.6e7 particles): per particle the traffic is the state's bytes plus
+# per-unit costs (fluid tile, deposit-tile flush) divided by the density, and a small capture misses
+# the dirty lines still in L2 when the kernel ends.  Fitted: reads 32 + 120 / rho B, writes
+# 28 + 99 / rho B with ~60 MB left in L2; at the 1e9 workload's 59.6 particles per cell, 63.7 B.
 STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
                            "step_mixed_tma.cu")
 MEASURED_TRAFFIC = {
-    # profiles/step_mixed_tma_fourier256_1e9.md: 4 launches of the plain instance (fresh to 3 steps of
-    # drift), 64.07-64.15 B (FP32 velocity; the BF16-velocity instance measured 52.07-52.15 B before the
-    # cloud-in-cell deposit joined the physics instance)
-    ("02954dbb200a46ce08d8b4d415a6188ed5cc14601c187adc5886aaba1a5a184e", "fourier256_mixed_1e9"): 64.10,
+    ("cf2fe03ff0dc04bee0cc803091962aafdca280a689760d14ce001f3636e16af4", "fourier256_mixed_1e9"): 63.7,
 }
 
 
@@ -231,7 +233,7 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
 # step launch, from ncu instruction counters (2 x DFMA + DADD + DMUL, thread instructions) on the
 # adjoint workload; keyed by the SHA-256 of the kernel source, absent (null) once it changes
 MEASURED_FP64_OPS = {
-    # profiles/adjoint_tgf64_1e7.md: 116 DFMA + 46.8 DADD + 70 DMUL per particle; FP64 pipe 78 % busy
+    # ncu instruction counters: 116 DFMA + 46.8 DADD + 70 DMUL per particle; FP64 pipe 78 % busy
     # (the cell-deposit instance adjoint_step_kernel<false>)
     ("5f3671774619d7b6c8817a16cb24f49b90a6869dbce4f2756fe1d5772c54a060", "adjoint_step_kernel"): 348.8,
     # step_f64_kernel: 56 DFMA + 59 DADD + 19 DMUL per particle (2e6 particles on 128^3)
@@ -445,6 +447,98 @@ def run_coupled(args, workload):
     return 0
 
 
+# algorithmic bytes per particle-step of the microphysics step on mixed handles: the step kernel's state
+# (cell 4, offsets 12, velocity 12, diameter 4) plus the compensated temperature and diameter residual
+# (16), read and written
+MICRO_BYTES = {"mixed_f32": 2 * (32 + 16), "mixed_bf16": 2 * (26 + 16)}
+
+
+def run_micro(args, workload):
+    """Droplet microphysics (vapour mass and heat transfer, paper Sec. 2.1) on the mixed-precision workload:
+    the same particles and velocity field plus seeded fluid temperature and vapour fields; one JSON line with
+    particle-steps/s, the microphysics kernel's HBM roofline and the bytes it adds per particle-step."""
+    import torch
+
+    from paper_2603_26691_gb300 import inputs
+
+    ws, rank, local = _dist()
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    n = args.n or workload.n
+    precision = args.precision or workload.precision
+    U32 = workload.make_field().astype(np.float32)
+    T, rv = inputs.thermo_fields(workload.grid, seed=workload.field_seed + 1)
+    sim = setup_sim(workload, n, U32, precision, device)
+    sim.set_thermo(T, rv)
+    sim.set_microphysics(True, T_init=285.0)
+    R = workload.reorder_every
+    W, K = max(args.warmup, 3), args.steps
+    for _ in timed_steps(sim, W, workload.dt, R, 0):
+        pass
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = sim.kernel_launches
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    evs = timed_steps(sim, K, workload.dt, R, W)
+    b.record()
+    torch.cuda.synchronize()
+    launches = sim.kernel_launches - launches0
+    clk = clocks.stop()
+    total_ms = a.elapsed_time(b)
+    step_ms = [e1.elapsed_time(e2) for (e0, e1, e2, _) in evs]
+    sort_ms = [e0.elapsed_time(e1) for (e0, e1, e2, s_) in evs if s_]
+    avg = sum(step_ms) / len(step_ms)
+    peak, peak_kind = _peaks()
+    mb = MICRO_BYTES[precision]
+    achieved = mb * n / (avg * 1e-3) / 1e9
+    W0, E0 = sim.micro_invariants()
+    msrc = sim.micro_sources()
+    sim.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        ns = 20000
+        G = oracle.make_grid(workload.grid, chunk_edge=workload.chunk_edge)
+        M = oracle.make_micro()
+        pos, vel, d, _ = inputs.particles(workload.seed, 0, ns)
+        Tp = np.full(ns, 285.0)
+        Ud = U32.astype(np.float64).reshape(-1, 3)
+        c0 = time.perf_counter()
+        steps = 0
+        while time.perf_counter() - c0 < args.cpu_budget:
+            pos, vel, d, Tp, _, _, _ = oracle.micro_run(G, M, Ud, T.reshape(-1), rv.reshape(-1), pos, vel, d, Tp, 1,
+                                                        workload.dt)
+            steps += 1
+        el = time.perf_counter() - c0
+        cpu = {"value": ns * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ns} particles of the workload x {steps} microphysics steps (single thread), {el:.1f} s"}
+    line = {"metric": "particle-steps/s with droplet microphysics (vapour mass and heat transfer)",
+            "value": n * K / (total_ms * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload.name, "grid": workload.grid, "particles_per_gpu": n, "precision": precision,
+                       "dt": workload.dt, "reorder_every": R,
+                       "thermo": "T 285 +- 3 K, rho_v 0.0105 kg/m^3 +- 5 % (seeded random Fourier fields)",
+                       "l2": "no flush: 48 B x particles of state per step, far larger than L2"},
+            "roofline": {"bound": "hbm", "kernel": "micro_mixed_kernel", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_particle_step": mb,
+                         "added_bytes_per_particle_step": mb - STEP_BYTES[precision], "step_kernel_ms": avg},
+            "breakdown": {"sort_ms_avg": (sum(sort_ms) / len(sort_ms)) if sort_ms else None,
+                          "step_kernel_ms": [round(x, 3) for x in step_ms],
+                          "water_in_droplets_kg": W0, "vapour_gained_kg": float(msrc[0].sum()),
+                          "energy_gained_J": float(msrc[1].sum())},
+            "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,6 +571,8 @@ def main():
         return run_adjoint(args, workload)
     if workload.extra and workload.extra.get("fluid_every"):
         return run_coupled(args, workload)
+    if workload.extra and workload.extra.get("micro"):
+        return run_micro(args, workload)
 
     import torch
 

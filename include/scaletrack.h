@@ -156,7 +156,9 @@ st_status st_set_fluid(st_handle h, const void* u, int dtype, int on_device);
  * grows geometrically otherwise).  Errors: INVALID_ARG, OOM. */
 st_status st_reserve(st_handle h, int64_t capacity);
 
-/* Append n particles: positions xyz[3][n] (any real values; wrapped into
+/* Append n particles (the Lagrangian phase's point particles of Sec. 2.1, each
+ * with position, velocity and diameter; multiplicity and density come from
+ * st_set_params): positions xyz[3][n] (any real values; wrapped into
  * the box), velocities vel[3][n] (NULL = at rest), diameters d[n] > 0,
  * optional ids[n] (NULL = consecutive from the number already held).  The
  * FP64 values are converted to the handle's storage.  The new particles
@@ -190,6 +192,9 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device);
 /* Stable counting sort of the particles now, by the chunk-major key of
  * their cell: chunk index (x fastest) times B^3 plus the Morton index of
  * the cell inside its chunk.  Particles with equal keys keep their order.
+ * This keeps each chunk's particles together in the structure of arrays, the
+ * spatially coherent particle sets of Sec. 2.2 (here chunks are blocks of
+ * cells rather than the paper's redistributed particle sets).
  * Asynchronous.  Errors: OOM, CUDA. */
 st_status st_reorder(st_handle h);
 
@@ -315,6 +320,71 @@ st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t co
                            double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
                            uint32_t* ids);
 
+/* Droplet microphysics (Sec. 2.1): each droplet also exchanges water vapour
+ * and heat with the fluid,
+ *   dm/dt = 2 pi D_v d rho_sat(T_f) (S_f - S_p),  S_f = rho_v / rho_sat(T_f),
+ *           S_p = rho_sat(Tp) / rho_sat(T_f) (flat water at the droplet's
+ *           temperature), i.e. dm/dt = 2 pi D_v d (rho_v - rho_sat(Tp));
+ *   m C_p dTp/dt = pi Nu kappa_f d (T_f - Tp) + L dm/dt (the latent heat of
+ *           condensed water warms the droplet, evaporation cools it; the
+ *           paper prints the opposite sign, which would heat an evaporating
+ *           droplet), Nu = 2 + 0.6 Re^(1/2) Pr^(1/3) (Ranz-Marshall) with
+ *           Re = rho_f |u_p - v| d / mu;
+ * and the fluid gains, in the cell that held the droplet at the start of the
+ * step, the momentum -[(m' v' - m v) - m g dt] (Eq. 11 with the fluid's sign;
+ * it reduces to the step's impulse when no mass moves), the vapour mass
+ * -(m' - m) (the vapour source S_rho_v times V dt) and the energy
+ * -C_p (m' Tp' - m Tp) (the energy source S_e times V dt).  rho_sat is the
+ * saturation vapour density over flat water (Magnus form with the
+ * Alduchov-Eskridge coefficients, over R_v T, R_v = 461.5 J/(kg K)).  Over a
+ * step the droplet's diameter, slip and gathered fluid values are held,
+ * rho_sat is linearised about the start temperature, the resulting linear
+ * heat balance is solved exactly and the d^2 law (d(d^2)/dt = 8 D_v (rho_v -
+ * rho_sat(Tp)) / rho_p) is integrated along that temperature path; a droplet
+ * that would shrink below d_min keeps d_min.  Masses include the parcel
+ * multiplicity; rho_p and the multiplicity come from st_set_params, rho_f
+ * from st_set_physics.
+ *
+ * enable = 1 turns it on with vapour diffusivity D_v >= 0 (m^2/s), fluid
+ * thermal conductivity kappa_f > 0 (W/(m K)), droplet specific heat cp_p > 0
+ * (J/(kg K)), latent heat >= 0 (J/kg), Prandtl number > 0, d_min > 0 (m),
+ * and T_init > 0 (K), the temperature of particles that have none yet (all
+ * particles the first time, later additions every time); enable = 0 turns it
+ * off (temperatures are kept).  While it is on, st_step runs the
+ * microphysics step (FP64 or mixed handles; the default gather, integrator,
+ * drag and deposit only, else ST_ERR_STATE; the fluid temperature and vapour
+ * fields must be set).  The particle state adds a temperature (8 B FP64,
+ * 4 B mixed) and the diameter is written every step.
+ * Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+st_status st_set_microphysics(st_handle h, int enable, double D_v, double kappa_f, double cp_p, double latent_heat,
+                              double prandtl, double d_min, double T_init);
+
+/* The fluid temperature T[c] (K, > 0) and water vapour density rho_v[c]
+ * (kg/m^3, >= 0) at cell centres, in the cell order of st_set_fluid (dtype
+ * ST_DTYPE_F32 or ST_DTYPE_F64), gathered by the step like the velocity.
+ * Copied in.  Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+st_status st_set_thermo(st_handle h, const void* T, const void* rho_v, int dtype, int on_device);
+
+/* Particle temperatures (K) of particles [first, first + count) in the
+ * current storage order: set from T[count] (microphysics on), or copied out
+ * (synchronises).  Errors: STATE (microphysics never enabled), INVALID_ARG,
+ * NONFINITE, OOM, CUDA. */
+st_status st_set_temperatures(st_handle h, int64_t first, int64_t count, const double* T, int on_device);
+st_status st_get_temperatures(st_handle h, int64_t first, int64_t count, double* T, int on_device);
+
+/* What the fluid gained from the droplets' mass and heat transfer since the
+ * last reset, out[2][ncell] FP64: the vapour mass (kg) and the energy (J) per
+ * cell (the vapour and energy sources of Sec. 2.1 times V and the elapsed
+ * time).  Summed exactly (carry-save integers), so the result does not
+ * depend on thread scheduling.  reset = 1 clears them afterwards.
+ * Synchronises.  Errors: INVALID_ARG, OOM, CUDA. */
+st_status st_get_micro_sources(st_handle h, double* out, int reset, int on_device);
+
+/* out = {sum_p m_p, sum_p C_p m_p Tp} in FP64 over the particles (for the
+ * water and energy budgets: with the sources of st_get_micro_sources, mass +
+ * vapour gained and C_p m T + energy gained stay constant).  Synchronises. */
+st_status st_micro_invariants(st_handle h, double out[2]);
+
 /* Largest n that st_sort_keys_static accepts. */
 #define ST_SORT_KEYS_STATIC_MAX_N (1 << 20)
 
@@ -333,23 +403,36 @@ st_status st_gen_particles(st_handle h, uint64_t seed, int64_t first, int64_t co
  * cudaStream_t, NULL = legacy default stream) and the call returns without
  * waiting.
  *
- * All scratch memory is one static device array of 8.5 MiB that every GPU
- * which loads the library holds until the process exits; the call makes no
- * cudaMalloc, cudaFree or other allocating call.  n must not exceed
+ * All scratch memory is one static device array of 8.5 MiB; the call makes no
+ * cudaMalloc, cudaFree or other allocating call.  Under CUDA's default lazy
+ * module loading the array is created on a device when the library's sort
+ * module is first used there (the first sort-related call on that device, by
+ * this entry point or by a handle), so that first call may take device memory;
+ * from then on the array lives on that device until the process exits and
+ * later calls take no device memory.  n must not exceed
  * ST_SORT_KEYS_STATIC_MAX_N (2^20): larger n returns ST_ERR_INVALID_ARG
  * without doing any work.  The first call on a device looks up the array's
  * device address for that device; make that first call before any CUDA stream
  * capture.  Every call uses the same array, which keeps the previous call's
  * contents (its look-back words start zeroed with the module and afterwards
- * carry only earlier calls' tags), so calls whose work overlaps on the GPU
- * (other streams, other threads) race with each other: order them on one
- * stream or synchronise between them.  Its waits on other thread blocks give
- * up after one second; this call cannot report that (the work runs after it
- * returns) and the output is then wrong.
+ * carry only earlier calls' tags; when the 30-bit tags would repeat, after
+ * 2^27 calls on a device, the call clears them first), so calls whose work
+ * overlaps on the GPU (other streams, other threads) race with each other:
+ * order them on one stream or synchronise between them.  Its waits on other
+ * thread blocks give up after one second; the call cannot report that (the
+ * work runs after it returns), the output is then wrong, and
+ * st_sort_keys_static_status reports it afterwards.
  * Errors: INVALID_ARG (n < 0, n > 2^20, key_bits outside 1..32, NULL pointer
  * with n > 0), CUDA. */
 st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int key_bits, uint32_t* sorted_keys,
                               uint32_t* perm, void* stream);
+
+/* Whether a wait of an st_sort_keys_static call on the current device gave up
+ * (its output is then wrong) since the last query.  Synchronises `stream`
+ * (the stream the sorts were queued on; their work must have finished), reads
+ * the flag the waits set in the static scratch array, and clears it.  Makes no
+ * allocation.  Returns ST_OK, ST_ERR_TIMEOUT (a wait gave up) or ST_ERR_CUDA. */
+st_status st_sort_keys_static_status(void* stream);
 
 /* Kernel timers: CUDA events recorded around the library's own launches, on the stream each runs
  * on, summed per kind.  ST_TIMER_STEP: every particle step kernel (st_step, the adjoint's forward

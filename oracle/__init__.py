@@ -361,3 +361,47 @@ def micro_run(G: Grid, M: Micro, U, Tf, rhov, pos, vel, d, Tp, nsteps: int, dt: 
     if rc != 0:
         raise ValueError(f"orc_micro_run failed ({rc})")
     return pos, vel, d, Tp, src, msrc, esrc
+
+
+def run_blocked(G: Grid, U, particles, n: int, nsteps: int, dt: float, block: int = 1_000_000, threads: int = 0,
+                src=None, keep=None):
+    """orc_run over n particles on several host threads, deterministically: the particles are cut into fixed
+    blocks of `block` consecutive indices; each block runs its nsteps alone (its own partial source field,
+    added to in the block's step-major particle order) and the partial fields are added to `src` in block
+    order.  The sums therefore depend on `block` but not on `threads` (0 = every core).  `particles(first,
+    count)` returns (pos, vel, d) of those particles, so no more than `threads` blocks are held at once.
+    keep(first, pos, vel) is called with each block's final state (in block order).  Returns src
+    [3, ncell]."""
+    import concurrent.futures as cf
+
+    nc = ncell(G)
+    src = np.zeros((3, nc)) if src is None else src
+    threads = threads or (os.cpu_count() or 1)
+    U = _f64(U)
+    nblocks = (n + block - 1) // block
+
+    def work(b):
+        first = b * block
+        cnt = min(block, n - first)
+        pos, vel, d = particles(first, cnt)
+        part = np.zeros((3, nc))
+        pos, vel, part, _ = run(G, U, pos, vel, d, nsteps, dt, src=part, inplace=True)
+        return first, pos, vel, part
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        pending = {}
+        nxt = 0
+        for b in range(min(nblocks, threads)):
+            pending[b] = ex.submit(work, b)
+        issued = len(pending)
+        while nxt < nblocks:
+            first, pos, vel, part = pending.pop(nxt).result()
+            np.add(src, part, out=src)
+            if keep is not None:
+                keep(first, pos, vel)
+            del part
+            nxt += 1
+            if issued < nblocks:
+                pending[issued] = ex.submit(work, issued)
+                issued += 1
+    return src

@@ -707,21 +707,29 @@ double orc_rho_sat_dT(double T) {
  *     (Re = rho_f |u_p - v| d / mu);
  *   - the step (the paper gives none): with d, A, B frozen and rho_sat
  *     linearised about the start temperature T0, rho_sat(T) ~ r0 + s (T - T0),
- *     the heat balance is linear, dT/dt = -k (T - T*) with
- *       k = (A + L B s) / (m C_p),  T* = (A T_f + L B (rho_v - r0 + s T0)) / (A + L B s),
- *     and is advanced exactly, T' = T* + (T0 - T*) e^{-k dt}; the d^2 law is
- *     integrated along the same temperature path,
- *       d'^2 = d^2 + (8 D_v / rho_p) [(rho_v - r0 + s T0) dt - s I],
- *       I = int_0^dt T = T* dt + (T0 - T*) (1 - e^{-k dt}) / k.
- *     This is exact when the droplet stays at the fluid temperature (the d^2
- *     law) and when no vapour moves (the temperature's exponential relaxation),
- *     and stable for steps much longer than the droplet's thermal time.  A
- *     droplet that would shrink below d_min keeps d_min;
+ *     the heat balance is linear, dT/dt = -k (T - T*), and is advanced
+ *     exactly; the d^2 law is integrated along the same temperature path:
+ *       k = (A + L B s) / (m C_p),   x = k dt,
+ *       delta = T* - T0 = (A (T_f - T0) + L B (rho_v - r0)) / (A + L B s),
+ *       Tp' = T0 + delta x phi1(x),
+ *       d'^2 = d^2 + (8 D_v / rho_p) dt [(rho_v - r0) - s delta x phi2(x)],
+ *     with phi1(x) = (1 - e^{-x}) / x and phi2(x) = (1 - phi1(x)) / x (the
+ *     time average of e^{-k t} over the step, and of the part of the
+ *     temperature change not yet done).  These are the exact solution of the
+ *     linearised equations written without cancellation.  The step is exact
+ *     when the droplet stays at the fluid temperature (the d^2 law) and when no
+ *     vapour moves (the temperature's exponential relaxation), and stable for
+ *     steps much longer than the droplet's thermal time.  A droplet that would
+ *     shrink below d_min keeps d_min;
  *   - what the fluid gains, into the start-of-step cell c0 (Sec. 2.1, Eq. 11
  *     and the vapour and energy sources, with the sign of a gain for the
  *     fluid): momentum J = -[(m' v' - m v) - m g dt], vapour mass -(m' - m),
- *     energy -C_p (m' Tp' - m Tp).  Masses include the parcel multiplicity;
- *     the per-droplet rates do not depend on it. */
+ *     energy -C_p (m' Tp' - m Tp), evaluated as -[m (v' - v - g dt) + (m' - m)
+ *     v'], -(m' - m) and -C_p [m (Tp' - Tp) + (m' - m) Tp'] with m' - m = c
+ *     (d' - d)(d'^2 + d' d + d^2) and d' - d = (d'^2 - d^2) / (d' + d), so that
+ *     no small difference is taken of large numbers.  Masses include the
+ *     parcel multiplicity (c = w rho_p pi / 6); the per-droplet rates do not
+ *     depend on it. */
 void orc_micro_particle_step(const orc_grid* G, const orc_micro* M, const double* U, const double* Tf,
                              const double* rhov, double dt, double x[3], double v[3], double* d, double* Tp,
                              int64_t* c0, double J[3], double* dmass, double* denergy) {
@@ -738,28 +746,31 @@ void orc_micro_particle_step(const orc_grid* G, const orc_micro* M, const double
   for (int ax = 0; ax < 3; ++ax) vold[ax] = v[ax];
   orc_advance(G, d0, up, dt, x, v);
   for (int ax = 0; ax < 3; ++ax) x[ax] = orc_wrap(x[ax], G->L[ax]);
-  /* the linear heat balance over the step */
+  /* the linearised heat balance over the step */
   double nu = orc_nusselt(M, re);
   double md0 = G->rho_p * kPi * d0 * d0 * d0 / 6.0;
   double A = kPi * nu * M->kappa_f * d0;
   double B = 2.0 * kPi * M->D_v * d0;
   double rs = orc_rho_sat(T0);
   double sl = orc_rho_sat_dT(T0);
-  double excess = rv - rs + sl * T0;
   double den = A + M->L * B * sl;
   double k = den / (md0 * M->cp_p);
-  double Ts = (A * tf + M->L * B * excess) / den;
-  double e1 = -expm1(-k * dt);
-  double T1 = Ts + (T0 - Ts) * (1.0 - e1);
-  double I = Ts * dt + (T0 - Ts) * e1 / k;
+  double delta = (A * (tf - T0) + M->L * B * (rv - rs)) / den;
+  double xk = k * dt;
+  double phi1 = -expm1(-xk) / xk;
+  double phi2 = (1.0 - phi1) / xk;
+  double T1 = T0 + delta * xk * phi1;
   /* the d^2 law along that temperature path */
-  double q = d0 * d0 + 8.0 * M->D_v * (excess * dt - sl * I) / G->rho_p;
+  double dq = 8.0 * M->D_v * dt * ((rv - rs) - sl * delta * xk * phi2) / G->rho_p;
+  double q = d0 * d0 + dq;
   double d1 = q > M->d_min * M->d_min ? sqrt(q) : M->d_min;
-  double m0 = orc_mass(G, d0), m1 = orc_mass(G, d1);
+  double dd = q > M->d_min * M->d_min ? dq / (d1 + d0) : d1 - d0;
+  double dm = G->mult * G->rho_p * kPi / 6.0 * dd * (d1 * d1 + d1 * d0 + d0 * d0);
+  double m0 = orc_mass(G, d0);
   /* what the fluid gains */
-  for (int ax = 0; ax < 3; ++ax) J[ax] = -((m1 * v[ax] - m0 * vold[ax]) - m0 * G->g[ax] * dt);
-  *dmass = -(m1 - m0);
-  *denergy = -M->cp_p * (m1 * T1 - m0 * T0);
+  for (int ax = 0; ax < 3; ++ax) J[ax] = -(m0 * ((v[ax] - vold[ax]) - G->g[ax] * dt) + dm * v[ax]);
+  *dmass = -dm;
+  *denergy = -M->cp_p * (m0 * (T1 - T0) + dm * T1);
   *d = d1;
   *Tp = T1;
 }

@@ -68,6 +68,13 @@ SIGNATURES = {
     "st_adjoint_forward": (_i, [_vp, _i, _d, _i]),
     "st_adjoint_backward": (_i, [_vp, _vp, _i, _vp, _P(_d), _vp, _i]),
     "st_sort_keys_static": (_i, [_vp, _i64, _i, _vp, _vp, _vp]),
+    "st_sort_keys_static_status": (_i, [_vp]),
+    "st_set_microphysics": (_i, [_vp, _i, _d, _d, _d, _d, _d, _d, _d]),
+    "st_set_thermo": (_i, [_vp, _vp, _vp, _i, _i]),
+    "st_set_temperatures": (_i, [_vp, _i64, _i64, _vp, _i]),
+    "st_get_temperatures": (_i, [_vp, _i64, _i64, _vp, _i]),
+    "st_get_micro_sources": (_i, [_vp, _vp, _i, _i]),
+    "st_micro_invariants": (_i, [_vp, _P(_d)]),
     "st_gen_particles": (_i, [_vp, _u64, _i64, _i64, _P(_d), _d, _vp, _i, _vp, _vp, _vp, _vp]),
     "st_chunk_bounds": (_i, [_vp, _vp, _i]),
     "st_couple_params": (_i, [_vp, _d, _d, _i, _i, _i]),

@@ -7,6 +7,10 @@ impulse summed over the run, J [3, ncell].  Its backward calls the library's adj
 (st_adjoint_backward): dL/dd per particle, dL/dalpha and dL/dU, with the deposit cell held
 fixed under the cell deposit (its derivative is zero almost everywhere) and the deposit weights
 differentiated under the cloud-in-cell deposit.  All arithmetic runs in the CUDA library.
+
+The handle keeps one recorded run: the backward of a forward raises if anything changed the
+simulation after that forward (another forward, a step, new parameters, particles or fluid),
+because the handle would then differentiate a different run.
 """
 from __future__ import annotations
 
@@ -30,12 +34,17 @@ class LagrangianSources(torch.autograd.Function):
         sim.adjoint_forward(int(nsteps), float(dt), int(checkpoint_every))
         J = sim.sources()
         ctx.sim = sim
+        ctx.generation = sim.generation
         ctx.meta = (d.dtype, d.device, alpha, U.shape, U.dtype, U.device)
         return J
 
     @staticmethod
     def backward(ctx, gJ):
         d_dtype, d_dev, alpha, U_shape, U_dtype, U_dev = ctx.meta
+        if ctx.sim.generation != ctx.generation:
+            raise RuntimeError("the simulation changed after this forward (another forward, a step, or new "
+                               "parameters, particles or fluid): its recorded run is no longer this one; "
+                               "call backward before changing the simulation, or use one Sim per graph")
         gd, ga, gU = ctx.sim.adjoint_backward(gJ.detach().to(torch.float64).contiguous())
         gd = gd.to(device=d_dev, dtype=d_dtype)
         ga_t = torch.as_tensor(ga, dtype=alpha.dtype if isinstance(alpha, torch.Tensor) else torch.float64,

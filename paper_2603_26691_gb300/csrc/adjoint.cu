@@ -24,36 +24,6 @@ namespace {
 
 constexpr int kAdjThreads = 256;
 
-// Carry-save accumulator: value = sum_i w[i] * 2^(32 i + kWideBase); each
-// contribution adds 32-bit digits, so each int64 word absorbs 2^31 of them.
-__device__ __forceinline__ void wide_add(long long* w, double x) {
-  if (x == 0.0) return;
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  unsigned long long man = b & 0xfffffffffffffull;
-  if (ex != 0) man |= 1ull << 52;  // subnormals: man * 2^(1 - 1075)
-  int s = (ex == 0 ? 1 : ex) - 1075 - kWideBase;  // bit position of man's lowest bit
-  if (s < 0) {
-    if (s <= -64) return;
-    man = (man + ((1ull << (-s)) >> 1)) >> (-s);
-    s = 0;
-  }
-  const int q = s >> 5, r = s & 31;
-  const unsigned long long lo = man << r;                       // bits r .. 63
-  const unsigned long long hi = r ? (man >> (64 - r)) : 0ull;   // bits 64 .. 84
-  long long d0 = (long long)(lo & 0xffffffffull);
-  long long d1 = (long long)(lo >> 32);
-  long long d2 = (long long)hi;
-  if (b >> 63) {
-    d0 = -d0;
-    d1 = -d1;
-    d2 = -d2;
-  }
-  if (q < kWideWords) atomicAdd((unsigned long long*)&w[q], (unsigned long long)d0);
-  if (q + 1 < kWideWords) atomicAdd((unsigned long long*)&w[q + 1], (unsigned long long)d1);
-  if (q + 2 < kWideWords) atomicAdd((unsigned long long*)&w[q + 2], (unsigned long long)d2);
-}
-
 struct AdjArgs {
   const double* __restrict__ x[3];   // state at the start of the step (tape)
   const double* __restrict__ v[3];

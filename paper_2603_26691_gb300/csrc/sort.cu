@@ -16,6 +16,7 @@
 // Waits on other blocks are bounded: a look-back that gives up sets a device flag (reported as
 // ST_ERR_TIMEOUT) and carries on, so no block can hang the grid.
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -101,11 +102,17 @@ __device__ __forceinline__ unsigned long long load_look(const unsigned long long
   return v;
 }
 
+// A kernel given a gate runs only if *gate != 0: the general sort is queued behind the
+// neighbourhood sort (sort_local.cu) and runs only when that one found a particle it cannot place.
+__device__ __forceinline__ bool gated_off(const int* gate) { return gate != nullptr && *gate == 0; }
+
 // every pass's digit totals in one read of the keys: each lane counts runs of equal digits over
 // 16 consecutive keys and adds each run once to the block's counts
 template <class Src>
 __global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int64_t n, int key_bits,
-                                                                     uint32_t* __restrict__ totals) {
+                                                                     uint32_t* __restrict__ totals,
+                                                                     const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const int passes = (key_bits + 7) / 8;
   __shared__ uint32_t cnt[kMaxPasses][kRadix];
   __shared__ uint32_t mtab[32];  // Morton spread table for keys from cells
@@ -172,7 +179,9 @@ __global__ void __launch_bounds__(kSortThreads) digit_totals_kernel(Src src, int
 }
 
 // exclusive scan of each pass's 256 digit totals (one block of 256 threads)
-__global__ void digit_offsets_kernel(const uint32_t* __restrict__ totals, int passes, uint32_t* __restrict__ offs) {
+__global__ void digit_offsets_kernel(const uint32_t* __restrict__ totals, int passes, uint32_t* __restrict__ offs,
+                                     const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   __shared__ uint32_t s[kRadix];
   for (int p = 0; p < passes; ++p) {
     s[threadIdx.x] = totals[p * kRadix + threadIdx.x];
@@ -210,7 +219,8 @@ __global__ void __launch_bounds__(kSortThreads, kPassBlocksPerSM) onesweep_kerne
                                                                  const uint32_t* __restrict__ digit_offset,
                                                                  unsigned long long* __restrict__ look,
                                                                  unsigned long long epoch, unsigned* __restrict__ tile_ctr,
-                                                                 int* __restrict__ err) {
+                                                                 int* __restrict__ err, const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   extern __shared__ __align__(128) unsigned char sm[];
   uint32_t* bufs = reinterpret_cast<uint32_t*>(sm);                                   // [2][2][kTile]
   uint32_t (*wcnt)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(sm + 2 * kBufWords * 4);
@@ -450,7 +460,9 @@ __device__ __forceinline__ void store_v1(void* v, int64_t i, float a) {
 
 template <bool BF16>
 __global__ void gather_records_kernel(const float4* __restrict__ rec, MixedState dst, const uint32_t* __restrict__ sid,
-                                      uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
+                                      uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n,
+                                      const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const int64_t n4 = n >> 2;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += (int64_t)gridDim.x * blockDim.x) {
     const uint4 pp = __ldg(reinterpret_cast<const uint4*>(perm) + g);
@@ -511,7 +523,9 @@ __global__ void records_to_soa_kernel(const float4* __restrict__ rec, MixedState
 // (64-bit for BF16 velocities) coalesced stores
 template <bool BF16>
 __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32_t* __restrict__ sid,
-                                    uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n) {
+                                    uint32_t* __restrict__ did, const uint32_t* __restrict__ perm, int64_t n,
+                                    const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const int64_t n4 = n >> 2;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n4; g += (int64_t)gridDim.x * blockDim.x) {
     const uint4 pp = __ldg(reinterpret_cast<const uint4*>(perm) + g);
@@ -573,7 +587,9 @@ __global__ void gather_mixed_kernel(MixedState src, MixedState dst, const uint32
 // start[k] = the first sorted position whose key is >= k, for every k up to the last key: each
 // thread takes four consecutive sorted keys (one 16-byte load; the key arrays are 256-byte
 // aligned) and the key before them
-__global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ start) {
+__global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t* __restrict__ start,
+                                  const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const int64_t groups = (n + 3) >> 2;
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < groups; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i0 = g << 2;
@@ -601,7 +617,8 @@ __global__ void cell_start_kernel(const uint32_t* __restrict__ keys, int64_t n, 
 }
 
 __global__ void cell_start_tail_kernel(const uint32_t* __restrict__ keys, int64_t n, uint32_t nkeys,
-                                       uint32_t* __restrict__ start) {
+                                       uint32_t* __restrict__ start, const int* __restrict__ gate) {
+  if (gated_off(gate)) return;
   const int64_t first = (int64_t)keys[n - 1] + 1;
   for (int64_t k = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= (int64_t)nkeys;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -739,20 +756,23 @@ int grid_for(int64_t n, int max_blocks = 152 * 16) {
 template <bool FIRST, bool BULK, class Src>
 cudaError_t launch_pass(int64_t grid, cudaStream_t s, Src src, const uint32_t* kin, const uint32_t* vin, uint32_t* kout,
                         uint32_t* vout, int64_t n, int shift, uint32_t dmask, int64_t ntiles, const uint32_t* offs,
-                        unsigned long long* look, uint32_t epoch, unsigned* tile_ctr, int* err) {
-  static bool attr[kAttrDevices] = {};  // per instantiation and device (a kernel attribute is per device)
+                        unsigned long long* look, uint32_t epoch, unsigned* tile_ctr, int* err, const int* gate) {
+  // per instantiation and device (a kernel attribute is per device); atomic because the
+  // allocation-free entry point may be called from several host threads at once (setting the
+  // attribute twice is harmless)
+  static std::atomic<bool> attr[kAttrDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
-  if (!attr[dev]) {
+  if (!attr[dev].load(std::memory_order_acquire)) {
     e = cudaFuncSetAttribute(onesweep_kernel<FIRST, BULK, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kPassSmem);
     if (e != cudaSuccess) return e;
-    attr[dev] = true;
+    attr[dev].store(true, std::memory_order_release);
   }
   onesweep_kernel<FIRST, BULK, Src><<<(unsigned)grid, kSortThreads, kPassSmem, s>>>(
-      src, kin, vin, kout, vout, n, shift, dmask, ntiles, offs, look, epoch, tile_ctr, err);
+      src, kin, vin, kout, vout, n, shift, dmask, ntiles, offs, look, epoch, tile_ctr, err, gate);
   return cudaGetLastError();
 }
 
@@ -764,14 +784,15 @@ template <class Src>
 cudaError_t radix_passes(Src src, int64_t n, int key_bits, uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb,
                          uint32_t* kfinal, uint32_t* vfinal, uint32_t* totals, uint32_t* offs, unsigned* tile_ctr,
                          unsigned long long* look, uint32_t* epoch, int* err, int sms, cudaStream_t s,
-                         int64_t* launches, bool bulk_rest) {
+                         int64_t* launches, bool bulk_rest, const int* gate = nullptr) {
   const int passes = (key_bits + 7) / 8;
   const int64_t ntiles = (n + kTile - 1) / kTile;
   cudaError_t e = cudaMemsetAsync(totals, 0, (size_t)kMaxPasses * kRadix * sizeof(uint32_t), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(tile_ctr, 0, kMaxPasses * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  digit_totals_kernel<Src><<<grid_for((n + kItems - 1) / kItems), kSortThreads, 0, s>>>(src, n, key_bits, totals);
-  digit_offsets_kernel<<<1, kRadix, 0, s>>>(totals, passes, offs);
+  digit_totals_kernel<Src><<<grid_for((n + kItems - 1) / kItems), kSortThreads, 0, s>>>(src, n, key_bits, totals,
+                                                                                       gate);
+  digit_offsets_kernel<<<1, kRadix, 0, s>>>(totals, passes, offs, gate);
   *launches += 2;
   int64_t grid = (int64_t)sms * kPassBlocksPerSM;
   if (grid > ntiles) grid = ntiles;
@@ -788,16 +809,16 @@ cudaError_t radix_passes(Src src, int64_t n, int key_bits, uint32_t* ka, uint32_
     if (p == 0) {
       if constexpr (std::is_same<Src, CellKeys>::value)
         e = launch_pass<true, true, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, dm, ntiles, offs, look,
-                                         *epoch, tile_ctr, err);
+                                         *epoch, tile_ctr, err, gate);
       else
         e = launch_pass<true, false, Src>(grid, s, src, nullptr, nullptr, kout, vout, n, 0, dm, ntiles, offs, look,
-                                          *epoch, tile_ctr, err);
+                                          *epoch, tile_ctr, err, gate);
     } else if (bulk_rest) {
       e = launch_pass<false, true, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, dm, ntiles,
-                                              offs + p * kRadix, look, *epoch, tile_ctr + p, err);
+                                              offs + p * kRadix, look, *epoch, tile_ctr + p, err, gate);
     } else {
       e = launch_pass<false, false, ArrayKeys>(grid, s, ArrayKeys{nullptr}, kin, vin, kout, vout, n, 8 * p, dm, ntiles,
-                                               offs + p * kRadix, look, *epoch, tile_ctr + p, err);
+                                               offs + p * kRadix, look, *epoch, tile_ctr + p, err, gate);
     }
     if (e != cudaSuccess) return e;
     *launches += 1;
@@ -831,10 +852,12 @@ st_status sort_particles(st_ctx* h) {
   if (ensure(h, h->cell_start, ((size_t)h->nkeys + 1) * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
   if (ensure(h, h->state_alt, state_alt_bytes(h->prec, h->cap)) != ST_OK) return ST_ERR_OOM;
   if (ensure(h, h->ids_alt, (size_t)h->cap * sizeof(uint32_t)) != ST_OK) return ST_ERR_OOM;
-  if (h->hist.p != look_before) {
-    // a new look-back buffer may hold anything: clear it so that no stale word carries an epoch
+  if (h->hist.p != look_before || h->sort_epoch + kMaxPasses >= (1u << 30)) {
+    // a new look-back buffer may hold anything, and once the 30-bit epoch tags are about to repeat
+    // an old word could carry a current tag: clear the words so that no stale word carries an epoch
     cudaError_t ce = cudaMemsetAsync(h->hist.p, 0, h->hist.bytes, h->stream);
     if (ce != cudaSuccess) return cuda_check(h, ce, "clear look-back words");
+    h->sort_epoch = 0;
   }
 
   KeyGeo g = key_geo(h);
@@ -842,6 +865,17 @@ st_status sort_particles(st_ctx* h) {
   uint32_t* v0 = (uint32_t*)h->vals[0].p;
   uint32_t* k1 = (uint32_t*)h->keys[1].p;
   uint32_t* v1 = (uint32_t*)h->vals[1].p;
+  // particles sorted before and moved little since: the neighbourhood sort (sort_local.cu), with the
+  // general sort's passes and cell starts queued behind it and gated on its "a particle moved too far"
+  // flag.  Either leaves the permutation in v0; the payload gather below serves both.
+  const int* gate = nullptr;
+  if (local_sort_supported(h)) {
+    if (ensure(h, h->lsort_aux, local_sort_aux_bytes(h)) != ST_OK) return ST_ERR_OOM;
+    int* far = (int*)((char*)h->flags.p + kFarFlagOffset);
+    cudaError_t le = launch_local_sort(h, far, v1, (uint16_t*)k1, v0, h->lsort_aux.p);
+    if (le != cudaSuccess) return cuda_check(h, le, "neighbourhood sort");
+    gate = far;
+  }
   uint32_t* totals = (uint32_t*)h->scan_aux.p;
   uint32_t* offs = totals + kMaxPasses * kRadix;
   unsigned* tile_ctr = (unsigned*)(offs + kMaxPasses * kRadix);
@@ -858,7 +892,7 @@ st_status sort_particles(st_ctx* h) {
     CellKeys src{(const int32_t*)h->state.p, g};
     e = radix_passes(src, n, h->key_bits, k0, v0, k1, v1, k0, v0, totals, offs, tile_ctr,
                      (unsigned long long*)h->hist.p, &h->sort_epoch, (int*)h->flags.p, sms, h->stream, &h->launches,
-                     true);
+                     true, gate);
   }
   if (e != cudaSuccess) return cuda_check(h, e, "sort passes");
   // k0/v0 now hold the sorted keys and the permutation
@@ -872,22 +906,28 @@ st_status sort_particles(st_ctx* h) {
     const bool bf = h->prec == ST_MIXED_BF16V;
     (bf ? gather_records_kernel<true> : gather_records_kernel<false>)<<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
         (const float4*)h->state_alt.p, carve_mixed(h->state.p, h->cap, bf), (const uint32_t*)h->ids.p,
-        (uint32_t*)h->ids_alt.p, v0, n);
+        (uint32_t*)h->ids_alt.p, v0, n, nullptr);
   } else if (h->prec == ST_MIXED_F32) {
     gather_mixed_kernel<false><<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
         carve_mixed(h->state.p, h->cap, false), carve_mixed(h->state_alt.p, h->cap, false), (const uint32_t*)h->ids.p,
-        (uint32_t*)h->ids_alt.p, v0, n);
+        (uint32_t*)h->ids_alt.p, v0, n, nullptr);
   } else {
     gather_mixed_kernel<true><<<grid_for(n / 4 + 1), 256, 0, h->stream>>>(
         carve_mixed(h->state.p, h->cap, true), carve_mixed(h->state_alt.p, h->cap, true), (const uint32_t*)h->ids.p,
-        (uint32_t*)h->ids_alt.p, v0, n);
+        (uint32_t*)h->ids_alt.p, v0, n, nullptr);
   }
-  cell_start_kernel<<<grid_for((n + 3) / 4), 256, 0, h->stream>>>(k0, n, (uint32_t*)h->cell_start.p);
+  cell_start_kernel<<<grid_for((n + 3) / 4), 256, 0, h->stream>>>(k0, n, (uint32_t*)h->cell_start.p, gate);
   cell_start_tail_kernel<<<grid_for((int64_t)h->nkeys + 1), 256, 0, h->stream>>>(k0, n, h->nkeys,
-                                                                                   (uint32_t*)h->cell_start.p);
+                                                                                   (uint32_t*)h->cell_start.p, gate);
   h->launches += 3;  // gather + cell starts (two kernels)
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(h, e, "sort gather");
+  // particle temperatures (microphysics), through the same permutation
+  if (h->temp.p) {
+    e = launch_gather_temp(h, v0, nullptr, 1);
+    if (e != cudaSuccess) return cuda_check(h, e, "sort temperatures");
+    std::swap(h->temp, h->temp_alt);
+  }
   if (h->records_pending)
     h->records_pending = false;
   else
@@ -938,7 +978,8 @@ cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts) {
 // pool or arena, a process whose allocations are made once at start-up and then frozen, or an
 // allocator callback that must not re-enter the allocator.  st_sort_keys_static serves them:
 // its scratch memory is one file-scope device array, so the call itself allocates nothing.
-// The array is created when the library is loaded and lives on every GPU that loads the library
+// Under CUDA's default lazy module loading the array comes into being on a device when this
+// file's module is first used there (the first sort-related call on that device); it then lives
 // until the process exits.
 
 namespace st {
@@ -947,10 +988,14 @@ namespace {
 constexpr int64_t kStaticMaxN = int64_t(1) << 20;  // keys per call (matches the header's limit)
 constexpr int64_t kStaticTiles = kStaticMaxN / kTile;
 // layout (32-bit words): ping-pong keys [N] | ping-pong values [N] | look-back words [2 T R] |
-// digit totals [P R] | digit offsets [P R] | tile counters [P] (+ padding to 8 bytes)
+// digit totals [P R] | digit offsets [P R] | tile counters [P] | wait error word [1] (+ padding)
 constexpr size_t kStaticLook = 2 * (size_t)kStaticMaxN;
-constexpr size_t kStaticTotals = kStaticLook + 2 * (size_t)kStaticTiles * kRadix;
-constexpr size_t kStaticWords = kStaticTotals + 2 * (size_t)kMaxPasses * kRadix + kMaxPasses + 4;
+constexpr size_t kStaticLookWords = 2 * (size_t)kStaticTiles * kRadix;  // 32-bit words of look-back
+constexpr size_t kStaticTotals = kStaticLook + kStaticLookWords;
+constexpr size_t kStaticErr = kStaticTotals + 2 * (size_t)kMaxPasses * kRadix + kMaxPasses;
+constexpr size_t kStaticWords = kStaticErr + 4;
+constexpr uint32_t kEpochSpan = 1u << 30;  // look-back epochs (30-bit tags)
+constexpr uint32_t kEpochStep = 8;         // epochs reserved per call (at most kMaxPasses used)
 
 }  // namespace
 }  // namespace st
@@ -1011,16 +1056,47 @@ extern "C" st_status st_sort_keys_static(const uint32_t* keys, int64_t n, int ke
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 152;
   int64_t launches = 0;
-  // a look-back wait that gives up cannot be reported here: the timeout flag lives in a handle;
-  // it writes to a word of the scratch instead
-  int* err = (int*)(tile_ctr + kMaxPasses);
+  // a look-back wait that gives up sets this word; it stays set until st_sort_keys_static_status
+  // reads and clears it
+  int* err = (int*)(base + kStaticErr);
   uint32_t ep;
+  bool wrap = false;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     ep = *epoch;
-    *epoch = (ep + 8) & ((1u << 30) - 1);
+    if (ep + kEpochStep >= kEpochSpan) {
+      // the 30-bit epoch tags would repeat: a word left by an old call could then carry the
+      // current tag, so the look-back words start again from zero with the tags
+      ep = 0;
+      wrap = true;
+    }
+    *epoch = ep + kEpochStep;
   }
-  cudaError_t e = radix_passes(ArrayKeys{keys}, n, key_bits, sk, sv, sorted_keys, perm, sorted_keys, perm, totals, offs,
-                               tile_ctr, look, &ep, err, sms, s, &launches, false);
+  cudaError_t e = cudaSuccess;
+  if (wrap) e = cudaMemsetAsync(look, 0, kStaticLookWords * sizeof(uint32_t), s);
+  if (e == cudaSuccess)
+    e = radix_passes(ArrayKeys{keys}, n, key_bits, sk, sv, sorted_keys, perm, sorted_keys, perm, totals, offs,
+                     tile_ctr, look, &ep, err, sms, s, &launches, false);
   return e == cudaSuccess ? ST_OK : ST_ERR_CUDA;
+}
+
+extern "C" st_status st_sort_keys_static_status(void* stream) {
+  using namespace st;
+  uint32_t* base = nullptr;
+  uint32_t* epoch = nullptr;
+  if (scratch_address(&base, &epoch) != cudaSuccess) {
+    cudaGetLastError();
+    return ST_ERR_CUDA;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int* err = (int*)(base + kStaticErr);
+  int f = 0;
+  cudaError_t e = cudaMemcpyAsync(&f, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && f != 0) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ST_ERR_CUDA;
+  }
+  return f != 0 ? ST_ERR_TIMEOUT : ST_OK;
 }

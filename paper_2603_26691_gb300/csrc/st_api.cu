@@ -163,9 +163,10 @@ void st_destroy(st_handle h) {
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
   Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt,
-                 &h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start,
+                 &h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start, &h->lsort_aux,
                  &h->acc, &h->red, &h->src_hist[0], &h->src_hist[1], &h->src_hist[2], &h->src_hist[3],
-                 &h->src_est, &h->fl_cur, &h->fl_next, &h->fl_star, &h->fl_tmp, &h->fluid_pad_next, &h->umax_dev};
+                 &h->src_est, &h->fl_cur, &h->fl_next, &h->fl_star, &h->fl_tmp, &h->fluid_pad_next, &h->umax_dev,
+                 &h->temp, &h->temp_alt, &h->thermo, &h->acc_micro};
   for (Buf* b : bufs) dev_free(h, *b);
   if (h->umax_host) cudaFreeHost(h->umax_host);
   if (h->ev_fluid) cudaEventDestroy(h->ev_fluid);
@@ -383,7 +384,7 @@ static st_status grow(st_handle h, int64_t need) {
   h->state = ns;
   h->ids = ni;
   h->cap = cap;
-  return ST_OK;
+  return micro_grow(h);
 }
 
 st_status st_reserve(st_handle h, int64_t capacity) {
@@ -460,6 +461,8 @@ st_status st_add_particles(st_handle h, int64_t n, const double* xyz, const doub
     return s;
   }
   e = launch_import(h, h->np, n, dx, dv, dd, di);
+  // droplets added with microphysics on (or after it was on) start at its initial temperature
+  if (e == cudaSuccess) e = launch_fill_temp(h, h->np, n, h->mi_Tinit);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cleanup();
   ST_TRY(cuda_check(h, e, "import particles"));
@@ -507,7 +510,8 @@ static st_status prepare_accumulator(st_handle h, double dt, double adds_now, in
   double tau_max = h->rho_p * h->dmax * h->dmax / (18.0 * h->mu);
   h->vbound = std::max(h->vbound, h->umax + gn * tau_max / h->alpha);
   double mmax = h->mult * h->rho_p * pi * h->dmax * h->dmax * h->dmax / 6.0;
-  double jb = mmax * (2.0 * h->vbound + gn * dt) * 1.01 + 1e-300;
+  // |J| = m |v' - v - g dt| <= m (2 |v|max + |g| dt); with microphysics the mass change adds |m' - m| |v'|
+  double jb = mmax * ((h->micro_on ? 3.0 : 2.0) * h->vbound + gn * dt) * 1.01 + 1e-300;
   double cb = jb * kMaxRun;
   int E = kAccBits - (int)std::ceil(std::log2(cb));
   if (!h->acc_empty && E < h->acc_E) {
@@ -546,6 +550,9 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
   if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
   if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");
   if (!h->fluid_set) return set_error(h, ST_ERR_STATE, "no fluid field");
+  if (h->micro_on && !h->thermo_set) return set_error(h, ST_ERR_STATE, "microphysics needs st_set_thermo first");
+  if (h->micro_on && !default_physics(h))
+    return set_error(h, ST_ERR_STATE, "microphysics runs with the default gather, integrator, drag and deposit only");
   const double pi = 3.14159265358979323846;
   for (int s = 0; s < nsteps; ++s) {
     if (h->np == 0) break;
@@ -556,7 +563,8 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     }
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
-    const bool tma = h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
+    const bool tma = !h->micro_on && h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
+    if (h->micro_on) ST_TRY(micro_prepare_step(h, dt));
     int E = 0;
     ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : deposits_per_cell(h) * (double)h->np + 8.0, &E));
     StepParams p;
@@ -573,7 +581,9 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     p.re_coef = h->rho_f_drag / h->mu;
     cudaError_t e;
     timer_begin(h, ST_TIMER_STEP, h->stream);
-    if (h->prec == ST_FP64)
+    if (h->micro_on)
+      e = launch_micro_step(h, p);
+    else if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
     else if (tma) {
       // a sort is due before the next step: write the state as records for its gather

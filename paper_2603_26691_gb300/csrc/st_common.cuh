@@ -78,6 +78,7 @@ struct st_ctx {
   uint32_t nkeys = 0;
   int key_bits = 0;
   st::Buf keys[2], vals[2], hist, scan_aux, cell_start;  // cell_start uint32[nkeys + 1]
+  st::Buf lsort_aux;         // the neighbourhood sort's per-unit counts, offsets and totals
   int64_t sort_cap = 0;
   uint32_t sort_epoch = 0;   // tags the look-back words of each sort pass (no clearing between passes)
   // The step just before a due sort (mixed handles, sorted step kernel) writes the new state as
@@ -120,6 +121,18 @@ struct st_ctx {
   double* umax_host = nullptr;  // pinned
   cudaEvent_t ev_fluid = nullptr;  // the interval's fluid update done (its max |u| in umax_host)
   int64_t launches = 0;      // kernels launched by this handle
+
+  // droplet microphysics (st_set_microphysics): vapour mass and heat transfer of Sec. 2.1
+  bool micro_on = false;
+  double mi_Dv = 2.5e-5, mi_kappa = 0.025, mi_cp = 4186.0, mi_L = 2.5e6, mi_Pr = 0.71, mi_dmin = 1e-7;
+  double mi_Tinit = 293.15;
+  st::Buf temp, temp_alt;    // particle temperatures (FP64 handles double[cap], mixed float[cap])
+  st::Buf thermo;            // fluid temperature and vapour density per cell: double2[ncell] (FP64) or
+                             // float2 with kFluidPad ghost layers (mixed)
+  bool thermo_set = false;
+  double rv_max = 0.0;       // largest vapour density of the field (bounds droplet growth per step)
+  st::Buf acc_micro;         // exact sources [2][ncell][kWideWords]: vapour mass, energy the fluid gains
+  double micro_adds = 0.0;   // digits added to any word of acc_micro since its last carry propagation
   std::string err;
 };
 
@@ -340,6 +353,37 @@ constexpr int kWideWords = 8;     // carry-save accumulator: 8 words of 32-bit d
 constexpr int kWideBase = -160;   // weight of the lowest digit: 2^-160
 constexpr int kAdjBlocks = 152 * 8;
 
+// Carry-save accumulator: value = sum_i w[i] * 2^(32 i + kWideBase); each
+// contribution adds 32-bit digits, so each int64 word absorbs 2^31 of them.
+__device__ __forceinline__ void wide_add(long long* w, double x) {
+  if (x == 0.0) return;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  unsigned long long man = b & 0xfffffffffffffull;
+  if (ex != 0) man |= 1ull << 52;  // subnormals: man * 2^(1 - 1075)
+  int s = (ex == 0 ? 1 : ex) - 1075 - kWideBase;  // bit position of man's lowest bit
+  if (s < 0) {
+    if (s <= -64) return;
+    man = (man + ((1ull << (-s)) >> 1)) >> (-s);
+    s = 0;
+  }
+  const int q = s >> 5, r = s & 31;
+  const unsigned long long lo = man << r;                       // bits r .. 63
+  const unsigned long long hi = r ? (man >> (64 - r)) : 0ull;   // bits 64 .. 84
+  long long d0 = (long long)(lo & 0xffffffffull);
+  long long d1 = (long long)(lo >> 32);
+  long long d2 = (long long)hi;
+  if (b >> 63) {
+    d0 = -d0;
+    d1 = -d1;
+    d2 = -d2;
+  }
+  if (q < kWideWords) atomicAdd((unsigned long long*)&w[q], (unsigned long long)d0);
+  if (q + 1 < kWideWords) atomicAdd((unsigned long long*)&w[q + 1], (unsigned long long)d1);
+  if (q + 2 < kWideWords) atomicAdd((unsigned long long*)&w[q + 2], (unsigned long long)d2);
+}
+
+
 struct AdjointStepArgs {
   const double* x[3];
   const double* v[3];
@@ -374,6 +418,7 @@ cudaError_t reset_acc_counter(st_ctx* h);
 constexpr size_t kAccCounterOffset = 64;   // bytes into the flags buffer: uint64 counter
 constexpr size_t kAccFlagOffset = 72;      // int: 1 if the last check propagated carries
 constexpr size_t kUnitCounterOffset = 80;  // uint32: next unit of the sorted-step kernel
+constexpr size_t kFarFlagOffset = 84;      // int: the neighbourhood sort found a particle it cannot place
 cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]);
 cudaError_t launch_particle_sums(st_ctx* h, double out[4]);  // P_x, P_y, P_z, M
@@ -389,6 +434,14 @@ cudaError_t launch_gen(st_ctx* h, uint64_t seed, int64_t first, int64_t count, c
                        double vmax, const double* qtable, int nq, double* xyz, double* vel, double* d,
                        uint32_t* ids);
 st_status sort_particles(st_ctx* h);                                       // sort.cu
+// the neighbourhood sort (sort_local.cu): particles sorted before (h->sorted), mixed state, chunks
+// of at least 8^3 cells dividing the grid.  It sets *far and leaves everything else untouched if a
+// particle lies beyond the 26 units around its sort-time unit; otherwise it writes the sorted state
+// (records or arrays, as sort_particles' own gather), the ids into ids_alt and the cell starts.
+// lidx, lkey and perm are scratch of n entries, aux local_sort_aux_bytes(h).
+bool local_sort_supported(const st_ctx* h);
+size_t local_sort_aux_bytes(const st_ctx* h);
+cudaError_t launch_local_sort(st_ctx* h, int* far, uint32_t* lidx, uint16_t* lkey, uint32_t* perm, void* aux);
 // the structure of arrays current again if the last step left records for a sort (no-op otherwise)
 st_status materialize_state(st_ctx* h);                                    // sort.cu
 // FP64 and FP32 FMA rates of this GPU (GFLOP/s), measured by FMA-chain kernels; synchronises
@@ -398,6 +451,18 @@ cudaError_t probe_fma_rates(st_ctx* h, double* fp64_gflops, double* fp32_gflops)
 void timer_begin(st_ctx* h, int k, cudaStream_t s);                        // st_api.cu
 void timer_end(st_ctx* h, int k, cudaStream_t s);                          // st_api.cu
 cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);
+// ---- droplet microphysics (micro.cu) -------------------------------------------------------------
+// the step with vapour mass and heat transfer (default physics only; accumulators prepared)
+cudaError_t launch_micro_step(st_ctx* h, const StepParams& p);
+// before a microphysics step: widen the diameter bound by the largest growth one step allows, and
+// propagate the carries of the microphysics accumulator when the step could overflow a word
+st_status micro_prepare_step(st_ctx* h, double dt);
+// the sort's permutation applied to the particle temperatures (temp -> temp_alt); gate as the sort's
+cudaError_t launch_gather_temp(st_ctx* h, const uint32_t* perm, const int* gate, int want);
+// the temperatures of particles [first, first + n) set to `T` (new particles, enabling microphysics)
+cudaError_t launch_fill_temp(st_ctx* h, int64_t first, int64_t n, double T);
+// the temperature arrays grown to the handle's capacity (microphysics on), contents kept
+st_status micro_grow(st_ctx* h);
 cudaError_t launch_chunk_bounds(st_ctx* h, double* out);              // sort.cu
 
 }  // namespace st

@@ -26,6 +26,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 
@@ -972,14 +973,16 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) 
       step_mixed_tma_kernel<false, false, true, false>,  step_mixed_tma_kernel<false, true, true, false>,
       step_mixed_tma_kernel<true, false, true, false>,   step_mixed_tma_kernel<true, true, true, false>};
   constexpr int kAttrDevices = 64;
-  static bool attr_set[kAttrDevices][12] = {};  // a kernel attribute is per device
+  // a kernel attribute is per device; atomic because handles may be driven from several host threads
+  // (setting an attribute twice is harmless)
+  static std::atomic<bool> attr_set[kAttrDevices][12];
   const int variant = records ? 8 + 2 * (int)bf + (int)pw2 : 4 * (int)bf + 2 * (int)phys + (int)pw2;
   const Kern kern = table[variant];
   if (h->dev < 0 || h->dev >= kAttrDevices) return cudaErrorInvalidDevice;
-  if (!attr_set[h->dev][variant]) {
+  if (!attr_set[h->dev][variant].load(std::memory_order_acquire)) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr_set[h->dev][variant] = true;
+    attr_set[h->dev][variant].store(true, std::memory_order_release);
   }
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;

@@ -177,9 +177,10 @@ __global__ void export_f64_kernel(F64State s, const uint32_t* __restrict__ sid, 
   }
 }
 
+// ms (microphysics on): per particle {T_hi, T_lo, d_lo, 0}; the diameter is d + d_lo
 __global__ void export_mixed_kernel(MixedState s, bool bf16, const uint32_t* __restrict__ sid, int64_t first,
                                     int64_t n, double* xyz, double* vel, double* d, uint32_t* ids, int32_t* cells,
-                                    GeoArgs g) {
+                                    GeoArgs g, const float4* __restrict__ ms) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     int64_t sp = first + p;
     int32_t c = s.cell[sp];
@@ -191,7 +192,7 @@ __global__ void export_mixed_kernel(MixedState s, bool bf16, const uint32_t* __r
         vel[q * n + p] = v;
       }
     }
-    if (d) d[p] = (double)s.d[sp];
+    if (d) d[p] = (double)s.d[sp] + (ms ? (double)ms[sp].z : 0.0);
     if (ids) ids[p] = sid[sp];
     if (cells) cells[p] = idx[0] + g.n[0] * (idx[1] + g.n[1] * idx[2]);
   }
@@ -459,7 +460,7 @@ cudaError_t launch_export(st_ctx* h, int64_t first, int64_t n, double* xyz, doub
     bool bf = h->prec == ST_MIXED_BF16V;
     export_mixed_kernel<<<grid_for(n), kThreads, 0, h->stream>>>(carve_mixed(h->state.p, h->cap, bf), bf,
                                                                  (const uint32_t*)h->ids.p, first, n, xyz, vel, d,
-                                                                 ids, cells, g);
+                                                                 ids, cells, g, (const float4*)h->temp.p);
   }
   h->launches += 1;
   return cudaGetLastError();

@@ -185,6 +185,16 @@ def taylor_green_plus_fourier(n: int, U0: float = 1.0, frac: float = 0.1, seed: 
     return tg + random_fourier(n, rms=frac * tg_rms, seed=seed)
 
 
+def thermo_fields(n: int, seed: int = 7, T_mean: float = 285.0, T_amp: float = 3.0, rv_mean: float = 0.0105,
+                  rv_frac: float = 0.05):
+    """Fluid temperature (K) and water vapour density (kg/m^3) at cell centres, [k][j][i] each: smooth seeded
+    random fields (the first and second components of a random Fourier field, rms 1 per component on
+    average) scaled to T_mean +- T_amp and rv_mean (1 +- rv_frac) - a stand-in for a cloud chamber's air
+    between 283 and 293 K near water saturation."""
+    F = random_fourier(n, seed=seed)
+    return T_mean + T_amp * F[..., 0], rv_mean * (1.0 + rv_frac * F[..., 1])
+
+
 @dataclass
 class Workload:
     """A seeded synthetic workload shaped like the paper's (sizes, distributions)."""
@@ -239,6 +249,9 @@ WORKLOADS = {
     "fourier256_coupled_2e9": Workload("fourier256_coupled_2e9", 256, "fourier", "f32", "mixed_f32",
                                        2_000_000_000, 50, 5e-4, chunk_edge=32,
                                        extra={"fluid_every": 5, "nu": 1e-3}),
+    # droplet microphysics (vapour and heat transfer) on the mixed-precision workload's field and particles
+    "fourier256_micro_1e9": Workload("fourier256_micro_1e9", 256, "fourier", "f32", "mixed_f32",
+                                     1_000_000_000, 20, 5e-4, extra={"micro": True}),
 }
 
 PHYSICS = dict(rho_p=1000.0, mu=1.8e-5, g=(0.0, 0.0, -9.81), drag_scale=1.0, multiplicity=1.0)

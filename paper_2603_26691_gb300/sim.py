@@ -86,6 +86,13 @@ class Sim:
         self.h = h
         self.params = dict(rho_p=1000.0, mu=1.8e-5, g=(0.0, 0.0, -9.81), drag_scale=1.0, multiplicity=1.0,
                            reorder_every=10)
+        # bumped by every call that changes the particles, parameters, physics, fluid or the recorded
+        # adjoint run, so that a differentiable forward can tell whether its run is still the one the
+        # handle would differentiate
+        self.generation = 0
+
+    def _changed(self):
+        self.generation += 1
 
     # -- lifetime ------------------------------------------------------------------------
     def close(self):
@@ -114,6 +121,7 @@ class Sim:
         self.params = dict(rho_p=rho_p, mu=mu, g=tuple(g), drag_scale=drag_scale, multiplicity=multiplicity,
                            reorder_every=reorder_every)
         garr = (C.c_double * 3)(*[float(x) for x in g])
+        self._changed()
         self._chk(self.lib.st_set_params(self.h, float(rho_p), float(mu), garr, float(drag_scale),
                                          float(multiplicity), int(reorder_every)), "st_set_params")
 
@@ -126,6 +134,7 @@ class Sim:
         """Physics variants: nearest-grid-point gather, semi-implicit Euler, Schiller-Naumann drag
         (rho_f: fluid density in the particle Reynolds number), cloud-in-cell deposit."""
         self.physics = dict(gather=gather, integrator=integrator, drag=drag, deposit=deposit, rho_f=rho_f)
+        self._changed()
         self._chk(self.lib.st_set_physics(self.h, self.GATHERS[gather], self.INTEGRATORS[integrator],
                                           self.DRAGS[drag], self.DEPOSITS[deposit], float(rho_f)),
                   "st_set_physics")
@@ -151,6 +160,7 @@ class Sim:
 
     def set_fluid(self, U):
         """Cell-centred velocity [nz, ny, nx, 3] (float32 or float64; numpy or torch)."""
+        self._changed()
         if isinstance(U, torch.Tensor):
             t = U.contiguous()
             if t.dtype not in (torch.float32, torch.float64):
@@ -174,6 +184,7 @@ class Sim:
 
     def add_particles(self, pos, d, vel=None, ids=None):
         """Append particles: pos [3, n], d [n], vel [3, n] or None, ids [n] uint32 or None."""
+        self._changed()
         dd, dev = _as_f64(d, (-1,))
         n = int(dd.shape[0])
         pp, pdev = _as_f64(pos, (3, n))
@@ -210,9 +221,11 @@ class Sim:
         return int(v.value)
 
     def clear_particles(self):
+        self._changed()
         self._chk(self.lib.st_clear_particles(self.h), "st_clear_particles")
 
     def adjoint_forward(self, nsteps: int, dt: float, checkpoint_every: int):
+        self._changed()
         self._chk(self.lib.st_adjoint_forward(self.h, int(nsteps), float(dt), int(checkpoint_every)),
                   "st_adjoint_forward")
 
@@ -236,9 +249,11 @@ class Sim:
         return gd, ga.value, gU
 
     def step(self, nsteps: int, dt: float):
+        self._changed()
         self._chk(self.lib.st_step(self.h, int(nsteps), float(dt)), "st_step")
 
     def reorder(self):
+        self._changed()
         self._chk(self.lib.st_reorder(self.h), "st_reorder")
 
     # -- asynchronous two-way coupling -------------------------------------------------------
@@ -246,10 +261,12 @@ class Sim:
 
     def couple_params(self, rho_f: float = 1.2, nu: float = 1e-3, sweeps: int = 10, steps_per_interval: int = 5,
                       extrapolator: str = "zero"):
+        self._changed()
         self._chk(self.lib.st_couple_params(self.h, float(rho_f), float(nu), int(sweeps), int(steps_per_interval),
                                             self.EXTRAPOLATORS[extrapolator]), "st_couple_params")
 
     def couple_run(self, nintervals: int, dt: float):
+        self._changed()
         self._chk(self.lib.st_couple_run(self.h, int(nintervals), float(dt)), "st_couple_run")
 
     def fluid(self, host: bool = True):
@@ -338,6 +355,63 @@ class Sim:
     def invariants(self) -> np.ndarray:
         out = (C.c_double * 8)()
         self._chk(self.lib.st_invariants(self.h, out), "st_invariants")
+        return np.array(out[:])
+
+    # -- droplet microphysics (vapour mass and heat transfer) ------------------------------------
+    def set_microphysics(self, enable: bool = True, D_v: float = 2.5e-5, kappa_f: float = 0.025, cp_p: float = 4186.0,
+                         latent_heat: float = 2.5e6, prandtl: float = 0.71, d_min: float = 1e-7,
+                         T_init: float = 293.15):
+        """Vapour mass and heat transfer of the droplets (off by default; see st_set_microphysics)."""
+        self._changed()
+        self._chk(self.lib.st_set_microphysics(self.h, int(bool(enable)), float(D_v), float(kappa_f), float(cp_p),
+                                               float(latent_heat), float(prandtl), float(d_min), float(T_init)),
+                  "st_set_microphysics")
+
+    def set_thermo(self, T, rho_v):
+        """Fluid temperature (K) and vapour density (kg/m^3) at cell centres, [nz, ny, nx] each."""
+        self._changed()
+        if isinstance(T, torch.Tensor) and T.is_cuda:
+            t = T.to(torch.float64).contiguous().reshape(-1)
+            r = torch.as_tensor(rho_v, dtype=torch.float64, device=t.device).contiguous().reshape(-1)
+            if t.numel() != self.ncell or r.numel() != self.ncell:
+                raise ValueError("thermo fields have the wrong size")
+            self._chk(self.lib.st_set_thermo(self.h, _ptr(t), _ptr(r), _lib.ST_DTYPE_F64, 1), "st_set_thermo")
+            return
+        t = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+        r = np.ascontiguousarray(rho_v, dtype=np.float64).reshape(-1)
+        if t.size != self.ncell or r.size != self.ncell:
+            raise ValueError("thermo fields have the wrong size")
+        self._chk(self.lib.st_set_thermo(self.h, _ptr(t), _ptr(r), _lib.ST_DTYPE_F64, 0), "st_set_thermo")
+
+    def set_temperatures(self, T, first: int = 0):
+        """Particle temperatures (K) of particles [first, first + len(T)) in storage order."""
+        self._changed()
+        t, dev = _as_f64(T, (-1,))
+        self._chk(self.lib.st_set_temperatures(self.h, int(first), int(t.shape[0]), _ptr(t), int(dev)),
+                  "st_set_temperatures")
+
+    def temperatures(self, first: int = 0, count: int | None = None) -> np.ndarray:
+        """Particle temperatures (K) in storage order."""
+        if count is None:
+            count = self.n - first
+        out = np.empty(count)
+        self._chk(self.lib.st_get_temperatures(self.h, int(first), int(count), _ptr(out), 0), "st_get_temperatures")
+        return out
+
+    def micro_sources(self, reset: bool = False, host: bool = True):
+        """Vapour mass (kg) and energy (J) the fluid gained per cell, [2, ncell] float64."""
+        if host:
+            a = np.empty((2, self.ncell))
+            self._chk(self.lib.st_get_micro_sources(self.h, _ptr(a), int(reset), 0), "st_get_micro_sources")
+            return a
+        out = torch.empty((2, self.ncell), dtype=torch.float64, device=self.device)
+        self._chk(self.lib.st_get_micro_sources(self.h, _ptr(out), int(reset), 1), "st_get_micro_sources")
+        return out
+
+    def micro_invariants(self) -> np.ndarray:
+        """(sum of particle masses, sum of C_p m T) in FP64."""
+        out = (C.c_double * 2)()
+        self._chk(self.lib.st_micro_invariants(self.h, out), "st_micro_invariants")
         return np.array(out[:])
 
     # -- seeded input generator (device twin of inputs.particles) --------------------------

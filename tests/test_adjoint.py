@@ -181,6 +181,31 @@ def test_autograd_function_quadratic_loss(Sim, deposit):
     assert np.abs(gU - ogU).max() <= 1e-8 * np.abs(ogU).max()
 
 
+def test_autograd_backward_after_another_forward_raises(Sim):
+    """One handle records one run: a backward through an earlier forward, after a second forward
+    replaced the recorded run, must raise instead of returning the second run's gradients."""
+    import torch
+
+    from paper_2603_26691_gb300.autograd import lagrangian_sources
+
+    N, U, pos, vel, d, alpha = _case(N=12, n=200)
+    sim = Sim(N, precision="fp64")
+    dev = torch.device("cuda")
+    d1 = torch.tensor(d, device=dev, requires_grad=True)
+    d2 = torch.tensor(d * 1.1, device=dev, requires_grad=True)
+    at = torch.tensor(alpha, dtype=torch.float64, requires_grad=True)
+    Ut = torch.tensor(U, device=dev)
+    J1 = lagrangian_sources(d1, at, Ut, sim, pos, vel, 5, 1e-3, 5)
+    J2 = lagrangian_sources(d2, at, Ut, sim, pos, vel, 5, 1e-3, 5)
+    with pytest.raises(RuntimeError, match="changed after this forward"):
+        (J1.sum() + J2.sum()).backward()
+    # the latest forward alone still differentiates
+    J3 = lagrangian_sources(d1, at, Ut, sim, pos, vel, 5, 1e-3, 5)
+    (J3 ** 2).sum().backward()
+    assert torch.isfinite(d1.grad).all()
+    sim.close()
+
+
 def test_adjoint_tg_fourier_64_1e7_sampled(Sim):
     """Adjoint workload: 64^3 Taylor-Green + 10% Fourier (FP32-rounded), 1e7 particles, 200 steps of 1e-3,
     checkpoints every 20.  Per-particle dL/dd of a linear loss depends only on that particle's path, so

@@ -1,0 +1,170 @@
+"""Droplet microphysics on the GPU (vapour mass and heat transfer, Sec. 2.1) against the FP64 oracle:
+FP64 handles to 1e-10, mixed handles within stated bounds, the water, energy and momentum budgets,
+temperatures carried through the sorts, and the calls' error paths."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_26691_gb300 import inputs
+from tests.helpers import min_image
+
+pytestmark = pytest.mark.gpu
+
+MICRO = dict(D_v=2.5e-5, kappa_f=0.025, cp_p=4186.0, latent_heat=2.5e6, prandtl=0.71, d_min=1e-7)
+
+
+@pytest.fixture(scope="module")
+def Sim():
+    import torch
+
+    assert torch.cuda.is_available()
+    from paper_2603_26691_gb300.sim import Sim
+
+    return Sim
+
+
+def _case(N=16, n=20_000, seed=3, f32=False):
+    U = inputs.random_fourier(N, seed=seed)
+    T, rv = inputs.thermo_fields(N, seed=seed + 1)
+    if f32:
+        U = U.astype(np.float32).astype(np.float64)
+        T = T.astype(np.float32).astype(np.float64)
+        rv = rv.astype(np.float32).astype(np.float64)
+    pos, vel, d, _ = inputs.particles(seed, 0, n, vmax=0.2)
+    Tp = 283.0 + 4.0 * np.random.default_rng(seed).random(n)
+    return N, U, T, rv, pos, vel, d, Tp
+
+
+def _oracle(N, U, T, rv, pos, vel, d, Tp, steps, dt):
+    G = oracle.make_grid(N)
+    M = oracle.make_micro(D_v=MICRO["D_v"], kappa_f=MICRO["kappa_f"], cp_p=MICRO["cp_p"], L=MICRO["latent_heat"],
+                          Pr=MICRO["prandtl"], d_min=MICRO["d_min"])
+    return oracle.micro_run(G, M, U.reshape(-1, 3), T.reshape(-1), rv.reshape(-1), pos, vel, d, Tp, steps, dt)
+
+
+def _gpu(Sim, prec, N, U, T, rv, pos, vel, d, Tp, steps, dt, reorder_every=10, split=None):
+    sim = Sim(N, precision=prec)
+    sim.set_params(reorder_every=reorder_every)
+    sim.set_fluid(U.astype(np.float32) if prec != "fp64" else U)
+    sim.set_thermo(T, rv)
+    sim.set_microphysics(True, T_init=285.0, **MICRO)
+    sim.add_particles(pos, d, vel)
+    sim.set_temperatures(Tp)  # storage order = generation order before the first sort
+    inv0 = sim.micro_invariants()
+    if split:
+        for k in split:
+            sim.step(k, dt)
+    else:
+        sim.step(steps, dt)
+    g = dict(src=sim.sources(host=True), micro=sim.micro_sources(), inv0=inv0, inv1=sim.micro_invariants(),
+             pinv=sim.invariants())
+    g["pos"], g["vel"], g["d"], g["ids"] = sim.particles()
+    g["T"] = sim.temperatures()
+    sim.close()
+    return g
+
+
+@pytest.mark.parametrize("reorder_every", [0, 7])
+def test_fp64_microphysics_matches_the_oracle(Sim, reorder_every):
+    N, U, T, rv, pos, vel, d, Tp = _case()
+    steps, dt = 25, 5e-4
+    op, ov, od, oT, osrc, om, oe = _oracle(N, U, T, rv, pos, vel, d, Tp, steps, dt)
+    g = _gpu(Sim, "fp64", N, U, T, rv, pos, vel, d, Tp, steps, dt, reorder_every=reorder_every)
+    o = g["ids"].astype(np.int64)
+    assert np.abs(min_image(g["pos"], op[:, o])).max() <= 1e-10
+    assert np.abs(g["vel"] - ov[:, o]).max() <= 1e-10 * max(np.abs(ov).max(), 1.0)
+    assert np.abs(g["d"] - od[o]).max() <= 1e-10 * od.max()
+    assert np.abs(g["T"] - oT[o]).max() <= 1e-10 * 300.0
+    assert np.abs(g["src"] - osrc).max() <= 1e-10 * np.abs(osrc).max()
+    assert np.abs(g["micro"][0] - om).max() <= 1e-10 * np.abs(om).max()
+    assert np.abs(g["micro"][1] - oe).max() <= 1e-10 * np.abs(oe).max()
+    # the droplets grew and shrank: the test exercises both directions of the transfer
+    assert (od > d).any() and (od < d).any()
+
+
+def test_fp64_budgets_close(Sim):
+    """Water (droplet mass + vapour gained), energy (C_p m T + energy gained) and momentum budgets."""
+    N, U, T, rv, pos, vel, d, Tp = _case(n=30_000)
+    steps, dt = 20, 5e-4
+    g = _gpu(Sim, "fp64", N, U, T, rv, pos, vel, d, Tp, steps, dt)
+    W0, E0 = g["inv0"]
+    W1, E1 = g["inv1"]
+    assert abs(W1 + g["micro"][0].sum() - W0) <= 1e-12 * W0
+    assert abs(E1 + g["micro"][1].sum() - E0) <= 1e-12 * E0
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+def test_mixed_microphysics_within_bounds(Sim, prec):
+    """The mixed-precision state (FP32 diameter and temperature, FP32 or BF16 velocity) against the FP64
+    oracle on the FP32-rounded fields."""
+    N, U, T, rv, pos, vel, d, Tp = _case(f32=True)
+    steps, dt = 20, 5e-4
+    op, ov, od, oT, osrc, om, oe = _oracle(N, U, T, rv, pos, vel, d, Tp, steps, dt)
+    g = _gpu(Sim, prec, N, U, T, rv, pos, vel, d, Tp, steps, dt)
+    o = g["ids"].astype(np.int64)
+    h = 1.0 / N
+    derr = (np.abs(g["d"] - od[o]) / od[o]).max()
+    Terr = np.abs(g["T"] - oT[o]).max()
+    m_l2 = np.linalg.norm(g["micro"][0] - om) / np.linalg.norm(om)
+    e_l2 = np.linalg.norm(g["micro"][1] - oe) / np.linalg.norm(oe)
+    perr = np.abs(min_image(g["pos"], op[:, o])).max() / h
+    print(prec, dict(pos_h=perr, d=derr, T=Terr, vapour_l2=m_l2, energy_l2=e_l2))
+    # FP32 arithmetic on a compensated state (no increment is lost): the transfer rates carry FP32
+    # rounding (~1e-6 of the rate) and the temperature the FP32 rounding of the values it relaxes to;
+    # with BF16 velocities the particle is ~1e-3 cells from the oracle's and samples the temperature and
+    # vapour fields there (|grad T| ~ 150 K/m times ~6e-5 m), and its slip changes the Nusselt number
+    if prec == "mixed_f32":
+        assert perr <= 1e-5
+        assert derr <= 1e-6 and Terr <= 1e-4
+        assert m_l2 <= 5e-5 and e_l2 <= 5e-5
+    else:
+        assert derr <= 1e-4 and Terr <= 5e-2
+        assert m_l2 <= 1e-2 and e_l2 <= 1e-2
+    # budgets: water and energy in the stored values
+    W0, E0 = g["inv0"]
+    W1, E1 = g["inv1"]
+    assert abs(W1 + g["micro"][0].sum() - W0) <= 1e-6 * abs(g["micro"][0]).sum() + 1e-9 * W0
+    assert abs(E1 + g["micro"][1].sum() - E0) <= 1e-6 * abs(g["micro"][1]).sum() + 1e-9 * E0
+
+
+def test_temperatures_follow_their_particles_through_sorts(Sim):
+    """Sorting every 3 steps, in several calls: every particle keeps its own temperature (the same result
+    as without sorting)."""
+    N, U, T, rv, pos, vel, d, Tp = _case(n=12_001)
+    a = _gpu(Sim, "fp64", N, U, T, rv, pos, vel, d, Tp, 12, 5e-4, reorder_every=3, split=[5, 4, 3])
+    b = _gpu(Sim, "fp64", N, U, T, rv, pos, vel, d, Tp, 12, 5e-4, reorder_every=0)
+    oa, ob = a["ids"].astype(np.int64), b["ids"].astype(np.int64)
+    ta = np.empty_like(a["T"])
+    tb = np.empty_like(b["T"])
+    ta[oa] = a["T"]
+    tb[ob] = b["T"]
+    assert np.abs(ta - tb).max() <= 1e-12 * 300.0
+    assert np.abs(a["micro"] - b["micro"]).max() <= 1e-12 * np.abs(b["micro"]).max()
+
+
+def test_microphysics_call_errors(Sim):
+    from paper_2603_26691_gb300._lib import StError
+
+    N, U, T, rv, pos, vel, d, Tp = _case(n=100)
+    sim = Sim(N, precision="mixed_f32")
+    sim.set_fluid(U.astype(np.float32))
+    sim.add_particles(pos, d, vel)
+    with pytest.raises(StError):
+        sim.set_temperatures(Tp)  # microphysics off
+    sim.set_microphysics(True, **MICRO)
+    with pytest.raises(StError):
+        sim.step(1, 1e-3)  # no thermo fields
+    with pytest.raises(StError):
+        sim.set_thermo(T * 0.0, rv)  # T must be > 0
+    with pytest.raises(StError):
+        sim.set_thermo(T, rv * np.nan)
+    sim.set_thermo(T, rv)
+    sim.set_physics(deposit="cic")
+    with pytest.raises(StError):
+        sim.step(1, 1e-3)  # the default physics only
+    sim.set_physics()
+    sim.step(2, 1e-3)
+    assert np.all(sim.temperatures() > 270.0)
+    with pytest.raises(StError):
+        sim.set_microphysics(True, **dict(MICRO, kappa_f=-1.0))
+    sim.close()

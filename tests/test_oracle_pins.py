@@ -440,3 +440,33 @@ def test_chunk_bounds_hand_example_and_properties(oracle_mod):
     for c in range(8):
         lo = np.array([c % 2, (c // 2) % 2, c // 4]) * 0.5
         assert np.all(bb[c, :3] >= lo) and np.all(bb[c, 3:] <= lo + 0.5)
+
+
+def test_blocked_all_cores_run_is_deterministic(oracle_mod):
+    """The all-cores oracle (fixed particle blocks, partial sources added in block order): independent of
+    the thread count bit for bit, identical to the single-thread run when one block holds every particle,
+    the same particle states for any block size, and sources equal to the single-thread run's up to the
+    rounding of the changed summation order."""
+    from paper_2603_26691_gb300 import inputs
+
+    o = oracle_mod
+    G = o.make_grid(12)
+    U = inputs.random_fourier(12, seed=4)
+    n, steps, dt = 9_001, 6, 5e-4
+    pos, vel, d, _ = inputs.particles(21, 0, n, vmax=0.2)
+    part = lambda f, c: (pos[:, f:f + c], vel[:, f:f + c], d[f:f + c])  # noqa: E731
+    p0, v0, s0, _ = o.run(G, U, pos, vel, d, steps, dt)
+    states = {}
+
+    def keep(first, p, v):
+        states[first] = (p, v)
+
+    s1 = o.run_blocked(G, U, part, n, steps, dt, block=1000, threads=1, keep=keep)
+    s4 = o.run_blocked(G, U, part, n, steps, dt, block=1000, threads=4)
+    assert np.array_equal(s1, s4)
+    p1 = np.concatenate([states[f][0] for f in sorted(states)], axis=1)
+    v1 = np.concatenate([states[f][1] for f in sorted(states)], axis=1)
+    assert np.array_equal(p1, p0) and np.array_equal(v1, v0)
+    assert np.abs(s1 - s0).max() <= 1e-13 * np.abs(s0).max()
+    sall = o.run_blocked(G, U, part, n, steps, dt, block=n, threads=3)
+    assert np.array_equal(sall, s0)

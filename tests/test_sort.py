@@ -25,6 +25,17 @@ def _oracle_keys(G, pos):
     return oracle.keys_of_positions(G, pos)
 
 
+def _cells_near(pos, N):
+    """Cells within one cell (per axis, periodic) of the given positions' cells, as a mask."""
+    mask = np.zeros(N ** 3, dtype=bool)
+    c = [np.clip(np.floor(pos[q] * N).astype(np.int64), 0, N - 1) for q in range(3)]
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                mask[(c[0] + dx) % N + N * (((c[1] + dy) % N) + N * ((c[2] + dz) % N))] = True
+    return mask
+
+
 def _compare_order(got_ids, want_order, ambiguous):
     """Same sequence of ids once particles that sit within the band of a face are removed."""
     amb = set(np.flatnonzero(ambiguous).tolist())
@@ -50,7 +61,11 @@ def test_reorder_matches_oracle_stable_sort(Sim, prec, N, B):
     want1 = oracle.sort_perm(k0)
     _compare_order(ids1, want1, amb0)
     counts = sim.cell_counts()
-    assert np.array_equal(counts, oracle.cell_counts(G, pos)) or amb0.any()
+    # every cell is compared except those next to a particle within the band of a face (which may
+    # belong to either side)
+    keep = ~_cells_near(pos[:, amb0], N)
+    assert keep.mean() > 0.99
+    assert np.array_equal(counts[keep], oracle.cell_counts(G, pos)[keep])
     assert counts.sum() == n
     # move, then sort again: the new order is the stable sort of the previous one
     steps, dt = 7, 1e-3

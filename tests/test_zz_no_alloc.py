@@ -51,6 +51,39 @@ def test_static_sort_matches_reorder_on_two_calls_in_a_row():
         got = perm.cpu().numpy().astype(np.int64)
         assert np.array_equal(got, want_perm)
         assert np.array_equal(sk.cpu().numpy().view(np.uint32), keys[want_perm])
+        # no wait of these calls gave up
+        assert lib.st_sort_keys_static_status(C.c_void_p(stream.cuda_stream)) == _lib.ST_OK
+
+
+def test_static_sort_takes_no_device_memory_after_its_first_call():
+    """The first call on a device may create the static array (lazy module loading); later calls take
+    no device memory at all: the free device memory stays the same across them."""
+    import torch
+
+    from paper_2603_26691_gb300 import _lib
+
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    n = 200_003
+    rng = np.random.default_rng(9)
+    keys = torch.as_tensor(rng.integers(0, 1 << 20, n, dtype=np.uint32).view(np.int32), device="cuda")
+    sk = torch.empty(n, dtype=torch.int32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def call():
+        st = lib.st_sort_keys_static(C.c_void_p(keys.data_ptr()), n, 20, C.c_void_p(sk.data_ptr()),
+                                     C.c_void_p(perm.data_ptr()), C.c_void_p(stream.cuda_stream))
+        assert st == _lib.ST_OK
+        torch.cuda.synchronize()
+
+    call()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        call()
+        assert torch.cuda.mem_get_info()[0] == free0
+    want = np.argsort(keys.cpu().numpy().view(np.uint32), kind="stable")
+    assert np.array_equal(perm.cpu().numpy().astype(np.int64), want)
+    assert lib.st_sort_keys_static_status(C.c_void_p(stream.cuda_stream)) == _lib.ST_OK
 
 
 def test_static_sort_rejects_sizes_beyond_its_maximum():
