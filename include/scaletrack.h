@@ -189,6 +189,16 @@ st_status st_step(st_handle h, int nsteps, double dt);
  * Errors: INVALID_ARG, CUDA. */
 st_status st_get_sources(st_handle h, double* out, int reset, int on_device);
 
+/* The accumulated source as the exact fixed-point integers it is kept in:
+ * words[3][ncell][4] (int64; component-major like st_get_sources) with
+ * digits words[..][0..2] in [0, 2^32) below a signed top word [3], value =
+ * sum_k words[k] 2^(32 k - E) kg m/s.  For summing several handles' sources
+ * (for instance one per GPU) exactly and in no particular order: shift each
+ * to the largest E and add the integers.  The carries are propagated in
+ * place first (the accumulated value does not change).  Synchronises.
+ * Errors: INVALID_ARG, CUDA. */
+st_status st_get_sources_fixed(st_handle h, int64_t* words, int* E, int on_device);
+
 /* Stable counting sort of the particles now, by the chunk-major key of
  * their cell: chunk index (x fastest) times B^3 plus the Morton index of
  * the cell inside its chunk.  Particles with equal keys keep their order.

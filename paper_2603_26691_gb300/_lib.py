@@ -58,6 +58,7 @@ SIGNATURES = {
     "st_num_particles": (_i, [_vp, _P(_i64)]),
     "st_step": (_i, [_vp, _i, _d]),
     "st_get_sources": (_i, [_vp, _vp, _i, _i]),
+    "st_get_sources_fixed": (_i, [_vp, _vp, _P(_i), _i]),
     "st_reorder": (_i, [_vp]),
     "st_get_particles": (_i, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _i]),
     "st_get_cells": (_i, [_vp, _i64, _i64, _vp, _i]),

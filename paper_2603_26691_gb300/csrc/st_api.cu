@@ -556,14 +556,13 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
   const double pi = 3.14159265358979323846;
   for (int s = 0; s < nsteps; ++s) {
     if (h->np == 0) break;
-    if (h->reorder_every > 0 && (!h->sorted || h->steps_since_sort >= h->reorder_every)) {
-      ST_TRY(st_reorder(h));
-    } else {
-      ST_TRY(materialize_state(h));
-    }
+    if (h->reorder_every > 0 && (!h->sorted || h->steps_since_sort >= h->reorder_every)) ST_TRY(st_reorder(h));
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
     const bool tma = !h->micro_on && h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
+    // a sort that deferred its payload gather: this step gathers, or (another kernel) gather first
+    const bool gather = h->perm_pending && tma && default_physics(h);
+    if (!gather) ST_TRY(materialize_state(h));
     if (h->micro_on) ST_TRY(micro_prepare_step(h, dt));
     int E = 0;
     ST_TRY(prepare_accumulator(h, dt, tma ? 8.0 : deposits_per_cell(h) * (double)h->np + 8.0, &E));
@@ -590,7 +589,8 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
       const bool records = default_physics(h) && h->reorder_every > 0 &&
                            h->steps_since_sort + 1 >= h->reorder_every &&
                            h->state_alt.bytes >= (size_t)h->cap * 32;
-      e = launch_step_mixed_tma(h, p, records);
+      e = launch_step_mixed_tma(h, p, records, gather);
+      if (e == cudaSuccess && gather) gather_step_done(h);
       if (e == cudaSuccess && records) h->records_pending = true;
     }
     else
@@ -632,6 +632,19 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device) {
     h->acc_load = 0.0;
   }
   return ST_OK;
+}
+
+st_status st_get_sources_fixed(st_handle h, int64_t* words, int* E, int on_device) {
+  ST_TRY(check_handle(h));
+  if (!words || !E) return set_error(h, ST_ERR_INVALID_ARG, "words and E are required");
+  // carries propagated in place (the value is unchanged), then the words copied out
+  ST_TRY(cuda_check(h, launch_normalize_acc(h), "normalise sources"));
+  cudaError_t e = cudaMemcpyAsync(words, h->acc.p, (size_t)h->geo.ncell * 3 * kAccWords * sizeof(long long),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  ST_TRY(cuda_check(h, e, "get fixed-point sources"));
+  *E = h->acc_E;
+  return check_flags(h);
 }
 
 st_status st_get_particles(st_handle h, int64_t first, int64_t count, double* xyz, double* vel, double* d,
@@ -756,6 +769,7 @@ st_status st_clear_particles(st_handle h) {
   ST_TRY(check_handle(h));
   h->np = 0;
   h->records_pending = false;
+  h->perm_pending = false;
   h->sorted = false;
   h->steps_since_sort = 0;
   h->dmax = 0.0;

@@ -305,6 +305,14 @@ class Sim:
         self._chk(self.lib.st_get_sources(self.h, C.c_void_p(out.data_ptr()), int(reset), 1), "st_get_sources")
         return out
 
+    def sources_fixed(self):
+        """The accumulated source as exact fixed-point integers: (words [3, ncell, 4] int64 device tensor
+        with 32-bit digits below a signed top word, E) with value = sum_k words[..., k] 2^(32 k - E)."""
+        w = torch.empty((3, self.ncell, 4), dtype=torch.int64, device=self.device)
+        E = C.c_int()
+        self._chk(self.lib.st_get_sources_fixed(self.h, _ptr(w), C.byref(E), 1), "st_get_sources_fixed")
+        return w, int(E.value)
+
     def source_density(self, elapsed: float, reset: bool = False, host: bool = False):
         """The momentum source of Sec. 2.1, Eq. 11, as a rate density: the accumulated impulse per cell
         divided by the cell volume and by the time it was accumulated over (`elapsed`, in s) [3, ncell]."""
