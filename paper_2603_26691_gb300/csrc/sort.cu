@@ -832,9 +832,13 @@ cudaError_t radix_passes(Src src, int64_t n, int key_bits, uint32_t* ka, uint32_
 
 }  // namespace
 
+static st_status run_deferred_gather(st_ctx* h);
+
 st_status sort_particles(st_ctx* h) {
   const int64_t n = h->np;
   if (n == 0) return ST_OK;
+  // a previous sort's gather still pending: the storage order it defined must be made real first
+  if (h->perm_pending) ST_TRY(run_deferred_gather(h));
   if (n >= (int64_t(1) << 32)) return set_error(h, ST_ERR_INVALID_ARG, "sorting needs fewer than 2^32 particles");
   const int64_t ntiles = (n + kTile - 1) / kTile;
   if (h->sort_cap < h->cap) {
@@ -900,6 +904,9 @@ st_status sort_particles(st_ctx* h) {
     gather_f64_kernel<<<grid_for(n), 256, 0, h->stream>>>(carve_f64(h->state.p, h->cap),
                                                           carve_f64(h->state_alt.p, h->cap), (const uint32_t*)h->ids.p,
                                                           (uint32_t*)h->ids_alt.p, v0, n);
+  } else if (h->records_pending && defer_gather(h)) {
+    // the next step is a sorted step that gathers through the permutation itself (GATHER instance)
+    h->perm_pending = true;
   } else if (h->records_pending) {
     // the step before this sort left the state as records in state_alt: gather them back into
     // the (stale) structure of arrays; only the ids change buffers
@@ -919,9 +926,10 @@ st_status sort_particles(st_ctx* h) {
   cell_start_kernel<<<grid_for((n + 3) / 4), 256, 0, h->stream>>>(k0, n, (uint32_t*)h->cell_start.p, gate);
   cell_start_tail_kernel<<<grid_for((int64_t)h->nkeys + 1), 256, 0, h->stream>>>(k0, n, h->nkeys,
                                                                                    (uint32_t*)h->cell_start.p, gate);
-  h->launches += 3;  // gather + cell starts (two kernels)
+  h->launches += h->perm_pending ? 2 : 3;  // gather + cell starts (two kernels)
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(h, e, "sort gather");
+  if (h->perm_pending) return ST_OK;  // records and ids stay where they are until the gather
   // particle temperatures (microphysics), through the same permutation
   if (h->temp.p) {
     e = launch_gather_temp(h, v0, nullptr, 1);
@@ -936,7 +944,35 @@ st_status sort_particles(st_ctx* h) {
   return ST_OK;
 }
 
+// the payload gather a sort deferred: records (state_alt, old order) and ids through the permutation
+// into the structure of arrays and ids_alt, as sort_particles would have done
+static st_status run_deferred_gather(st_ctx* h) {
+  const bool bf = h->prec == ST_MIXED_BF16V;
+  (bf ? gather_records_kernel<true> : gather_records_kernel<false>)<<<grid_for(h->np / 4 + 1), 256, 0, h->stream>>>(
+      (const float4*)h->state_alt.p, carve_mixed(h->state.p, h->cap, bf), (const uint32_t*)h->ids.p,
+      (uint32_t*)h->ids_alt.p, (const uint32_t*)h->vals[0].p, h->np, nullptr);
+  h->launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_check(h, e, "deferred sort gather");
+  std::swap(h->ids, h->ids_alt);
+  h->perm_pending = false;
+  h->records_pending = false;
+  return ST_OK;
+}
+
+bool defer_gather(const st_ctx* h) {
+  return h->prec != ST_FP64 && !h->micro_on && default_physics(h) && tma_step_supported(h) &&
+         h->reorder_every != 1 && h->np > 0;
+}
+
+void gather_step_done(st_ctx* h) {
+  std::swap(h->ids, h->ids_alt);
+  h->perm_pending = false;
+  h->records_pending = false;
+}
+
 st_status materialize_state(st_ctx* h) {
+  if (h->perm_pending) return run_deferred_gather(h);
   if (!h->records_pending) return ST_OK;
   const bool bf = h->prec == ST_MIXED_BF16V;
   (bf ? records_to_soa_kernel<true> : records_to_soa_kernel<false>)<<<grid_for(h->np), 256, 0, h->stream>>>(

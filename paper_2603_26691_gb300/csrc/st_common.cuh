@@ -86,6 +86,11 @@ struct st_ctx {
   // `state`; the sort gathers from the records.  Until then the offsets, velocities and
   // diameters in `state` are stale: every other reader calls materialize_state first.
   bool records_pending = false;
+  // The sort's payload gather deferred to the next step (records_pending stays set): the sorted order
+  // is the permutation in vals[0] (cell starts already updated), the state is still the records in
+  // the old order and the ids in `ids`.  The next sorted step gathers; any other reader calls
+  // materialize_state, which runs the gather.
+  bool perm_pending = false;
 
   // kernel timers (st_timers_*): pending event pairs per kind, folded into sums on read
   bool timing = false;
@@ -403,7 +408,9 @@ bool tma_step_supported(const st_ctx* h);                               // step_
 // records = true (mixed handles, default physics): the new state goes out as 32-byte records into
 // state_alt (plus the cells into the structure of arrays) for the sort that follows; see
 // records_pending
-cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records);  // step_mixed_tma.cu
+// gather = true: the first step after a sort whose payload gather was deferred (perm_pending); it reads
+// the records through the permutation and writes the sorted state, diameters and ids included
+cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records, bool gather);  // step_mixed_tma.cu
 cudaError_t launch_rescale_acc(st_ctx* h, int shift);
 cudaError_t launch_normalize_acc(st_ctx* h);
 // the particle steps of st_step (sort when due, accumulator bookkeeping, step kernel)
@@ -444,6 +451,11 @@ size_t local_sort_aux_bytes(const st_ctx* h);
 cudaError_t launch_local_sort(st_ctx* h, int* far, uint32_t* lidx, uint16_t* lkey, uint32_t* perm, void* aux);
 // the structure of arrays current again if the last step left records for a sort (no-op otherwise)
 st_status materialize_state(st_ctx* h);                                    // sort.cu
+// whether a sort may leave its payload gather to the next step (mixed, sorted-step kernel, default
+// physics, no microphysics, and the next step does not itself write records), and the bookkeeping
+// once that step has gathered (ids swapped, nothing pending)
+bool defer_gather(const st_ctx* h);                                        // sort.cu
+void gather_step_done(st_ctx* h);                                          // sort.cu
 // FP64 and FP32 FMA rates of this GPU (GFLOP/s), measured by FMA-chain kernels; synchronises
 cudaError_t probe_fma_rates(st_ctx* h, double* fp64_gflops, double* fp32_gflops);  // util.cu
 // timer marks around a launch of kind k on stream s (no-ops unless st_timers_enable is on); the

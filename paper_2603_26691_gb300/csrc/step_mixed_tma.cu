@@ -20,6 +20,12 @@
 //     with fire-and-forget integer atomic adds (exact and independent of the
 //     order of the adds); sorted storage keeps runs long and the touched
 //     accumulator lines hot in L2.
+// The first step after a sort may also do that sort's payload gather (the GATHER instance): the sort
+// leaves a permutation and the previous step's 32-byte records {cell, offsets | velocity, diameter}
+// in the old order, and the consumers load their own particles' records (and ids) through the
+// permutation instead of reading staged arrays, then store the new state - diameters and ids too -
+// in sorted order.  The separate gather would write the sorted arrays only for this step to read
+// them back.
 // Every wait is bounded: a wait that gives up sets an error flag and the CTA
 // returns.
 #include <cuda.h>
@@ -95,6 +101,10 @@ struct TmaArgs {
   int E;                              // global accumulator exponent
   float s1, s2;                       // s1 * s2 = 2^(E - kDepShift): global units -> deposit-tile units
   float4* __restrict__ rec;           // record output: two float4 per particle (see st_common.cuh)
+  const uint32_t* __restrict__ perm;  // GATHER: storage index (old order) of each sorted position
+  const float4* __restrict__ grec;    // GATHER: the records in the old order
+  const uint32_t* __restrict__ ids_in;   // GATHER: ids in the old order
+  uint32_t* __restrict__ ids_out;        // GATHER: ids in sorted order
   int ngp, semi, sn, cic;             // physics variants (the PHYS instance): nearest grid point,
   float re_coef;                      // semi-implicit Euler, Schiller-Naumann drag (Re = re_coef |u-v| d),
                                       // cloud-in-cell deposit
@@ -323,7 +333,7 @@ __device__ __forceinline__ void commit_record(const TmaArgs& a, int* dep, int kk
   }
 }
 
-template <bool BF16, bool PW2, bool REC, bool PHYS>
+template <bool BF16, bool PW2, bool REC, bool PHYS, bool GATHER>
 __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const __grid_constant__ TmaArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -390,6 +400,12 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
             return;
           }
           unsigned char* dst = ring + st * kStageBytes;
+          if (GATHER) {
+            // the consumers load their particles themselves; the stage only serves as their scratch
+            mbar_arrive(&full[st]);
+            ++gt;
+            continue;
+          }
           mbar_expect_tx(&full[st], stage_bytes<BF16>(cnt));
           bulk_load(dst, a.s.cell + t0, cnt * 4, &full[st]);
           for (int q = 0; q < 3; ++q) bulk_load(dst + (1 + q) * kT * 4, a.s.xi[q] + t0, cnt * 4, &full[st]);
@@ -450,7 +466,38 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
       const int64_t p0 = t0 + L;
       int cell[4];
       float xi[3][4], v[3][4], dv[4];
-      {
+      uint32_t gid[4] = {0u, 0u, 0u, 0u};
+      if constexpr (GATHER) {
+        // the lane's particles through the permutation: a 32-byte record and an id each (particles
+        // outside the unit get harmless values and are neither stored nor deposited)
+        const int glo = (int)max((int64_t)0, min((int64_t)4, S - p0));
+        const int ghi = (int)max((int64_t)0, min((int64_t)4, E - p0));
+        // p0 is a multiple of 4 and below E <= the capacity (a multiple of 64) when the lane owns any
+        // particle; the stage's tail lanes past the unit read nothing
+        const uint4 pp = ghi > glo ? __ldcs(reinterpret_cast<const uint4*>(a.perm + p0)) : make_uint4(0, 0, 0, 0);
+        const uint32_t pj[4] = {pp.x, pp.y, pp.z, pp.w};
+        Rec32 r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j >= glo && j < ghi) {
+            r[j] = ld_rec32(a.grec + 2 * (int64_t)pj[j]);
+            gid[j] = __ldg(a.ids_in + pj[j]);
+          } else {
+            r[j] = Rec32{0.0f, 0.5f, 0.5f, 0.5f, 0.0f, 0.0f, 0.0f, 1e-5f};
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          cell[j] = __float_as_int(r[j].c);
+          xi[0][j] = r[j].x0;
+          xi[1][j] = r[j].x1;
+          xi[2][j] = r[j].x2;
+          v[0][j] = r[j].v0;
+          v[1][j] = r[j].v1;
+          v[2][j] = r[j].v2;
+          dv[j] = r[j].d;
+        }
+      } else {
         int4 c4 = *reinterpret_cast<const int4*>(src + L * 4);
         cell[0] = c4.x;
         cell[1] = c4.y;
@@ -693,6 +740,10 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
                    Rec32{__int_as_float(cell[j]), xi[0][j], xi[1][j], xi[2][j], v[0][j], v[1][j], v[2][j], dj[j]});
         }
       } else if (all_own) {
+        if (GATHER) {
+          __stcs((float4*)(a.s.d + p0), make_float4(dv[0], dv[1], dv[2], dv[3]));
+          __stcs((uint4*)(a.ids_out + p0), make_uint4(gid[0], gid[1], gid[2], gid[3]));
+        }
         __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
         for (int q = 0; q < 3; ++q)
           __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
@@ -713,6 +764,10 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         for (int j = 0; j < 4; ++j) {
           if (!own[j]) continue;
           a.s.cell[p0 + j] = cell[j];
+          if (GATHER) {
+            a.s.d[p0 + j] = dv[j];
+            a.ids_out[p0 + j] = gid[j];
+          }
           for (int q = 0; q < 3; ++q) {
             a.s.xi[q][p0 + j] = xi[q][j];
             if (BF16)
@@ -958,25 +1013,30 @@ bool tma_step_supported(const st_ctx* h) {
   return h->fluid_pad.p != nullptr;
 }
 
-cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) {
+cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records, bool gather) {
   const bool bf = h->prec == ST_MIXED_BF16V;
   const bool phys = p.ngp || p.semi || p.sn || p.cic;
-  if (records && phys) return cudaErrorInvalidValue;
+  if ((records || gather) && phys) return cudaErrorInvalidValue;
+  if (records && gather) return cudaErrorInvalidValue;
   bool pw2 = true;
   for (int q = 0; q < 3; ++q) pw2 = pw2 && (h->geo.n[q] & (h->geo.n[q] - 1)) == 0;
   using Kern = void (*)(const CUtensorMap, const TmaArgs);
-  static const Kern table[12] = {
-      step_mixed_tma_kernel<false, false, false, false>, step_mixed_tma_kernel<false, true, false, false>,
-      step_mixed_tma_kernel<false, false, false, true>,  step_mixed_tma_kernel<false, true, false, true>,
-      step_mixed_tma_kernel<true, false, false, false>,  step_mixed_tma_kernel<true, true, false, false>,
-      step_mixed_tma_kernel<true, false, false, true>,   step_mixed_tma_kernel<true, true, false, true>,
-      step_mixed_tma_kernel<false, false, true, false>,  step_mixed_tma_kernel<false, true, true, false>,
-      step_mixed_tma_kernel<true, false, true, false>,   step_mixed_tma_kernel<true, true, true, false>};
+  static const Kern table[16] = {
+      step_mixed_tma_kernel<false, false, false, false, false>, step_mixed_tma_kernel<false, true, false, false, false>,
+      step_mixed_tma_kernel<false, false, false, true, false>,  step_mixed_tma_kernel<false, true, false, true, false>,
+      step_mixed_tma_kernel<true, false, false, false, false>,  step_mixed_tma_kernel<true, true, false, false, false>,
+      step_mixed_tma_kernel<true, false, false, true, false>,   step_mixed_tma_kernel<true, true, false, true, false>,
+      step_mixed_tma_kernel<false, false, true, false, false>,  step_mixed_tma_kernel<false, true, true, false, false>,
+      step_mixed_tma_kernel<true, false, true, false, false>,   step_mixed_tma_kernel<true, true, true, false, false>,
+      step_mixed_tma_kernel<false, false, false, false, true>,  step_mixed_tma_kernel<false, true, false, false, true>,
+      step_mixed_tma_kernel<true, false, false, false, true>,   step_mixed_tma_kernel<true, true, false, false, true>};
   constexpr int kAttrDevices = 64;
   // a kernel attribute is per device; atomic because handles may be driven from several host threads
   // (setting an attribute twice is harmless)
-  static std::atomic<bool> attr_set[kAttrDevices][12];
-  const int variant = records ? 8 + 2 * (int)bf + (int)pw2 : 4 * (int)bf + 2 * (int)phys + (int)pw2;
+  static std::atomic<bool> attr_set[kAttrDevices][16];
+  const int variant = gather    ? 12 + 2 * (int)bf + (int)pw2
+                      : records ? 8 + 2 * (int)bf + (int)pw2
+                                : 4 * (int)bf + 2 * (int)phys + (int)pw2;
   const Kern kern = table[variant];
   if (h->dev < 0 || h->dev >= kAttrDevices) return cudaErrorInvalidDevice;
   if (!attr_set[h->dev][variant].load(std::memory_order_acquire)) {
@@ -999,6 +1059,11 @@ cudaError_t launch_step_mixed_tma(st_ctx* h, const StepParams& p, bool records) 
   TmaArgs a;
   a.s = carve_mixed(h->state.p, h->cap, bf);
   a.rec = records ? (float4*)h->state_alt.p : nullptr;
+  // the deferred gather of the last sort: permutation, records (old order) and ids in, ids out
+  a.perm = gather ? (const uint32_t*)h->vals[0].p : nullptr;
+  a.grec = gather ? (const float4*)h->state_alt.p : nullptr;
+  a.ids_in = gather ? (const uint32_t*)h->ids.p : nullptr;
+  a.ids_out = gather ? (uint32_t*)h->ids_alt.p : nullptr;
   a.ngp = p.ngp;
   a.semi = p.semi;
   a.sn = p.sn;

@@ -109,3 +109,40 @@ def test_sorting_from_records_equals_sorting_from_arrays(Sim, prec):
         out.append(g)
     for k in out[0]:
         assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+def test_deferred_gather_paths_agree(Sim, prec):
+    """A sort after a record-writing step leaves its payload gather to the next sorted step.  Sorting
+    again first, changing the physics (a kernel that cannot gather) or reading the state in between all
+    run the gather at once; every path gives the same bits as gathering right away."""
+    grid, B, n = (32, 32, 32), 8, 60_001
+
+    def run(read_between):
+        sim = _setup(Sim, prec, grid, B, n, seed=47, reorder_every=5)
+        out = []
+        rd = (lambda: sim.invariants()) if read_between else (lambda: None)
+        sim.step(5, 5e-4)          # sort, 4 plain steps, the record-writing step
+        rd()
+        sim.reorder()              # deferred gather
+        rd()
+        sim.reorder()              # the pending gather first, then a sort from the arrays
+        rd()
+        sim.step(5, 5e-4)
+        rd()
+        sim.reorder()              # after a record-writing step again: deferred
+        rd()
+        sim.set_physics(deposit="cic")
+        sim.step(2, 5e-4)          # the physics instance cannot gather: the gather runs first
+        sim.set_physics()
+        rd()
+        sim.step(6, 5e-4)          # through a deferred sort and its gathering step
+        out.append(sim.sources(host=True))
+        out.append(sim.cells())
+        out.extend(sim.particles())
+        sim.close()
+        return out
+
+    a, b = run(False), run(True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
