@@ -405,3 +405,42 @@ def run_blocked(G: Grid, U, particles, n: int, nsteps: int, dt: float, block: in
                 pending[issued] = ex.submit(work, issued)
                 issued += 1
     return src
+
+
+def adjoint_blocked(G: Grid, U, particles, n: int, nsteps: int, dt: float, lam, block: int = 20_000,
+                    threads: int = 0, keep=None):
+    """orc_adjoint over n particles on several host threads, deterministically: fixed blocks of `block`
+    consecutive particles, each block's adjoint run alone (its trajectory stored whole), the blocks'
+    dL/dalpha and dL/dU added in block order (independent of `threads`; 0 = every core).  The loss is
+    any L(Jtot) with lam = dL/dJtot held fixed (a loss linear in Jtot), so the particles' contributions
+    are independent.  `particles(first, count)` returns (pos0, vel0, d); keep(first, grad_d) receives each
+    block's dL/dd in block order.  Returns (dL/dalpha, dL/dU [ncell, 3])."""
+    import concurrent.futures as cf
+
+    threads = threads or (os.cpu_count() or 1)
+    U = _f64(U)
+    lam = _f64(lam).reshape(3, -1)
+    nblocks = (n + block - 1) // block
+    ga_tot = 0.0
+    gU_tot = np.zeros((ncell(G), 3))
+
+    def work(b):
+        first = b * block
+        cnt = min(block, n - first)
+        pos, vel, d = particles(first, cnt)
+        gd, ga, gU = adjoint(G, U, pos, vel, d, nsteps, dt, lam)
+        return first, gd, ga, gU
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        pending = {b: ex.submit(work, b) for b in range(min(nblocks, threads))}
+        issued = len(pending)
+        for b in range(nblocks):
+            first, gd, ga, gU = pending.pop(b).result()
+            ga_tot = ga_tot + ga
+            np.add(gU_tot, gU, out=gU_tot)
+            if keep is not None:
+                keep(first, gd)
+            if issued < nblocks:
+                pending[issued] = ex.submit(work, issued)
+                issued += 1
+    return ga_tot, gU_tot

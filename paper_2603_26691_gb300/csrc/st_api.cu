@@ -560,8 +560,12 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     // the sorted-step kernel adds one tile flush per covering unit (at most 8 per cell) and counts
     // its global commits itself; the other kernels may add one contribution per particle
     const bool tma = !h->micro_on && h->prec != ST_FP64 && h->sorted && tma_step_supported(h);
-    // a sort that deferred its payload gather: this step gathers, or (another kernel) gather first
-    const bool gather = h->perm_pending && tma && default_physics(h);
+    // a sort is due before the next step: this step writes the state as records for its gather
+    const bool records = tma && default_physics(h) && h->reorder_every > 0 &&
+                         h->steps_since_sort + 1 >= h->reorder_every && h->state_alt.bytes >= (size_t)h->cap * 32;
+    // a sort that deferred its payload gather: this step gathers, unless it is another kernel or
+    // writes records itself (then the gather runs first)
+    const bool gather = h->perm_pending && tma && default_physics(h) && !records;
     if (!gather) ST_TRY(materialize_state(h));
     if (h->micro_on) ST_TRY(micro_prepare_step(h, dt));
     int E = 0;
@@ -585,10 +589,6 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     else if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
     else if (tma) {
-      // a sort is due before the next step: write the state as records for its gather
-      const bool records = default_physics(h) && h->reorder_every > 0 &&
-                           h->steps_since_sort + 1 >= h->reorder_every &&
-                           h->state_alt.bytes >= (size_t)h->cap * 32;
       e = launch_step_mixed_tma(h, p, records, gather);
       if (e == cudaSuccess && gather) gather_step_done(h);
       if (e == cudaSuccess && records) h->records_pending = true;

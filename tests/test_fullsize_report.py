@@ -87,3 +87,55 @@ def test_fourier256_1e9_against_the_all_cores_oracle():
            "oracle_particle_steps_per_s": n * steps / t_cpu})
     assert pos_err <= 1e-5 and vel_err <= 1e-5
     assert l2 <= 2e-4
+
+
+def test_adjoint_64_1e7_gradients_against_the_all_cores_oracle():
+    """The adjoint workload at full size (64^3 Taylor-Green + 10 % Fourier in FP32, 1e7 particles, 200
+    steps of 1e-3, checkpoints every 20) for a loss with dL/dJtot = lam (seeded): dL/dalpha and the whole
+    dL/dU field against the oracle's adjoint of all 1e7 particles on every host core (blocks added in
+    block order), and dL/dd of a seeded sample of particles."""
+    import torch
+
+    from paper_2603_26691_gb300.sim import Sim
+
+    w = inputs.WORKLOADS["tgf64_adjoint_1e7"]
+    U = w.make_field()
+    N, n = w.grid, w.n
+    lam = np.random.default_rng(17).standard_normal((3, N ** 3)) * 1e-3
+    q = inputs.lognormal_qtable()
+    t0 = time.perf_counter()
+    sim = Sim(N, precision="fp64")
+    sim.set_params(reorder_every=0)
+    sim.set_fluid(U)
+    sim.reserve(n)
+    for first in range(0, n, 5_000_000):
+        cnt = min(5_000_000, n - first)
+        p, v, dd, ids = sim.gen_particles(w.seed, first, cnt, q)
+        sim.add_particles(p, dd, v, ids)
+    sim.adjoint_forward(w.steps, w.dt, w.extra["checkpoint"])
+    gd, ga, gU = sim.adjoint_backward(torch.as_tensor(lam, device="cuda"))
+    gd, gU = gd.cpu().numpy(), gU.cpu().numpy()
+    sim.close()
+    t_gpu = time.perf_counter() - t0
+    G = oracle.make_grid(N)
+    sample = np.sort(np.random.default_rng(5).choice(n, 2000, replace=False))
+    ogd_sample = {}
+
+    def keep(first, g):
+        sel = sample[(sample >= first) & (sample < first + len(g))]
+        for i in sel:
+            ogd_sample[int(i)] = g[i - first]
+
+    t1 = time.perf_counter()
+    threads = os.cpu_count() or 1
+    oga, ogU = oracle.adjoint_blocked(G, U, lambda f, c: inputs.particles(w.seed, f, c, qtable=q)[:3], n, w.steps,
+                                      w.dt, lam, block=20_000, threads=threads, keep=keep)
+    t_cpu = time.perf_counter() - t1
+    ogd = np.array([ogd_sample[int(i)] for i in sample])
+    ga_err = abs(ga - oga) / abs(oga)
+    gU_err = np.abs(gU - ogU).max() / np.abs(ogU).max()
+    gd_err = np.abs(gd[sample] - ogd).max() / np.abs(ogd).max()
+    print({"grad_alpha": ga, "oracle": oga, "rel": ga_err, "grad_U_rel_max": gU_err,
+           "grad_U_rel_l2": np.linalg.norm(gU - ogU) / np.linalg.norm(ogU), "grad_d_sample_rel_max": gd_err,
+           "gpu_s": t_gpu, "oracle_all_cores_s": t_cpu, "threads": threads})
+    assert ga_err <= 1e-9 and gU_err <= 1e-9 and gd_err <= 1e-9

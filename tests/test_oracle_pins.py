@@ -470,3 +470,26 @@ def test_blocked_all_cores_run_is_deterministic(oracle_mod):
     assert np.abs(s1 - s0).max() <= 1e-13 * np.abs(s0).max()
     sall = o.run_blocked(G, U, part, n, steps, dt, block=n, threads=3)
     assert np.array_equal(sall, s0)
+
+
+def test_blocked_adjoint_matches_the_single_run(oracle_mod):
+    """The all-cores adjoint (fixed blocks, gradients added in block order) equals the single-thread
+    adjoint up to the rounding of the changed summation order, and is independent of the thread count."""
+    from paper_2603_26691_gb300 import inputs
+
+    o = oracle_mod
+    G = o.make_grid(8)
+    U = inputs.random_fourier(8, seed=6)
+    n, steps, dt = 1_201, 5, 1e-3
+    pos, vel, d, _ = inputs.particles(31, 0, n, vmax=0.1)
+    lam = np.random.default_rng(4).standard_normal((3, 512))
+    gd0, ga0, gU0 = o.adjoint(G, U, pos, vel, d, steps, dt, lam)
+    part = lambda f, c: (pos[:, f:f + c], vel[:, f:f + c], d[f:f + c])  # noqa: E731
+    gds = {}
+    ga1, gU1 = o.adjoint_blocked(G, U, part, n, steps, dt, lam, block=300, threads=1,
+                                 keep=lambda f, g: gds.__setitem__(f, g))
+    ga4, gU4 = o.adjoint_blocked(G, U, part, n, steps, dt, lam, block=300, threads=4)
+    assert ga1 == ga4 and np.array_equal(gU1, gU4)
+    assert np.array_equal(np.concatenate([gds[f] for f in sorted(gds)]), gd0)
+    assert abs(ga1 - ga0) <= 1e-13 * abs(ga0)
+    assert np.abs(gU1 - gU0).max() <= 1e-13 * np.abs(gU0).max()
