@@ -11,14 +11,20 @@ from tests.helpers import face_distance, linear_cells, min_image
 pytestmark = pytest.mark.gpu
 
 # Stated bounds.  FP32 storage: position in cell widths h, velocity relative to |v| + 1 m/s,
-# sources relative to the oracle's L2 / max norm.  BF16 velocity storage rounds the velocity to
-# 8 significant bits (unit roundoff 2^-8) every step and the integrator carries each rounding
-# forward with a factor e^{-a dt} <= 1, so after S steps the velocity error is at most
-# S 2^-8 (|v|max + 1) and the position error at most S 2^-8 times the path S dt max(|v|, 1);
-# sources 1e-2 relative L2.
-BOUNDS = {
-    "mixed_f32": dict(pos_h=1e-5, vel=1e-5, src_l2=1e-5, src_max=1e-4),
-    "mixed_bf16": dict(pos_path="steps", vel="steps", src_l2=1e-2, src_max=None),
+# sources relative to the oracle's L2 / max norm.
+BOUNDS = {"mixed_f32": dict(pos_h=1e-5, vel=1e-5, src_l2=1e-5, src_max=1e-4)}
+# BF16 velocity storage rounds the velocity to 8 significant bits (unit roundoff 2^-8) every step
+# and the integrator carries each rounding forward with a factor e^{-a dt} <= 1, so after S steps
+# the velocity error is at most S 2^-8 (|v| + 1) and the position error at most S 2^-8 times the
+# path S dt max(|v|, 1) (0.078 and 0.156 for the two cases below).  The rounding errors of
+# successive steps have random signs, so the errors found are far below that worst case; the
+# bounds are stated at about twice the values measured on GB300 (velocity relative to |v| + 1,
+# position relative to the path, sources relative L2):
+#   64^3, 200003 particles, 20 steps: 8.1e-3, 3.0e-3, 5.4e-3
+#   32^3, 5001 particles, 40 steps:   1.37e-2, 4.2e-3, 8.0e-3
+BF16_BOUNDS = {
+    (64, 200_003, 20): dict(vel=1.6e-2, pos_path=6e-3, src_l2=1.1e-2),
+    (32, 5_001, 40): dict(vel=2.7e-2, pos_path=8.5e-3, src_l2=1.6e-2),
 }
 
 
@@ -74,12 +80,9 @@ def test_mixed_within_bounds_fourier(Sim, prec, N, n, steps):
     err = _errors(g, opos, ovel, osrc, N)
     err["pos_path"] = err["pos_h"] / N / _path(np.abs(ovel).max(), steps, dt)
     print(prec, N, n, {k: float(v) for k, v in err.items()})
-    b = {k: (steps * 2.0 ** -8 if v == "steps" else v) for k, v in BOUNDS[prec].items()}
-    if prec == "mixed_bf16":
-        err["vel"] = (np.abs(g["vel"] - ovel[:, g["ids"].astype(np.int64)])).max() / (np.abs(ovel).max() + 1.0)
+    b = BOUNDS[prec] if prec == "mixed_f32" else BF16_BOUNDS[(N, n, steps)]
     for k, lim in b.items():
-        if lim is not None:
-            assert err[k] <= lim, (prec, k, err[k], lim)
+        assert err[k] <= lim, (prec, k, err[k], lim)
     # cells agree bit-exactly away from faces (band = the position bound, in cell widths)
     order = g["ids"].astype(np.int64)
     band = b["pos_h"] if "pos_h" in b else b["pos_path"] * _path(np.abs(ovel).max(), steps, dt) * N
