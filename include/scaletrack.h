@@ -395,6 +395,38 @@ st_status st_get_micro_sources(st_handle h, double* out, int reset, int on_devic
  * vapour gained and C_p m T + energy gained stay constant).  Synchronises. */
 st_status st_micro_invariants(st_handle h, double out[2]);
 
+/* Chunked particle sets (Sec. 2.2: a GPU computes one chunk after another and
+ * hides the transfer of a finished chunk behind the next one's computation),
+ * for particle sets larger than device memory.  st_chunks_create turns the
+ * handle (no resident particles) into one that keeps its particles as chunks
+ * of chunk_particles (rounded up to a multiple of 64) in pinned host memory,
+ * in the handle's own storage form (32 B per particle mixed, 56 B FP64, plus
+ * a 4 B id), with three device slots of that capacity.  st_chunks_add appends
+ * n particles (xyz[3][n], vel[3][n] or NULL, d[n]; ids continue from the
+ * number already held) as ceil(n / C) new chunks, the last one possibly not
+ * full.  st_chunks_step advances every particle nsteps steps of dt: chunk by
+ * chunk in order, each copied in, sorted and stepped as resident particles
+ * are (sorting every reorder_every steps), and copied back, with the copies of
+ * the next and the previous chunk overlapping the computation on a second
+ * stream; the sources go into the handle's accumulator (st_get_sources).
+ * Positions and velocities equal those of the same particles stepped
+ * resident; the sources equal a resident run's up to the FP32 rounding of the
+ * run sums (their grouping depends on the storage order).  ms (NULL or 4
+ * doubles) receives the wall time of the pass and the summed times of the
+ * computations, uploads and downloads (CUDA events), which show the overlap.
+ * st_chunks_get copies particles [first, first + count) of the chunks'
+ * storage order to host arrays (positions in FP64 as st_get_particles).
+ * st_chunks_count gives the particle and chunk counts.  While a handle holds
+ * chunks, st_add_particles is refused and st_step sees no particles.
+ * Synchronous.  Errors: STATE, INVALID_ARG, OOM (device slots or pinned host
+ * memory), CUDA. */
+st_status st_chunks_create(st_handle h, int64_t chunk_particles);
+st_status st_chunks_add(st_handle h, int64_t n, const double* xyz, const double* vel, const double* d, int on_device);
+st_status st_chunks_step(st_handle h, int nsteps, double dt, double* ms);
+st_status st_chunks_get(st_handle h, int64_t first, int64_t count, double* xyz, double* vel, double* d,
+                        uint32_t* ids);
+st_status st_chunks_count(st_handle h, int64_t* particles, int64_t* chunks);
+
 /* Largest n that st_sort_keys_static accepts. */
 #define ST_SORT_KEYS_STATIC_MAX_N (1 << 20)
 

@@ -70,6 +70,11 @@ SIGNATURES = {
     "st_adjoint_backward": (_i, [_vp, _vp, _i, _vp, _P(_d), _vp, _i]),
     "st_sort_keys_static": (_i, [_vp, _i64, _i, _vp, _vp, _vp]),
     "st_sort_keys_static_status": (_i, [_vp]),
+    "st_chunks_create": (_i, [_vp, _i64]),
+    "st_chunks_add": (_i, [_vp, _i64, _vp, _vp, _vp, _i]),
+    "st_chunks_step": (_i, [_vp, _i, _d, _P(_d)]),
+    "st_chunks_get": (_i, [_vp, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "st_chunks_count": (_i, [_vp, _P(_i64), _P(_i64)]),
     "st_set_microphysics": (_i, [_vp, _i, _d, _d, _d, _d, _d, _d, _d]),
     "st_set_thermo": (_i, [_vp, _vp, _vp, _i, _i]),
     "st_set_temperatures": (_i, [_vp, _i64, _i64, _vp, _i]),

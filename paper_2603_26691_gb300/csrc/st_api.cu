@@ -162,6 +162,7 @@ void st_destroy(st_handle h) {
   if (!h) return;
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
+  chunk_store_free(h);  // its slot buffers first: the handle's own are freed below
   Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt,
                  &h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start, &h->lsort_aux,
                  &h->acc, &h->red, &h->src_hist[0], &h->src_hist[1], &h->src_hist[2], &h->src_hist[3],
@@ -399,6 +400,7 @@ st_status st_add_particles(st_handle h, int64_t n, const double* xyz, const doub
   if (n < 0) return set_error(h, ST_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return ST_OK;
   if (!xyz || !d) return set_error(h, ST_ERR_INVALID_ARG, "xyz and d are required");
+  if (h->chunks && !h->chunk_adding) return set_error(h, ST_ERR_STATE, "the handle holds chunks: st_chunks_add");
   if (h->np + n > (int64_t(1) << 34)) return set_error(h, ST_ERR_INVALID_ARG, "too many particles");
   ST_TRY(materialize_state(h));
   // stage host data on the device

@@ -42,6 +42,10 @@ struct Geometry {
 
 }  // namespace st
 
+namespace st {
+struct ChunkStore;
+}
+
 struct st_ctx {
   int dev = 0;
   st::Geometry geo{};
@@ -138,10 +142,17 @@ struct st_ctx {
   double rv_max = 0.0;       // largest vapour density of the field (bounds droplet growth per step)
   st::Buf acc_micro;         // exact sources [2][ncell][kWideWords]: vapour mass, energy the fluid gains
   double micro_adds = 0.0;   // digits added to any word of acc_micro since its last carry propagation
+
+  // chunked particle sets (st_chunks_*): the chunks in pinned host memory and the device slots
+  st::ChunkStore* chunks = nullptr;
+  bool chunk_adding = false;  // st_chunks_add is importing through the resident path
   std::string err;
 };
 
 namespace st {
+
+// ---- chunked particle sets (chunks.cu) ------------------------------------------------------
+void chunk_store_free(st_ctx* h);
 
 // ---- host helpers (st_api.cu) -------------------------------------------------------------
 st_status set_error(st_ctx* h, st_status s, const std::string& msg);

@@ -365,6 +365,43 @@ class Sim:
         self._chk(self.lib.st_invariants(self.h, out), "st_invariants")
         return np.array(out[:])
 
+    # -- chunked particle sets (larger than device memory) -------------------------------------------
+    def chunks_create(self, chunk_particles: int):
+        """Keep the particles as chunks of chunk_particles in pinned host memory (see st_chunks_create)."""
+        self._changed()
+        self._chk(self.lib.st_chunks_create(self.h, int(chunk_particles)), "st_chunks_create")
+
+    def chunks_add(self, pos, d, vel=None):
+        """Append particles (pos [3, n], d [n], vel [3, n] or None) as new chunks."""
+        self._changed()
+        dd, dev = _as_f64(d, (-1,))
+        n = int(dd.shape[0])
+        pp, _ = _as_f64(pos, (3, n))
+        vv = None if vel is None else _as_f64(vel, (3, n))[0]
+        self._chk(self.lib.st_chunks_add(self.h, n, _ptr(pp), _ptr(vv), _ptr(dd), int(dev)), "st_chunks_add")
+
+    def chunks_step(self, nsteps: int, dt: float):
+        """Advance every chunk; returns {wall, compute, h2d, d2h} in ms (CUDA events)."""
+        self._changed()
+        ms = (C.c_double * 4)()
+        self._chk(self.lib.st_chunks_step(self.h, int(nsteps), float(dt), ms), "st_chunks_step")
+        return dict(zip(("wall_ms", "compute_ms", "h2d_ms", "d2h_ms"), ms[:]))
+
+    def chunks_count(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._chk(self.lib.st_chunks_count(self.h, C.byref(a), C.byref(b)), "st_chunks_count")
+        return int(a.value), int(b.value)
+
+    def chunks_particles(self, first: int = 0, count: int | None = None):
+        """(pos [3, count], vel [3, count], d [count], ids [count]) of the chunks, host arrays."""
+        if count is None:
+            count = self.chunks_count()[0] - first
+        pos, vel = np.empty((3, count)), np.empty((3, count))
+        d, ids = np.empty(count), np.empty(count, dtype=np.uint32)
+        self._chk(self.lib.st_chunks_get(self.h, int(first), int(count), _ptr(pos), _ptr(vel), _ptr(d), _ptr(ids)),
+                  "st_chunks_get")
+        return pos, vel, d, ids
+
     # -- droplet microphysics (vapour mass and heat transfer) ------------------------------------
     def set_microphysics(self, enable: bool = True, D_v: float = 2.5e-5, kappa_f: float = 0.025, cp_p: float = 4186.0,
                          latent_heat: float = 2.5e6, prandtl: float = 0.71, d_min: float = 1e-7,
