@@ -146,3 +146,29 @@ def test_deferred_gather_paths_agree(Sim, prec):
     a, b = run(False), run(True)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+def test_deferred_gather_with_the_general_sort(Sim, prec):
+    """Fast particles make the neighbourhood sort give way to the general sort while a sort's payload
+    gather is left to the next step: the ids then move in a kernel of their own.  Reading the state
+    after every step turns each step's records back into arrays, so that no gather is deferred; both
+    runs give the same bits."""
+    grid, B, n = (32, 32, 32), 8, 80_001
+
+    def run(read_between):
+        sim = _setup(Sim, prec, grid, B, n, seed=49, reorder_every=5)
+        pos, vel, d, _ = inputs.particles(50, n, 50, vmax=400.0)
+        sim.add_particles(pos, d, vel)
+        for _ in range(16):
+            sim.step(1, 5e-4)
+            if read_between:
+                sim.cells()
+        out = [sim.sources(host=True), sim.cells(), sim.cell_counts()]
+        out.extend(sim.particles())
+        sim.close()
+        return out
+
+    a, b = run(False), run(True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
