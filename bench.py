@@ -46,7 +46,7 @@ STEP_BYTES = {"mixed_f32": 32 + 28, "mixed_bf16": 26 + 22, "fp64": 56 + 48}
 STEP_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc",
                            "step_mixed_tma.cu")
 MEASURED_TRAFFIC = {
-    ("cf2fe03ff0dc04bee0cc803091962aafdca280a689760d14ce001f3636e16af4", "fourier256_mixed_1e9"): 63.7,
+    ("60b071c54a91e3012ad6c63e88a76bb30d9207bc9d8bacad1e0b3315e78fbbac", "fourier256_mixed_1e9"): 63.7,
 }
 
 
@@ -374,6 +374,34 @@ def run_adjoint(args, workload):
            "adjoint_kernel_ms_per_launch": tmc["adjoint"][0] / max(tmc["adjoint"][1], 1),
            "step_kernel_ms_per_launch": tmc["step"][0] / max(tmc["step"][1], 1)}
     sim.close()
+    # the same workload on a mixed FP32-velocity handle: the FP32 adjoint (general mixed step forward,
+    # FP32 reverse step), its gradients compared with the FP64 run's
+    sim32 = setup_sim(workload, n, U32, "mixed_f32", device)
+    sim32.set_params(reorder_every=0)
+    # the same warm-up runs as the FP64 handle's, so that both timed runs start from the same state
+    # (up to the FP32 rounding of the mixed handle)
+    for _ in range(max(args.warmup, 1)):
+        sim32.adjoint_forward(ck, dt, ck)
+        sim32.adjoint_backward(lam)
+    torch.cuda.synchronize()
+    sim32.timers(True)
+    f0e, f1e, f2e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    f0e.record()
+    sim32.adjoint_forward(steps, dt, ck)
+    f1e.record()
+    gd32, ga32, gU32 = sim32.adjoint_backward(lam)
+    f2e.record()
+    torch.cuda.synchronize()
+    tmf = sim32.timers()
+    sim32.timers(False)
+    sim32.close()
+    ff_ms, fb_ms = f0e.elapsed_time(f1e), f1e.elapsed_time(f2e)
+    fp32 = {"forward_ms": ff_ms, "backward_ms": fb_ms, "particle_steps_per_s": n * steps / ((ff_ms + fb_ms) * 1e-3),
+            "adjoint_kernel_ms_per_launch": tmf["adjoint"][0] / max(tmf["adjoint"][1], 1),
+            "step_kernel_ms_per_launch": tmf["step"][0] / max(tmf["step"][1], 1),
+            "grad_alpha_rel_diff_to_fp64": abs(ga32 - ga) / abs(ga),
+            "grad_U_rel_l2_diff_to_fp64": float((torch.linalg.vector_norm(gU32 - gU) / torch.linalg.vector_norm(gU)).item()),
+            "grad_d_rel_l2_diff_to_fp64": float((torch.linalg.vector_norm(gd32 - gd) / torch.linalg.vector_norm(gd)).item())}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -398,7 +426,7 @@ def run_adjoint(args, workload):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "breakdown": {"forward_ms": fwd_ms, "backward_ms": bwd_ms, "timers": tm,
                           "grad_alpha": ga, "grad_d_norm": float(torch.linalg.vector_norm(gd).item()),
-                          "cic_deposit": cic}}
+                          "cic_deposit": cic, "fp32_adjoint": fp32}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

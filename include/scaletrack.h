@@ -246,17 +246,21 @@ st_status st_clear_particles(st_handle h);
 /* Forward run for differentiation: advance all particles nsteps steps of
  * length dt (no reordering during the run), adding the impulses to the source
  * accumulator as st_step does, and keep checkpoints of positions and
- * velocities every checkpoint_every steps (6 x n x 8 bytes each).  With
- * Jtot the time-summed per-cell source, st_adjoint_backward then returns the
- * gradient of any loss L(Jtot).  The method has no adjoint in the paper; this
- * differentiates the step of Sec. 2.1 (Eqs. 9-11) as implemented here: with
- * the cell deposit the deposit cell is held fixed (its derivative is zero
- * almost everywhere); with the cloud-in-cell deposit (st_set_physics) its
- * trilinear weights are differentiated as well.  FP64 handles with the
- * trilinear gather, the exponential integrator and Stokes drag only.
+ * velocities every checkpoint_every steps (FP64 handles: 6 x n x 8 bytes
+ * each; mixed FP32-velocity handles: the cells, offsets and velocities, 28 x n
+ * bytes, n rounded up to 64, stepped by the general mixed kernel in storage
+ * order).  With Jtot the time-summed per-cell source, st_adjoint_backward then
+ * returns the gradient of any loss L(Jtot).  The method has no adjoint in the
+ * paper; this differentiates the step of Sec. 2.1 (Eqs. 9-11) as implemented
+ * here: with the cell deposit the deposit cell is held fixed (its derivative
+ * is zero almost everywhere); with the cloud-in-cell deposit (st_set_physics,
+ * FP64 handles) its trilinear weights are differentiated as well.  The
+ * trilinear gather, the exponential integrator and Stokes drag only.  On
+ * mixed handles the adjoint runs in FP32 (see st_adjoint_backward).
  * Changing particles, parameters, the physics or the fluid, or reordering,
  * invalidates the recorded run.
- * Errors: STATE (not FP64, other physics, no particles), INVALID_ARG,
+ * Errors: STATE (BF16-velocity handle, microphysics on, other physics, the
+ * cloud-in-cell deposit on a mixed handle, no particles), INVALID_ARG,
  * NONFINITE, OOM, CUDA. */
 st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every);
 
@@ -267,7 +271,10 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
  * the current storage order, *grad_alpha = dL/d(drag_scale) (host pointer
  * always), grad_U[ncell][3] = dL/dU in the layout of st_set_fluid.  All sums
  * are formed in a fixed order or in exact fixed point, so results are
- * bit-reproducible.  Synchronises.
+ * bit-reproducible.  Mixed handles: the reverse step runs in FP32 (lam
+ * rounded to FP32, FP32 adjoints of position and velocity, each step's
+ * dL/dd and dL/d(drag_scale) terms accumulated in FP64, each FP32 dL/dU
+ * term added exactly).  Synchronises.
  * Errors: STATE (no recorded run), INVALID_ARG, OOM, CUDA. */
 st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device, double* grad_d,
                               double* grad_alpha, double* grad_U, int on_device);

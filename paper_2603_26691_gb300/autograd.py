@@ -1,9 +1,9 @@
 """Differentiable time-summed source field: a torch.autograd.Function over the CUDA adjoint.
 
 J = LagrangianSources.apply(d, alpha, U, sim, pos0, vel0, nsteps, dt, checkpoint_every)
-runs nsteps FP64 steps of the particles (initial positions pos0, velocities vel0,
-diameters d) with drag scale alpha through the frozen fluid U, and returns the per-cell
-impulse summed over the run, J [3, ncell].  Its backward calls the library's adjoint
+runs nsteps steps of the particles (initial positions pos0, velocities vel0, diameters d) with
+drag scale alpha through the frozen fluid U - in FP64 on an FP64 Sim, in FP32 on a mixed
+FP32-velocity Sim - and returns the per-cell impulse summed over the run, J [3, ncell].  Its backward calls the library's adjoint
 (st_adjoint_backward): dL/dd per particle, dL/dalpha and dL/dU, with the deposit cell held
 fixed under the cell deposit (its derivative is zero almost everywhere) and the deposit weights
 differentiated under the cloud-in-cell deposit.  All arithmetic runs in the CUDA library.

@@ -1,5 +1,5 @@
-// Hand-written adjoint of the FP64 Lagrangian step, run backward through
-// checkpointed segments with recomputation.
+// Hand-written adjoint of the Lagrangian step (FP64 handles in FP64, mixed FP32-velocity handles in
+// FP32), run backward through checkpointed segments with recomputation.
 //
 // For a loss L(Jtot) of the time-summed per-cell source, with
 // lam = dL/dJtot given per cell, one reverse step of one particle runs the
@@ -190,6 +190,148 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
   }
 }
 
+// ---- the FP32 adjoint of the mixed-precision step ----
+//
+// The same reverse sweep in FP32 on the mixed state: the tape gives the start-of-step cell, the
+// offsets in it and the velocity; the trilinear stencil is the forward kernel's (base cell and
+// fractions from the offset, corners read from the ghost-padded FP32 field), the deposit cell the
+// start cell.  Position adjoints are per metre, as in the FP64 adjoint (the periodic wrap and the
+// whole-cell carry are translations).  Each step's dL/dd and dL/dalpha contributions are FP32 and
+// accumulate in FP64; each corner's dL/dU contribution (an FP32 product) is added exactly.
+
+struct AdjMixedArgs {
+  MixedState tape;
+  const float* __restrict__ d;
+  float* __restrict__ xb[3];
+  float* __restrict__ vb[3];
+  double* __restrict__ db;
+  double* __restrict__ ab_part;
+  const float4* __restrict__ Up;     // ghost-padded field
+  const float* __restrict__ lam;     // [3][ncell]
+  long long* __restrict__ Uw;
+  int64_t n, ncell;
+  int nx, ny, nz;
+  float inv_h[3];
+  float dt, cadt, inv_ca, mcoef, g[3], gdt[3];
+  double inv_alpha;
+};
+
+__global__ void __launch_bounds__(kAdjThreads) adjoint_mixed_kernel(const AdjMixedArgs a) {
+  const int n3[3] = {a.nx, a.ny, a.nz};
+  const int64_t row = a.nx + 2 * kFluidPad, slab = row * (a.ny + 2 * kFluidPad);
+  double alphab_sum = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int c = a.tape.cell[p];
+    const int ci[3] = {cell_i(c), cell_j(c), cell_k(c)};
+    float v[3], xb[3], vb[3], f[3];
+    int i0[3], lo[3], hi[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float o = a.tape.xi[q][p];
+      v[q] = ((const float*)a.tape.v[q])[p];
+      xb[q] = a.xb[q][p];
+      vb[q] = a.vb[q][p];
+      const bool up_half = o >= 0.5f;
+      i0[q] = ci[q] - (up_half ? 0 : 1);  // -1 .. n - 1
+      f[q] = o + (up_half ? -0.5f : 0.5f);
+      lo[q] = i0[q] < 0 ? i0[q] + n3[q] : i0[q];
+      hi[q] = i0[q] + 1 >= n3[q] ? i0[q] + 1 - n3[q] : i0[q] + 1;
+    }
+    const float d = a.d[p];
+    const int64_t key = ci[0] + (int64_t)a.nx * (ci[1] + (int64_t)a.ny * ci[2]);
+    const float4* b = a.Up + (i0[0] + kFluidPad) + row * (i0[1] + kFluidPad) + slab * (i0[2] + kFluidPad);
+    float4 Uc[8];
+    float W[8];
+    float up[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
+      Uc[k] = __ldg(b + di + row * dj + slab * dk);
+      W[k] = (di ? f[0] : 1.0f - f[0]) * (dj ? f[1] : 1.0f - f[1]) * (dk ? f[2] : 1.0f - f[2]);
+      up[0] = fmaf(W[k], Uc[k].x, up[0]);
+      up[1] = fmaf(W[k], Uc[k].y, up[1]);
+      up[2] = fmaf(W[k], Uc[k].z, up[2]);
+    }
+    const float dd = d * d;
+    const float adt = a.cadt / dd;     // a dt
+    const float inv_ra = dd * a.inv_ca;  // 1 / a
+    const float ra = 1.0f / inv_ra;
+    const float inv_ra2 = inv_ra * inv_ra;
+    const float inv_d = 1.0f / d;
+    const float E1 = -expm1f(-adt);
+    const float E = 1.0f - E1;
+    const float Q = E1 * inv_ra;
+    const float m = a.mcoef * dd * d;
+    float wt[3], vn[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      wt[q] = fmaf(a.g[q], inv_ra, up[q]);
+      vn[q] = fmaf(v[q] - wt[q], E, wt[q]);
+    }
+    const float Jb[3] = {a.lam[key], a.lam[a.ncell + key], a.lam[2 * a.ncell + key]};
+    float mb = 0.0f, Eb = 0.0f, E1b = 0.0f, Qb = 0.0f, ab = 0.0f;
+    float ub[3], vsb[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float vnb = vb[q] - m * Jb[q];
+      vsb[q] = fmaf(m, Jb[q], fmaf(vnb, E, xb[q] * Q));
+      mb -= ((vn[q] - v[q]) - a.gdt[q]) * Jb[q];
+      const float wtb = fmaf(vnb, E1, xb[q] * (a.dt - Q));
+      E1b = fmaf(vnb, wt[q], E1b);
+      Eb = fmaf(vnb, v[q], Eb);
+      Qb = fmaf(xb[q], v[q] - wt[q], Qb);
+      ub[q] = wtb;
+      ab -= wtb * a.g[q] * inv_ra2;
+    }
+    E1b = fmaf(Qb, inv_ra, E1b);
+    ab -= Qb * E1 * inv_ra2;
+    ab = fmaf(a.dt * E, E1b - Eb, ab);
+    alphab_sum += (double)(ab * ra) * a.inv_alpha;
+    a.db[p] += (double)(ab * (-2.0f * ra * inv_d) + mb * 3.0f * m * inv_d);
+    float dot[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
+      dot[k] = fmaf(Uc[k].x, ub[0], fmaf(Uc[k].y, ub[1], Uc[k].z * ub[2]));
+      const int64_t corner = (di ? hi[0] : lo[0]) + (int64_t)a.nx * ((dj ? hi[1] : lo[1]) + (int64_t)a.ny * (dk ? hi[2] : lo[2]));
+      long long* w = a.Uw + corner * 3 * kWideWords;
+      wide_add_f32(w, W[k] * ub[0]);
+      wide_add_f32(w + kWideWords, W[k] * ub[1]);
+      wide_add_f32(w + 2 * kWideWords, W[k] * ub[2]);
+    }
+    auto lerp = [](float p0, float p1, float t) { return fmaf(t, p1 - p0, p0); };
+    float fb[3];
+    {
+      const float e00 = dot[1] - dot[0], e10 = dot[3] - dot[2], e01 = dot[5] - dot[4], e11 = dot[7] - dot[6];
+      fb[0] = lerp(lerp(e00, e10, f[1]), lerp(e01, e11, f[1]), f[2]);
+      const float g00 = dot[2] - dot[0], g10 = dot[3] - dot[1], g01 = dot[6] - dot[4], g11 = dot[7] - dot[5];
+      fb[1] = lerp(lerp(g00, g10, f[0]), lerp(g01, g11, f[0]), f[2]);
+      const float h00 = dot[4] - dot[0], h10 = dot[5] - dot[1], h01 = dot[6] - dot[2], h11 = dot[7] - dot[3];
+      fb[2] = lerp(lerp(h00, h10, f[0]), lerp(h01, h11, f[0]), f[1]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      a.xb[q][p] = fmaf(fb[q], a.inv_h[q], xb[q]);
+      a.vb[q][p] = vsb[q];
+    }
+  }
+  __shared__ double sh[kAdjThreads / 32];
+  double s = alphab_sum;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) t += sh[w];
+    a.ab_part[blockIdx.x] += t;
+  }
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 // value of each carry-save accumulator in FP64: out[c][q]
 __global__ void wide_to_f64_kernel(const long long* __restrict__ Uw, double* __restrict__ out, int64_t m) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -239,6 +381,47 @@ cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s) {
     adjoint_step_kernel<true><<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
   else
     adjoint_step_kernel<false><<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_step_mixed(st_ctx* h, const AdjointMixedArgs& s) {
+  AdjMixedArgs a;
+  a.tape = s.tape;
+  a.d = s.d;
+  for (int q = 0; q < 3; ++q) {
+    a.xb[q] = s.xb[q];
+    a.vb[q] = s.vb[q];
+    a.inv_h[q] = (float)h->geo.inv_h[q];
+    a.g[q] = (float)h->g[q];
+    a.gdt[q] = (float)(h->g[q] * s.dt);
+  }
+  a.db = s.db;
+  a.ab_part = s.ab_part;
+  a.Up = (const float4*)h->fluid_pad.p;
+  a.lam = s.lam32;
+  a.Uw = s.Uw;
+  a.n = h->np;
+  a.ncell = h->geo.ncell;
+  a.nx = h->geo.n[0];
+  a.ny = h->geo.n[1];
+  a.nz = h->geo.n[2];
+  const double ca = 18.0 * h->mu * h->alpha / h->rho_p;
+  a.dt = (float)s.dt;
+  a.cadt = (float)(ca * s.dt);
+  a.inv_ca = (float)(1.0 / ca);
+  a.mcoef = (float)(h->mult * h->rho_p * 3.14159265358979323846 / 6.0);
+  a.inv_alpha = 1.0 / h->alpha;
+  adjoint_mixed_kernel<<<kAdjBlocks, kAdjThreads, 0, h->stream>>>(a);
+  h->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f64_to_f32(st_ctx* h, const double* in, float* out, int64_t m) {
+  int64_t b = (m + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  f64_to_f32_kernel<<<(int)b, 256, 0, h->stream>>>(in, out, m);
   h->launches += 1;
   return cudaGetLastError();
 }

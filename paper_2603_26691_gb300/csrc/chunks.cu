@@ -7,8 +7,9 @@
 // chunk capacity C (cell | offsets | velocities | diameters, then the ids), so a chunk moves with two
 // copies each way.  Three device slots rotate: while chunk k computes in its slot (the handle's own
 // state buffers are bound to it, the chunk is sorted and stepped exactly as resident particles are),
-// chunk k+1 is copied into the next slot and chunk k-1 out of the previous one, on a second stream
-// ordered by events.  A particle's arithmetic does not depend on the other particles, so positions and
+// chunk k+1 is copied into the next slot and chunk k-1 out of the previous one, on an upload and a
+// download stream of their own (the two directions of the host link run at once), ordered by
+// events.  A particle's arithmetic does not depend on the other particles, so positions and
 // velocities are those of a resident run; the sources of every chunk go into the handle's exact
 // accumulator, whose sum does not depend on the order of the chunks.
 #include <algorithm>
@@ -26,7 +27,7 @@ struct ChunkStore {
   std::vector<char*> host;        // pinned: state block (state_bytes(prec, C)) then ids (4 C)
   size_t state_bytes_ = 0;
   Buf slot_state[3], slot_ids[3];  // device slots (slot 0 starts as the handle's own buffers)
-  cudaStream_t copy = nullptr;
+  cudaStream_t up_s = nullptr, down_s = nullptr;
   cudaEvent_t up[3] = {}, done[3] = {}, down[3] = {}, t0 = nullptr, t1 = nullptr;
   double ms_compute = 0.0, ms_h2d = 0.0, ms_d2h = 0.0;
 };
@@ -34,7 +35,8 @@ struct ChunkStore {
 void chunk_store_free(st_ctx* h) {
   ChunkStore* cs = h->chunks;
   if (!cs) return;
-  if (cs->copy) cudaStreamSynchronize(cs->copy);
+  if (cs->up_s) cudaStreamSynchronize(cs->up_s);
+  if (cs->down_s) cudaStreamSynchronize(cs->down_s);
   for (char* p : cs->host) cudaFreeHost(p);
   for (int s = 0; s < 3; ++s) {
     // slot buffers that are not (any longer) the handle's own
@@ -50,7 +52,8 @@ void chunk_store_free(st_ctx* h) {
   }
   if (cs->t0) cudaEventDestroy(cs->t0);
   if (cs->t1) cudaEventDestroy(cs->t1);
-  if (cs->copy) cudaStreamDestroy(cs->copy);
+  if (cs->up_s) cudaStreamDestroy(cs->up_s);
+  if (cs->down_s) cudaStreamDestroy(cs->down_s);
   delete cs;
   h->chunks = nullptr;
 }
@@ -121,7 +124,8 @@ st_status st_chunks_create(st_handle h, int64_t chunk_particles) {
     if (s == ST_OK) s = dev_alloc(h, cs->slot_ids[k], ib);
   }
   cudaError_t e = cudaSuccess;
-  if (s == ST_OK) e = cudaStreamCreateWithFlags(&cs->copy, cudaStreamNonBlocking);
+  if (s == ST_OK) e = cudaStreamCreateWithFlags(&cs->up_s, cudaStreamNonBlocking);
+  if (s == ST_OK && e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs->down_s, cudaStreamNonBlocking);
   for (int k = 0; k < 3 && s == ST_OK && e == cudaSuccess; ++k) {
     e = cudaEventCreate(&cs->up[k]);
     if (e == cudaSuccess) e = cudaEventCreate(&cs->done[k]);
@@ -230,7 +234,7 @@ st_status st_chunks_step(st_handle h, int nsteps, double dt, double* ms) {
   const int64_t K = (int64_t)cs->count.size();
   if (K == 0 || nsteps == 0) return ST_OK;
   const size_t sb = cs->state_bytes_, ib = (size_t)cs->C * 4;
-  cudaStream_t cp = cs->copy, comp = h->stream;
+  cudaStream_t up = cs->up_s, down = cs->down_s, comp = h->stream;
   std::vector<cudaEvent_t> tev;  // per chunk: h2d start/end, compute start/end, d2h start/end
   auto ev = [&]() {
     cudaEvent_t e = nullptr;
@@ -240,17 +244,18 @@ st_status st_chunks_step(st_handle h, int nsteps, double dt, double* ms) {
   };
   std::vector<cudaEvent_t> marks;
   cudaError_t e = cudaEventRecord(cs->t0, comp);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(cp, cs->t0, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(up, cs->t0, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(down, cs->t0, 0);
   auto upload = [&](int64_t k) -> cudaError_t {
     const int s = (int)(k % 3);
     cudaError_t r = cudaSuccess;
-    if (k >= 3) r = cudaStreamWaitEvent(cp, cs->down[s], 0);  // chunk k-3's download left the slot
+    if (k >= 3) r = cudaStreamWaitEvent(up, cs->down[s], 0);  // chunk k-3's download left the slot
     cudaEvent_t a = ev(), b = ev();
-    if (r == cudaSuccess) r = cudaEventRecord(a, cp);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(cs->slot_state[s].p, cs->host[k], sb, cudaMemcpyHostToDevice, cp);
-    if (r == cudaSuccess) r = cudaMemcpyAsync(cs->slot_ids[s].p, cs->host[k] + sb, ib, cudaMemcpyHostToDevice, cp);
-    if (r == cudaSuccess) r = cudaEventRecord(b, cp);
-    if (r == cudaSuccess) r = cudaEventRecord(cs->up[s], cp);
+    if (r == cudaSuccess) r = cudaEventRecord(a, up);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(cs->slot_state[s].p, cs->host[k], sb, cudaMemcpyHostToDevice, up);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(cs->slot_ids[s].p, cs->host[k] + sb, ib, cudaMemcpyHostToDevice, up);
+    if (r == cudaSuccess) r = cudaEventRecord(b, up);
+    if (r == cudaSuccess) r = cudaEventRecord(cs->up[s], up);
     marks.push_back(a);
     marks.push_back(b);
     return r;
@@ -283,20 +288,23 @@ st_status st_chunks_step(st_handle h, int nsteps, double dt, double* ms) {
     if (st != ST_OK) break;
     e = cudaEventRecord(cs->done[s], comp);
     // chunk k back to its pinned block once computed
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cp, cs->done[s], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(down, cs->done[s], 0);
     cudaEvent_t c = ev(), dd = ev();
-    if (e == cudaSuccess) e = cudaEventRecord(c, cp);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cs->host[k], cs->slot_state[s].p, sb, cudaMemcpyDeviceToHost, cp);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(cs->host[k] + sb, cs->slot_ids[s].p, ib, cudaMemcpyDeviceToHost, cp);
-    if (e == cudaSuccess) e = cudaEventRecord(dd, cp);
-    if (e == cudaSuccess) e = cudaEventRecord(cs->down[s], cp);
+    if (e == cudaSuccess) e = cudaEventRecord(c, down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cs->host[k], cs->slot_state[s].p, sb, cudaMemcpyDeviceToHost, down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cs->host[k] + sb, cs->slot_ids[s].p, ib, cudaMemcpyDeviceToHost, down);
+    if (e == cudaSuccess) e = cudaEventRecord(dd, down);
+    if (e == cudaSuccess) e = cudaEventRecord(cs->down[s], down);
     d2h_ev.push_back({c, dd});
     st = cuda_check(h, e, "chunk download");
   }
-  if (st == ST_OK) e = cudaEventRecord(cs->t1, cp);
-  cudaError_t e2 = cudaStreamSynchronize(cp);
+  // the last download ends the pass (it follows every upload and computation through the events)
+  if (st == ST_OK) e = cudaEventRecord(cs->t1, down);
+  cudaError_t e1 = cudaStreamSynchronize(up);
+  cudaError_t e2 = cudaStreamSynchronize(down);
   cudaError_t e3 = cudaStreamSynchronize(comp);
-  if (st == ST_OK) st = cuda_check(h, e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3), "chunk pass");
+  if (st == ST_OK)
+    st = cuda_check(h, e != cudaSuccess ? e : (e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3)), "chunk pass");
   h->np = 0;
   h->sorted = false;
   if (st == ST_OK && ms) {
@@ -323,7 +331,7 @@ st_status st_chunks_get(st_handle h, int64_t first, int64_t count, double* xyz, 
                         uint32_t* ids) {
   ST_TRY(chunk_check(h));
   ChunkStore* cs = h->chunks;
-  ST_TRY(cuda_check(h, cudaStreamSynchronize(cs->copy), "chunk copies"));
+  ST_TRY(cuda_check(h, cudaStreamSynchronize(cs->down_s), "chunk copies"));
   int64_t total = 0;
   for (int64_t c : cs->count) total += c;
   if (first < 0 || count < 0 || first + count > total) return set_error(h, ST_ERR_INVALID_ARG, "range out of bounds");

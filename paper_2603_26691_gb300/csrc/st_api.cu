@@ -780,9 +780,129 @@ st_status st_clear_particles(st_handle h) {
   return ST_OK;
 }
 
+static int64_t round64(int64_t n);
+static cudaError_t copy_mixed7(const MixedState& dst, const MixedState& src, int64_t n, cudaStream_t st);
+
+// The FP32 adjoint of a mixed FP32-velocity handle: like the FP64 one (segments from the last,
+// each recomputed from its checkpoint with the general mixed kernel keeping the state at the start of
+// every step, then reversed step by step), with FP32 adjoints of position and velocity.
+static st_status adjoint_backward_mixed(st_handle h, const double* lam, int lam_on_device, double* grad_d,
+                                        double* grad_alpha, double* grad_U, int on_device) {
+  const int64_t n = h->np, nc = h->geo.ncell, cn = round64(n);
+  const int C = h->adj_every, nsteps = h->adj_nsteps;
+  const int K = (nsteps + C - 1) / C;
+  const double pi = 3.14159265358979323846;
+  const size_t sb = (size_t)28 * cn;  // one state: cell, offsets, velocities
+  Buf blam, lam32, work, tape, adj, db, abp, Uw, tmp;
+  auto cleanup = [&]() {
+    for (Buf* b : {&blam, &lam32, &work, &tape, &adj, &db, &abp, &Uw, &tmp}) dev_free(h, *b);
+  };
+  st_status s = dev_alloc(h, work, state_bytes(ST_MIXED_F32, cn));
+  if (s == ST_OK) s = dev_alloc(h, tape, (size_t)C * sb);
+  if (s == ST_OK) s = dev_alloc(h, adj, (size_t)6 * cn * sizeof(float));
+  if (s == ST_OK) s = dev_alloc(h, db, (size_t)cn * sizeof(double));
+  if (s == ST_OK) s = dev_alloc(h, abp, (size_t)kAdjBlocks * sizeof(double));
+  if (s == ST_OK) s = dev_alloc(h, Uw, (size_t)nc * 3 * kWideWords * sizeof(long long));
+  if (s == ST_OK) s = dev_alloc(h, lam32, (size_t)3 * nc * sizeof(float));
+  if (s == ST_OK && !lam_on_device) s = dev_alloc(h, blam, (size_t)3 * nc * sizeof(double));
+  if (s == ST_OK && !on_device) s = dev_alloc(h, tmp, (size_t)3 * nc * sizeof(double));
+  if (s != ST_OK) {
+    cleanup();
+    return s;
+  }
+  cudaError_t e = cudaSuccess;
+  const double* dlam = lam;
+  if (!lam_on_device) {
+    e = cudaMemcpyAsync(blam.p, lam, (size_t)3 * nc * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    dlam = (const double*)blam.p;
+  }
+  if (e == cudaSuccess) e = launch_f64_to_f32(h, dlam, (float*)lam32.p, 3 * nc);
+  if (e == cudaSuccess) e = cudaMemsetAsync(adj.p, 0, adj.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(db.p, 0, db.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(abp.p, 0, abp.bytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(Uw.p, 0, Uw.bytes, h->stream);
+  const MixedState st = carve_mixed(h->state.p, h->cap, false);
+  MixedState ws = carve_mixed(work.p, cn, false);
+  ws.d = st.d;
+  float* A = (float*)adj.p;
+  StepParams p;
+  p.dt = h->adj_dt;
+  p.ca = 18.0 * h->mu * h->alpha / h->rho_p;
+  p.mcoef = h->mult * h->rho_p * pi / 6.0;
+  for (int q = 0; q < 3; ++q) p.g[q] = h->g[q];
+  p.E = 0;
+  p.scale = 1.0;
+  for (int seg = K - 1; seg >= 0 && e == cudaSuccess; --seg) {
+    const int s0 = seg * C, s1 = std::min(nsteps, s0 + C);
+    e = cudaMemcpyAsync(work.p, (char*)h->ckpt.p + (size_t)seg * sb, sb, cudaMemcpyDeviceToDevice, h->stream);
+    for (int k = s0; k < s1 && e == cudaSuccess; ++k) {
+      e = cudaMemcpyAsync((char*)tape.p + (size_t)(k - s0) * sb, work.p, sb, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess && k + 1 < s1) {
+        timer_begin(h, ST_TIMER_STEP, h->stream);
+        e = launch_step_mixed_state(h, ws, n, nullptr, p);
+        timer_end(h, ST_TIMER_STEP, h->stream);
+      }
+    }
+    for (int k = s1 - 1; k >= s0 && e == cudaSuccess; --k) {
+      AdjointMixedArgs a;
+      a.tape = carve_mixed((char*)tape.p + (size_t)(k - s0) * sb, cn, false);
+      a.d = st.d;
+      for (int q = 0; q < 3; ++q) {
+        a.xb[q] = A + q * cn;
+        a.vb[q] = A + (3 + q) * cn;
+      }
+      a.db = (double*)db.p;
+      a.ab_part = (double*)abp.p;
+      a.lam32 = (const float*)lam32.p;
+      a.Uw = (long long*)Uw.p;
+      a.dt = h->adj_dt;
+      timer_begin(h, ST_TIMER_ADJOINT, h->stream);
+      e = launch_adjoint_step_mixed(h, a);
+      timer_end(h, ST_TIMER_ADJOINT, h->stream);
+    }
+  }
+  std::vector<double> hab(kAdjBlocks);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hab.data(), abp.p, kAdjBlocks * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && grad_d)
+    e = cudaMemcpyAsync(grad_d, db.p, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        h->stream);
+  if (e == cudaSuccess && grad_U) {
+    double* dst = on_device ? grad_U : (double*)tmp.p;
+    e = launch_wide_to_f64(h, (const long long*)Uw.p, dst, 3 * nc);
+    if (e == cudaSuccess && !on_device)
+      e = cudaMemcpyAsync(grad_U, dst, (size_t)3 * nc * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cleanup();
+  ST_TRY(cuda_check(h, e, "adjoint backward (FP32)"));
+  if (grad_alpha) {
+    double t = 0.0;
+    for (int b = 0; b < kAdjBlocks; ++b) t += hab[b];
+    *grad_alpha = t;
+  }
+  return ST_OK;
+}
+
+// the mixed state's first seven arrays (cell, offsets, velocities) at a stride of cap particles
+static cudaError_t copy_mixed7(const MixedState& dst, const MixedState& src, int64_t n, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(dst.cell, src.cell, n * 4, cudaMemcpyDeviceToDevice, st);
+  for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+    e = cudaMemcpyAsync(dst.xi[q], src.xi[q], n * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst.v[q], src.v[q], n * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  return e;
+}
+
+static int64_t round64(int64_t n) { return (n + 63) & ~int64_t(63); }
+
 st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_every) {
   ST_TRY(check_handle(h));
-  if (h->prec != ST_FP64) return set_error(h, ST_ERR_STATE, "the adjoint needs an FP64 handle");
+  if (h->prec == ST_MIXED_BF16V)
+    return set_error(h, ST_ERR_STATE, "the adjoint needs an FP64 or an FP32-velocity handle");
+  if (h->micro_on) return set_error(h, ST_ERR_STATE, "the adjoint does not cover the microphysics");
+  if (h->prec != ST_FP64 && h->phys_deposit != ST_DEPOSIT_CELL)
+    return set_error(h, ST_ERR_STATE, "the FP32 adjoint needs the deposit into the containing cell");
   if (h->phys_gather != ST_GATHER_TRILINEAR || h->phys_integrator != ST_INTEGRATOR_EXPONENTIAL ||
       h->phys_drag != ST_DRAG_STOKES)
     return set_error(h, ST_ERR_STATE,
@@ -793,12 +913,21 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
   if (h->np == 0) return set_error(h, ST_ERR_STATE, "no particles");
   const int64_t n = h->np;
   const int K = (nsteps + checkpoint_every - 1) / checkpoint_every;
-  ST_TRY(ensure(h, h->ckpt, (size_t)K * 6 * n * sizeof(double)));
+  const bool mixed = h->prec != ST_FP64;
+  if (mixed) ST_TRY(materialize_state(h));
+  // checkpoints: x, v in FP64 (48 B per particle), or cell, offsets, velocities (28 B) at a stride of
+  // n rounded up to 64
+  const size_t ck_bytes = mixed ? (size_t)28 * round64(n) : (size_t)6 * n * sizeof(double);
+  ST_TRY(ensure(h, h->ckpt, (size_t)K * ck_bytes));
   const double pi = 3.14159265358979323846;
   F64State s = carve_f64(h->state.p, h->cap);
   double* ck = (double*)h->ckpt.p;
   for (int step = 0; step < nsteps; ++step) {
-    if (step % checkpoint_every == 0) {
+    if (mixed && step % checkpoint_every == 0) {
+      const MixedState slot = carve_mixed((char*)h->ckpt.p + (size_t)(step / checkpoint_every) * ck_bytes,
+                                          round64(n), false);
+      ST_TRY(cuda_check(h, copy_mixed7(slot, carve_mixed(h->state.p, h->cap, false), n, h->stream), "checkpoint"));
+    } else if (step % checkpoint_every == 0) {
       double* slot = ck + (size_t)(step / checkpoint_every) * 6 * n;
       cudaError_t e = cudaSuccess;
       for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
@@ -819,7 +948,8 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
     p.scale = std::ldexp(1.0, E);
     p.cic = h->phys_deposit == ST_DEPOSIT_CIC;  // the other physics are the defaults here
     timer_begin(h, ST_TIMER_STEP, h->stream);
-    const cudaError_t fe = launch_step_f64(h, p);
+    // mixed handles: the general kernel in storage order, which the backward pass recomputes with
+    const cudaError_t fe = mixed ? launch_step_mixed(h, p) : launch_step_f64(h, p);
     timer_end(h, ST_TIMER_STEP, h->stream);
     ST_TRY(cuda_check(h, fe, "adjoint forward step"));
   }
@@ -835,6 +965,7 @@ st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device,
   ST_TRY(check_handle(h));
   if (!h->adj_ready) return set_error(h, ST_ERR_STATE, "no st_adjoint_forward run to differentiate");
   if (!lam) return set_error(h, ST_ERR_INVALID_ARG, "lam is NULL");
+  if (h->prec != ST_FP64) return adjoint_backward_mixed(h, lam, lam_on_device, grad_d, grad_alpha, grad_U, on_device);
   const int64_t n = h->np, nc = h->geo.ncell;
   const int C = h->adj_every, nsteps = h->adj_nsteps;
   const int K = (nsteps + C - 1) / C;

@@ -371,6 +371,26 @@ constexpr int kAdjBlocks = 152 * 8;
 
 // Carry-save accumulator: value = sum_i w[i] * 2^(32 i + kWideBase); each
 // contribution adds 32-bit digits, so each int64 word absorbs 2^31 of them.
+// an FP32 value into the same accumulator: its 24-bit significand spans at most two words
+__device__ __forceinline__ void wide_add_f32(long long* w, float x) {
+  if (x == 0.0f) return;
+  const uint32_t b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xff);
+  unsigned long long man = b & 0x7fffffu;
+  if (ex != 0) man |= 1u << 23;                       // subnormals: man * 2^(1 - 150)
+  const int s = (ex == 0 ? 1 : ex) - 150 - kWideBase;  // >= 11: every FP32 value is on the grid
+  const int q = s >> 5, r = s & 31;
+  const unsigned long long lo = man << r;  // < 2^55
+  long long d0 = (long long)(lo & 0xffffffffull);
+  long long d1 = (long long)(lo >> 32);
+  if (b >> 31) {
+    d0 = -d0;
+    d1 = -d1;
+  }
+  if (d0 != 0 && q < kWideWords) atomicAdd((unsigned long long*)&w[q], (unsigned long long)d0);
+  if (d1 != 0 && q + 1 < kWideWords) atomicAdd((unsigned long long*)&w[q + 1], (unsigned long long)d1);
+}
+
 __device__ __forceinline__ void wide_add(long long* w, double x) {
   if (x == 0.0) return;
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -413,8 +433,27 @@ struct AdjointStepArgs {
   double dt;
 };
 cudaError_t launch_adjoint_step(st_ctx* h, const AdjointStepArgs& s);
+// the FP32 adjoint of the mixed-precision step (FP32-velocity handles): the tape holds the state at
+// the start of the step (cell, offsets, velocities; diameters in d), the adjoints of position and
+// velocity are FP32 arrays, dL/dd and dL/dalpha accumulate in FP64, dL/dU goes into the same exact
+// carry-save accumulator as the FP64 adjoint; lam32 = dL/dJtot per cell in FP32 [3][ncell]
+struct AdjointMixedArgs {
+  MixedState tape;
+  const float* d;
+  float* xb[3];
+  float* vb[3];
+  double* db;
+  double* ab_part;
+  const float* lam32;
+  long long* Uw;
+  double dt;
+};
+cudaError_t launch_adjoint_step_mixed(st_ctx* h, const AdjointMixedArgs& s);
+cudaError_t launch_f64_to_f32(st_ctx* h, const double* in, float* out, int64_t m);
 cudaError_t launch_wide_to_f64(st_ctx* h, const long long* Uw, double* out, int64_t m);
 cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p);
+// the general mixed step on any state of the handle's capacity layout; acc = nullptr deposits nothing
+cudaError_t launch_step_mixed_state(st_ctx* h, const MixedState& s, int64_t n, long long* acc, const StepParams& p);
 bool tma_step_supported(const st_ctx* h);                               // step_mixed_tma.cu
 // records = true (mixed handles, default physics): the new state goes out as 32-byte records into
 // state_alt (plus the cells into the structure of arrays) for the sort that follows; see

@@ -316,8 +316,10 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
         __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
       for (int q = 0; q < 3; ++q) store_v<BF16>(a, q, p0, v[q]);
     }
-    // ---- deposit: runs of equal key over the warp's 128 particles ----
-    if (!CIC) {
+    // ---- deposit: runs of equal key over the warp's 128 particles (none without an accumulator:
+    // the adjoint's recomputation) ----
+    if (!a.acc) {
+    } else if (!CIC) {
       deposit_runs(a, lane, key, J);
     } else {
       // cloud in cell: one pass of runs per stencil corner (sorted particles share corners)
@@ -348,12 +350,17 @@ __global__ void __launch_bounds__(256) step_mixed_kernel(const MixedArgs a) {
 }  // namespace
 
 cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p) {
+  return launch_step_mixed_state(h, carve_mixed(h->state.p, h->cap, h->prec == ST_MIXED_BF16V), h->np,
+                                 (long long*)h->acc.p, p);
+}
+
+cudaError_t launch_step_mixed_state(st_ctx* h, const MixedState& s, int64_t n, long long* acc, const StepParams& p) {
   MixedArgs a;
   bool bf = h->prec == ST_MIXED_BF16V;
-  a.s = carve_mixed(h->state.p, h->cap, bf);
+  a.s = s;
   a.U = (const float4*)h->fluid_pad.p;
-  a.acc = (long long*)h->acc.p;
-  a.n = h->np;
+  a.acc = acc;
+  a.n = n;
   a.ncell = h->geo.ncell;
   a.nx = h->geo.n[0];
   a.ny = h->geo.n[1];
@@ -372,7 +379,7 @@ cudaError_t launch_step_mixed(st_ctx* h, const StepParams& p) {
   a.semi = p.semi;
   a.sn = p.sn;
   a.re_coef = (float)p.re_coef;
-  int64_t warps = (h->np + 127) / 128;
+  int64_t warps = (n + 127) / 128;
   int64_t blocks = (warps * 32 + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;

@@ -22,10 +22,11 @@
 //     accumulator lines hot in L2.
 // The first step after a sort may also do that sort's payload gather (the GATHER instance): the sort
 // leaves a permutation and the previous step's 32-byte records {cell, offsets | velocity, diameter}
-// in the old order, and the consumers load their own particles' records (and ids) through the
-// permutation instead of reading staged arrays, then store the new state - diameters and ids too -
-// in sorted order.  The separate gather would write the sorted arrays only for this step to read
-// them back.
+// in the old order, and each consumer thread copies its own particles' records through the
+// permutation into its own part of the stage ring with 16-byte asynchronous copies, one stage ahead
+// of its computation (their ids into registers, stored in sorted order at the start of the stage
+// they belong to), then stores the new state - diameters too - in sorted order.  The separate
+// gather would write the sorted arrays only for this step to read them back.
 // Every wait is bounded: a wait that gives up sets an error flag and the CTA
 // returns.
 #include <cuda.h>
@@ -333,6 +334,49 @@ __device__ __forceinline__ void commit_record(const TmaArgs& a, int* dep, int kk
   }
 }
 
+// GATHER: the permutation entries of a lane's four sorted positions p0 .. p0 + 3 (p0 a multiple of
+// 4), zeros when it owns none of them within [S, E) (then p0 may lie past the buffer)
+__device__ __forceinline__ uint4 gather_perm(const TmaArgs& a, int64_t p0, int64_t S, int64_t E) {
+  const bool any = p0 + 4 > S && p0 < E;
+  return any ? __ldcs(reinterpret_cast<const uint4*>(a.perm + p0)) : make_uint4(0, 0, 0, 0);
+}
+// GATHER: the ids of the owned positions among p0 .. p0 + 3 through the permutation (0 elsewhere)
+__device__ __forceinline__ uint4 gather_ids(const TmaArgs& a, uint4 pp, int64_t p0, int64_t S, int64_t E) {
+  const uint32_t pj[4] = {pp.x, pp.y, pp.z, pp.w};
+  uint32_t id[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) id[j] = (p0 + j >= S && p0 + j < E) ? __ldg(a.ids_in + pj[j]) : 0u;
+  return make_uint4(id[0], id[1], id[2], id[3]);
+}
+// GATHER: store ids gathered for positions p0 .. p0 + 3 (the owned ones)
+__device__ __forceinline__ void store_ids(const TmaArgs& a, uint4 id, int64_t p0, int64_t S, int64_t E) {
+  if (p0 >= S && p0 + 4 <= E) {
+    __stcs(reinterpret_cast<uint4*>(a.ids_out + p0), id);
+  } else {
+    const uint32_t v[4] = {id.x, id.y, id.z, id.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (p0 + j >= S && p0 + j < E) a.ids_out[p0 + j] = v[j];
+  }
+}
+// GATHER: copy the records of the owned positions among p0 .. p0 + 3 into the lane's eight 16-byte
+// pieces of a stage (piece h at h kT 4 + L 4 bytes, L = 4 x the consumer thread: the places of the
+// lane's particles in the stage's eight 4-byte arrays, so that the warp's deposit compaction, which
+// uses the first 16 places of its own particles in the first four arrays, touches its own lanes'
+// pieces only).  Record j's halves go to pieces 2j and 2j + 1.
+__device__ __forceinline__ void gather_issue(unsigned char* stage, int L, const TmaArgs& a, uint4 pp, int64_t p0,
+                                             int64_t S, int64_t E) {
+  const uint32_t pj[4] = {pp.x, pp.y, pp.z, pp.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (p0 + j >= S && p0 + j < E) {
+      const float4* r = a.grec + 2 * (int64_t)pj[j];
+      cp_async16(stage + (2 * j) * kT * 4 + L * 4, r);
+      cp_async16(stage + (2 * j + 1) * kT * 4 + L * 4, r + 1);
+    }
+  }
+}
+
 template <bool BF16, bool PW2, bool REC, bool PHYS, bool GATHER>
 __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ CUtensorMap fluid_map,
                                                                       const __grid_constant__ TmaArgs a) {
@@ -455,47 +499,60 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
     const bool use_tile = (E - S) <= kDepMaxCount;  // every digit word stays below 2^31
     const int64_t A = S & ~int64_t(7);
     const int64_t Z = (E + 7) & ~int64_t(7);
+    const int L = 4 * ctid;
+    // GATHER: the unit's first stage is copied now (its latency is exposed once per unit), and the
+    // permutation entries of the stage after the one in flight are held in registers
+    uint4 pnext = make_uint4(0, 0, 0, 0), gid = make_uint4(0, 0, 0, 0);
+    if constexpr (GATHER) {
+      const uint4 pf = gather_perm(a, A + L, S, E);
+      gather_issue(ring + (gt % kStages) * kStageBytes, L, a, pf, A + L, S, E);
+      cp_async_commit();
+      gid = gather_ids(a, pf, A + L, S, E);
+      pnext = gather_perm(a, A + kT + L, S, E);
+    }
     for (int64_t t0 = A; t0 < Z; t0 += kT) {
       const int st = (int)(gt % kStages);
       if (!mbar_wait(&full[st], (gt / kStages) & 1)) {
+        if (GATHER) cp_async_wait<0>();
         atomicOr(a.err, 8);
         return;
       }
       const unsigned char* src = ring + st * kStageBytes;
-      const int L = 4 * ctid;
       const int64_t p0 = t0 + L;
       int cell[4];
       float xi[3][4], v[3][4], dv[4];
-      uint32_t gid[4] = {0u, 0u, 0u, 0u};
       if constexpr (GATHER) {
-        // the lane's particles through the permutation: a 32-byte record and an id each (particles
-        // outside the unit get harmless values and are neither stored nor deposited)
+        // the next stage's records into the other stage buffer, then wait for this stage's (every
+        // consumer thread reads only the pieces it copied itself)
+        // this stage's ids (loaded a stage ago) go out now; the next stage's come in
+        store_ids(a, gid, p0, S, E);
+        if (t0 + kT < Z) {
+          gather_issue(ring + ((gt + 1) % kStages) * kStageBytes, L, a, pnext, p0 + kT, S, E);
+          cp_async_commit();
+          gid = gather_ids(a, pnext, p0 + kT, S, E);
+          pnext = gather_perm(a, p0 + 2 * kT, S, E);
+          cp_async_wait<1>();
+        } else {
+          cp_async_wait<0>();
+        }
+        // positions outside the unit get harmless values and are neither stored nor deposited
         const int glo = (int)max((int64_t)0, min((int64_t)4, S - p0));
         const int ghi = (int)max((int64_t)0, min((int64_t)4, E - p0));
-        // p0 is a multiple of 4 and below E <= the capacity (a multiple of 64) when the lane owns any
-        // particle; the stage's tail lanes past the unit read nothing
-        const uint4 pp = ghi > glo ? __ldcs(reinterpret_cast<const uint4*>(a.perm + p0)) : make_uint4(0, 0, 0, 0);
-        const uint32_t pj[4] = {pp.x, pp.y, pp.z, pp.w};
-        Rec32 r[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+          float4 r0 = make_float4(0.0f, 0.5f, 0.5f, 0.5f), r1 = make_float4(0.0f, 0.0f, 0.0f, 1e-5f);
           if (j >= glo && j < ghi) {
-            r[j] = ld_rec32(a.grec + 2 * (int64_t)pj[j]);
-            gid[j] = __ldg(a.ids_in + pj[j]);
-          } else {
-            r[j] = Rec32{0.0f, 0.5f, 0.5f, 0.5f, 0.0f, 0.0f, 0.0f, 1e-5f};
+            r0 = *reinterpret_cast<const float4*>(src + (2 * j) * kT * 4 + L * 4);
+            r1 = *reinterpret_cast<const float4*>(src + (2 * j + 1) * kT * 4 + L * 4);
           }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          cell[j] = __float_as_int(r[j].c);
-          xi[0][j] = r[j].x0;
-          xi[1][j] = r[j].x1;
-          xi[2][j] = r[j].x2;
-          v[0][j] = r[j].v0;
-          v[1][j] = r[j].v1;
-          v[2][j] = r[j].v2;
-          dv[j] = r[j].d;
+          cell[j] = __float_as_int(r0.x);
+          xi[0][j] = r0.y;
+          xi[1][j] = r0.z;
+          xi[2][j] = r0.w;
+          v[0][j] = r1.x;
+          v[1][j] = r1.y;
+          v[2][j] = r1.z;
+          dv[j] = r1.w;
         }
       } else {
         int4 c4 = *reinterpret_cast<const int4*>(src + L * 4);
@@ -561,6 +618,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
       // padded field and commit to the global accumulator.
       int key[4];
       float J[4][3];
+      unsigned vpk[3][2];  // BF16: the new velocities as packed pairs (particles 0-1, 2-3)
 #pragma unroll
       for (int jp = 0; jp < 4; jp += 2) {
         int ci[2][3];
@@ -670,11 +728,13 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
           unpack2(fma2(DVW, EE, WT), vn[0], vn[1]);
           if (BF16) {
             // the stored (rounded) velocity change, so that the deposit balances the particles'
-            // momentum
+            // momentum; the pair is rounded by one packing conversion, kept packed for the store
             float m0, m1;
             unpack2(M, m0, m1);
-            vn[0] = __bfloat162float(__float2bfloat16_rn(vn[0]));
-            vn[1] = __bfloat162float(__float2bfloat16_rn(vn[1]));
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(vn[0], vn[1]);
+            vpk[q][jp >> 1] = *reinterpret_cast<const unsigned*>(&b2);
+            vn[0] = __low2float(b2);
+            vn[1] = __high2float(b2);
             J[jp][q] = -m0 * ((vn[0] - v[q][jp]) - a.gdt[q]);
             J[jp + 1][q] = -m1 * ((vn[1] - v[q][jp + 1]) - a.gdt[q]);
           } else {
@@ -741,21 +801,15 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         }
       } else if (all_own) {
         if (GATHER) {
-          __stcs((float4*)(a.s.d + p0), make_float4(dv[0], dv[1], dv[2], dv[3]));
-          __stcs((uint4*)(a.ids_out + p0), make_uint4(gid[0], gid[1], gid[2], gid[3]));
+          // the diameters, read again from the lane's record pieces
+          const float* dp = reinterpret_cast<const float*>(src + kT * 4 + L * 4) + 3;
+          __stcs((float4*)(a.s.d + p0), make_float4(dp[0], dp[2 * kT], dp[4 * kT], dp[6 * kT]));
         }
         __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
         for (int q = 0; q < 3; ++q)
           __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
         if (BF16) {
-          for (int q = 0; q < 3; ++q) {
-            __nv_bfloat162 lo = __floats2bfloat162_rn(v[q][0], v[q][1]);
-            __nv_bfloat162 hi = __floats2bfloat162_rn(v[q][2], v[q][3]);
-            uint2 r;
-            r.x = *reinterpret_cast<unsigned*>(&lo);
-            r.y = *reinterpret_cast<unsigned*>(&hi);
-            __stcs((uint2*)((__nv_bfloat16*)a.s.v[q] + p0), r);
-          }
+          for (int q = 0; q < 3; ++q) __stcs((uint2*)((__nv_bfloat16*)a.s.v[q] + p0), make_uint2(vpk[q][0], vpk[q][1]));
         } else {
           for (int q = 0; q < 3; ++q)
             __stcs((float4*)((float*)a.s.v[q] + p0), make_float4(v[q][0], v[q][1], v[q][2], v[q][3]));
@@ -764,10 +818,7 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         for (int j = 0; j < 4; ++j) {
           if (!own[j]) continue;
           a.s.cell[p0 + j] = cell[j];
-          if (GATHER) {
-            a.s.d[p0 + j] = dv[j];
-            a.ids_out[p0 + j] = gid[j];
-          }
+          if (GATHER) a.s.d[p0 + j] = reinterpret_cast<const float*>(src + (2 * j + 1) * kT * 4 + L * 4)[3];
           for (int q = 0; q < 3; ++q) {
             a.s.xi[q][p0 + j] = xi[q][j];
             if (BF16)
