@@ -678,8 +678,15 @@ def main():
     rec_step = [precision != "fp64" and reorder_every > 0 and (W + i + 1) % reorder_every == 0
                 for i in range(K)]
     rec_bytes = {"mixed_f32": 68, "mixed_bf16": 62}.get(precision)  # read the state, write cells + records
-    plain_ms = [t for t, r in zip(step_ms, rec_step) if not r] or step_ms
+    # the first step after each sort that followed a record-writing step gathers the records through
+    # the sort's permutation itself (the gathering instance): read permutation, record and id (40 B),
+    # write the state with diameters and the id (36 B; 30 B with BF16 velocities)
+    gat_step = [precision != "fp64" and reorder_every > 1 and (W + i) % reorder_every == 0 and W + i > 0
+                for i in range(K)]
+    gat_bytes = {"mixed_f32": 76, "mixed_bf16": 70}.get(precision)
+    plain_ms = [t for t, r, g in zip(step_ms, rec_step, gat_step) if not r and not g] or step_ms
     rec_ms = [t for t, r in zip(step_ms, rec_step) if r]
+    gat_ms = [t for t, g in zip(step_ms, gat_step) if g]
     step_all_avg = sum(step_ms) / len(step_ms)
     step_avg = sum(plain_ms) / len(plain_ms)
     bytes_per_launch = STEP_BYTES[precision] * n
@@ -706,7 +713,12 @@ def main():
                                  "step_kernel_ms_avg": (sum(rec_ms) / len(rec_ms)) if rec_ms else None,
                                  "bytes_per_particle": rec_bytes,
                                  "frac": (rec_bytes * n / (sum(rec_ms) / len(rec_ms) * 1e-3) / 1e9 / peak)
-                                 if rec_ms else None}}
+                                 if rec_ms else None},
+                "gathering_steps": {"launches": len(gat_ms),
+                                    "step_kernel_ms_avg": (sum(gat_ms) / len(gat_ms)) if gat_ms else None,
+                                    "bytes_per_particle": gat_bytes,
+                                    "frac": (gat_bytes * n / (sum(gat_ms) / len(gat_ms) * 1e-3) / 1e9 / peak)
+                                    if gat_ms else None}}
 
     if precision == "fp64":  # the FP64 step is bound by FP64 arithmetic, not by HBM
         roofline = dict(fp64_step_roofline(n, step_avg, *fp64_peak(sim)), kernel="step_f64_kernel", launches=len(step_ms),
