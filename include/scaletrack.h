@@ -108,7 +108,9 @@ const char* st_last_error(st_handle h);
 /* Change the CUDA stream later calls are ordered on. */
 st_status st_set_stream(st_handle h, void* stream);
 
-/* Wait for all work the handle has queued. */
+/* Wait for all work the handle has queued, the asynchronous transfers
+ * (st_set_fluid_async, st_get_sources_async) included, and report pending
+ * errors. */
 st_status st_synchronize(st_handle h);
 
 /* Physical parameters (Sec. 2.1): particle density rho_p > 0, fluid dynamic
@@ -198,6 +200,32 @@ st_status st_get_sources(st_handle h, double* out, int reset, int on_device);
  * place first (the accumulated value does not change).  Synchronises.
  * Errors: INVALID_ARG, CUDA. */
 st_status st_get_sources_fixed(st_handle h, int64_t* words, int* E, int on_device);
+
+/* Asynchronous host transfers, so that a loop of field in, step, sources
+ * out keeps the GPU computing while data crosses the host link (the paper's
+ * coupling, Sec. 2.3, overlaps the transfers with the particle step).  The
+ * handle owns an upload and a download stream beside its compute stream and
+ * a staging buffer for one field and two source fields (allocated at the
+ * first call; freed by st_destroy).
+ *
+ * st_set_fluid_async: like st_set_fluid from host memory u (dtype as
+ * there; pinned memory for the copy to overlap), but it returns once the
+ * copy is queued.  The new field takes effect for the work queued after
+ * this call (steps already queued keep the previous one).  The host must
+ * leave u unchanged until the next call on the handle other than
+ * st_get_sources_async, which waits for the copy and reads its scan: a
+ * field with NaN or Inf is not taken and that call returns NONFINITE.
+ *
+ * st_get_sources_async: like st_get_sources to host memory out (pinned for
+ * the copy to overlap), reset as there, but it returns once the conversion
+ * and the copy are queued; out holds the sources after st_synchronize,
+ * which waits for the compute, upload and download streams and reports any
+ * pending error (NONFINITE from an upload, TIMEOUT from a device-side
+ * wait).  Two staging buffers alternate, so two calls may be in flight; out
+ * must stay valid and unread until then.
+ * Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
+st_status st_set_fluid_async(st_handle h, const void* u, int dtype);
+st_status st_get_sources_async(st_handle h, double* out, int reset);
 
 /* Stable counting sort of the particles now, by the chunk-major key of
  * their cell: chunk index (x fastest) times B^3 plus the Morton index of

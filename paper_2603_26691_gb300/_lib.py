@@ -47,6 +47,8 @@ SIGNATURES = {
     "st_last_error": (C.c_char_p, [_vp]),
     "st_set_stream": (_i, [_vp, _vp]),
     "st_synchronize": (_i, [_vp]),
+    "st_set_fluid_async": (_i, [_vp, _vp, _i]),
+    "st_get_sources_async": (_i, [_vp, _vp, _i]),
     "st_set_params": (_i, [_vp, _d, _d, _P(_d), _d, _d, _i]),
     "st_set_physics": (_i, [_vp, _i, _i, _i, _i, _d]),
     "st_timers_enable": (_i, [_vp, _i]),

@@ -68,7 +68,7 @@ using namespace st;
 static bool finite3(const double* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
 // Report (and clear) device-side error flags raised by bounded waits that gave up.
-static st_status check_flags(st_handle h) {
+st_status st::check_flags(st_ctx* h) {
   int f = 0;
   cudaError_t e = cudaMemcpyAsync(&f, h->flags.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -80,11 +80,13 @@ static st_status check_flags(st_handle h) {
   return ST_OK;
 }
 
+// every call below first reads the result of a pending asynchronous field upload (st_set_fluid_async)
 static st_status check_handle(st_handle h) {
   if (!h) return ST_ERR_INVALID_ARG;
   h->err.clear();
   cudaError_t e = cudaSetDevice(h->dev);
-  return cuda_check(h, e, "cudaSetDevice");
+  ST_TRY(cuda_check(h, e, "cudaSetDevice"));
+  return settle_fluid(h);
 }
 
 extern "C" {
@@ -163,6 +165,7 @@ void st_destroy(st_handle h) {
   cudaSetDevice(h->dev);
   cudaStreamSynchronize(h->stream);
   chunk_store_free(h);  // its slot buffers first: the handle's own are freed below
+  xfer_free(h);
   Buf* bufs[] = {&h->fluid, &h->fluid_pad, &h->flags, &h->ckpt, &h->state, &h->state_alt, &h->ids, &h->ids_alt,
                  &h->keys[0], &h->keys[1], &h->vals[0], &h->vals[1], &h->hist, &h->scan_aux, &h->cell_start, &h->lsort_aux,
                  &h->acc, &h->red, &h->src_hist[0], &h->src_hist[1], &h->src_hist[2], &h->src_hist[3],
@@ -191,6 +194,7 @@ st_status st_set_stream(st_handle h, void* stream) {
 st_status st_synchronize(st_handle h) {
   ST_TRY(check_handle(h));
   ST_CUDA(h, cudaStreamSynchronize(h->stream));
+  ST_CUDA(h, xfer_sync(h));
   return check_flags(h);
 }
 
@@ -548,6 +552,7 @@ static st_status prepare_accumulator(st_handle h, double dt, double adds_now, in
 extern "C++" {
 namespace st {
 st_status run_steps(st_ctx* h, int nsteps, double dt) {
+  ST_TRY(settle_fluid(h));
   if (nsteps < 0) return set_error(h, ST_ERR_INVALID_ARG, "nsteps < 0");
   if (!std::isfinite(dt)) return set_error(h, ST_ERR_NONFINITE, "dt is not finite");
   if (!(dt > 0)) return set_error(h, ST_ERR_INVALID_ARG, "dt must be > 0");

@@ -44,6 +44,7 @@ struct Geometry {
 
 namespace st {
 struct ChunkStore;
+struct Xfer;
 }
 
 struct st_ctx {
@@ -146,6 +147,8 @@ struct st_ctx {
   // chunked particle sets (st_chunks_*): the chunks in pinned host memory and the device slots
   st::ChunkStore* chunks = nullptr;
   bool chunk_adding = false;  // st_chunks_add is importing through the resident path
+  // asynchronous host transfers (st_set_fluid_async, st_get_sources_async): streams, staging buffers
+  st::Xfer* xfer = nullptr;
   std::string err;
 };
 
@@ -153,6 +156,15 @@ namespace st {
 
 // ---- chunked particle sets (chunks.cu) ------------------------------------------------------
 void chunk_store_free(st_ctx* h);
+
+// ---- asynchronous host transfers (xfer.cu) --------------------------------------------------
+void xfer_free(st_ctx* h);
+cudaError_t xfer_sync(st_ctx* h);  // waits for the upload and download streams
+// read the scan result of a pending asynchronous field upload (waits for it): the field's bound, or
+// ST_ERR_NONFINITE when it was not taken; no-op without one
+st_status settle_fluid(st_ctx* h);
+// device error flags raised by bounded waits that gave up (reported and cleared)
+st_status check_flags(st_ctx* h);
 
 // ---- host helpers (st_api.cu) -------------------------------------------------------------
 st_status set_error(st_ctx* h, st_status s, const std::string& msg);
@@ -480,9 +492,15 @@ cudaError_t launch_acc_to_f64(st_ctx* h, double* out, int E);
 cudaError_t launch_acc_sum(st_ctx* h, double out[3]);
 cudaError_t launch_particle_sums(st_ctx* h, double out[4]);  // P_x, P_y, P_z, M
 cudaError_t launch_maxabs(st_ctx* h, const void* p, int64_t n, int dtype, double* out_max, int* nonfinite);
+// the same scan on `stream`, its 16-byte result {max bits, flag} left in dev_red and copied to host_red
+// (pinned) asynchronously
+cudaError_t launch_maxabs_on(st_ctx* h, const void* p, int64_t n, int dtype, cudaStream_t stream,
+                             unsigned long long* dev_red, unsigned long long* host_red);
 cudaError_t launch_particle_scan(st_ctx* h, const double* vel, const double* d, int64_t n, double* vmax,
                                  double* dmax, double* dmin, int* nonfinite);
 cudaError_t launch_fluid_pack(st_ctx* h, const void* u, int dtype);
+// the same, skipped on the device when *skip != 0
+cudaError_t launch_fluid_pack_if(st_ctx* h, const void* u, int dtype, const int* skip);
 cudaError_t launch_import(st_ctx* h, int64_t first, int64_t n, const double* xyz, const double* vel,
                           const double* d, const uint32_t* ids);
 cudaError_t launch_export(st_ctx* h, int64_t first, int64_t n, double* xyz, double* vel, double* d,

@@ -66,7 +66,9 @@ __global__ void particle_scan_kernel(const double* __restrict__ xyz, const doubl
 // ---- fluid packing -----------------------------------------------------------------------
 
 template <typename T>
-__global__ void pack_f64_kernel(const T* __restrict__ u, D4* __restrict__ out, int64_t ncell) {
+__global__ void pack_f64_kernel(const T* __restrict__ u, D4* __restrict__ out, int64_t ncell,
+                                const int* __restrict__ skip = nullptr) {
+  if (skip && *skip) return;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x)
     out[c] = D4{(double)u[3 * c], (double)u[3 * c + 1], (double)u[3 * c + 2], 0.0};
 }
@@ -75,7 +77,8 @@ __global__ void pack_f64_kernel(const T* __restrict__ u, D4* __restrict__ out, i
 // holds cell ((a - P) mod nx, (b - P) mod ny, (c - P) mod nz)
 template <typename T>
 __global__ void pack_f32_padded_kernel(const T* __restrict__ u, float4* __restrict__ out, int nx, int ny, int nz,
-                                       int P) {
+                                       int P, const int* __restrict__ skip = nullptr) {
+  if (skip && *skip) return;
   const int64_t px = nx + 2 * P, py = ny + 2 * P, pz = nz + 2 * P;
   const int64_t total = px * py * pz;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -414,25 +417,44 @@ cudaError_t launch_particle_scan(st_ctx* h, const double* xyz, const double* d, 
   return cudaSuccess;
 }
 
-cudaError_t launch_fluid_pack(st_ctx* h, const void* u, int dtype) {
+cudaError_t launch_fluid_pack(st_ctx* h, const void* u, int dtype) { return launch_fluid_pack_if(h, u, dtype, nullptr); }
+
+cudaError_t launch_fluid_pack_if(st_ctx* h, const void* u, int dtype, const int* skip) {
   int64_t nc = h->geo.ncell;
   if (h->prec == ST_FP64) {
     if (dtype == ST_DTYPE_F64)
-      pack_f64_kernel<double><<<grid_for(nc), kThreads, 0, h->stream>>>((const double*)u, (D4*)h->fluid.p, nc);
+      pack_f64_kernel<double><<<grid_for(nc), kThreads, 0, h->stream>>>((const double*)u, (D4*)h->fluid.p, nc, skip);
     else
-      pack_f64_kernel<float><<<grid_for(nc), kThreads, 0, h->stream>>>((const float*)u, (D4*)h->fluid.p, nc);
+      pack_f64_kernel<float><<<grid_for(nc), kThreads, 0, h->stream>>>((const float*)u, (D4*)h->fluid.p, nc, skip);
   } else {
     const Geometry& G = h->geo;
     const int64_t tot = (int64_t)(G.n[0] + 2 * kFluidPad) * (G.n[1] + 2 * kFluidPad) * (G.n[2] + 2 * kFluidPad);
     if (dtype == ST_DTYPE_F64)
       pack_f32_padded_kernel<double><<<grid_for(tot), kThreads, 0, h->stream>>>(
-          (const double*)u, (float4*)h->fluid_pad.p, G.n[0], G.n[1], G.n[2], kFluidPad);
+          (const double*)u, (float4*)h->fluid_pad.p, G.n[0], G.n[1], G.n[2], kFluidPad, skip);
     else
       pack_f32_padded_kernel<float><<<grid_for(tot), kThreads, 0, h->stream>>>(
-          (const float*)u, (float4*)h->fluid_pad.p, G.n[0], G.n[1], G.n[2], kFluidPad);
+          (const float*)u, (float4*)h->fluid_pad.p, G.n[0], G.n[1], G.n[2], kFluidPad, skip);
   }
   h->launches += 1;
   return cudaGetLastError();
+}
+
+cudaError_t launch_maxabs_on(st_ctx* h, const void* p, int64_t n, int dtype, cudaStream_t stream,
+                             unsigned long long* dev_red, unsigned long long* host_red) {
+  cudaError_t e = cudaMemsetAsync(dev_red, 0, 16, stream);
+  if (e != cudaSuccess) return e;
+  if (n > 0) {
+    int* flag = (int*)(dev_red + 1);
+    if (dtype == ST_DTYPE_F64)
+      maxabs_kernel<double><<<grid_for(n), kThreads, 0, stream>>>((const double*)p, n, dev_red, flag);
+    else
+      maxabs_kernel<float><<<grid_for(n), kThreads, 0, stream>>>((const float*)p, n, dev_red, flag);
+    h->launches += 1;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaMemcpyAsync(host_red, dev_red, 16, cudaMemcpyDeviceToHost, stream);
 }
 
 cudaError_t launch_import(st_ctx* h, int64_t first, int64_t n, const double* xyz, const double* vel, const double* d,

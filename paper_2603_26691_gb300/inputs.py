@@ -252,6 +252,9 @@ WORKLOADS = {
     # droplet microphysics (vapour and heat transfer) on the mixed-precision workload's field and particles
     "fourier256_micro_1e9": Workload("fourier256_micro_1e9", 256, "fourier", "f32", "mixed_f32",
                                      1_000_000_000, 20, 5e-4, extra={"micro": True}),
+    # the mixed-precision workload's field and particles held in pinned host memory as chunks of 2.5e8
+    "fourier256_chunks_1e9": Workload("fourier256_chunks_1e9", 256, "fourier", "f32", "mixed_f32",
+                                      1_000_000_000, 10, 5e-4, extra={"chunk": 250_000_000}),
 }
 
 PHYSICS = dict(rho_p=1000.0, mu=1.8e-5, g=(0.0, 0.0, -9.81), drag_scale=1.0, multiplicity=1.0)

@@ -291,7 +291,28 @@ class Sim:
         return out
 
     def synchronize(self):
+        """Wait for the handle's queued work and asynchronous transfers; report pending errors."""
         self._chk(self.lib.st_synchronize(self.h), "st_synchronize")
+
+    def set_fluid_async(self, U: torch.Tensor):
+        """Queue the upload of a host field [nz, ny, nx, 3] (float32 or float64 CPU tensor, pinned for the
+        copy to overlap) for the work queued next; U must stay unchanged until the next call on the Sim
+        other than sources_async (see st_set_fluid_async)."""
+        self._changed()
+        if U.is_cuda or U.dtype not in (torch.float32, torch.float64) or not U.is_contiguous():
+            raise ValueError("a contiguous float32 or float64 host tensor is required")
+        if U.numel() != 3 * self.ncell:
+            raise ValueError("fluid field has the wrong size")
+        dt = _lib.ST_DTYPE_F32 if U.dtype == torch.float32 else _lib.ST_DTYPE_F64
+        self._chk(self.lib.st_set_fluid_async(self.h, C.c_void_p(U.data_ptr()), dt), "st_set_fluid_async")
+
+    def sources_async(self, out: torch.Tensor, reset: bool = False):
+        """Queue the copy of the accumulated sources into the float64 host tensor out [3, ncell] (pinned for
+        the copy to overlap); out holds them after synchronize() (see st_get_sources_async)."""
+        if out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != 3 * self.ncell:
+            raise ValueError("a contiguous float64 host tensor of 3 x ncell values is required")
+        self._chk(self.lib.st_get_sources_async(self.h, C.c_void_p(out.data_ptr()), int(bool(reset))),
+                  "st_get_sources_async")
 
     # -- outputs ---------------------------------------------------------------------------
     def sources(self, reset: bool = False, out: torch.Tensor | None = None, host: bool = False):
