@@ -831,11 +831,26 @@ def main():
     e_el = e2e_loop(True)
     # the same loop with the synchronous calls (each waits for its copy), for comparison
     s_el = e2e_loop(False)
+    # this machine's host link for the same buffers (one copy each way, CUDA events): the end-to-end rate
+    # depends on it, and it differs between boxes of the pool
+    link = {}
+    if E > 0:
+        dU = torch.empty(Uh.shape, dtype=Uh.dtype, device=device)
+        dS = torch.empty(src_h[0].shape, dtype=torch.float64, device=device)
+        for name, dst, src_t in (("h2d_gbs", dU, Uh), ("d2h_gbs", src_h[0], dS)):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            dst.copy_(src_t, non_blocking=True)
+            ea.record()
+            dst.copy_(src_t, non_blocking=True)
+            eb.record()
+            torch.cuda.synchronize()
+            link[name] = src_t.numel() * src_t.element_size() / (ea.elapsed_time(eb) * 1e-3) / 1e9
+        del dU, dS
     e2e = {"value": n * ws * E / e_el if E > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(U32.nbytes),
            "d2h_bytes_per_step": int(src_h[0].numel() * 8), "steps": E,
            "what": "per step: fluid field H2D from pinned host, step (sort when due), sources D2H to pinned host, "
                    "queued with st_set_fluid_async / st_get_sources_async and overlapping the steps",
-           "synchronous_calls_value": n * ws * E / s_el if E > 0 else None}
+           "synchronous_calls_value": n * ws * E / s_el if E > 0 else None, "host_link": link}
 
     # physics variants on the same particles, sorted: the sorted-particle step kernel's physics
     # instance

@@ -78,3 +78,22 @@ def test_chunk_calls_refuse_misuse(Sim):
     sim.chunks_step(2, 1e-3)
     assert sim.n == 0 and sim.chunks_count() == (1000, 2)
     sim.close()
+
+
+def test_chunk_reads_check_their_range(Sim):
+    from paper_2603_26691_gb300._lib import StError
+
+    N = 16
+    pos, vel, d, _ = inputs.particles(63, 0, 1500)
+    sim = Sim(N, precision="mixed_f32")
+    sim.set_fluid(inputs.taylor_green(N).astype(np.float32))
+    sim.chunks_create(640)
+    sim.chunks_add(pos, d, vel)
+    assert sim.chunks_count() == (1500, 3)
+    p, v, dd, ids = sim.chunks_particles(1400, 100)  # across the last chunk's end
+    assert np.array_equal(ids, np.arange(1400, 1500, dtype=np.uint32))
+    with pytest.raises(StError):
+        sim.chunks_particles(1400, 101)
+    with pytest.raises(StError):
+        sim.chunks_create(640)  # once per handle
+    sim.close()

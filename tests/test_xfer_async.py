@@ -81,3 +81,32 @@ def test_nonfinite_field_is_refused_and_the_previous_one_kept(torch_mod):
     got = sim.sources(host=True)
     sim.close()
     assert np.array_equal(want, got)
+
+
+def test_async_reads_without_reset_and_a_synchronous_field_after_an_async_one(torch_mod):
+    """Sources read asynchronously without a reset hold the running sum (as the synchronous read does),
+    and a synchronous st_set_fluid issued after an asynchronous one is the field the next step uses."""
+    torch = torch_mod
+    N, dt = 16, 5e-4
+    U1 = (inputs.random_fourier(N, seed=23) * 8.0).astype(np.float32)
+    U2 = (U1 * 1.5).astype(np.float32)
+    ref = _sim("mixed_f32", N, U1, n=30_001)
+    ref.step(2, dt)
+    r1 = ref.sources(host=True)
+    ref.set_fluid(U2)
+    ref.step(2, dt)
+    r2 = ref.sources(host=True)
+    ref.close()
+    sim = _sim("mixed_f32", N, U1, n=30_001)
+    o1 = torch.empty((3, N ** 3), dtype=torch.float64).pin_memory()
+    o2 = torch.empty((3, N ** 3), dtype=torch.float64).pin_memory()
+    sim.step(2, dt)
+    sim.sources_async(o1)
+    sim.set_fluid_async(torch.from_numpy(U1 * 3.0).pin_memory())
+    sim.set_fluid(U2)  # waits for the upload above and replaces it
+    sim.step(2, dt)
+    sim.sources_async(o2)
+    sim.synchronize()
+    sim.close()
+    assert np.array_equal(o1.numpy(), r1)
+    assert np.array_equal(o2.numpy(), r2)
