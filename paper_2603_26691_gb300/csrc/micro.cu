@@ -50,19 +50,25 @@ struct MicroConst {
 };
 
 __device__ __forceinline__ double ex(double x) { return exp(x); }
-__device__ __forceinline__ float ex(float x) { return expf(x); }
 __device__ __forceinline__ double em1(double x) { return expm1(x); }
-__device__ __forceinline__ float em1(float x) { return expm1f(x); }
 __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+__device__ __forceinline__ double dv(double a, double b) { return a / b; }
+// FP32: the hardware's approximate exponential and division (errors of a few units in the last place,
+// for arguments of order one and divisors far from the FP32 range's ends), which the FP32 state's
+// own rounding dominates; the step's increments enter the state through error-free sums
+__device__ __forceinline__ float ex(float x) { return __expf(x); }
+__device__ __forceinline__ float em1(float x) { return expm1f(x); }
 __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+__device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
 
 // saturation vapour density over flat water at T (K) and its temperature derivative
 template <class R>
 __device__ __forceinline__ void rho_sat(R T, R& rs, R& slope) {
   const R t = T - R(273.15);
   const R a = t + R(243.04);
-  rs = R(610.94) * ex(R(17.625) * t / a) / (R(461.5) * T);
-  slope = rs * (R(17.625 * 243.04) / (a * a) - R(1) / T);
+  const R ia = dv(R(1), a), iT = dv(R(1), T);
+  rs = R(610.94 / 461.5) * ex(R(17.625) * t * ia) * iT;
+  slope = rs * (R(17.625 * 243.04) * ia * ia - iT);
 }
 
 // phi1(x) = (1 - e^-x) / x and phi2(x) = (1 - phi1) / x, x >= 0: their Taylor series below 1/4
@@ -73,8 +79,9 @@ __device__ __forceinline__ void phis(R x, R& p1, R& p2) {
     p2 = R(0.5) - x * (R(1.0 / 6) - x * (R(1.0 / 24) - x * (R(1.0 / 120) - x * (R(1.0 / 720) - x * R(1.0 / 5040)))));
     p1 = R(1) - x * p2;
   } else {
-    p1 = -em1(-x) / x;
-    p2 = (R(1) - p1) / x;
+    const R ix = dv(R(1), x);
+    p1 = -em1(-x) * ix;
+    p2 = (R(1) - p1) * ix;
   }
 }
 
@@ -91,8 +98,8 @@ __device__ __forceinline__ bool transfer(const MicroConst<R>& c, R dt, R d0, R T
   rho_sat(T0, rs, sl);
   const R den = A + c.L * B * sl;
   const R md0 = c.mdrop * d0 * d0 * d0;
-  const R k = den / (md0 * c.cp);
-  const R delta = (A * (tf - T0) + c.L * B * (rv - rs)) / den;
+  const R k = dv(den, md0 * c.cp);
+  const R delta = dv(A * (tf - T0) + c.L * B * (rv - rs), den);
   const R x = k * dt;
   R p1, p2;
   phis(x, p1, p2);
@@ -102,7 +109,7 @@ __device__ __forceinline__ bool transfer(const MicroConst<R>& c, R dt, R d0, R T
   const bool clamped = !(q > c.dmin * c.dmin);
   if (!clamped) {
     d1 = sq(q);
-    dd = dq / (d1 + d0);
+    dd = dv(dq, d1 + d0);
   } else {
     d1 = c.dmin;
     dd = d1 - d0;
@@ -315,12 +322,18 @@ __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedA
         b[q] = ci[q] - (hi ? 0 : 1) + kFluidPad;
       }
       float up[3] = {0.0f, 0.0f, 0.0f}, tf = 0.0f, rv = 0.0f;
+      // the padded field has fewer than 2^31 cells: 32-bit corner offsets from the base corner
+      const int c0 = b[0] + px * b[1] + pxy * b[2];
+      const float4* ub = a.Up + c0;
+      const float2* tb = a.thp + c0;
+      const float wx[2] = {1.0f - f[0], f[0]}, wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+#pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
-        const int64_t c = (b[0] + dx) + (int64_t)px * (b[1] + dy) + (int64_t)pxy * (b[2] + dz);
-        const float4 u = __ldg(a.Up + c);
-        const float2 t = __ldg(a.thp + c);
+        const float w = wx[dx] * wy[dy] * wz[dz];
+        const int o = dx + px * dy + pxy * dz;
+        const float4 u = __ldg(ub + o);
+        const float2 t = __ldg(tb + o);
         up[0] = fmaf(w, u.x, up[0]);
         up[1] = fmaf(w, u.y, up[1]);
         up[2] = fmaf(w, u.z, up[2]);
@@ -380,8 +393,8 @@ __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedA
     const bool head = run_sums(lane, key, gain);
     if (head && key >= 0) {
       for (int q = 0; q < 3; ++q) acc_add_f32(a.acc + kAccWords * (q * a.ncell + key), gain[q], a.E);
-      wide_add(a.macc + kWideWords * key, (double)gain[3]);
-      wide_add(a.macc + kWideWords * (a.ncell + key), (double)gain[4]);
+      wide_add_f32(a.macc + kWideWords * key, gain[3]);
+      wide_add_f32(a.macc + kWideWords * (a.ncell + key), gain[4]);
     }
   }
 }
