@@ -452,7 +452,8 @@ st_status st_micro_invariants(st_handle h, double out[2]);
  * st_chunks_get copies particles [first, first + count) of the chunks'
  * storage order to host arrays (positions in FP64 as st_get_particles).
  * st_chunks_count gives the particle and chunk counts.  While a handle holds
- * chunks, st_add_particles is refused and st_step sees no particles.
+ * chunks, st_add_particles, st_reserve and enabling the microphysics are
+ * refused (STATE) and st_step sees no particles.
  * Synchronous.  Errors: STATE, INVALID_ARG, OOM (device slots or pinned host
  * memory), CUDA. */
 st_status st_chunks_create(st_handle h, int64_t chunk_particles);

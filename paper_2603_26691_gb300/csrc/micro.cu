@@ -722,6 +722,8 @@ st_status st_set_microphysics(st_handle h, int enable, double D_v, double kappa_
     h->micro_on = false;
     return ST_OK;
   }
+  // chunks carry the state without the particle temperatures
+  if (h->chunks) return set_error(h, ST_ERR_STATE, "microphysics and chunks do not combine");
   const double v[7] = {D_v, kappa_f, cp_p, latent_heat, prandtl, d_min, T_init};
   for (double x : v)
     if (!std::isfinite(x)) return set_error(h, ST_ERR_NONFINITE, "non-finite microphysics parameter");

@@ -395,6 +395,8 @@ static st_status grow(st_handle h, int64_t need) {
 st_status st_reserve(st_handle h, int64_t capacity) {
   ST_TRY(check_handle(h));
   if (capacity < 0 || capacity > (int64_t(1) << 34)) return set_error(h, ST_ERR_INVALID_ARG, "capacity out of range");
+  // a handle with chunks keeps its buffers at the chunk capacity (they are the chunks' device slots)
+  if (h->chunks) return set_error(h, ST_ERR_STATE, "the handle holds chunks");
   return grow(h, capacity);
 }
 

@@ -75,6 +75,10 @@ def test_chunk_calls_refuse_misuse(Sim):
     sim.chunks_add(pos, d, vel)
     with pytest.raises(StError):
         sim.add_particles(pos, d, vel)  # resident adds refused while chunks are held
+    with pytest.raises(StError):
+        sim.reserve(10_000)  # the buffers are the chunks' device slots
+    with pytest.raises(StError):
+        sim.set_microphysics(True)  # chunks carry no particle temperatures
     sim.chunks_step(2, 1e-3)
     assert sim.n == 0 and sim.chunks_count() == (1000, 2)
     sim.close()
