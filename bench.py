@@ -797,19 +797,22 @@ def main():
     chunk_bounds_ms = cb0.elapsed_time(cb1)
 
     # end to end through the C ABI with host buffers: each step receives the fluid field from
-    # pinned host memory and returns the per-cell sources to pinned host memory (one buffer per
-    # step), the transfers queued with the asynchronous calls so that they overlap the steps, the
-    # sorts left to the library's own schedule (inside st_step); the timed region ends when the last
-    # sources are in host memory.  One untimed pass of the same loop first (staging buffers, first
-    # use of the transfer kernels).
+    # pinned host memory and returns the per-cell sources to pinned host memory (two buffers in
+    # turn, as a consumer of the results would use them), the transfers queued with the asynchronous
+    # calls so that they overlap the steps, the sorts left to the library's own schedule (inside
+    # st_step); the timed region ends when the last sources are in host memory.  One untimed pass of
+    # the same loop first (staging buffers, first use of the transfer kernels).  Few pinned buffers:
+    # with twenty, after a long test run in the same box, some of them took device -> host copies at
+    # 20 GB/s instead of 193
     Uh = torch.from_numpy(U32).pin_memory()
     E = args.e2e_steps
-    src_h = [torch.empty((3, sim.ncell), dtype=torch.float64).pin_memory() for _ in range(max(E, 1))]
+    src_h = [torch.empty((3, sim.ncell), dtype=torch.float64).pin_memory() for _ in range(2)]
     import ctypes as C
 
     lib = sim.lib
 
     def e2e_loop(asynchronous):
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         if asynchronous and E > 0:
             sim.set_fluid_async(Uh)
@@ -818,11 +821,11 @@ def main():
                 sim._chk(lib.st_set_fluid(sim.h, C.c_void_p(Uh.data_ptr()), 0, 0), "st_set_fluid")
             sim.step(1, dt)
             if asynchronous:
-                sim.sources_async(src_h[s], reset=True)
+                sim.sources_async(src_h[s % 2], reset=True)
                 if s + 1 < E:
                     sim.set_fluid_async(Uh)
             else:
-                sim._chk(lib.st_get_sources(sim.h, C.c_void_p(src_h[s].data_ptr()), 1, 0), "st_get_sources")
+                sim._chk(lib.st_get_sources(sim.h, C.c_void_p(src_h[s % 2].data_ptr()), 1, 0), "st_get_sources")
         sim.synchronize()
         return max(time.perf_counter() - t0, 1e-9)
 
@@ -845,6 +848,16 @@ def main():
             eb.record()
             torch.cuda.synchronize()
             link[name] = src_t.numel() * src_t.element_size() / (ea.elapsed_time(eb) * 1e-3) / 1e9
+        # and into every one of the loop's host buffers (pinned memory can land on a slower node)
+        rates = []
+        for b in src_h:
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record()
+            b.copy_(dS, non_blocking=True)
+            eb.record()
+            torch.cuda.synchronize()
+            rates.append(b.numel() * 8 / (ea.elapsed_time(eb) * 1e-3) / 1e9)
+        link["d2h_gbs_each_buffer_min_max"] = [min(rates), max(rates)]
         del dU, dS
     e2e = {"value": n * ws * E / e_el if E > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(U32.nbytes),
            "d2h_bytes_per_step": int(src_h[0].numel() * 8), "steps": E,
