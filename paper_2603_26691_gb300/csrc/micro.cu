@@ -286,6 +286,13 @@ __device__ __forceinline__ float load_v(const MixedArgs& a, int q, int64_t p) {
 __device__ __forceinline__ int relocate(float& o, int ci, int n) {
   const float fl = floorf(o);
   o = fminf(fmaxf(o - fl, 0.0f), 0.99999994f);
+  // a move of less than one box length: one periodic correction (no 64-bit remainder)
+  if (fabsf(fl) < 1048576.0f) {
+    int k = ci + (int)fl;
+    if (k >= n) k -= n;
+    else if (k < 0) k += n;
+    if ((unsigned)k < (unsigned)n) return k;
+  }
   long long k = ((long long)ci + (long long)fl) % n;
   return (int)(k < 0 ? k + n : k);
 }
