@@ -297,6 +297,97 @@ __device__ __forceinline__ int relocate(float& o, int ci, int n) {
   return (int)(k < 0 ? k + n : k);
 }
 
+// One particle of the mixed state: gather, motion, relocation, mass and heat transfer.  In: the
+// packed cell, offsets, velocities (as FP32; BF16 handles' stored values), the diameter's high part and
+// {T_hi, T_lo, d_lo, 0}.  Out: the same updated (velocities rounded to their stored precision), the
+// start cell's index and the fluid's gains {momentum x, y, z, vapour mass, energy}.
+template <bool BF16>
+__device__ __forceinline__ void micro_particle(const MixedArgs& a, const int (&n3)[3], int px, int pxy, int32_t& cell,
+                                               float (&xi)[3], float (&v)[3], float& dhi, float4& st, int& key,
+                                               float (&gain)[5]) {
+  const int ci[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+  const float d0 = dhi, T0 = st.x;  // the rates need only FP32 values
+  key = ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
+  // stencil on cell centres from (cell, offset): offset >= 1/2 -> base cell, fraction o - 1/2
+  float f[3];
+  int b[3];
+  for (int q = 0; q < 3; ++q) {
+    const bool hi = xi[q] >= 0.5f;
+    f[q] = xi[q] + (hi ? -0.5f : 0.5f);
+    b[q] = ci[q] - (hi ? 0 : 1) + kFluidPad;
+  }
+  float up[3] = {0.0f, 0.0f, 0.0f}, tf = 0.0f, rv = 0.0f;
+  // the padded field has fewer than 2^31 cells: 32-bit corner offsets from the base corner
+  const int c0 = b[0] + px * b[1] + pxy * b[2];
+  const float4* ub = a.Up + c0;
+  const float2* tb = a.thp + c0;
+  const float wx[2] = {1.0f - f[0], f[0]}, wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+    const float w = wx[dx] * wy[dy] * wz[dz];
+    const int o = dx + px * dy + pxy * dz;
+    const float4 u = __ldg(ub + o);
+    const float2 t = __ldg(tb + o);
+    up[0] = fmaf(w, u.x, up[0]);
+    up[1] = fmaf(w, u.y, up[1]);
+    up[2] = fmaf(w, u.z, up[2]);
+    tf = fmaf(w, t.x, tf);
+    rv = fmaf(w, t.y, rv);
+  }
+  const float r0 = up[0] - v[0], r1 = up[1] - v[1], r2 = up[2] - v[2];
+  const float re = a.c.re_coef * sqrtf(fmaf(r0, r0, fmaf(r1, r1, r2 * r2))) * d0;
+  // motion: the exponential integrator, then relocation of (cell, offset)
+  const float inv_a = d0 * d0 * a.inv_ca;
+  const float E1 = -expm1f(-a.dt / inv_a);
+  const float Em = 1.0f - E1;
+  const float Q = E1 * inv_a;
+  float vn[3], jm[3];
+  int nc[3];
+  for (int q = 0; q < 3; ++q) {
+    const float wt = fmaf(a.g[q], inv_a, up[q]);
+    const float dvw = v[q] - wt;
+    float vq = fmaf(dvw, Em, wt);
+    if (BF16) {
+      vq = __bfloat162float(__float2bfloat16_rn(vq));
+      jm[q] = (vq - v[q]) - a.gdt[q];  // the stored change: the deposit balances the stored momentum
+    } else {
+      jm[q] = -fmaf(dvw, E1, a.gdt[q]);  // v' - v - g dt without subtracting the rounded v'
+    }
+    vn[q] = vq;
+    float o = fmaf(fmaf(wt, a.dt, dvw * Q), a.inv_h[q], xi[q]);
+    nc[q] = relocate(o, ci[q], n3[q]);
+    xi[q] = o;
+    v[q] = vq;
+  }
+  cell = pack_cell(nc[0], nc[1], nc[2]);
+  float d1, dd, dT, dm;
+  const bool clamped = transfer(a.c, a.dt, d0, T0, tf, rv, re, d1, dd, dT, dm);
+  // the increments, added exactly to the compensated state; the clamp at d_min sets the diameter
+  float dn = dhi, dl = st.z;
+  if (clamped) {
+    dd = (a.c.dmin - dhi) - dl;
+    dn = a.c.dmin;
+    dl = 0.0f;
+  } else {
+    add_pair(dn, dl, dd);
+  }
+  add_pair(st.x, st.y, dT);
+  st.z = dl;
+  dhi = dn;
+  const float T1 = T0 + dT;
+  const float m0 = a.c.mcoef * d0 * d0 * d0;
+  for (int q = 0; q < 3; ++q) gain[q] = -(m0 * jm[q] + dm * vn[q]);
+  gain[3] = -dm;
+  gain[4] = -a.c.cp * (m0 * dT + dm * T1);  // dT: the increment the stored temperature took
+}
+
+__device__ __forceinline__ void micro_commit(const MixedArgs& a, int key, const float (&g)[5]) {
+  for (int q = 0; q < 3; ++q) acc_add_f32(a.acc + kAccWords * (q * a.ncell + key), g[q], a.E);
+  wide_add_f32(a.macc + kWideWords * key, g[3]);
+  wide_add_f32(a.macc + kWideWords * (a.ncell + key), g[4]);
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedArgs a) {
   const int lane = threadIdx.x & 31;
@@ -309,100 +400,28 @@ __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedA
     int key = -1;
     float gain[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     if (p < a.n) {
-      const int32_t cell = a.s.cell[p];
-      const int ci[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+      int32_t cell = a.s.cell[p];
       float xi[3], v[3];
       for (int q = 0; q < 3; ++q) {
         xi[q] = a.s.xi[q][p];
         v[q] = load_v<BF16>(a, q, p);
       }
-      const float dhi = a.s.d[p];
+      float dhi = a.s.d[p];
       float4 st = a.ms[p];
-      const float d0 = dhi, T0 = st.x;  // the rates need only FP32 values
-      key = ci[0] + a.nx * (ci[1] + a.ny * ci[2]);
-      // stencil on cell centres from (cell, offset): offset >= 1/2 -> base cell, fraction o - 1/2
-      float f[3];
-      int b[3];
+      micro_particle<BF16>(a, n3, px, pxy, cell, xi, v, dhi, st, key, gain);
+      a.s.cell[p] = cell;
       for (int q = 0; q < 3; ++q) {
-        const bool hi = xi[q] >= 0.5f;
-        f[q] = xi[q] + (hi ? -0.5f : 0.5f);
-        b[q] = ci[q] - (hi ? 0 : 1) + kFluidPad;
-      }
-      float up[3] = {0.0f, 0.0f, 0.0f}, tf = 0.0f, rv = 0.0f;
-      // the padded field has fewer than 2^31 cells: 32-bit corner offsets from the base corner
-      const int c0 = b[0] + px * b[1] + pxy * b[2];
-      const float4* ub = a.Up + c0;
-      const float2* tb = a.thp + c0;
-      const float wx[2] = {1.0f - f[0], f[0]}, wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-        const float w = wx[dx] * wy[dy] * wz[dz];
-        const int o = dx + px * dy + pxy * dz;
-        const float4 u = __ldg(ub + o);
-        const float2 t = __ldg(tb + o);
-        up[0] = fmaf(w, u.x, up[0]);
-        up[1] = fmaf(w, u.y, up[1]);
-        up[2] = fmaf(w, u.z, up[2]);
-        tf = fmaf(w, t.x, tf);
-        rv = fmaf(w, t.y, rv);
-      }
-      const float r0 = up[0] - v[0], r1 = up[1] - v[1], r2 = up[2] - v[2];
-      const float re = a.c.re_coef * sqrtf(fmaf(r0, r0, fmaf(r1, r1, r2 * r2))) * d0;
-      // motion: the exponential integrator, then relocation of (cell, offset)
-      const float inv_a = d0 * d0 * a.inv_ca;
-      const float E1 = -expm1f(-a.dt / inv_a);
-      const float Em = 1.0f - E1;
-      const float Q = E1 * inv_a;
-      float vn[3], jm[3];
-      int nc[3];
-      for (int q = 0; q < 3; ++q) {
-        const float wt = fmaf(a.g[q], inv_a, up[q]);
-        const float dvw = v[q] - wt;
-        float vq = fmaf(dvw, Em, wt);
-        if (BF16) {
-          vq = __bfloat162float(__float2bfloat16_rn(vq));
-          jm[q] = (vq - v[q]) - a.gdt[q];  // the stored change: the deposit balances the stored momentum
-        } else {
-          jm[q] = -fmaf(dvw, E1, a.gdt[q]);  // v' - v - g dt without subtracting the rounded v'
-        }
-        vn[q] = vq;
-        float o = fmaf(fmaf(wt, a.dt, dvw * Q), a.inv_h[q], xi[q]);
-        nc[q] = relocate(o, ci[q], n3[q]);
-        a.s.xi[q][p] = o;
+        a.s.xi[q][p] = xi[q];
         if (BF16)
-          ((__nv_bfloat16*)a.s.v[q])[p] = __float2bfloat16_rn(vq);
+          ((__nv_bfloat16*)a.s.v[q])[p] = __float2bfloat16_rn(v[q]);
         else
-          ((float*)a.s.v[q])[p] = vq;
+          ((float*)a.s.v[q])[p] = v[q];
       }
-      a.s.cell[p] = pack_cell(nc[0], nc[1], nc[2]);
-      float d1, dd, dT, dm;
-      const bool clamped = transfer(a.c, a.dt, d0, T0, tf, rv, re, d1, dd, dT, dm);
-      // the increments, added exactly to the compensated state; the clamp at d_min sets the diameter
-      float dn = dhi, dl = st.z;
-      if (clamped) {
-        dd = (a.c.dmin - dhi) - dl;
-        dn = a.c.dmin;
-        dl = 0.0f;
-      } else {
-        add_pair(dn, dl, dd);
-      }
-      add_pair(st.x, st.y, dT);
-      st.z = dl;
-      a.s.d[p] = dn;
+      a.s.d[p] = dhi;
       a.ms[p] = st;
-      const float T1 = T0 + dT;
-      const float m0 = a.c.mcoef * d0 * d0 * d0;
-      for (int q = 0; q < 3; ++q) gain[q] = -(m0 * jm[q] + dm * vn[q]);
-      gain[3] = -dm;
-      gain[4] = -a.c.cp * (m0 * dT + dm * T1);  // dT: the increment the stored temperature took
     }
     const bool head = run_sums(lane, key, gain);
-    if (head && key >= 0) {
-      for (int q = 0; q < 3; ++q) acc_add_f32(a.acc + kAccWords * (q * a.ncell + key), gain[q], a.E);
-      wide_add_f32(a.macc + kWideWords * key, gain[3]);
-      wide_add_f32(a.macc + kWideWords * (a.ncell + key), gain[4]);
-    }
+    if (head && key >= 0) micro_commit(a, key, gain);
   }
 }
 
