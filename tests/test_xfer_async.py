@@ -28,12 +28,12 @@ def _sim(prec, N, U0, seed=91, n=50_003):
     return sim
 
 
-@pytest.mark.parametrize("prec", ["mixed_f32", "fp64"])
-def test_async_loop_equals_sync_loop(torch_mod, prec):
+@pytest.mark.parametrize("prec,field", [("mixed_f32", "f32"), ("fp64", "f64"), ("mixed_bf16", "f64")])
+def test_async_loop_equals_sync_loop(torch_mod, prec, field):
     torch = torch_mod
     N, steps, dt = 32, 7, 5e-4
     base = inputs.random_fourier(N, seed=21) * 8.0
-    dtype = np.float32 if prec != "fp64" else np.float64
+    dtype = np.float32 if field == "f32" else np.float64
     fields = [(base * (1.0 + 0.1 * s)).astype(dtype) for s in range(steps)]
     sync = _sim(prec, N, fields[0])
     want = []
