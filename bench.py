@@ -251,11 +251,11 @@ def timed_steps(sim, steps, dt, reorder_every, step_index0):
 MEASURED_FP64_OPS = {
     # ncu instruction counters: 116 DFMA + 46.8 DADD + 70 DMUL per particle; FP64 pipe 78 % busy
     # (the cell-deposit instance adjoint_step_kernel<false>)
-    ("87fe090fc117f7be124b1a5cec802705e0348ebfd57464ae2caf6d50b9b98746", "adjoint_step_kernel"): 348.8,
+    ("7058c7dec6f0337f8a2714b29236374ca8c7a5319af284358b7f1554335a4733", "adjoint_step_kernel"): 348.8,
     # step_f64_kernel: 56 DFMA + 59 DADD + 19 DMUL per particle (2e6 particles on 128^3)
     ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 190.0,
 }
-MEASURED_FP64_PIPE = {("87fe090fc117f7be124b1a5cec802705e0348ebfd57464ae2caf6d50b9b98746", "adjoint_step_kernel"): 0.777,
+MEASURED_FP64_PIPE = {("7058c7dec6f0337f8a2714b29236374ca8c7a5319af284358b7f1554335a4733", "adjoint_step_kernel"): 0.777,
                       ("8fc2e56686bddc20dfeca2e836f247c15b1f3655db751a7a9f10af9a572c8820", "step_f64_kernel"): 0.858}
 F64_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2603_26691_gb300", "csrc", "step_f64.cu")
 
