@@ -597,7 +597,7 @@ def run_chunks(args, workload):
     from paper_2603_26691_gb300.sim import Sim
 
     n = args.n or workload.n
-    C = workload.extra["chunk"]
+    C = args.chunk or workload.extra["chunk"]
     U32 = workload.make_field().astype(np.float32)
     sim = Sim(workload.grid, precision=workload.precision, chunk_edge=workload.chunk_edge, device=device)
     sim.set_params(reorder_every=workload.reorder_every)
@@ -659,6 +659,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk", type=int, default=None, help="particles per chunk (chunk-streaming workload)")
     ap.add_argument("--variant-steps", type=int, default=3, help="steps per physics variant (0 = skip)")
     args = ap.parse_args()
 
