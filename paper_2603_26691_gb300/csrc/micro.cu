@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "st_common.cuh"
+#include "st_ptx.cuh"
 
 namespace st {
 namespace {
@@ -267,6 +268,7 @@ struct MixedArgs {
   const float2* __restrict__ thp;  // (T_f, rho_v) with kFluidPad ghost layers
   long long* __restrict__ acc;
   long long* __restrict__ macc;
+  float4* __restrict__ rec;        // the step before a sort: the new state as 32-byte records (else null)
   int64_t n, ncell;
   int nx, ny, nz;
   float inv_h[3];
@@ -410,14 +412,20 @@ __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedA
       float4 st = a.ms[p];
       micro_particle<BF16>(a, n3, px, pxy, cell, xi, v, dhi, st, key, gain);
       a.s.cell[p] = cell;
-      for (int q = 0; q < 3; ++q) {
-        a.s.xi[q][p] = xi[q];
-        if (BF16)
-          ((__nv_bfloat16*)a.s.v[q])[p] = __float2bfloat16_rn(v[q]);
-        else
-          ((float*)a.s.v[q])[p] = v[q];
+      if (a.rec) {
+        // the cells stay in the arrays (the sort's keys); the state goes out as one 32-byte record
+        // for the sort's gather (BF16 velocities are exact in FP32)
+        ptx::st_rec32(a.rec + 2 * p, ptx::Rec32{__int_as_float(cell), xi[0], xi[1], xi[2], v[0], v[1], v[2], dhi});
+      } else {
+        for (int q = 0; q < 3; ++q) {
+          a.s.xi[q][p] = xi[q];
+          if (BF16)
+            ((__nv_bfloat16*)a.s.v[q])[p] = __float2bfloat16_rn(v[q]);
+          else
+            ((float*)a.s.v[q])[p] = v[q];
+        }
+        a.s.d[p] = dhi;
       }
-      a.s.d[p] = dhi;
       a.ms[p] = st;
     }
     const bool head = run_sums(lane, key, gain);
@@ -593,7 +601,7 @@ size_t temp_elem(const st_ctx* h) { return h->prec == ST_FP64 ? sizeof(double) :
 
 }  // namespace
 
-cudaError_t launch_micro_step(st_ctx* h, const StepParams& p) {
+cudaError_t launch_micro_step(st_ctx* h, const StepParams& p, bool records) {
   const int64_t warps = (h->np + 31) / 32;
   const int blocks = blocks_for(warps * 32);
   if (h->prec == ST_FP64) {
@@ -629,6 +637,7 @@ cudaError_t launch_micro_step(st_ctx* h, const StepParams& p) {
     a.thp = (const float2*)h->thermo.p;
     a.acc = (long long*)h->acc.p;
     a.macc = (long long*)h->acc_micro.p;
+    a.rec = records ? (float4*)h->state_alt.p : nullptr;
     a.n = h->np;
     a.ncell = h->geo.ncell;
     a.nx = h->geo.n[0];

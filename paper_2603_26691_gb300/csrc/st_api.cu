@@ -593,8 +593,13 @@ st_status run_steps(st_ctx* h, int nsteps, double dt) {
     p.re_coef = h->rho_f_drag / h->mu;
     cudaError_t e;
     timer_begin(h, ST_TIMER_STEP, h->stream);
-    if (h->micro_on)
-      e = launch_micro_step(h, p);
+    if (h->micro_on) {
+      // the step before a due sort leaves its output as records for the sort's gather
+      const bool mrec = h->prec != ST_FP64 && h->reorder_every > 0 && h->steps_since_sort + 1 >= h->reorder_every &&
+                        h->state_alt.bytes >= (size_t)h->cap * 32;
+      e = launch_micro_step(h, p, mrec);
+      if (e == cudaSuccess && mrec) h->records_pending = true;
+    }
     else if (h->prec == ST_FP64)
       e = launch_step_f64(h, p);
     else if (tma) {

@@ -533,7 +533,8 @@ void timer_end(st_ctx* h, int k, cudaStream_t s);                          // st
 cudaError_t launch_cell_counts(st_ctx* h, int64_t* counts);
 // ---- droplet microphysics (micro.cu) -------------------------------------------------------------
 // the step with vapour mass and heat transfer (default physics only; accumulators prepared)
-cudaError_t launch_micro_step(st_ctx* h, const StepParams& p);
+// records (mixed handles): the new state as 32-byte records into state_alt (cells also into the arrays)
+cudaError_t launch_micro_step(st_ctx* h, const StepParams& p, bool records = false);
 // before a microphysics step: widen the diameter bound by the largest growth one step allows, and
 // propagate the carries of the microphysics accumulator when the step could overflow a word
 st_status micro_prepare_step(st_ctx* h, double dt);

@@ -168,3 +168,30 @@ def test_microphysics_call_errors(Sim):
     with pytest.raises(StError):
         sim.set_microphysics(True, **dict(MICRO, kappa_f=-1.0))
     sim.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed_f32", "mixed_bf16"])
+def test_mixed_microphysics_sort_from_records_equals_sort_from_arrays(Sim, prec):
+    """With a sort every 5 steps the microphysics step before each sort leaves its state as 32-byte records
+    for the sort's gather; reading the water budget after every step turns them back into arrays first,
+    so that the sort gathers from the arrays: both runs give the same bits."""
+    N, U, T, rv, pos, vel, d, Tp = _case(f32=True, n=15_001)
+    out = []
+    for read_between in (False, True):
+        sim = Sim(N, precision=prec)
+        sim.set_params(reorder_every=5)
+        sim.set_fluid(U.astype(np.float32))
+        sim.set_thermo(T, rv)
+        sim.set_microphysics(True, T_init=285.0, **MICRO)
+        sim.add_particles(pos, d, vel)
+        sim.set_temperatures(Tp)
+        for _ in range(17):
+            sim.step(1, 5e-4)
+            if read_between:
+                sim.micro_invariants()
+        g = [sim.sources(host=True), sim.micro_sources(), sim.temperatures()]
+        g.extend(sim.particles())
+        sim.close()
+        out.append(g)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
