@@ -333,18 +333,33 @@ __global__ void f64_to_f32_kernel(const double* __restrict__ in, float* __restri
 }
 
 // value of each carry-save accumulator in FP64: out[c][q]
+// carry propagation: digits in [0, 2^32) below a signed top word
+__device__ __forceinline__ void wide_carry(long long* v) {
+  long long c = 0;
+  for (int k = 0; k < kWideWords - 1; ++k) {
+    const long long t = v[k] + c;
+    v[k] = t & 0xffffffffll;
+    c = t >> 32;
+  }
+  v[kWideWords - 1] += c;
+}
+
 __global__ void wide_to_f64_kernel(const long long* __restrict__ Uw, double* __restrict__ out, int64_t m) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    // compensated sum from the smallest word up
-    double s = 0.0, c = 0.0;
-    for (int k = 0; k < kWideWords; ++k) {
-      const double t = ldexp((double)Uw[i * kWideWords + k], 32 * k + kWideBase);
-      const double y = t - c;
-      const double z = s + y;
-      c = (z - s) - y;
-      s = z;
+    // sign and magnitude first: summing signed words (a normalised negative value is words near 2^32
+    // below a top word of -1) would cancel
+    long long v[kWideWords];
+    for (int k = 0; k < kWideWords; ++k) v[k] = Uw[i * kWideWords + k];
+    wide_carry(v);
+    const bool neg = v[kWideWords - 1] < 0;
+    if (neg) {
+      for (int k = 0; k < kWideWords; ++k) v[k] = -v[k];
+      wide_carry(v);
     }
-    out[i] = s;
+    // non-negative terms, smallest first
+    double s = 0.0;
+    for (int k = 0; k < kWideWords; ++k) s += ldexp((double)v[k], 32 * k + kWideBase);
+    out[i] = neg ? -s : s;
   }
 }
 

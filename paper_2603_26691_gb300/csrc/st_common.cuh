@@ -329,6 +329,19 @@ __device__ __forceinline__ void acc_value(const long long* w, unsigned long long
   hi = (long long)d[2] + (long long)((unsigned long long)top << 32);
 }
 
+// a two's-complement 128-bit integer hi:lo as a double, through its sign and magnitude: summing the
+// signed halves directly would cancel, losing a small negative value (hi = -1, lo close to 2^64)
+__host__ __device__ __forceinline__ double i128_to_f64(unsigned long long lo, long long hi) {
+  const bool neg = hi < 0;
+  unsigned long long mlo = lo, mhi = (unsigned long long)hi;
+  if (neg) {
+    mlo = ~lo + 1ull;
+    mhi = ~mhi + (mlo == 0 ? 1ull : 0ull);
+  }
+  const double m = (double)mhi * 0x1p64 + (double)mlo;
+  return neg ? -m : m;
+}
+
 // 128-bit add with carry-out, used by the exact reductions (returns the old value from memory)
 __device__ __forceinline__ void atomic_add_i128(unsigned long long* p, unsigned long long lo,
                                                 unsigned long long hi) {

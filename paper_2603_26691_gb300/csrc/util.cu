@@ -209,7 +209,7 @@ __global__ void acc_to_f64_kernel(const long long* __restrict__ acc, double* __r
     unsigned long long lo;
     long long hi;
     acc_value(acc + kAccWords * i, lo, hi);
-    out[i] = ((double)hi * 0x1p64 + (double)lo) * inv_scale;
+    out[i] = i128_to_f64(lo, hi) * inv_scale;
   }
 }
 
@@ -557,7 +557,7 @@ cudaError_t launch_acc_sum(st_ctx* h, double out[3]) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return e;
   double inv = std::ldexp(1.0, -h->acc_E);
-  for (int q = 0; q < 3; ++q) out[q] = ((double)(long long)hb[2 * q + 1] * 0x1p64 + (double)hb[2 * q]) * inv;
+  for (int q = 0; q < 3; ++q) out[q] = i128_to_f64(hb[2 * q], (long long)hb[2 * q + 1]) * inv;
   return cudaSuccess;
 }
 

@@ -229,3 +229,54 @@ def test_fourier256_bf16v_1e9_sampled(torch_cuda):
     # about twice the errors measured on GB300 for this sample (velocity 7.8e-3, position 2.4e-3 of the
     # path), the same as the 20-step BF16 parity case at 64^3; the worst case is 20 x 2^-8 = 0.078
     assert vel_err <= 1.6e-2 and pos_path <= 5e-3
+
+
+def test_fourier256_micro_1e9_sampled(torch_cuda):
+    """The microphysics workload at full size (the bench's fourier256_micro_1e9: the mixed workload's field
+    and 1e9 particles plus seeded temperature and vapour fields, 20 steps of 5e-4, sort every 10): a
+    seeded 2e4-particle subsample's positions, diameters and temperatures against the oracle (the fields
+    are frozen, so each particle's path depends on itself alone), and the water budget of the full run."""
+    from paper_2603_26691_gb300.sim import Sim
+
+    torch = torch_cuda
+    w = inputs.WORKLOADS["fourier256_micro_1e9"]
+    U = w.make_field()
+    N = w.grid
+    T, rv = inputs.thermo_fields(N, seed=w.field_seed + 1)
+    T32 = T.astype(np.float32).astype(np.float64)
+    rv32 = rv.astype(np.float32).astype(np.float64)
+    sim = Sim(N, precision="mixed_f32", chunk_edge=w.chunk_edge)
+    sim.set_params(reorder_every=w.reorder_every)
+    sim.set_fluid(U.astype(np.float32))
+    sim.set_thermo(T, rv)
+    sim.set_microphysics(True, T_init=285.0)
+    _populate(sim, w, w.n)
+    W0, _ = sim.micro_invariants()
+    sim.step(w.steps, w.dt)
+    W1, _ = sim.micro_invariants()
+    vapour = sim.micro_sources()[0].sum()
+    sample = np.sort(np.random.default_rng(4).choice(w.n, 20_000, replace=False))
+    gpos, gvel, gd, _ = _sample_state(torch, sim, sample)
+    where = torch.full((w.n,), -1, dtype=torch.int64, device="cuda")
+    where[torch.as_tensor(sample, device="cuda")] = torch.arange(len(sample), device="cuda")
+    gT = np.empty(len(sample))
+    for first in range(0, w.n, 50_000_000):
+        cnt = min(50_000_000, w.n - first)
+        ids = sim.particles(first, cnt, host=False)[3]
+        k = where[ids.to(torch.int64)].cpu().numpy()
+        sel = k >= 0
+        gT[k[sel]] = sim.temperatures(first, cnt)[sel]
+    sim.close()
+    torch.cuda.empty_cache()
+    # water: droplets plus vapour gained (the budget of the microphysics parity test)
+    assert abs(W1 + vapour - W0) <= 1e-6 * abs(vapour) + 1e-9 * W0
+    pos, vel, d, _ = inputs.particles_at(w.seed, sample)
+    G = oracle.make_grid(N)
+    M = oracle.make_micro(D_v=2.5e-5, kappa_f=0.025, cp_p=4186.0, L=2.5e6, Pr=0.71, d_min=1e-7)
+    opos, ovel, od, oT, _, _, _ = oracle.micro_run(G, M, U.reshape(-1, 3), T32.reshape(-1), rv32.reshape(-1), pos, vel,
+                                                   d, np.full(len(sample), 285.0), w.steps, w.dt)
+    errs = {"pos_h": np.abs(min_image(gpos, opos)).max() * N, "d": (np.abs(gd - od) / od).max(),
+            "T": np.abs(gT - oT).max()}
+    print(errs)
+    # the mixed microphysics bounds of the parity test
+    assert errs["pos_h"] <= 1e-5 and errs["d"] <= 1e-6 and errs["T"] <= 1e-4
