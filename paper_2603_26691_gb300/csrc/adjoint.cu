@@ -23,6 +23,7 @@ namespace st {
 namespace {
 
 constexpr int kAdjThreads = 256;
+constexpr int kAdjDirectGroups = 20;  // more distinct stencils than this in a warp: no grouping
 
 struct AdjArgs {
   const double* __restrict__ x[3];   // state at the start of the step (tape)
@@ -197,7 +198,9 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_step_kernel(const AdjArgs
 // fractions from the offset, corners read from the ghost-padded FP32 field), the deposit cell the
 // start cell.  Position adjoints are per metre, as in the FP64 adjoint (the periodic wrap and the
 // whole-cell carry are translations).  Each step's dL/dd and dL/dalpha contributions are FP32 and
-// accumulate in FP64; each corner's dL/dU contribution (an FP32 product) is added exactly.
+// accumulate in FP64.  The dL/dU products of the particles of a warp that share a stencil are summed
+// in FP32 (in an order fixed by the stencils, so the result is reproducible) and each sum is added
+// exactly: one set of L2 reduction operations per distinct stencil instead of per particle.
 
 struct AdjMixedArgs {
   MixedState tape;
@@ -217,102 +220,147 @@ struct AdjMixedArgs {
 };
 
 __global__ void __launch_bounds__(kAdjThreads) adjoint_mixed_kernel(const AdjMixedArgs a) {
+  __shared__ GroupBuf<8> gb[kAdjThreads / 32];
   const int n3[3] = {a.nx, a.ny, a.nz};
   const int64_t row = a.nx + 2 * kFluidPad, slab = row * (a.ny + 2 * kFluidPad);
+  const int lane = threadIdx.x & 31;
+  GroupBuf<8>& b8 = gb[threadIdx.x >> 5];
   double alphab_sum = 0.0;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int c = a.tape.cell[p];
-    const int ci[3] = {cell_i(c), cell_j(c), cell_k(c)};
-    float v[3], xb[3], vb[3], f[3];
-    int i0[3], lo[3], hi[3];
+  // warp-uniform trip count: the dL/dU commits below are warp-collective
+  for (int64_t wbase = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); wbase < a.n;
+       wbase += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = wbase + lane;
+    int key = -1;  // the stencil's lowest corner cell; -1: no particle on this lane
+    float W[8], ub[3];
+    if (p < a.n) {
+      const int c = a.tape.cell[p];
+      const int ci[3] = {cell_i(c), cell_j(c), cell_k(c)};
+      float v[3], xb[3], vb[3], f[3];
+      int i0[3], lo[3];
 #pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float o = a.tape.xi[q][p];
+        v[q] = ((const float*)a.tape.v[q])[p];
+        xb[q] = a.xb[q][p];
+        vb[q] = a.vb[q][p];
+        const bool up_half = o >= 0.5f;
+        i0[q] = ci[q] - (up_half ? 0 : 1);  // -1 .. n - 1
+        f[q] = o + (up_half ? -0.5f : 0.5f);
+        lo[q] = i0[q] < 0 ? i0[q] + n3[q] : i0[q];
+      }
+      const float d = a.d[p];
+      const int64_t cell_key = ci[0] + (int64_t)a.nx * (ci[1] + (int64_t)a.ny * ci[2]);
+      key = lo[0] + a.nx * (lo[1] + a.ny * lo[2]);
+      const float4* b = a.Up + (i0[0] + kFluidPad) + row * (i0[1] + kFluidPad) + slab * (i0[2] + kFluidPad);
+      float4 Uc[8];
+      float up[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
+        Uc[k] = __ldg(b + di + row * dj + slab * dk);
+        W[k] = (di ? f[0] : 1.0f - f[0]) * (dj ? f[1] : 1.0f - f[1]) * (dk ? f[2] : 1.0f - f[2]);
+        up[0] = fmaf(W[k], Uc[k].x, up[0]);
+        up[1] = fmaf(W[k], Uc[k].y, up[1]);
+        up[2] = fmaf(W[k], Uc[k].z, up[2]);
+      }
+      const float dd = d * d;
+      const float adt = a.cadt / dd;     // a dt
+      const float inv_ra = dd * a.inv_ca;  // 1 / a
+      const float ra = 1.0f / inv_ra;
+      const float inv_ra2 = inv_ra * inv_ra;
+      const float inv_d = 1.0f / d;
+      const float E1 = -expm1f(-adt);
+      const float E = 1.0f - E1;
+      const float Q = E1 * inv_ra;
+      const float m = a.mcoef * dd * d;
+      float wt[3], vn[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        wt[q] = fmaf(a.g[q], inv_ra, up[q]);
+        vn[q] = fmaf(v[q] - wt[q], E, wt[q]);
+      }
+      const float Jb[3] = {a.lam[cell_key], a.lam[a.ncell + cell_key], a.lam[2 * a.ncell + cell_key]};
+      float mb = 0.0f, Eb = 0.0f, E1b = 0.0f, Qb = 0.0f, ab = 0.0f;
+      float vsb[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float vnb = vb[q] - m * Jb[q];
+        vsb[q] = fmaf(m, Jb[q], fmaf(vnb, E, xb[q] * Q));
+        mb -= ((vn[q] - v[q]) - a.gdt[q]) * Jb[q];
+        const float wtb = fmaf(vnb, E1, xb[q] * (a.dt - Q));
+        E1b = fmaf(vnb, wt[q], E1b);
+        Eb = fmaf(vnb, v[q], Eb);
+        Qb = fmaf(xb[q], v[q] - wt[q], Qb);
+        ub[q] = wtb;
+        ab -= wtb * a.g[q] * inv_ra2;
+      }
+      E1b = fmaf(Qb, inv_ra, E1b);
+      ab -= Qb * E1 * inv_ra2;
+      ab = fmaf(a.dt * E, E1b - Eb, ab);
+      alphab_sum += (double)(ab * ra) * a.inv_alpha;
+      a.db[p] += (double)(ab * (-2.0f * ra * inv_d) + mb * 3.0f * m * inv_d);
+      float dot[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dot[k] = fmaf(Uc[k].x, ub[0], fmaf(Uc[k].y, ub[1], Uc[k].z * ub[2]));
+      auto lerp = [](float p0, float p1, float t) { return fmaf(t, p1 - p0, p0); };
+      float fb[3];
+      {
+        const float e00 = dot[1] - dot[0], e10 = dot[3] - dot[2], e01 = dot[5] - dot[4], e11 = dot[7] - dot[6];
+        fb[0] = lerp(lerp(e00, e10, f[1]), lerp(e01, e11, f[1]), f[2]);
+        const float g00 = dot[2] - dot[0], g10 = dot[3] - dot[1], g01 = dot[6] - dot[4], g11 = dot[7] - dot[5];
+        fb[1] = lerp(lerp(g00, g10, f[0]), lerp(g01, g11, f[0]), f[2]);
+        const float h00 = dot[4] - dot[0], h10 = dot[5] - dot[1], h01 = dot[6] - dot[2], h11 = dot[7] - dot[3];
+        fb[2] = lerp(lerp(h00, h10, f[0]), lerp(h01, h11, f[0]), f[1]);
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        a.xb[q][p] = fmaf(fb[q], a.inv_h[q], xb[q]);
+        a.vb[q][p] = vsb[q];
+      }
+    }
+    // dL/dU, each corner's FP32 product added exactly.  Where the warp's particles share stencils (sorted
+    // storage, several particles per cell) they are first reordered so that equal stencils are adjacent
+    // (they share all eight corners) and each corner's products are summed over the group
+    auto corners_of = [&](int k0, int (&corner)[8]) {
+      const int l0 = k0 < 0 ? 0 : k0 % a.nx, r = k0 < 0 ? 0 : k0 / a.nx;
+      const int l1 = r % a.ny, l2 = r / a.ny;
+      const int h0 = l0 + 1 == a.nx ? 0 : l0 + 1, h1 = l1 + 1 == a.ny ? 0 : l1 + 1, h2 = l2 + 1 == a.nz ? 0 : l2 + 1;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        corner[k] = ((k & 1) ? h0 : l0) + a.nx * ((((k >> 1) & 1) ? h1 : l1) + a.ny * (((k >> 2) & 1) ? h2 : l2));
+    };
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const int groups = __popc(__ballot_sync(0xffffffffu, (grp & ((1u << lane) - 1u)) == 0u));
+    int corner[8];
+    if (groups > kAdjDirectGroups) {
+      // few shared stencils: the reordering and the sums would cost more than they save
+      if (key >= 0) {
+        corners_of(key, corner);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          long long* w = a.Uw + (int64_t)corner[k] * 3 * kWideWords;
+          wide_add_f32(w, W[k] * ub[0]);
+          wide_add_f32(w + kWideWords, W[k] * ub[1]);
+          wide_add_f32(w + 2 * kWideWords, W[k] * ub[2]);
+        }
+      }
+      continue;
+    }
+    const int slot = key_group_slot(lane, grp);
+    const int gkey = group_permute_key(b8.key, slot, lane, key);
+    corners_of(gkey, corner);
+#pragma unroll 1
     for (int q = 0; q < 3; ++q) {
-      const float o = a.tape.xi[q][p];
-      v[q] = ((const float*)a.tape.v[q])[p];
-      xb[q] = a.xb[q][p];
-      vb[q] = a.vb[q][p];
-      const bool up_half = o >= 0.5f;
-      i0[q] = ci[q] - (up_half ? 0 : 1);  // -1 .. n - 1
-      f[q] = o + (up_half ? -0.5f : 0.5f);
-      lo[q] = i0[q] < 0 ? i0[q] + n3[q] : i0[q];
-      hi[q] = i0[q] + 1 >= n3[q] ? i0[q] + 1 - n3[q] : i0[q] + 1;
-    }
-    const float d = a.d[p];
-    const int64_t key = ci[0] + (int64_t)a.nx * (ci[1] + (int64_t)a.ny * ci[2]);
-    const float4* b = a.Up + (i0[0] + kFluidPad) + row * (i0[1] + kFluidPad) + slab * (i0[2] + kFluidPad);
-    float4 Uc[8];
-    float W[8];
-    float up[3] = {0.0f, 0.0f, 0.0f};
+      float g[8];
+      const float uq = q == 0 ? ub[0] : (q == 1 ? ub[1] : ub[2]);  // no local-memory indexing
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
-      Uc[k] = __ldg(b + di + row * dj + slab * dk);
-      W[k] = (di ? f[0] : 1.0f - f[0]) * (dj ? f[1] : 1.0f - f[1]) * (dk ? f[2] : 1.0f - f[2]);
-      up[0] = fmaf(W[k], Uc[k].x, up[0]);
-      up[1] = fmaf(W[k], Uc[k].y, up[1]);
-      up[2] = fmaf(W[k], Uc[k].z, up[2]);
-    }
-    const float dd = d * d;
-    const float adt = a.cadt / dd;     // a dt
-    const float inv_ra = dd * a.inv_ca;  // 1 / a
-    const float ra = 1.0f / inv_ra;
-    const float inv_ra2 = inv_ra * inv_ra;
-    const float inv_d = 1.0f / d;
-    const float E1 = -expm1f(-adt);
-    const float E = 1.0f - E1;
-    const float Q = E1 * inv_ra;
-    const float m = a.mcoef * dd * d;
-    float wt[3], vn[3];
+      for (int k = 0; k < 8; ++k) g[k] = key >= 0 ? W[k] * uq : 0.0f;
+      group_permute(b8, slot, lane, g);
+      const bool head = run_sums(lane, gkey, g);
+      if (head && gkey >= 0) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      wt[q] = fmaf(a.g[q], inv_ra, up[q]);
-      vn[q] = fmaf(v[q] - wt[q], E, wt[q]);
-    }
-    const float Jb[3] = {a.lam[key], a.lam[a.ncell + key], a.lam[2 * a.ncell + key]};
-    float mb = 0.0f, Eb = 0.0f, E1b = 0.0f, Qb = 0.0f, ab = 0.0f;
-    float ub[3], vsb[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float vnb = vb[q] - m * Jb[q];
-      vsb[q] = fmaf(m, Jb[q], fmaf(vnb, E, xb[q] * Q));
-      mb -= ((vn[q] - v[q]) - a.gdt[q]) * Jb[q];
-      const float wtb = fmaf(vnb, E1, xb[q] * (a.dt - Q));
-      E1b = fmaf(vnb, wt[q], E1b);
-      Eb = fmaf(vnb, v[q], Eb);
-      Qb = fmaf(xb[q], v[q] - wt[q], Qb);
-      ub[q] = wtb;
-      ab -= wtb * a.g[q] * inv_ra2;
-    }
-    E1b = fmaf(Qb, inv_ra, E1b);
-    ab -= Qb * E1 * inv_ra2;
-    ab = fmaf(a.dt * E, E1b - Eb, ab);
-    alphab_sum += (double)(ab * ra) * a.inv_alpha;
-    a.db[p] += (double)(ab * (-2.0f * ra * inv_d) + mb * 3.0f * m * inv_d);
-    float dot[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int di = k & 1, dj = (k >> 1) & 1, dk = (k >> 2) & 1;
-      dot[k] = fmaf(Uc[k].x, ub[0], fmaf(Uc[k].y, ub[1], Uc[k].z * ub[2]));
-      const int64_t corner = (di ? hi[0] : lo[0]) + (int64_t)a.nx * ((dj ? hi[1] : lo[1]) + (int64_t)a.ny * (dk ? hi[2] : lo[2]));
-      long long* w = a.Uw + corner * 3 * kWideWords;
-      wide_add_f32(w, W[k] * ub[0]);
-      wide_add_f32(w + kWideWords, W[k] * ub[1]);
-      wide_add_f32(w + 2 * kWideWords, W[k] * ub[2]);
-    }
-    auto lerp = [](float p0, float p1, float t) { return fmaf(t, p1 - p0, p0); };
-    float fb[3];
-    {
-      const float e00 = dot[1] - dot[0], e10 = dot[3] - dot[2], e01 = dot[5] - dot[4], e11 = dot[7] - dot[6];
-      fb[0] = lerp(lerp(e00, e10, f[1]), lerp(e01, e11, f[1]), f[2]);
-      const float g00 = dot[2] - dot[0], g10 = dot[3] - dot[1], g01 = dot[6] - dot[4], g11 = dot[7] - dot[5];
-      fb[1] = lerp(lerp(g00, g10, f[0]), lerp(g01, g11, f[0]), f[2]);
-      const float h00 = dot[4] - dot[0], h10 = dot[5] - dot[1], h01 = dot[6] - dot[2], h11 = dot[7] - dot[3];
-      fb[2] = lerp(lerp(h00, h10, f[0]), lerp(h01, h11, f[0]), f[1]);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      a.xb[q][p] = fmaf(fb[q], a.inv_h[q], xb[q]);
-      a.vb[q][p] = vsb[q];
+        for (int k = 0; k < 8; ++k) wide_add_f32(a.Uw + ((int64_t)corner[k] * 3 + q) * kWideWords, g[k]);
+      }
     }
   }
   __shared__ double sh[kAdjThreads / 32];

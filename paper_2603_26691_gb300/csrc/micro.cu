@@ -135,58 +135,6 @@ __device__ __forceinline__ void add_pair(float& hi, float& lo, float x) {
   hi = h2;
 }
 
-// sum of v over the run of equal key that starts at this lane (runs in lane order), for lanes that
-// start a run (others: partial sums)
-template <class R, int K>
-__device__ __forceinline__ bool run_sums(int lane, int key, R (&v)[K]) {
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  const bool head = (lane == 0) || (prev != key);
-  const unsigned heads = __ballot_sync(0xffffffffu, head);
-  const unsigned above = lane == 31 ? 0u : (heads & ~((2u << lane) - 1u));
-  const int end = above ? (__ffs(above) - 2) : 31;
-  for (int off = 1; off < 32; off <<= 1) {
-    R t[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) t[q] = __shfl_down_sync(0xffffffffu, v[q], off);
-    if (lane + off <= end) {
-#pragma unroll
-      for (int q = 0; q < K; ++q) v[q] += t[q];
-    }
-  }
-  return head;
-}
-
-// Reorders a warp's lanes so that equal keys are adjacent: groups in the order of their lowest lane,
-// lanes inside a group in lane order.  Drifted particles put several start cells into one warp in
-// alternation; grouped, each distinct cell is one run for run_sums and one commit, instead of one per
-// lane-contiguous run.  The order depends only on the keys, so the sums stay reproducible.
-struct GroupBuf {
-  float g[5][32];
-  int key[32];
-};
-
-__device__ __forceinline__ void group_by_key(GroupBuf& b, int lane, int& key, float (&gain)[5]) {
-  const unsigned grp = __match_any_sync(0xffffffffu, key);
-  const int leader = __ffs(grp) - 1;
-  const int rank = __popc(grp & ((1u << lane) - 1u));
-  const int size = leader == lane ? __popc(grp) : 0;
-  int incl = size;  // inclusive prefix of the group sizes over the leaders, in lane order
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += t;
-  }
-  const int pos = __shfl_sync(0xffffffffu, incl - size, leader) + rank;
-  __syncwarp();  // the previous round's reads are done
-#pragma unroll
-  for (int q = 0; q < 5; ++q) b.g[q][pos] = gain[q];
-  b.key[pos] = key;
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < 5; ++q) gain[q] = b.g[q][lane];
-  key = b.key[lane];
-}
-
 // ---- FP64 state -----------------------------------------------------------------------------------
 
 struct F64Args {
@@ -423,7 +371,7 @@ __device__ __forceinline__ void micro_commit(const MixedArgs& a, int key, const 
 
 template <bool BF16>
 __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedArgs a) {
-  __shared__ GroupBuf perm[kMicroThreads / 32];
+  __shared__ GroupBuf<5> perm[kMicroThreads / 32];
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;

@@ -444,6 +444,82 @@ __device__ __forceinline__ void wide_add(long long* w, double x) {
   if (q + 2 < kWideWords) atomicAdd((unsigned long long*)&w[q + 2], (unsigned long long)d2);
 }
 
+// ---- sums over a warp's lanes of equal key, before one exact commit per key ----
+
+// sum of v over the run of equal key that starts at this lane (runs in lane order), for lanes that
+// start a run (others: partial sums).  Every lane of the warp calls it.
+template <class R, int K>
+__device__ __forceinline__ bool run_sums(int lane, int key, R (&v)[K]) {
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = (lane == 0) || (prev != key);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned above = lane == 31 ? 0u : (heads & ~((2u << lane) - 1u));
+  const int end = above ? (__ffs(above) - 2) : 31;
+  for (int off = 1; off < 32; off <<= 1) {
+    R t[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) t[q] = __shfl_down_sync(0xffffffffu, v[q], off);
+    if (lane + off <= end) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] += t[q];
+    }
+  }
+  return head;
+}
+
+// The place of this lane when a warp's lanes are reordered so that equal keys are adjacent: groups in
+// the order of their lowest lane, lanes inside a group in lane order.  A permutation of 0..31 that
+// depends only on the keys, so sums formed over the reordered lanes are reproducible.  Particles that
+// drifted from their sort-time cells put several keys into one warp in alternation; reordered, each
+// distinct key is one run for run_sums and one commit.
+__device__ __forceinline__ int key_group_slot(int lane, unsigned grp) {  // grp: the lanes of this lane's key
+  const int leader = __ffs(grp) - 1;
+  const int rank = __popc(grp & ((1u << lane) - 1u));
+  const int size = leader == lane ? __popc(grp) : 0;
+  int incl = size;  // inclusive prefix of the group sizes over the leaders, in lane order
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += t;
+  }
+  return __shfl_sync(0xffffffffu, incl - size, leader) + rank;
+}
+__device__ __forceinline__ int key_group_slot(int lane, int key) {
+  return key_group_slot(lane, (unsigned)__match_any_sync(0xffffffffu, key));
+}
+
+// per-warp staging of K values and the key for the reordering
+template <int K>
+struct GroupBuf {
+  float g[K][32];
+  int key[32];
+};
+
+// moves this lane's values to its slot and takes the values that land on this lane
+template <int K>
+__device__ __forceinline__ void group_permute(GroupBuf<K>& b, int slot, int lane, float (&v)[K]) {
+  __syncwarp();  // the previous use's reads are done
+#pragma unroll
+  for (int q = 0; q < K; ++q) b.g[q][slot] = v[q];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = b.g[q][lane];
+}
+__device__ __forceinline__ int group_permute_key(int* keys, int slot, int lane, int key) {
+  __syncwarp();
+  keys[slot] = key;
+  __syncwarp();
+  return keys[lane];
+}
+
+// both at once, for a single use: afterwards equal keys are adjacent
+template <int K>
+__device__ __forceinline__ void group_by_key(GroupBuf<K>& b, int lane, int& key, float (&v)[K]) {
+  const int slot = key_group_slot(lane, key);
+  group_permute(b, slot, lane, v);
+  key = group_permute_key(b.key, slot, lane, key);
+}
+
 
 struct AdjointStepArgs {
   const double* x[3];

@@ -140,3 +140,40 @@ def test_fp32_adjoint_on_a_non_cubic_grid(Sim):
     print(err)
     # FP32 rounding through 25 steps forward and back (the cubic case above measures ~2e-7 to 6e-7)
     assert err["J"] <= 2e-6 and err["gd"] <= 1e-5 and err["ga"] <= 1e-5 and err["gU"] <= 1e-5
+
+
+def test_fp32_adjoint_sorted_dense_stencils_grouped(Sim):
+    """Sorted by cell at about 40 particles per cell, most warps hold several particles with the same
+    trilinear stencil, and their dL/dU products are summed in FP32 before one exact commit per stencil:
+    J, dL/dalpha, dL/dU and dL/dd against the oracle's FP64 adjoint, and bit-identical gradients from a
+    second run (the grouping depends only on the stencils)."""
+    N, n, alpha = 8, 20_000, 0.9
+    U = (inputs.taylor_green(N) + 0.1 * inputs.random_fourier(N, seed=21)).astype(np.float32).astype(np.float64)
+    pos, vel, d, _ = inputs.particles(80, 0, n, vmax=0.2)
+    d = d * 1.5
+    lam = _smooth_lam(N)
+    nsteps, dt, ck = 20, 1e-3, 5
+    runs = []
+    for _ in range(2):
+        sim = Sim(N, precision="mixed_f32")
+        sim.set_params(drag_scale=alpha, reorder_every=0)
+        sim.set_fluid(U.astype(np.float32))
+        sim.add_particles(pos, d, vel)
+        sim.reorder()
+        p0, v0, d0, _ = sim.particles()
+        sim.adjoint_forward(nsteps, dt, ck)
+        J = sim.sources(host=True)
+        gd, ga, gU = sim.adjoint_backward(lam)
+        sim.close()
+        runs.append((p0, v0, d0, J, gd, ga, gU))
+    for a, b in zip(runs[0][3:], runs[1][3:]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    p0, v0, d0, J, gd, ga, gU = runs[0]
+    G = oracle.make_grid(N, alpha=alpha)
+    _, _, oJ, _ = oracle.run(G, U, p0, v0, d0, nsteps, dt)
+    ogd, oga, ogU = oracle.adjoint(G, U, p0, v0, d0, nsteps, dt, lam)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)  # noqa: E731
+    err = dict(J=rel(J, oJ), gd=rel(gd, ogd), ga=abs(ga - oga) / abs(oga), gU=rel(gU, ogU))
+    print(err)
+    # FP32 rounding through 20 steps forward and back, and FP32 sums over up to 32 products per stencil
+    assert err["J"] <= 2e-6 and err["gd"] <= 1e-5 and err["ga"] <= 1e-5 and err["gU"] <= 1e-5
