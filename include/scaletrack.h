@@ -301,8 +301,10 @@ st_status st_adjoint_forward(st_handle h, int nsteps, double dt, int checkpoint_
  * are formed in a fixed order or in exact fixed point, so results are
  * bit-reproducible.  Mixed handles: the reverse step runs in FP32 (lam
  * rounded to FP32, FP32 adjoints of position and velocity, each step's
- * dL/dd and dL/d(drag_scale) terms accumulated in FP64, each FP32 dL/dU
- * term added exactly).  Synchronises.
+ * dL/dd and dL/d(drag_scale) terms accumulated in FP64; the FP32 dL/dU
+ * terms of particles in one warp that share a trilinear stencil summed in
+ * FP32 in an order fixed by the stencils, each sum added exactly).
+ * Synchronises.
  * Errors: STATE (no recorded run), INVALID_ARG, OOM, CUDA. */
 st_status st_adjoint_backward(st_handle h, const double* lam, int lam_on_device, double* grad_d,
                               double* grad_alpha, double* grad_U, int on_device);
