@@ -25,8 +25,9 @@
 // particle carries {T_hi, T_lo, d_lo, 0} (16 B): T = T_hi + T_lo and d = d + d_lo, each increment
 // added with an error-free two-sum, so the stored state loses no increment.
 //
-// One particle per lane; the five gains are summed over runs of equal start cell across the warp and
-// each run is added once to the exact accumulators: momentum to the fixed-point source accumulator,
+// One particle per lane; the warp's lanes are reordered so that equal start cells are adjacent (an
+// order fixed by the cells), the five gains are summed over each cell's lanes and each sum is added
+// once to the exact accumulators: momentum to the fixed-point source accumulator,
 // vapour and energy to a carry-save accumulator wide enough to need no exponent.  Only the default
 // physics (trilinear gather, exponential integrator, Stokes drag, cell deposit).
 #include <algorithm>
