@@ -826,7 +826,12 @@ def main():
 
     lib = sim.lib
 
+    # events on the compute stream around each step's work there (step, sort when due, source
+    # conversion and reset): their span against the host clock shows whether the loop kept the GPU busy
+    evs_e2e = []
+
     def e2e_loop(asynchronous):
+        evs_e2e.clear()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if asynchronous and E > 0:
@@ -834,21 +839,35 @@ def main():
         for s in range(E):
             if not asynchronous:
                 sim._chk(lib.st_set_fluid(sim.h, C.c_void_p(Uh.data_ptr()), 0, 0), "st_set_fluid")
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record()
             sim.step(1, dt)
             if asynchronous:
                 sim.sources_async(src_h[s % 2], reset=True)
+                eb.record()
                 if s + 1 < E:
                     sim.set_fluid_async(Uh)
             else:
                 sim._chk(lib.st_get_sources(sim.h, C.c_void_p(src_h[s % 2].data_ptr()), 1, 0), "st_get_sources")
+                eb.record()
+            evs_e2e.append((ea, eb))
         sim.synchronize()
         return max(time.perf_counter() - t0, 1e-9)
+
+    def e2e_stream_ms():
+        if not evs_e2e:
+            return None
+        busy = sum(a.elapsed_time(b) for a, b in evs_e2e) / len(evs_e2e)
+        span = evs_e2e[0][0].elapsed_time(evs_e2e[-1][1]) / len(evs_e2e)
+        return {"span_per_step": span, "step_and_conversion_per_step": busy}
 
     torch.cuda.synchronize()
     e2e_loop(True)
     e_el = e2e_loop(True)
+    e_stream = e2e_stream_ms()
     # the same loop with the synchronous calls (each waits for its copy), for comparison
     s_el = e2e_loop(False)
+    s_stream = e2e_stream_ms()
     # this machine's host link for the same buffers (one copy each way, CUDA events): the end-to-end rate
     # depends on it, and it differs between boxes of the pool
     link = {}
@@ -878,7 +897,9 @@ def main():
            "d2h_bytes_per_step": int(src_h[0].numel() * 8), "steps": E,
            "what": "per step: fluid field H2D from pinned host, step (sort when due), sources D2H to pinned host, "
                    "queued with st_set_fluid_async / st_get_sources_async and overlapping the steps",
-           "synchronous_calls_value": n * ws * E / s_el if E > 0 else None, "host_link": link}
+           "synchronous_calls_value": n * ws * E / s_el if E > 0 else None, "host_link": link,
+           "wall_ms_per_step": e_el * 1e3 / E if E > 0 else None, "compute_stream_ms": e_stream,
+           "synchronous_compute_stream_ms": s_stream}
 
     # physics variants on the same particles, sorted: the sorted-particle step kernel's physics
     # instance
