@@ -364,10 +364,35 @@ __device__ __forceinline__ void micro_particle(const MixedArgs& a, const int (&n
   gain[4] = -a.c.cp * (m0 * dT + dm * T1);  // dT: the increment the stored temperature took
 }
 
-__device__ __forceinline__ void micro_commit(const MixedArgs& a, int key, const float (&g)[5]) {
-  for (int q = 0; q < 3; ++q) acc_add_f32(a.acc + kAccWords * (q * a.ncell + key), g[q], a.E);
-  wide_add_f32(a.macc + kWideWords * key, g[3]);
-  wide_add_f32(a.macc + kWideWords * (a.ncell + key), g[4]);
+// The group sums of the head lanes added to the exact accumulators, the commits spread over the lanes:
+// the H heads' 5 H (value, cell) items in component-major order through the warp's staging buffer, one
+// item per lane and round.  A round then runs one or two of the add routines on many lanes instead of
+// all five on the few head lanes; the adds are exact, so the sums are the same.
+__device__ __forceinline__ void micro_commit(const MixedArgs& a, GroupBuf<5>& b, int lane, bool head, int key,
+                                             const float (&g)[5]) {
+  const unsigned hm = __ballot_sync(0xffffffffu, head);
+  const int H = __popc(hm);
+  __syncwarp();  // the reordering's reads of the buffer are done
+  if (head) {
+    const int r = __popc(hm & ((1u << lane) - 1u));
+#pragma unroll
+    for (int q = 0; q < 5; ++q) b.g[q][r] = g[q];
+    b.key[r] = key;
+  }
+  __syncwarp();
+  // item i: component q = floor(i / H), head r = i - q H; (i + 1/2) / H lies at least 1/(2 H) >= 1/64
+  // from an integer, far more than the reciprocal's rounding moves it
+  const float inv_h = __frcp_rn((float)(H > 0 ? H : 1));
+  for (int i = lane; i < 5 * H; i += 32) {
+    const int q = (int)(((float)i + 0.5f) * inv_h);
+    const int r = i - q * H;
+    const float v = b.g[q][r];
+    const int k = b.key[r];
+    if (q < 3)
+      acc_add_f32(a.acc + kAccWords * ((int64_t)q * a.ncell + k), v, a.E);
+    else
+      wide_add_f32(a.macc + kWideWords * ((int64_t)(q - 3) * a.ncell + k), v);
+  }
 }
 
 template <bool BF16>
@@ -409,9 +434,10 @@ __global__ void __launch_bounds__(kMicroThreads) micro_mixed_kernel(const MixedA
       }
       a.ms[p] = st;
     }
-    group_by_key(perm[threadIdx.x >> 5], lane, key, gain);
-    const bool head = run_sums(lane, key, gain);
-    if (head && key >= 0) micro_commit(a, key, gain);
+    GroupBuf<5>& gb = perm[threadIdx.x >> 5];
+    group_by_key(gb, lane, key, gain);
+    const bool head = run_sums(lane, key, gain) && key >= 0;
+    micro_commit(a, gb, lane, head, key, gain);
   }
 }
 
