@@ -359,21 +359,23 @@ __device__ __forceinline__ void store_ids(const TmaArgs& a, uint4 id, int64_t p0
       if (p0 + j >= S && p0 + j < E) a.ids_out[p0 + j] = v[j];
   }
 }
-// GATHER: copy the records of the owned positions among p0 .. p0 + 3 into the lane's eight 16-byte
-// pieces of a stage (piece h at h kT 4 + L 4 bytes, L = 4 x the consumer thread: the places of the
-// lane's particles in the stage's eight 4-byte arrays, so that the warp's deposit compaction, which
-// uses the first 16 places of its own particles in the first four arrays, touches its own lanes'
-// pieces only).  Record j's halves go to pieces 2j and 2j + 1.
-__device__ __forceinline__ void gather_issue(unsigned char* stage, int L, const TmaArgs& a, uint4 pp, int64_t p0,
-                                             int64_t S, int64_t E) {
+// GATHER: ask L2 for the records of the owned positions among p0 .. p0 + 3 (a stage before their
+// loads)
+__device__ __forceinline__ void gather_prefetch(const TmaArgs& a, uint4 pp, int64_t p0, int64_t S, int64_t E) {
   const uint32_t pj[4] = {pp.x, pp.y, pp.z, pp.w};
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (p0 + j >= S && p0 + j < E) {
-      const float4* r = a.grec + 2 * (int64_t)pj[j];
-      cp_async16(stage + (2 * j) * kT * 4 + L * 4, r);
-      cp_async16(stage + (2 * j + 1) * kT * 4 + L * 4, r + 1);
-    }
+  for (int j = 0; j < 4; ++j)
+    if (p0 + j >= S && p0 + j < E) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.grec + 2 * (int64_t)pj[j]));
+}
+// GATHER: the diameters of the owned positions among p0 .. p0 + 3, stored in sorted order as soon as
+// their records arrive (a step does not change them)
+__device__ __forceinline__ void store_d(const TmaArgs& a, const Rec32 (&r)[4], int64_t p0, int64_t S, int64_t E) {
+  if (p0 >= S && p0 + 4 <= E) {
+    __stcs(reinterpret_cast<float4*>(a.s.d + p0), make_float4(r[0].d, r[1].d, r[2].d, r[3].d));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (p0 + j >= S && p0 + j < E) a.s.d[p0 + j] = r[j].d;
   }
 }
 
@@ -500,20 +502,17 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
     const int64_t A = S & ~int64_t(7);
     const int64_t Z = (E + 7) & ~int64_t(7);
     const int L = 4 * ctid;
-    // GATHER: the unit's first stage is copied now (its latency is exposed once per unit), and the
-    // permutation entries of the stage after the one in flight are held in registers
-    uint4 pnext = make_uint4(0, 0, 0, 0), gid = make_uint4(0, 0, 0, 0);
+    // GATHER: the permutation entries of this stage and of the next, and this stage's ids, are
+    // held in registers a stage ahead
+    uint4 pcur = make_uint4(0, 0, 0, 0), pnext = make_uint4(0, 0, 0, 0), gid = make_uint4(0, 0, 0, 0);
     if constexpr (GATHER) {
-      const uint4 pf = gather_perm(a, A + L, S, E);
-      gather_issue(ring + (gt % kStages) * kStageBytes, L, a, pf, A + L, S, E);
-      cp_async_commit();
-      gid = gather_ids(a, pf, A + L, S, E);
+      pcur = gather_perm(a, A + L, S, E);
+      gid = gather_ids(a, pcur, A + L, S, E);
       pnext = gather_perm(a, A + kT + L, S, E);
     }
     for (int64_t t0 = A; t0 < Z; t0 += kT) {
       const int st = (int)(gt % kStages);
       if (!mbar_wait(&full[st], (gt / kStages) & 1)) {
-        if (GATHER) cp_async_wait<0>();
         atomicOr(a.err, 8);
         return;
       }
@@ -522,37 +521,36 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
       int cell[4];
       float xi[3][4], v[3][4], dv[4];
       if constexpr (GATHER) {
-        // the next stage's records into the other stage buffer, then wait for this stage's (every
-        // consumer thread reads only the pieces it copied itself)
-        // this stage's ids (loaded a stage ago) go out now; the next stage's come in
-        store_ids(a, gid, p0, S, E);
-        if (t0 + kT < Z) {
-          gather_issue(ring + ((gt + 1) % kStages) * kStageBytes, L, a, pnext, p0 + kT, S, E);
-          cp_async_commit();
-          gid = gather_ids(a, pnext, p0 + kT, S, E);
-          pnext = gather_perm(a, p0 + 2 * kT, S, E);
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
-        }
-        // positions outside the unit get harmless values and are neither stored nor deposited
+        // this stage's records through the permutation, one 256-bit load each (asked of L2 a stage
+        // ago); positions outside the unit get harmless values and are neither stored nor deposited
         const int glo = (int)max((int64_t)0, min((int64_t)4, S - p0));
         const int ghi = (int)max((int64_t)0, min((int64_t)4, E - p0));
+        const uint32_t pj[4] = {pcur.x, pcur.y, pcur.z, pcur.w};
+        Rec32 r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          r[j] = (j >= glo && j < ghi) ? ld_rec32(a.grec + 2 * (int64_t)pj[j])
+                                       : Rec32{0.0f, 0.5f, 0.5f, 0.5f, 0.0f, 0.0f, 0.0f, 1e-5f};
+        // this stage's ids (loaded a stage ago) go out now; the next stage's come in, and its records
+        // are asked for
+        store_ids(a, gid, p0, S, E);
+        if (t0 + kT < Z) {
+          gather_prefetch(a, pnext, p0 + kT, S, E);
+          gid = gather_ids(a, pnext, p0 + kT, S, E);
+          pcur = pnext;
+          pnext = gather_perm(a, p0 + 2 * kT, S, E);
+        }
+        store_d(a, r, p0, S, E);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          float4 r0 = make_float4(0.0f, 0.5f, 0.5f, 0.5f), r1 = make_float4(0.0f, 0.0f, 0.0f, 1e-5f);
-          if (j >= glo && j < ghi) {
-            r0 = *reinterpret_cast<const float4*>(src + (2 * j) * kT * 4 + L * 4);
-            r1 = *reinterpret_cast<const float4*>(src + (2 * j + 1) * kT * 4 + L * 4);
-          }
-          cell[j] = __float_as_int(r0.x);
-          xi[0][j] = r0.y;
-          xi[1][j] = r0.z;
-          xi[2][j] = r0.w;
-          v[0][j] = r1.x;
-          v[1][j] = r1.y;
-          v[2][j] = r1.z;
-          dv[j] = r1.w;
+          cell[j] = __float_as_int(r[j].c);
+          xi[0][j] = r[j].x0;
+          xi[1][j] = r[j].x1;
+          xi[2][j] = r[j].x2;
+          v[0][j] = r[j].v0;
+          v[1][j] = r[j].v1;
+          v[2][j] = r[j].v2;
+          dv[j] = r[j].d;
         }
       } else {
         int4 c4 = *reinterpret_cast<const int4*>(src + L * 4);
@@ -800,11 +798,6 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
                    Rec32{__int_as_float(cell[j]), xi[0][j], xi[1][j], xi[2][j], v[0][j], v[1][j], v[2][j], dj[j]});
         }
       } else if (all_own) {
-        if (GATHER) {
-          // the diameters, read again from the lane's record pieces
-          const float* dp = reinterpret_cast<const float*>(src + kT * 4 + L * 4) + 3;
-          __stcs((float4*)(a.s.d + p0), make_float4(dp[0], dp[2 * kT], dp[4 * kT], dp[6 * kT]));
-        }
         __stcs((int4*)(a.s.cell + p0), make_int4(cell[0], cell[1], cell[2], cell[3]));
         for (int q = 0; q < 3; ++q)
           __stcs((float4*)(a.s.xi[q] + p0), make_float4(xi[q][0], xi[q][1], xi[q][2], xi[q][3]));
@@ -818,7 +811,6 @@ __global__ void __maxnreg__(128) step_mixed_tma_kernel(const __grid_constant__ C
         for (int j = 0; j < 4; ++j) {
           if (!own[j]) continue;
           a.s.cell[p0 + j] = cell[j];
-          if (GATHER) a.s.d[p0 + j] = reinterpret_cast<const float*>(src + (2 * j + 1) * kT * 4 + L * 4)[3];
           for (int q = 0; q < 3; ++q) {
             a.s.xi[q][p0 + j] = xi[q][j];
             if (BF16)
