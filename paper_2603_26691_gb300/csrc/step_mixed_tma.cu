@@ -22,11 +22,11 @@
 //     accumulator lines hot in L2.
 // The first step after a sort may also do that sort's payload gather (the GATHER instance): the sort
 // leaves a permutation and the previous step's 32-byte records {cell, offsets | velocity, diameter}
-// in the old order, and each consumer thread copies its own particles' records through the
-// permutation into its own part of the stage ring with 16-byte asynchronous copies, one stage ahead
-// of its computation (their ids into registers, stored in sorted order at the start of the stage
-// they belong to), then stores the new state - diameters too - in sorted order.  The separate
-// gather would write the sorted arrays only for this step to read them back.
+// in the old order, and each consumer thread loads its own particles' records through the
+// permutation with one 256-bit load each, asked of L2 by a prefetch one stage ahead (their ids come
+// a stage ahead into registers and are stored in sorted order at the start of the stage they belong
+// to; the diameters are stored as soon as the records arrive), then stores the new state in sorted
+// order.  The separate gather would write the sorted arrays only for this step to read them back.
 // Every wait is bounded: a wait that gives up sets an error flag and the CTA
 // returns.
 #include <cuda.h>
