@@ -407,8 +407,14 @@ cudaError_t launch_local_sort(st_ctx* h, int* far, uint32_t* lidx, uint16_t* lke
   usort_dest_kernel<<<(g.nunits + 127) / 128, 128, 0, s>>>(g, cnt, rel, total);
   usort_scan_kernel<<<1, 1024, 0, s>>>(total, g.nunits, base);
   usort_scatter_kernel<<<ublocks, kLThreads, 0, s>>>(cur.cell, cs_old, g, cntw, rel, base, lidx, lkey, far);
-  usort_rank_kernel<<<std::min(g.nunits, 152 * 4), kRThreads, 0, s>>>(g, base, lidx, lkey, perm,
-                                                                      (uint32_t*)h->cell_start.p, h->np, far);
+  // rank: as many blocks as are resident at once (its registers allow three of 512 threads per SM),
+  // each taking every grid-th unit, so that no block waits for a second wave
+  int sms = 152, per_sm = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, usort_rank_kernel, kRThreads, 0);
+  const int rblocks = std::min(g.nunits, sms * std::max(per_sm, 1));
+  usort_rank_kernel<<<rblocks, kRThreads, 0, s>>>(g, base, lidx, lkey, perm, (uint32_t*)h->cell_start.p, h->np,
+                                                  far);
   h->launches += 5;
   return cudaGetLastError();
 }
