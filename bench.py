@@ -843,10 +843,12 @@ def main():
             ea.record()
             sim.step(1, dt)
             if asynchronous:
-                sim.sources_async(src_h[s % 2], reset=True)
-                eb.record()
+                # the next step's field is queued before this step's sources: its upload then never
+                # waits behind their download where both directions share a copy engine
                 if s + 1 < E:
                     sim.set_fluid_async(Uh)
+                sim.sources_async(src_h[s % 2], reset=True)
+                eb.record()
             else:
                 sim._chk(lib.st_get_sources(sim.h, C.c_void_p(src_h[s % 2].data_ptr()), 1, 0), "st_get_sources")
                 eb.record()
