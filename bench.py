@@ -865,11 +865,19 @@ def main():
 
     torch.cuda.synchronize()
     e2e_loop(True)
+    if ws > 1:
+        torch.distributed.barrier()
     e_el = e2e_loop(True)
     e_stream = e2e_stream_ms()
     # the same loop with the synchronous calls (each waits for its copy), for comparison
+    if ws > 1:
+        torch.distributed.barrier()
     s_el = e2e_loop(False)
     s_stream = e2e_stream_ms()
+    if ws > 1:  # the whole job's time: the slowest rank's
+        t = torch.tensor([e_el, s_el], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e_el, s_el = float(t[0].item()), float(t[1].item())
     # this machine's host link for the same buffers (one copy each way, CUDA events): the end-to-end rate
     # depends on it, and it differs between boxes of the pool
     link = {}
