@@ -55,16 +55,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                "l"(src), "r"(bytes), "r"(sptr(bar))
                : "memory");
 }
-// 16-byte asynchronous copies global -> shared by the issuing thread (completion tracked per thread in
-// commit groups; the data is visible to that thread after the wait)
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sptr(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 // One 32-byte particle record {cell bits, offsets | velocity, diameter} as a single 256-bit
 // global access (sm_100 and later; the address must be 32-byte aligned): one sector per particle.
 struct Rec32 {
