@@ -223,6 +223,11 @@ st_status st_get_sources_fixed(st_handle h, int64_t* words, int* E, int on_devic
  * pending error (NONFINITE from an upload, TIMEOUT from a device-side
  * wait).  Two staging buffers alternate, so two calls may be in flight; out
  * must stay valid and unread until then.
+ *
+ * In a loop of steps, queue the next step's field (st_set_fluid_async)
+ * before this step's sources (st_get_sources_async): the upload then runs
+ * beside the step instead of waiting behind the sources' download where the
+ * two directions share a copy engine.
  * Errors: INVALID_ARG, NONFINITE, OOM, CUDA. */
 st_status st_set_fluid_async(st_handle h, const void* u, int dtype);
 st_status st_get_sources_async(st_handle h, double* out, int reset);
